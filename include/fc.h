@@ -1,0 +1,198 @@
+/*
+ * fc.h -- C ABI of the GB300 Feldman-Cousins grid-fit library (libfc.so).
+ *
+ * The library computes, for true grid points p and universes u, the
+ * Feldman-Cousins statistic of the paper's §2 procedure and Algorithm 1:
+ *
+ *   1. s = S(p), the true point's spectrum;
+ *   2. fake data d = Poisson(max(0, s + L_p z)), L_p = chol(diag(s) F diag(s)),
+ *      z ~ N(0, I) from Philox4x32-10, in the full-bin space, then collapsed;
+ *   3. chi2_g = (s_g - d)^T A (s_g - d) for every grid point g (Eq. 1 with
+ *      the inverse covariance A = M^-1; Algorithm 2's residual form);
+ *   4. q_min = the first grid index attaining the minimum (strict "<");
+ *   5. rebuild M = C [diag(s_qmin) F diag(s_qmin) + diag(s_qmin)] C^T at q_min,
+ *      invert it and rescan, until q_min repeats or max_iter scans are done;
+ *   6. dchi2 = chi2_p - chi2_min, both under the last scan's A.
+ *
+ * Conventions for every entry point:
+ *   - Return value: FC_OK (0) or a negative fc_status; nothing aborts, throws
+ *     across the ABI or traps on the device.  fc_last_error() gives a message
+ *     for the calling thread's last non-OK status.
+ *   - Matrices and spectra are row-major, float64 unless stated.
+ *   - Pointer arguments may be host or device memory (detected per call);
+ *     the library copies inputs it keeps and never frees caller memory.
+ *   - Output arrays belong to the caller and are written only on success.
+ *   - Work runs on the context's CUDA stream; synchronous entry points return
+ *     after the stream has finished the work.
+ *   - A context is not thread-safe, except fc_submit / fc_poll / fc_cancel,
+ *     which may be called from any thread.
+ */
+#ifndef FC_H_
+#define FC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FC_API __attribute__((visibility("default")))
+#else
+#define FC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc_ctx fc_ctx;
+
+typedef enum {
+    FC_OK = 0,
+    FC_PENDING = 1,          /* fc_poll: job still queued or running           */
+    FC_ERR_ARG = -1,         /* invalid argument (sizes, ids, pointers, NaN)   */
+    FC_ERR_NOT_SPD = -2,     /* a covariance had a non-positive Cholesky pivot */
+    FC_ERR_BUDGET = -3,      /* would exceed the context's device-memory budget*/
+    FC_ERR_CUDA = -4,        /* a CUDA runtime call failed                     */
+    FC_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out             */
+    FC_ERR_CANCELLED = -6,   /* job cancelled before it finished               */
+    FC_ERR_NOT_FOUND = -7,   /* unknown grid id or ticket                      */
+    FC_ERR_STATE = -8        /* call not valid in the current state            */
+} fc_status;
+
+enum { FC_PREC_FP64 = 0,     /* plain path: every step in binary64 on CUDA cores        */
+       FC_PREC_MIXED = 1 };  /* BF16 tensor-core screen (tcgen05) + binary64 rescoring  */
+enum { FC_FLUCT_POISSON_SYS = 0,  /* d = Poisson(max(0, s + L z)), L = chol(diag(s)F diag(s)) */
+       FC_FLUCT_GAUSS = 1 };      /* test mode: d = s + L z, L = chol(diag(s)F diag(s)+diag(s)) */
+enum { FC_COV_ITERATE = 0,   /* §2 step 5: refit the covariance at q_min until stable   */
+       FC_COV_FIXED = 1,     /* Algorithm 1 as printed: A = M(p)^-1, one scan           */
+       FC_COV_IDENTITY = 2 };/* test mode: A = I, one scan (nearest neighbour)          */
+
+typedef struct {
+    int32_t max_iter;   /* scans per universe including the first, >= 1 (default 5)  */
+    int32_t precision;  /* FC_PREC_*  (default FC_PREC_MIXED)                        */
+    int32_t top_k;      /* candidates kept by the mixed screen, 1..16 (default 8)    */
+    int32_t fluct;      /* FC_FLUCT_* (default FC_FLUCT_POISSON_SYS)                 */
+    int32_t cov;        /* FC_COV_*   (default FC_COV_ITERATE)                       */
+} fc_opts;
+
+/* Per-context counters of the last fc_run_points call (and totals). */
+typedef struct {
+    int64_t universes;        /* universes fitted                                   */
+    int64_t scans;            /* universe-scans performed (sum of nscans)           */
+    int64_t chi2_evals;       /* universes x G per scan actually performed          */
+    int64_t distinct_cov;     /* covariances built and inverted                     */
+    int64_t screened;         /* universe-scans decided by the tensor-core screen   */
+    int64_t rescored;         /* universe-scans that needed binary64 rescoring      */
+    int64_t fallback;         /* universe-scans whose certificate failed -> fp64 scan */
+    double  ms_fake, ms_cov, ms_screen, ms_rescore, ms_total;  /* stage times       */
+} fc_stats;
+
+/* Fill *o with the defaults listed above. */
+FC_API void fc_default_opts(fc_opts* o);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (0 = no cap).  cuda_stream is a cudaStream_t to
+ * run on (NULL = the context creates its own non-blocking stream).
+ * Errors: FC_ERR_ARG (out NULL), FC_ERR_CUDA (no such device / no memory). */
+FC_API fc_status fc_create(fc_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+
+/* Destroy a context and free its device memory.  Waits for queued jobs. */
+FC_API fc_status fc_destroy(fc_ctx* ctx);
+
+/* Load the grid spectra (the paper's S(q) for every q in the linearised grid
+ * of §2).  S: G x N_full float64 row-major, finite and >= 0 (host or device).
+ * collapse: N_full int32 entries mapping full bin -> fit bin in [0, N_fit), or
+ * NULL for the identity (then N_fit must equal N_full).  1 <= N_full, N_fit <= 200.
+ * The spectra are kept resident (float64 plus the BF16 copy of the screen).
+ * On success *grid_id receives the new grid's id.
+ * Errors: FC_ERR_ARG, FC_ERR_BUDGET, FC_ERR_CUDA. */
+FC_API fc_status fc_load_grid(fc_ctx* ctx, const double* S, int64_t G, int32_t N_full,
+                       const int32_t* collapse, int32_t N_fit, int32_t* grid_id);
+
+/* Set the fractional systematic covariance F (N_full x N_full float64,
+ * symmetric) of a loaded grid.  The systematic covariance of spectrum s is
+ * diag(s) F diag(s); the statistical part is diag(s).  Invalidates the grid's
+ * covariance cache.  Errors: FC_ERR_ARG, FC_ERR_NOT_FOUND. */
+FC_API fc_status fc_set_frac_cov(fc_ctx* ctx, int32_t grid_id, const double* F, int32_t N_full);
+
+/* Remove a grid and its caches.  Errors: FC_ERR_NOT_FOUND, FC_ERR_STATE (a
+ * queued job still uses it). */
+FC_API fc_status fc_unload_grid(fc_ctx* ctx, int32_t grid_id);
+
+/* Feldman-Cousins pass for P true points x U universes (Algorithm 1 plus the
+ * covariance refit of §2).  ps: P int64 grid indices in [0, G).  Outputs, laid
+ * out [P][U] row-major: dchi2 (float64, required), bestfit (int64 final
+ * best-fit grid index, nullable), nscans (int8 scans performed, nullable).
+ * opts NULL = defaults.  Results depend only on (grid, F, seed, p, u, opts):
+ * not on P, on the order of ps, or on other jobs sharing the device.
+ * Errors: FC_ERR_ARG, FC_ERR_NOT_FOUND, FC_ERR_STATE (F not set),
+ * FC_ERR_NOT_SPD, FC_ERR_BUDGET, FC_ERR_CUDA, FC_ERR_TIMEOUT. */
+FC_API fc_status fc_run_points(fc_ctx* ctx, int32_t grid_id, const int64_t* ps, int32_t P, uint64_t seed,
+                        int32_t U, const fc_opts* opts, double* dchi2, int64_t* bestfit, int8_t* nscans);
+
+/* fc_run_points for one true point p (Algorithm 1's buildDeltaChi2 signature:
+ * point, covariance via the grid's F, spectra, N_univ). */
+FC_API fc_status fc_run_point(fc_ctx* ctx, int32_t grid_id, int64_t p, uint64_t seed, int32_t U,
+                       const fc_opts* opts, double* dchi2, int64_t* bestfit, int8_t* nscans);
+
+/* Fake data only (§2 step 2): d [P][U][N_fit] float32 (integer counts in the
+ * Poisson mode), drawn exactly as fc_run_points draws them.  fluct: FC_FLUCT_*.
+ * Errors as fc_run_points. */
+FC_API fc_status fc_fake_data(fc_ctx* ctx, int32_t grid_id, const int64_t* ps, int32_t P, uint64_t seed,
+                       int32_t U, int32_t fluct, float* d);
+
+/* Fit-space inverse covariance A(q) = M(q)^-1 (N_fit x N_fit float64) and the
+ * Cholesky factor L_p of the systematic covariance diag(s_p) F diag(s_p)
+ * (N_full x N_full float64, lower, upper part zero) as the library computes
+ * them (§2 step 5; step 2).  Either output may be NULL.  Errors as above. */
+FC_API fc_status fc_covariance(fc_ctx* ctx, int32_t grid_id, int64_t q, double* A, double* L_sys);
+
+/* One scan (§2 steps 3-4) of caller data against the grid under A(q_cov[u]):
+ * d [U][N_fit] float32, q_cov [U] int64.  Outputs [U]: best (int64 first
+ * index of the minimum), chi2_min (float64, residual form).  precision selects
+ * the plain binary64 scan or the tensor-core screen with certified binary64
+ * rescoring.  Errors as above. */
+FC_API fc_status fc_scan(fc_ctx* ctx, int32_t grid_id, const float* d, const int64_t* q_cov, int32_t U,
+                  int32_t precision, int32_t top_k, int64_t* best, double* chi2_min);
+
+/* Per-row quantiles (linear interpolation between order statistics, numpy's
+ * default): x [rows][n] float64, probs [nq] in [0,1], out [rows][nq].  Used
+ * for the critical values of Fig. 1.  Errors: FC_ERR_ARG, FC_ERR_CUDA. */
+FC_API fc_status fc_quantiles(fc_ctx* ctx, const double* x, int32_t rows, int32_t n, const double* probs,
+                       int32_t nq, double* out);
+
+/* Asynchronous serving (continuous batching).  A job = fc_run_points'
+ * arguments; output pointers must stay valid until fc_poll returns a final
+ * status.  fc_submit admits the job when the context's memory budget allows
+ * (FC_ERR_BUDGET if it can never fit) and returns a ticket; queued jobs run
+ * interleaved with running ones on the device. */
+typedef struct {
+    int32_t grid_id;
+    const int64_t* ps;
+    int32_t P;
+    uint64_t seed;
+    int32_t U;
+    fc_opts opts;
+    double* dchi2;
+    int64_t* bestfit;
+    int8_t* nscans;
+} fc_job;
+
+FC_API fc_status fc_submit(fc_ctx* ctx, const fc_job* job, uint64_t* ticket);
+/* FC_PENDING while the job runs; its final status once (then the ticket is
+ * released: a second poll gives FC_ERR_NOT_FOUND).  *latency_ms (nullable)
+ * receives submit-to-completion time for a finished job. */
+FC_API fc_status fc_poll(fc_ctx* ctx, uint64_t ticket, double* latency_ms);
+/* Cancel a queued or running job; it finishes with FC_ERR_CANCELLED. */
+FC_API fc_status fc_cancel(fc_ctx* ctx, uint64_t ticket);
+
+/* Counters of the last synchronous run on this context. */
+FC_API fc_status fc_get_stats(fc_ctx* ctx, fc_stats* out);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+FC_API const char* fc_last_error(const fc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC_H_ */

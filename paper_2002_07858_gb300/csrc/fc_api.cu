@@ -1,0 +1,1067 @@
+// fc_api.cu -- host runtime behind the C ABI of include/fc.h.
+//
+// A context owns one CUDA stream, a device-memory budget, the resident grids
+// (spectra, centred BF16 screen image, covariance cache) and a serving worker.
+// fc_run_points drives the per-universe procedure of §2 over a batch of true
+// points: fake data (step 2), then scans (steps 3-4) with the covariance
+// rebuilt at each universe's current best fit (step 5) until it repeats, and
+// finally dchi2 (step 6) in residual form.  All arithmetic runs in the
+// kernels of fc_kernels.cu / fc_screen.cu; the host only sizes buffers,
+// assigns covariance-cache slots and reads back counts between scans.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fc.h"
+#include "fc_internal.cuh"
+
+using namespace fcdev;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+fc_status fail(fc_status st, const std::string& msg) {
+    t_last_error = msg;
+    return st;
+}
+
+#define FC_CUDA(call)                                                                           \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(FC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+#define FC_TRY(expr)                  \
+    do {                              \
+        fc_status s_ = (expr);        \
+        if (s_ != FC_OK) return s_;   \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- context --
+
+struct Grid {
+    int32_t id = -1;
+    int64_t G = 0, G_pad = 0;
+    int nf = 0, nfit = 0, K = 0;
+    bool has_F = false;
+    bool identity_collapse = true;
+    double* S_full = nullptr;   // [G][nf]
+    double* S_fit = nullptr;    // [G][nfit]
+    double* centre = nullptr;   // [nfit]
+    double* Sc = nullptr;       // [G][nfit] centred
+    float* Sc32 = nullptr;      // [G][nfit]
+    float* nrm = nullptr;       // [G]
+    uint16_t* Bt = nullptr;     // screen B image [G_pad/BN][2K/8][BN/8][8][8]
+    int32_t* collapse = nullptr;
+    double* F = nullptr;
+    // covariance cache (slot per grid index; slot `cap-1` reserved for A = I)
+    int64_t cap = 0;
+    int32_t n_slots = 0;
+    std::vector<int32_t> slot_host;  // [G]
+    int32_t ident_slot = -1;
+    int32_t* slot_of = nullptr;      // device [G]
+    double* A64 = nullptr;
+    double* W64 = nullptr;
+    float* A32 = nullptr;
+    float* rho = nullptr;
+    float* Qc = nullptr;             // [cap][G_pad] (mixed)
+    float* Qb = nullptr;
+    double* Q64 = nullptr;           // [cap][G]   (plain)
+    std::vector<uint8_t> q32_ready, q64_ready;
+    int busy = 0;                    // queued jobs referencing the grid
+};
+
+struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct JobRec;
+
+struct fc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    size_t used = 0;
+    int n_sm = 148;
+    std::unordered_map<void*, size_t> allocs;
+    std::map<int32_t, std::unique_ptr<Grid>> grids;
+    int32_t next_grid = 1;
+    std::map<std::string, Scratch> scratch;
+    int* status_dev = nullptr;
+    unsigned long long* counters_dev = nullptr;
+    fc_stats stats{};
+    std::mutex api_mu;  // serialises device work of this context
+    // serving
+    std::mutex q_mu;
+    std::condition_variable q_cv;
+    std::deque<std::shared_ptr<JobRec>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<JobRec>> jobs;
+    uint64_t next_ticket = 1;
+    std::thread worker;
+    bool stop = false;
+    bool worker_started = false;
+};
+
+namespace {
+
+fc_status dalloc(fc_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(FC_ERR_BUDGET, "device-memory budget exceeded (" + std::to_string(c->used + bytes) + " > " +
+                                       std::to_string(c->budget) + " bytes)");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(FC_ERR_BUDGET, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    c->used += bytes;
+    c->allocs[*p] = bytes;
+    return FC_OK;
+}
+
+template <class T>
+fc_status dalloc_t(fc_ctx* c, T** p, size_t count) {
+    void* v = nullptr;
+    fc_status s = dalloc(c, &v, count * sizeof(T));
+    *p = (T*)v;
+    return s;
+}
+
+void dfree(fc_ctx* c, void* p) {
+    if (!p) return;
+    auto it = c->allocs.find(p);
+    if (it != c->allocs.end()) {
+        c->used -= it->second;
+        c->allocs.erase(it);
+    }
+    cudaFree(p);
+}
+
+// grow-only named scratch buffer
+template <class T>
+fc_status scratch(fc_ctx* c, const char* name, size_t count, T** out) {
+    Scratch& s = c->scratch[name];
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (s.bytes < bytes) {
+        dfree(c, s.p);
+        s.p = nullptr;
+        s.bytes = 0;
+        const size_t want = bytes + bytes / 4;
+        void* p = nullptr;
+        FC_TRY(dalloc(c, &p, want));
+        s.p = p;
+        s.bytes = want;
+    }
+    *out = (T*)s.p;
+    return FC_OK;
+}
+
+fc_status copy_in(fc_ctx* c, void* dst, const void* src, size_t bytes) {
+    const cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    FC_CUDA(cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+    return FC_OK;
+}
+
+fc_status copy_out(fc_ctx* c, void* dst, const void* src, size_t bytes) {
+    const cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    FC_CUDA(cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+    return FC_OK;
+}
+
+fc_status sync(fc_ctx* c) {
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    FC_CUDA(cudaGetLastError());
+    return FC_OK;
+}
+
+fc_status check_status(fc_ctx* c) {
+    int st = 0;
+    FC_CUDA(cudaMemcpyAsync(&st, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    FC_TRY(sync(c));
+    if (st) {
+        FC_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream));
+        if (st & kDevTimeout) return fail(FC_ERR_TIMEOUT, "a device-side wait timed out");
+        if (st & kDevNotSpd) return fail(FC_ERR_NOT_SPD, "covariance matrix is not positive definite");
+        return fail(FC_ERR_CUDA, "device reported error flags " + std::to_string(st));
+    }
+    return FC_OK;
+}
+
+Grid* find_grid(fc_ctx* c, int32_t id) {
+    auto it = c->grids.find(id);
+    return it == c->grids.end() ? nullptr : it->second.get();
+}
+
+void free_cache(fc_ctx* c, Grid* g) {
+    dfree(c, g->slot_of); g->slot_of = nullptr;
+    dfree(c, g->A64); g->A64 = nullptr;
+    dfree(c, g->W64); g->W64 = nullptr;
+    dfree(c, g->A32); g->A32 = nullptr;
+    dfree(c, g->rho); g->rho = nullptr;
+    dfree(c, g->Qc); g->Qc = nullptr;
+    dfree(c, g->Qb); g->Qb = nullptr;
+    dfree(c, g->Q64); g->Q64 = nullptr;
+    g->cap = 0;
+    g->n_slots = 0;
+    g->ident_slot = -1;
+    g->slot_host.clear();
+    g->q32_ready.clear();
+    g->q64_ready.clear();
+}
+
+// Covariance cache: one slot per distinct grid index used as a fit covariance.
+fc_status ensure_cache(fc_ctx* c, Grid* g) {
+    if (g->cap) return FC_OK;
+    const size_t per_slot = (size_t)g->nfit * g->nfit * (8 + 8 + 4) + 4;
+    size_t free_b = 0, total_b = 0;
+    FC_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    size_t limit = free_b / 4;
+    if (c->budget) limit = std::min(limit, (c->budget > c->used ? c->budget - c->used : 0) / 2);
+    int64_t cap = std::min<int64_t>(g->G + 1, (int64_t)(limit / per_slot));
+    if (cap < 2) return fail(FC_ERR_BUDGET, "no room for the covariance cache");
+    g->cap = cap;
+    g->slot_host.assign(g->G, -1);
+    g->q32_ready.assign(cap, 0);
+    g->q64_ready.assign(cap, 0);
+    FC_TRY(dalloc_t(c, &g->slot_of, g->G));
+    launch_fill_i32(g->slot_of, g->G, -1, c->stream);
+    FC_TRY(dalloc_t(c, &g->A64, (size_t)cap * g->nfit * g->nfit));
+    FC_TRY(dalloc_t(c, &g->W64, (size_t)cap * g->nfit * g->nfit));
+    FC_TRY(dalloc_t(c, &g->A32, (size_t)cap * g->nfit * g->nfit));
+    FC_TRY(dalloc_t(c, &g->rho, (size_t)cap));
+    return FC_OK;
+}
+
+fc_status ensure_q32_storage(fc_ctx* c, Grid* g) {
+    if (g->Qc) return FC_OK;
+    FC_TRY(dalloc_t(c, &g->Qc, (size_t)g->cap * g->G_pad));
+    FC_TRY(dalloc_t(c, &g->Qb, (size_t)g->cap * g->G_pad));
+    return FC_OK;
+}
+
+fc_status ensure_q64_storage(fc_ctx* c, Grid* g) {
+    if (g->Q64) return FC_OK;
+    FC_TRY(dalloc_t(c, &g->Q64, (size_t)g->cap * g->G));
+    return FC_OK;
+}
+
+// Make sure every grid index in `qs` has a covariance slot (build + invert the
+// missing ones) and, for the given path, its q-vector.
+fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int cov_mode, bool need_q32,
+                       bool need_q64, std::vector<int32_t>* slots_out) {
+    FC_TRY(ensure_cache(c, g));
+    std::vector<int32_t> new_q, new_s, q32_list, q64_list;
+    if (slots_out) slots_out->clear();
+    auto want_q = [&](int32_t s) {
+        if (need_q32 && !g->q32_ready[s]) { q32_list.push_back(s); g->q32_ready[s] = 1; }
+        if (need_q64 && !g->q64_ready[s]) { q64_list.push_back(s); g->q64_ready[s] = 1; }
+    };
+    if (cov_mode == FC_COV_IDENTITY) {
+        if (g->ident_slot < 0) {
+            if (g->n_slots >= g->cap) return fail(FC_ERR_BUDGET, "covariance cache full");
+            g->ident_slot = g->n_slots++;
+            new_q.push_back(0);
+            new_s.push_back(g->ident_slot);
+        }
+        want_q(g->ident_slot);
+        if (slots_out) slots_out->push_back(g->ident_slot);
+    } else {
+        for (int32_t q : qs) {
+            int32_t s = g->slot_host[q];
+            if (s < 0) {
+                if (g->n_slots >= g->cap)
+                    return fail(FC_ERR_BUDGET, "covariance cache full (" + std::to_string(g->cap) + " slots)");
+                s = g->n_slots++;
+                g->slot_host[q] = s;
+                new_q.push_back(q);
+                new_s.push_back(s);
+            }
+            want_q(s);
+            if (slots_out) slots_out->push_back(s);
+        }
+    }
+    int32_t *dq = nullptr, *ds = nullptr;
+    const size_t nn = std::max(new_q.size(), std::max(q32_list.size(), q64_list.size()));
+    FC_TRY(scratch(c, "slot_q", nn + 1, &dq));
+    FC_TRY(scratch(c, "slot_s", nn + 1, &ds));
+    if (!new_q.empty()) {
+        double* work = nullptr;
+        FC_TRY(scratch(c, "cov_work", new_q.size() * g->nfit * g->nfit, &work));
+        FC_CUDA(cudaMemcpyAsync(dq, new_q.data(), new_q.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        FC_CUDA(cudaMemcpyAsync(ds, new_s.data(), new_s.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        launch_build_cov(g->S_full, g->nf, g->nfit, g->identity_collapse ? nullptr : g->collapse, g->F, dq, ds,
+                         (int)new_q.size(), cov_mode == FC_COV_IDENTITY ? 2 : 0, g->A64, g->W64, g->A32, g->rho,
+                         work, c->status_dev, c->stream);
+        if (cov_mode != FC_COV_IDENTITY) launch_set_slots(dq, ds, (int)new_q.size(), g->slot_of, c->stream);
+        c->stats.distinct_cov += (int64_t)new_q.size();
+        FC_TRY(check_status(c));
+    }
+    if (!q32_list.empty()) {
+        FC_TRY(ensure_q32_storage(c, g));
+        FC_CUDA(cudaMemcpyAsync(ds, q32_list.data(), q32_list.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        launch_qvec32(g->Sc32, g->nrm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(), g->Qc,
+                      g->Qb, c->stream);
+        FC_TRY(sync(c));
+    }
+    if (!q64_list.empty()) {
+        FC_TRY(ensure_q64_storage(c, g));
+        FC_CUDA(cudaMemcpyAsync(ds, q64_list.data(), q64_list.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        launch_qvec64(g->Sc, g->G, g->nfit, g->A64, ds, (int)q64_list.size(), g->G, g->Q64, c->stream);
+        FC_TRY(sync(c));
+    }
+    return FC_OK;
+}
+
+fc_status validate_opts(const fc_opts* o, const Grid* g) {
+    if (o->max_iter < 1 || o->max_iter > 127) return fail(FC_ERR_ARG, "max_iter must be in [1, 127]");
+    if (o->precision != FC_PREC_FP64 && o->precision != FC_PREC_MIXED) return fail(FC_ERR_ARG, "bad precision");
+    if (o->top_k < 1 || o->top_k > kMaxTopK) return fail(FC_ERR_ARG, "top_k must be in [1, 16]");
+    if (o->fluct != FC_FLUCT_POISSON_SYS && o->fluct != FC_FLUCT_GAUSS) return fail(FC_ERR_ARG, "bad fluct");
+    if (o->cov < FC_COV_ITERATE || o->cov > FC_COV_IDENTITY) return fail(FC_ERR_ARG, "bad cov mode");
+    if (o->precision == FC_PREC_MIXED && g->K > 64)
+        return fail(FC_ERR_ARG, "the tensor-core screen supports N_fit <= 63 (use FC_PREC_FP64)");
+    return FC_OK;
+}
+
+__global__ void k_init_cur(const int64_t* __restrict__ ps, int64_t n, int U, int32_t* __restrict__ cur) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) cur[i] = (int32_t)ps[i / U];
+}
+
+__global__ void k_ps32(const int64_t* __restrict__ ps, int P, int32_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P) out[i] = (int32_t)ps[i];
+}
+
+__global__ void k_widen(const int32_t* __restrict__ a, int64_t n, int64_t* __restrict__ b) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+__global__ void k_gather_cur(const int32_t* __restrict__ list, int n, const int32_t* __restrict__ cur,
+                             int32_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = cur[list[i]];
+}
+
+inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// Distinct grid indices currently used as fit covariances by the active set.
+fc_status distinct_cur(fc_ctx* c, Grid* g, const int32_t* active, int64_t n_active, const int32_t* cur,
+                       std::vector<int32_t>& out) {
+    uint8_t* flag = nullptr;
+    int32_t *list = nullptr, *cnt = nullptr;
+    FC_TRY(scratch(c, "flag", (size_t)g->G, &flag));
+    FC_TRY(scratch(c, "dlist", (size_t)std::min<int64_t>(g->G, n_active) + 1, &list));
+    FC_TRY(scratch(c, "dcount", 1, &cnt));
+    FC_CUDA(cudaMemsetAsync(flag, 0, (size_t)g->G, c->stream));
+    FC_CUDA(cudaMemsetAsync(cnt, 0, 4, c->stream));
+    launch_mark_used(active, n_active, cur, flag, c->stream);
+    launch_compact_flags(flag, g->G, list, cnt, c->stream);
+    int32_t h = 0;
+    FC_CUDA(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, c->stream));
+    FC_TRY(sync(c));
+    out.resize(h);
+    if (h) {
+        FC_CUDA(cudaMemcpyAsync(out.data(), list, (size_t)h * 4, cudaMemcpyDeviceToHost, c->stream));
+        FC_TRY(sync(c));
+    }
+    std::sort(out.begin(), out.end());
+    return FC_OK;
+}
+
+// The per-scan loop shared by fc_run_points and fc_scan.
+//   d      [n][nfit] fake (or caller) data on the device
+//   cur    [n] covariance grid index per universe (updated in place)
+//   p_of   [n / U] true point per block of U universes (int32)
+// Outputs (device): best32 [n], nscan [n], dchi2 [n], chi2min [n].
+fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, const float* d, int32_t* cur,
+                    const int32_t* p_of, int32_t* best32, int8_t* nscan, double* dchi2, double* chi2min) {
+    const int max_iter = (o.cov == FC_COV_ITERATE) ? o.max_iter : 1;
+    const bool mixed = (o.precision == FC_PREC_MIXED);
+    const int topk = o.top_k <= 8 ? 8 : 16;
+    int32_t *active = nullptr, *next = nullptr, *fin = nullptr, *uslot = nullptr, *cnts = nullptr;
+    FC_TRY(scratch(c, "active", (size_t)n, &active));
+    FC_TRY(scratch(c, "next", (size_t)n, &next));
+    FC_TRY(scratch(c, "fin", (size_t)n, &fin));
+    FC_TRY(scratch(c, "uslot", (size_t)n, &uslot));
+    FC_TRY(scratch(c, "cnts", 8, &cnts));
+    launch_iota_i32(active, n, c->stream);
+    int64_t n_active = n;
+    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 3 * sizeof(unsigned long long), c->stream));
+    for (int scan_no = 1; scan_no <= max_iter && n_active > 0; ++scan_no) {
+        // ---- covariances for this scan
+        std::vector<int32_t> qs, slots;
+        if (o.cov == FC_COV_IDENTITY) {
+            FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, &slots));
+            launch_fill_i32(uslot, n_active, slots[0], c->stream);
+        } else {
+            FC_TRY(distinct_cur(c, g, active, n_active, cur, qs));
+            FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, nullptr));
+            launch_lookup_slots(active, n_active, cur, g->slot_of, uslot, c->stream);
+        }
+        c->stats.chi2_evals += n_active * g->G;
+        c->stats.scans += n_active;
+        // ---- scan: best32[u] for every active universe
+        if (!mixed) {
+            launch_scan64(active, n_active, uslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
+                          c->stream);
+        } else {
+            const int64_t n_slots = g->n_slots;
+            const int64_t max_tiles = n_active / kBM + std::min<int64_t>(n_slots, n_active) + 1;
+            int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
+                    *fb = nullptr;
+            uint16_t* Yt = nullptr;
+            float *alpha = nullptr, *cval = nullptr;
+            int32_t* cidx = nullptr;
+            FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
+            FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
+            FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
+            FC_TRY(scratch(c, "tslot", (size_t)max_tiles, &tslot));
+            FC_TRY(scratch(c, "tuniv", (size_t)max_tiles * kBM, &tuniv));
+            FC_TRY(scratch(c, "Yt", (size_t)max_tiles * kBM * 2 * g->K, &Yt));
+            FC_TRY(scratch(c, "alpha", (size_t)max_tiles * kBM, &alpha));
+            FC_TRY(scratch(c, "cval", (size_t)max_tiles * kBM * topk, &cval));
+            FC_TRY(scratch(c, "cidx", (size_t)max_tiles * kBM * topk, &cidx));
+            FC_TRY(scratch(c, "fb", (size_t)n_active, &fb));
+            launch_group(active, n_active, uslot, (int)n_slots, tcnt, tbase, tfill, cnts, tslot, tuniv, max_tiles,
+                         c->stream);
+            int32_t n_tiles = 0;
+            FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts, 4, cudaMemcpyDeviceToHost, c->stream));
+            FC_TRY(sync(c));
+            launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, Yt, alpha, c->stream);
+            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb, tslot, n_tiles, g->G, g->G_pad, cval, cidx,
+                               c->status_dev, c->n_sm, c->stream))
+                return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
+            FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
+            launch_decide(tslot, tuniv, n_tiles, topk, cval, cidx, alpha, g->nrm, g->Qc, g->Qb, g->G_pad, d,
+                          g->centre, g->S_fit, g->nfit, g->W64, best32, fb, cnts + 1, c->counters_dev, c->stream);
+            FC_TRY(check_status(c));
+            int32_t n_fb = 0;
+            FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+            FC_TRY(sync(c));
+            if (n_fb > 0) {
+                // certificate failed: exact binary64 scan for these universes
+                std::vector<int32_t> fq;
+                if (o.cov == FC_COV_IDENTITY) {
+                    FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
+                } else {
+                    int32_t* fcur = nullptr;
+                    FC_TRY(scratch(c, "fcur", (size_t)n_fb, &fcur));
+                    k_gather_cur<<<nb(n_fb), 256, 0, c->stream>>>(fb, n_fb, cur, fcur);
+                    fq.resize(n_fb);
+                    FC_CUDA(cudaMemcpyAsync(fq.data(), fcur, (size_t)n_fb * 4, cudaMemcpyDeviceToHost, c->stream));
+                    FC_TRY(sync(c));
+                    std::sort(fq.begin(), fq.end());
+                    fq.erase(std::unique(fq.begin(), fq.end()), fq.end());
+                    FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
+                }
+                int32_t* fslot = nullptr;
+                FC_TRY(scratch(c, "fslot", (size_t)n_fb, &fslot));
+                if (o.cov == FC_COV_IDENTITY)
+                    launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
+                else
+                    launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
+                launch_scan64(fb, n_fb, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
+                              c->stream);
+            }
+        }
+        // ---- advance: converged or exhausted universes finish under this scan's A
+        FC_CUDA(cudaMemsetAsync(cnts + 2, 0, 8, c->stream));
+        launch_advance(active, n_active, best32, cur, nscan, scan_no, max_iter, next, cnts + 2, fin, cnts + 3,
+                       c->stream);
+        int32_t hc[2] = {0, 0};
+        FC_CUDA(cudaMemcpyAsync(hc, cnts + 2, 8, cudaMemcpyDeviceToHost, c->stream));
+        FC_TRY(sync(c));
+        if (hc[1] > 0) {
+            int32_t* fslot = nullptr;
+            FC_TRY(scratch(c, "finslot", (size_t)hc[1], &fslot));
+            if (o.cov == FC_COV_IDENTITY)
+                launch_fill_i32(fslot, hc[1], g->ident_slot, c->stream);
+            else
+                launch_lookup_slots(fin, hc[1], cur, g->slot_of, fslot, c->stream);
+            launch_finish(fin, hc[1], fslot, best32, p_of, U, d, g->S_fit, g->nfit, g->W64, dchi2, chi2min,
+                          c->stream);
+        }
+        std::swap(active, next);
+        std::swap(c->scratch["active"], c->scratch["next"]);
+        n_active = hc[0];
+        FC_TRY(check_status(c));
+    }
+    unsigned long long cn[3] = {0, 0, 0};
+    FC_CUDA(cudaMemcpyAsync(cn, c->counters_dev, sizeof(cn), cudaMemcpyDeviceToHost, c->stream));
+    FC_TRY(sync(c));
+    c->stats.screened += (int64_t)cn[0];
+    c->stats.rescored += (int64_t)cn[1];
+    c->stats.fallback += (int64_t)cn[2];
+    return FC_OK;
+}
+
+fc_status run_points_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P, uint64_t seed, int32_t U,
+                          const fc_opts* opts_in, double* dchi2, int64_t* bestfit, int8_t* nscans,
+                          float* fake_only, int fluct_only) {
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
+    if (P < 0 || U < 0 || (P > 0 && !ps)) return fail(FC_ERR_ARG, "bad P, U or ps");
+    if (!fake_only && P > 0 && U > 0 && !dchi2) return fail(FC_ERR_ARG, "dchi2 output is required");
+    fc_opts o;
+    fc_default_opts(&o);
+    if (opts_in) o = *opts_in;
+    if (fake_only) o.fluct = fluct_only;
+    FC_TRY(validate_opts(&o, g));
+    const int64_t n = (int64_t)P * U;
+    if (n == 0) return FC_OK;
+    if (n > (int64_t)INT32_MAX / 2) return fail(FC_ERR_ARG, "P * U too large");
+    std::vector<int64_t> hps(P);
+    if (is_device_ptr(ps)) {
+        FC_CUDA(cudaMemcpy(hps.data(), ps, (size_t)P * 8, cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(hps.data(), ps, (size_t)P * 8);
+    }
+    for (int64_t p : hps)
+        if (p < 0 || p >= g->G) return fail(FC_ERR_ARG, "true point index out of range");
+    c->stats = fc_stats{};
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaEventRecord(e0, c->stream);
+    int64_t* ps_dev = nullptr;
+    double* L64 = nullptr;
+    float *L32 = nullptr, *s32 = nullptr, *d = nullptr;
+    int32_t *cur = nullptr, *p_of = nullptr, *best32 = nullptr;
+    int8_t* ns = nullptr;
+    double *dchi2_dev = nullptr, *chi2min = nullptr;
+    FC_TRY(scratch(c, "ps", (size_t)P, &ps_dev));
+    FC_CUDA(cudaMemcpyAsync(ps_dev, hps.data(), (size_t)P * 8, cudaMemcpyHostToDevice, c->stream));
+    FC_TRY(scratch(c, "L64", (size_t)P * g->nf * g->nf, &L64));
+    FC_TRY(scratch(c, "L32", (size_t)P * g->nf * g->nf, &L32));
+    FC_TRY(scratch(c, "s32", (size_t)P * g->nf, &s32));
+    launch_chol_sys(g->S_full, g->nf, g->F, ps_dev, P, o.fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
+                    c->status_dev, c->stream);
+    FC_TRY(check_status(c));
+    if (fake_only && is_device_ptr(fake_only)) {
+        d = fake_only;
+    } else {
+        FC_TRY(scratch(c, "d", (size_t)n * g->nfit, &d));
+    }
+    launch_fake_data(L32, s32, g->nf, g->identity_collapse ? nullptr : g->collapse, g->nfit, ps_dev, P, U, seed,
+                     o.fluct == FC_FLUCT_GAUSS, d, c->stream);
+    cudaEventRecord(e1, c->stream);
+    if (fake_only) {
+        if (d != fake_only) FC_TRY(copy_out(c, fake_only, d, (size_t)n * g->nfit * sizeof(float)));
+        FC_TRY(sync(c));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(e2);
+        return FC_OK;
+    }
+    FC_TRY(scratch(c, "cur", (size_t)n, &cur));
+    FC_TRY(scratch(c, "p_of", (size_t)P, &p_of));
+    FC_TRY(scratch(c, "best32", (size_t)n, &best32));
+    FC_TRY(scratch(c, "nscan", (size_t)n, &ns));
+    FC_TRY(scratch(c, "chi2min", (size_t)n, &chi2min));
+    const bool dev_out = is_device_ptr(dchi2);
+    if (dev_out) {
+        dchi2_dev = dchi2;
+    } else {
+        FC_TRY(scratch(c, "dchi2", (size_t)n, &dchi2_dev));
+    }
+    k_init_cur<<<nb(n), 256, 0, c->stream>>>(ps_dev, n, U, cur);
+    k_ps32<<<nb(P), 256, 0, c->stream>>>(ps_dev, P, p_of);
+    FC_TRY(scan_loop(c, g, n, U, o, d, cur, p_of, best32, ns, dchi2_dev, chi2min));
+    if (!dev_out) FC_TRY(copy_out(c, dchi2, dchi2_dev, (size_t)n * 8));
+    if (bestfit) {
+        int64_t* b64 = nullptr;
+        if (is_device_ptr(bestfit)) {
+            b64 = bestfit;
+        } else {
+            FC_TRY(scratch(c, "best64", (size_t)n, &b64));
+        }
+        k_widen<<<nb(n), 256, 0, c->stream>>>(best32, n, b64);
+        if (b64 != bestfit) FC_TRY(copy_out(c, bestfit, b64, (size_t)n * 8));
+    }
+    if (nscans) FC_TRY(copy_out(c, nscans, ns, (size_t)n));
+    cudaEventRecord(e2, c->stream);
+    FC_TRY(sync(c));
+    float t_fake = 0, t_all = 0;
+    cudaEventElapsedTime(&t_fake, e0, e1);
+    cudaEventElapsedTime(&t_all, e0, e2);
+    c->stats.ms_fake = t_fake;
+    c->stats.ms_total = t_all;
+    c->stats.universes = n;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    return FC_OK;
+}
+
+// --------------------------------------------------------------- serving ---
+
+}  // namespace
+
+struct JobRec {
+    fc_job job;
+    std::vector<int64_t> ps;
+    std::atomic<int> state{FC_PENDING};
+    std::atomic<bool> cancelled{false};
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    size_t reserve = 0;
+};
+
+namespace {
+
+void worker_main(fc_ctx* c) {
+    cudaSetDevice(c->device);
+    for (;;) {
+        std::shared_ptr<JobRec> jr;
+        {
+            std::unique_lock<std::mutex> lk(c->q_mu);
+            c->q_cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+            if (c->queue.empty() && c->stop) return;
+            jr = c->queue.front();
+            c->queue.pop_front();
+        }
+        fc_status st;
+        if (jr->cancelled.load()) {
+            st = FC_ERR_CANCELLED;
+        } else {
+            std::lock_guard<std::mutex> lk(c->api_mu);
+            st = run_points_impl(c, jr->job.grid_id, jr->ps.data(), jr->job.P, jr->job.seed, jr->job.U,
+                                 &jr->job.opts, jr->job.dchi2, jr->job.bestfit, jr->job.nscans, nullptr, 0);
+            if (jr->cancelled.load()) st = FC_ERR_CANCELLED;
+        }
+        {
+            std::lock_guard<std::mutex> lk(c->q_mu);
+            auto it = c->grids.find(jr->job.grid_id);
+            if (it != c->grids.end()) it->second->busy--;
+            jr->t_done = std::chrono::steady_clock::now();
+            jr->state.store(st);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI -----
+
+extern "C" {
+
+void fc_default_opts(fc_opts* o) {
+    if (!o) return;
+    o->max_iter = 5;
+    o->precision = FC_PREC_MIXED;
+    o->top_k = 8;
+    o->fluct = FC_FLUCT_POISSON_SYS;
+    o->cov = FC_COV_ITERATE;
+}
+
+fc_status fc_create(fc_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+    if (!out) return fail(FC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    FC_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(FC_ERR_ARG, "no such CUDA device");
+    FC_CUDA(cudaSetDevice(device));
+    auto c = std::make_unique<fc_ctx>();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    cudaDeviceProp prop;
+    FC_CUDA(cudaGetDeviceProperties(&prop, device));
+    c->n_sm = prop.multiProcessorCount;
+    if (prop.major != 10) return fail(FC_ERR_ARG, "libfc is built for sm_103a (Blackwell Ultra); device is sm_" +
+                                                      std::to_string(prop.major) + std::to_string(prop.minor));
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        FC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    FC_TRY(dalloc_t(c.get(), &c->status_dev, 1));
+    FC_TRY(dalloc_t(c.get(), &c->counters_dev, 4));
+    FC_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream));
+    FC_CUDA(cudaStreamSynchronize(c->stream));
+    *out = c.release();
+    return FC_OK;
+}
+
+fc_status fc_destroy(fc_ctx* c) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    {
+        std::lock_guard<std::mutex> lk(c->q_mu);
+        c->stop = true;
+    }
+    c->q_cv.notify_all();
+    if (c->worker.joinable()) c->worker.join();
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->allocs) cudaFree(kv.first);
+    c->allocs.clear();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return FC_OK;
+}
+
+fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const int32_t* collapse, int32_t nfit,
+                       int32_t* grid_id) {
+    if (!c || !S || !grid_id) return fail(FC_ERR_ARG, "NULL argument");
+    if (G < 1 || G > (int64_t)INT32_MAX - 1) return fail(FC_ERR_ARG, "G out of range");
+    if (nf < 1 || nf > kMaxBins || nfit < 1 || nfit > kMaxBins) return fail(FC_ERR_ARG, "bins out of range [1, 200]");
+    if (!collapse && nfit != nf) return fail(FC_ERR_ARG, "N_fit must equal N_full without a collapse map");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    std::vector<int32_t> hcoll;
+    if (collapse) {
+        hcoll.resize(nf);
+        if (is_device_ptr(collapse))
+            FC_CUDA(cudaMemcpy(hcoll.data(), collapse, (size_t)nf * 4, cudaMemcpyDeviceToHost));
+        else
+            memcpy(hcoll.data(), collapse, (size_t)nf * 4);
+        std::vector<int> seen(nfit, 0);
+        for (int32_t v : hcoll) {
+            if (v < 0 || v >= nfit) return fail(FC_ERR_ARG, "collapse map entry out of [0, N_fit)");
+            seen[v] = 1;
+        }
+        for (int v : seen)
+            if (!v) return fail(FC_ERR_ARG, "collapse map leaves a fit bin empty");
+    }
+    auto g = std::make_unique<Grid>();
+    g->G = G;
+    g->G_pad = ((G + kBN - 1) / kBN) * kBN;
+    g->nf = nf;
+    g->nfit = nfit;
+    g->K = screen_k(nfit);
+    bool ident = true;
+    if (collapse)
+        for (int i = 0; i < nf; ++i) ident = ident && (hcoll[i] == i) && (nf == nfit);
+    g->identity_collapse = ident;
+    fc_status st = FC_OK;
+    auto cleanup = [&](fc_status s) {
+        dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
+        dfree(c, g->nrm); dfree(c, g->Bt); dfree(c, g->collapse);
+        return s;
+    };
+    if ((st = dalloc_t(c, &g->S_full, (size_t)G * nf)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->S_fit, (size_t)G * nfit)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->centre, (size_t)nfit)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->Sc, (size_t)G * nfit)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->Sc32, (size_t)G * nfit)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->nrm, (size_t)G)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->Bt, (size_t)g->G_pad * 2 * g->K)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->collapse, (size_t)nf)) != FC_OK) return cleanup(st);
+    if ((st = copy_in(c, g->S_full, S, (size_t)G * nf * 8)) != FC_OK) return cleanup(st);
+    if (collapse)
+        FC_CUDA(cudaMemcpyAsync(g->collapse, hcoll.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, c->stream));
+    // spectra must be finite and non-negative
+    {
+        double* mm = nullptr;
+        if ((st = scratch(c, "minmax", 2, &mm)) != FC_OK) return cleanup(st);
+        std::vector<double> hs;
+        // reduce on the host view of a device copy only when S came from the device
+        const bool dev = is_device_ptr(S);
+        if (!dev) {
+            for (int64_t e = 0; e < G * nf; ++e)
+                if (!(S[e] >= 0.0) || !std::isfinite(S[e])) return cleanup(fail(FC_ERR_ARG, "spectra must be finite and >= 0"));
+        } else {
+            hs.resize((size_t)G * nf);
+            FC_CUDA(cudaMemcpy(hs.data(), S, hs.size() * 8, cudaMemcpyDeviceToHost));
+            for (double v : hs)
+                if (!(v >= 0.0) || !std::isfinite(v)) return cleanup(fail(FC_ERR_ARG, "spectra must be finite and >= 0"));
+        }
+    }
+    launch_collapse(g->S_full, G, nf, ident ? nullptr : g->collapse, nfit, g->S_fit, c->stream);
+    launch_centre(g->S_fit, G, nfit, g->centre, nullptr, c->stream);
+    launch_centred(g->S_fit, g->centre, G, g->G_pad, nfit, g->K, g->Sc, g->Sc32, g->nrm, g->Bt, c->stream);
+    if ((st = sync(c)) != FC_OK) return cleanup(st);
+    {
+        std::lock_guard<std::mutex> lq(c->q_mu);
+        g->id = c->next_grid++;
+        *grid_id = g->id;
+        c->grids[g->id] = std::move(g);
+    }
+    return FC_OK;
+}
+
+fc_status fc_set_frac_cov(fc_ctx* c, int32_t grid_id, const double* F, int32_t nf) {
+    if (!c || !F) return fail(FC_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (nf != g->nf) return fail(FC_ERR_ARG, "F must be N_full x N_full");
+    std::vector<double> h((size_t)nf * nf);
+    if (is_device_ptr(F))
+        FC_CUDA(cudaMemcpy(h.data(), F, h.size() * 8, cudaMemcpyDeviceToHost));
+    else
+        memcpy(h.data(), F, h.size() * 8);
+    for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < nf; ++j) {
+            const double a = h[(size_t)i * nf + j], b = h[(size_t)j * nf + i];
+            if (!std::isfinite(a)) return fail(FC_ERR_ARG, "F must be finite");
+            if (std::fabs(a - b) > 1e-12 * (std::fabs(a) + std::fabs(b)) + 1e-300)
+                return fail(FC_ERR_ARG, "F must be symmetric");
+        }
+    free_cache(c, g);
+    if (!g->F) FC_TRY(dalloc_t(c, &g->F, (size_t)nf * nf));
+    FC_CUDA(cudaMemcpyAsync(g->F, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    FC_TRY(sync(c));
+    g->has_F = true;
+    return FC_OK;
+}
+
+fc_status fc_unload_grid(fc_ctx* c, int32_t grid_id) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    std::unique_ptr<Grid> owned;
+    {
+        std::lock_guard<std::mutex> lq(c->q_mu);
+        if (g->busy > 0) return fail(FC_ERR_STATE, "grid is used by a queued job");
+        owned = std::move(c->grids[grid_id]);
+        c->grids.erase(grid_id);
+    }
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_cache(c, g);
+    dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
+    dfree(c, g->nrm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->F);
+    return FC_OK;
+}
+
+fc_status fc_run_points(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P, uint64_t seed, int32_t U,
+                        const fc_opts* opts, double* dchi2, int64_t* bestfit, int8_t* nscans) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    return run_points_impl(c, grid_id, ps, P, seed, U, opts, dchi2, bestfit, nscans, nullptr, 0);
+}
+
+fc_status fc_run_point(fc_ctx* c, int32_t grid_id, int64_t p, uint64_t seed, int32_t U, const fc_opts* opts,
+                       double* dchi2, int64_t* bestfit, int8_t* nscans) {
+    return fc_run_points(c, grid_id, &p, 1, seed, U, opts, dchi2, bestfit, nscans);
+}
+
+fc_status fc_fake_data(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P, uint64_t seed, int32_t U,
+                       int32_t fluct, float* d) {
+    if (!c || !d) return fail(FC_ERR_ARG, "NULL argument");
+    if (fluct != FC_FLUCT_POISSON_SYS && fluct != FC_FLUCT_GAUSS) return fail(FC_ERR_ARG, "bad fluct");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    fc_opts o;
+    fc_default_opts(&o);
+    o.precision = FC_PREC_FP64;
+    return run_points_impl(c, grid_id, ps, P, seed, U, &o, nullptr, nullptr, nullptr, d, fluct);
+}
+
+fc_status fc_covariance(fc_ctx* c, int32_t grid_id, int64_t q, double* A, double* L_sys) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set");
+    if (q < 0 || q >= g->G) return fail(FC_ERR_ARG, "grid index out of range");
+    if (A) {
+        std::vector<int32_t> qs{(int32_t)q}, slots;
+        FC_TRY(ensure_slots(c, g, qs, FC_COV_ITERATE, false, false, &slots));
+        FC_TRY(copy_out(c, A, g->A64 + (size_t)slots[0] * g->nfit * g->nfit, (size_t)g->nfit * g->nfit * 8));
+    }
+    if (L_sys) {
+        int64_t* pd = nullptr;
+        double* L64 = nullptr;
+        float *L32 = nullptr, *s32 = nullptr;
+        FC_TRY(scratch(c, "cov_ps", 1, &pd));
+        FC_TRY(scratch(c, "cov_L64", (size_t)g->nf * g->nf, &L64));
+        FC_TRY(scratch(c, "cov_L32", (size_t)g->nf * g->nf, &L32));
+        FC_TRY(scratch(c, "cov_s32", (size_t)g->nf, &s32));
+        FC_CUDA(cudaMemcpyAsync(pd, &q, 8, cudaMemcpyHostToDevice, c->stream));
+        launch_chol_sys(g->S_full, g->nf, g->F, pd, 1, 0, L64, L32, s32, nullptr, c->status_dev, c->stream);
+        FC_TRY(check_status(c));
+        FC_TRY(copy_out(c, L_sys, L64, (size_t)g->nf * g->nf * 8));
+    }
+    return sync(c);
+}
+
+fc_status fc_scan(fc_ctx* c, int32_t grid_id, const float* d, const int64_t* q_cov, int32_t U, int32_t precision,
+                  int32_t top_k, int64_t* best, double* chi2_min) {
+    if (!c || !d || !q_cov || !best) return fail(FC_ERR_ARG, "NULL argument");
+    if (U < 0) return fail(FC_ERR_ARG, "U < 0");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set");
+    fc_opts o;
+    fc_default_opts(&o);
+    o.precision = precision;
+    o.top_k = top_k;
+    o.max_iter = 1;
+    FC_TRY(validate_opts(&o, g));
+    if (U == 0) return FC_OK;
+    std::vector<int64_t> hq(U);
+    if (is_device_ptr(q_cov))
+        FC_CUDA(cudaMemcpy(hq.data(), q_cov, (size_t)U * 8, cudaMemcpyDeviceToHost));
+    else
+        memcpy(hq.data(), q_cov, (size_t)U * 8);
+    for (int64_t q : hq)
+        if (q < 0 || q >= g->G) return fail(FC_ERR_ARG, "q_cov out of range");
+    c->stats = fc_stats{};
+    float* dd = nullptr;
+    int64_t* q64 = nullptr;
+    int32_t *cur = nullptr, *best32 = nullptr;
+    int8_t* ns = nullptr;
+    double *dchi2 = nullptr, *cm = nullptr;
+    FC_TRY(scratch(c, "d", (size_t)U * g->nfit, &dd));
+    FC_TRY(scratch(c, "scan_q", (size_t)U, &q64));
+    FC_TRY(scratch(c, "cur", (size_t)U, &cur));
+    FC_TRY(scratch(c, "best32", (size_t)U, &best32));
+    FC_TRY(scratch(c, "nscan", (size_t)U, &ns));
+    FC_TRY(scratch(c, "dchi2", (size_t)U, &dchi2));
+    FC_TRY(scratch(c, "chi2min", (size_t)U, &cm));
+    FC_TRY(copy_in(c, dd, d, (size_t)U * g->nfit * 4));
+    FC_CUDA(cudaMemcpyAsync(q64, hq.data(), (size_t)U * 8, cudaMemcpyHostToDevice, c->stream));
+    // every universe is its own "point" block (U = 1): p_of = its covariance index
+    k_init_cur<<<nb(U), 256, 0, c->stream>>>(q64, U, 1, cur);
+    int32_t* p_of = nullptr;
+    FC_TRY(scratch(c, "scan_pof", (size_t)U, &p_of));
+    k_ps32<<<nb(U), 256, 0, c->stream>>>(q64, U, p_of);
+    FC_TRY(scan_loop(c, g, U, 1, o, dd, cur, p_of, best32, ns, dchi2, cm));
+    int64_t* b64 = nullptr;
+    FC_TRY(scratch(c, "best64", (size_t)U, &b64));
+    k_widen<<<nb(U), 256, 0, c->stream>>>(best32, U, b64);
+    FC_TRY(copy_out(c, best, b64, (size_t)U * 8));
+    if (chi2_min) FC_TRY(copy_out(c, chi2_min, cm, (size_t)U * 8));
+    return sync(c);
+}
+
+fc_status fc_quantiles(fc_ctx* c, const double* x, int32_t rows, int32_t n, const double* probs, int32_t nq,
+                       double* out) {
+    if (!c || !x || !probs || !out) return fail(FC_ERR_ARG, "NULL argument");
+    if (rows < 0 || n < 1 || n > 16384 || nq < 1 || nq > 1024) return fail(FC_ERR_ARG, "bad sizes (n <= 16384)");
+    std::vector<double> hp(nq);
+    if (is_device_ptr(probs))
+        FC_CUDA(cudaMemcpy(hp.data(), probs, (size_t)nq * 8, cudaMemcpyDeviceToHost));
+    else
+        memcpy(hp.data(), probs, (size_t)nq * 8);
+    for (double p : hp)
+        if (!(p >= 0.0 && p <= 1.0)) return fail(FC_ERR_ARG, "probabilities must be in [0, 1]");
+    if (rows == 0) return FC_OK;
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    double *dx = nullptr, *dp = nullptr, *dout = nullptr;
+    FC_TRY(scratch(c, "qx", (size_t)rows * n, &dx));
+    FC_TRY(scratch(c, "qp", (size_t)nq, &dp));
+    FC_TRY(scratch(c, "qout", (size_t)rows * nq, &dout));
+    FC_TRY(copy_in(c, dx, x, (size_t)rows * n * 8));
+    FC_CUDA(cudaMemcpyAsync(dp, hp.data(), (size_t)nq * 8, cudaMemcpyHostToDevice, c->stream));
+    launch_quantiles(dx, rows, n, dp, nq, dout, c->stream);
+    FC_TRY(copy_out(c, out, dout, (size_t)rows * nq * 8));
+    return sync(c);
+}
+
+fc_status fc_submit(fc_ctx* c, const fc_job* job, uint64_t* ticket) {
+    if (!c || !job || !ticket) return fail(FC_ERR_ARG, "NULL argument");
+    if (job->P < 0 || job->U < 0 || (job->P > 0 && !job->ps) || (job->P > 0 && job->U > 0 && !job->dchi2))
+        return fail(FC_ERR_ARG, "bad job");
+    auto jr = std::make_shared<JobRec>();
+    jr->job = *job;
+    jr->ps.resize(job->P);
+    if (job->P > 0) {
+        if (is_device_ptr(job->ps)) {
+            cudaSetDevice(c->device);
+            FC_CUDA(cudaMemcpy(jr->ps.data(), job->ps, (size_t)job->P * 8, cudaMemcpyDeviceToHost));
+        } else {
+            memcpy(jr->ps.data(), job->ps, (size_t)job->P * 8);
+        }
+    }
+    jr->job.ps = jr->ps.data();
+    jr->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(c->q_mu);
+    auto it = c->grids.find(job->grid_id);
+    if (it == c->grids.end()) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    const Grid* g = it->second.get();
+    // device memory this job needs at most (fake data, state, candidates); it must fit the budget
+    const size_t n = (size_t)job->P * job->U;
+    const size_t need = n * ((size_t)g->nfit * 4 + 64 + 16 * 8 + (size_t)g->K * 4);
+    if (c->budget && need > c->budget) return fail(FC_ERR_BUDGET, "job can never fit the device-memory budget");
+    it->second->busy++;
+    const uint64_t t = c->next_ticket++;
+    c->jobs[t] = jr;
+    c->queue.push_back(jr);
+    if (!c->worker_started) {
+        c->worker = std::thread(worker_main, c);
+        c->worker_started = true;
+    }
+    c->q_cv.notify_one();
+    *ticket = t;
+    return FC_OK;
+}
+
+fc_status fc_poll(fc_ctx* c, uint64_t ticket, double* latency_ms) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->q_mu);
+    auto it = c->jobs.find(ticket);
+    if (it == c->jobs.end()) return fail(FC_ERR_NOT_FOUND, "unknown ticket");
+    const int st = it->second->state.load();
+    if (st == FC_PENDING) return FC_PENDING;
+    if (latency_ms)
+        *latency_ms =
+            std::chrono::duration<double, std::milli>(it->second->t_done - it->second->t_submit).count();
+    c->jobs.erase(it);
+    if (st != FC_OK) return fail((fc_status)st, "job failed");
+    return FC_OK;
+}
+
+fc_status fc_cancel(fc_ctx* c, uint64_t ticket) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->q_mu);
+    auto it = c->jobs.find(ticket);
+    if (it == c->jobs.end()) return fail(FC_ERR_NOT_FOUND, "unknown ticket");
+    it->second->cancelled.store(true);
+    return FC_OK;
+}
+
+fc_status fc_get_stats(fc_ctx* c, fc_stats* out) {
+    if (!c || !out) return fail(FC_ERR_ARG, "NULL argument");
+    *out = c->stats;
+    return FC_OK;
+}
+
+const char* fc_last_error(const fc_ctx*) { return t_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// fc_internal.cuh -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace fcdev {
+
+// Screen tile shape: BM universes (TMEM lanes) x BN grid points (TMEM columns).
+constexpr int kBM = 128;
+constexpr int kBN = 256;
+constexpr int kMaxTopK = 16;
+constexpr int kMaxBins = 200;
+
+// Error flags written by kernels into the context's device status word.
+enum : int {
+    kDevOk = 0,
+    kDevNotSpd = 1,
+    kDevTimeout = 2,
+    kDevBadIndex = 4,
+};
+
+// Padded fit dimension of the tensor-core screen: at least one spare column
+// (it carries the error-bound term), rounded up to the MMA K-step of 16.
+inline int screen_k(int nfit) { return ((nfit + 1 + 15) / 16) * 16; }
+
+// ---- ingest (a1) ----
+void launch_collapse(const double* S_full, int64_t G, int nf, const int32_t* collapse, int nfit, double* S_fit,
+                     cudaStream_t st);
+void launch_centre(const double* S_fit, int64_t G, int nfit, double* centre, double* work, cudaStream_t st);
+void launch_centred(const double* S_fit, const double* centre, int64_t G, int64_t G_pad, int nfit, int K,
+                    double* Sc, float* Sc32, float* nrm, uint16_t* Btiles, cudaStream_t st);
+
+// ---- covariances (a2) ----
+// L_p (binary64 and binary32 copies) for every true point; gauss adds diag(s).
+void launch_chol_sys(const double* S_full, int nf, const double* F, const int64_t* ps, int P, int gauss,
+                     double* L64, float* L32, float* s32, double* work, int* status, cudaStream_t st);
+// A(q) = M(q)^-1 for a list of (slot, q): A64, W64 (A = W^T W), A32, rho (max abs row sum of A).
+void launch_build_cov(const double* S_full, int nf, int nfit, const int32_t* collapse, const double* F,
+                      const int32_t* q_list, const int32_t* slot_list, int n, int cov_mode, double* A64,
+                      double* W64, float* A32, float* rho, double* work, int* status, cudaStream_t st);
+// q_g = s~_g^T A s~_g for slots: binary64 (plain) or binary32 central + lower bound (mixed).
+void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
+                   int64_t ldq, double* Q64, cudaStream_t st);
+void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad, int nfit, const float* A32,
+                   const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, cudaStream_t st);
+
+// ---- fake data (a3) ----
+void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* collapse, int nfit,
+                      const int64_t* ps, int P, int U, uint64_t seed, int gauss, float* d, cudaStream_t st);
+
+// ---- scan bookkeeping ----
+void launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t st);
+void launch_iota_i32(int32_t* p, int64_t n, cudaStream_t st);
+void launch_mark_used(const int32_t* active, int64_t n_active, const int32_t* cur, uint8_t* flag, cudaStream_t st);
+void launch_compact_flags(uint8_t* flag, int64_t G, int32_t* list, int32_t* count, cudaStream_t st);
+void launch_lookup_slots(const int32_t* active, int64_t n_active, const int32_t* cur, const int32_t* slot_of,
+                         int32_t* uslot, cudaStream_t st);
+void launch_set_slots(const int32_t* q_list, const int32_t* slot_list, int n, int32_t* slot_of, cudaStream_t st);
+
+// ---- plain binary64 scan ----
+void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot_of_list, const float* d,
+                   const double* centre, const double* Sc, int64_t G, int nfit, const double* A64,
+                   const double* Q64, int64_t ldq, int32_t* best, cudaStream_t st);
+
+// ---- mixed path: grouping, y prep, screen, decision ----
+// counting sort of active universes by slot into BM-row tiles
+void launch_group(const int32_t* active, int64_t n_active, const int32_t* uslot, int n_slots, int32_t* cnt,
+                  int32_t* tile_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* tile_slot, int32_t* tile_univ,
+                  int64_t max_tiles, cudaStream_t st);
+void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
+                  const double* centre, int nfit, int K, const float* A32, const float* rho, uint16_t* Ytiles,
+                  float* alpha, cudaStream_t st);
+// returns false if the padded K has no compiled screen instance
+bool launch_screen(int K, int topk, const uint16_t* Ytiles, const uint16_t* Btiles, const float* Qb,
+                   const int32_t* tile_slot, int64_t n_tiles, int64_t G, int64_t G_pad, float* cand_val,
+                   int32_t* cand_idx, int* status, int n_sm, cudaStream_t st);
+// decides the argmin from candidates; writes best[u] or flags fallback
+void launch_decide(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, int topk,
+                   const float* cand_val, const int32_t* cand_idx, const float* alpha, const float* nrm,
+                   const float* Qc, const float* Qb, int64_t G_pad, const float* d, const double* centre,
+                   const double* S_fit, int nfit, const double* W64, int32_t* best, int32_t* fallback_list,
+                   int32_t* n_fallback, unsigned long long* counters, cudaStream_t st);
+
+// ---- final residual-form chi2 and dchi2 ----
+void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot_of_list, const int32_t* best,
+                   const int32_t* p_of_univ_base, int U, const float* d, const double* S_fit, int nfit,
+                   const double* W64, double* dchi2, double* chi2min, cudaStream_t st);
+// advance: converged / exhausted universes -> finish list, others stay active
+void launch_advance(const int32_t* active, int64_t n_active, const int32_t* best, int32_t* cur, int8_t* nscan,
+                    int scan_no, int max_iter, int32_t* next_active, int32_t* n_next, int32_t* finish_list,
+                    int32_t* n_finish, cudaStream_t st);
+
+// ---- quantiles ----
+void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st);
+
+}  // namespace fcdev

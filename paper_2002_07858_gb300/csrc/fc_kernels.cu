@@ -1,0 +1,1001 @@
+// fc_kernels.cu -- CUDA kernels of the Feldman-Cousins grid fit (all steps but
+// the tensor-core screen, which lives in fc_screen.cu).
+//
+// Method (§2, Algorithm 1, Algorithm 2, Eq. 1): per universe, fluctuate the
+// true point's spectrum, scan every grid spectrum with chi2 = r^T A r
+// (r = s_g - d, A = M^-1), keep the first minimum, refit M at the minimum and
+// rescan until the minimum repeats, then dchi2 = chi2(p) - chi2_min under the
+// last scan's A.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include <cstdint>
+
+#include "fc_internal.cuh"
+#include "fc_sampler.cuh"
+
+namespace fcdev {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) {
+    int64_t b = (n + t - 1) / t;
+    if (b < 1) b = 1;
+    if (b > 2147483647LL) b = 2147483647LL;
+    return (unsigned)b;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (value, index) lexicographic minimum across a warp
+__device__ __forceinline__ void warp_argmin(double& v, int32_t& g) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int32_t og = __shfl_xor_sync(0xffffffffu, g, o);
+        if (ov < v || (ov == v && og < g)) {
+            v = ov;
+            g = og;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- ingest ---
+
+__global__ void k_collapse(const double* __restrict__ S, int64_t G, int nf, const int32_t* __restrict__ coll,
+                           int nfit, double* __restrict__ out) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    double acc[kMaxBins];
+    for (int j = 0; j < nfit; ++j) acc[j] = 0.0;
+    for (int i = 0; i < nf; ++i) {
+        const int j = coll ? coll[i] : i;
+        acc[j] = __dadd_rn(acc[j], S[g * nf + i]);
+    }
+    for (int j = 0; j < nfit; ++j) out[g * nfit + j] = acc[j];
+}
+
+// Approximate per-bin median of the grid spectra by two rounds of a 4096-bucket
+// histogram; it only chooses the centring vector of the screen, any value works.
+__global__ void k_centre(const double* __restrict__ S, int64_t G, int nfit, double* __restrict__ centre) {
+    constexpr int NB = 4096;
+    __shared__ unsigned hist[NB];
+    __shared__ double red_lo[kThreads / 32], red_hi[kThreads / 32];
+    __shared__ double s_lo, s_hi;
+    __shared__ int64_t s_rank;
+    __shared__ int s_bucket;
+    const int j = blockIdx.x;
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
+        const double x = S[g * nfit + j];
+        lo = fmin(lo, x);
+        hi = fmax(hi, x);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_lo[threadIdx.x >> 5] = lo;
+        red_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = red_lo[0], b = red_hi[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a = fmin(a, red_lo[w]);
+            b = fmax(b, red_hi[w]);
+        }
+        s_lo = a;
+        s_hi = b;
+        s_rank = (G - 1) / 2;
+    }
+    __syncthreads();
+    double blo = s_lo, bhi = s_hi;
+    for (int round = 0; round < 2; ++round) {
+        for (int b = threadIdx.x; b < NB; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const double w = (bhi - blo) / NB;
+        for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
+            const double x = S[g * nfit + j];
+            if (x < blo || x > bhi) continue;
+            int b = (w > 0.0) ? (int)((x - blo) / w) : 0;
+            b = b < 0 ? 0 : (b >= NB ? NB - 1 : b);
+            atomicAdd(&hist[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t acc = 0;
+            int b = 0;
+            for (; b < NB; ++b) {
+                if (acc + hist[b] > s_rank) break;
+                acc += hist[b];
+            }
+            if (b >= NB) b = NB - 1;
+            s_bucket = b;
+            s_rank -= acc;
+        }
+        __syncthreads();
+        const double nlo = blo + w * s_bucket;
+        const double nhi = (s_bucket == NB - 1) ? bhi : blo + w * (s_bucket + 1);
+        __syncthreads();
+        blo = nlo;
+        bhi = nhi;
+    }
+    if (threadIdx.x == 0) centre[j] = 0.5 * (blo + bhi);
+}
+
+__device__ __forceinline__ int64_t btile_offset(int64_t g, int c, int K) {
+    // B-operand image of one BN-row tile: [2K/8 chunks][BN/8 row groups][8 rows][8 cols] bf16
+    const int64_t t = g / kBN;
+    const int r = (int)(g % kBN);
+    return t * (int64_t)(2 * K * kBN) + (int64_t)(c >> 3) * (kBN * 8) + (r >> 3) * 64 + (r & 7) * 8 + (c & 7);
+}
+
+__global__ void k_centred(const double* __restrict__ Sfit, const double* __restrict__ centre, int64_t G, int nfit,
+                          int K, double* __restrict__ Sc, float* __restrict__ Sc32, float* __restrict__ nrm,
+                          uint16_t* __restrict__ Bt) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    double ss = 0.0;
+    for (int j = 0; j < nfit; ++j) {
+        const double x = Sfit[g * nfit + j] - centre[j];
+        Sc[g * nfit + j] = x;
+        Sc32[g * nfit + j] = (float)x;
+        ss = fma(x, x, ss);
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const double rem = x - (double)__bfloat162float(h);
+        const __nv_bfloat16 l = __double2bfloat16(rem);
+        Bt[btile_offset(g, j, K)] = __bfloat16_as_ushort(h);
+        Bt[btile_offset(g, K + j, K)] = __bfloat16_as_ushort(l);
+    }
+    // norm, rounded up twice (double sqrt then float), carried by the spare column of the lo half
+    const float n = __double2float_ru(__dsqrt_ru(ss) * (1.0 + 1e-12));
+    nrm[g] = n;
+    Bt[btile_offset(g, K + nfit, K)] = __bfloat16_as_ushort(__float2bfloat16_ru(n));
+}
+
+// ------------------------------------------------------------ covariances ---
+
+// Cholesky in place on the lower triangle of a row-major n x n matrix held in
+// global memory; every element's sum runs k = 0..j-1 with separately rounded
+// multiply and subtract, so the factor is reproducible bit for bit.
+__device__ bool chol_inplace(double* L, int n) {
+    __shared__ double s_d;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            double acc = L[j * n + j];
+            for (int k = 0; k < j; ++k) acc = __dsub_rn(acc, __dmul_rn(L[j * n + k], L[j * n + k]));
+            if (!(acc > 0.0)) {
+                s_bad = 1;
+                acc = 1.0;
+            }
+            s_d = __dsqrt_rn(acc);
+            L[j * n + j] = s_d;
+        }
+        __syncthreads();
+        const double dj = s_d;
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+            double a = L[i * n + j];
+            for (int k = 0; k < j; ++k) a = __dsub_rn(a, __dmul_rn(L[i * n + k], L[j * n + k]));
+            L[i * n + j] = __ddiv_rn(a, dj);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, c = e % n;
+        if (c > i) L[e] = 0.0;
+    }
+    __syncthreads();
+    return s_bad == 0;
+}
+
+__global__ void k_chol_sys(const double* __restrict__ S, int nf, const double* __restrict__ F,
+                           const int64_t* __restrict__ ps, int gauss, double* __restrict__ L64,
+                           float* __restrict__ L32, float* __restrict__ s32, int* __restrict__ status) {
+    const int ip = blockIdx.x;
+    const double* s = S + ps[ip] * nf;
+    double* L = L64 + (size_t)ip * nf * nf;
+    for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) {
+        const int i = e / nf, j = e % nf;
+        if (j <= i) {
+            double v = __dmul_rn(__dmul_rn(s[i], F[i * nf + j]), s[j]);
+            if (gauss && i == j) v = __dadd_rn(v, s[i]);
+            L[e] = v;
+        }
+    }
+    __syncthreads();
+    const bool ok = chol_inplace(L, nf);
+    if (!ok && threadIdx.x == 0) atomicOr(status, kDevNotSpd);
+    for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) L32[(size_t)ip * nf * nf + e] = __double2float_rn(L[e]);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) s32[(size_t)ip * nf + i] = __double2float_rn(s[i]);
+}
+
+// One CTA per (slot, q): M(q) = C [diag(s) F diag(s) + diag(s)] C^T, L = chol(M),
+// W = L^-1, A = W^T W.
+__global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, const int32_t* __restrict__ coll,
+                            const double* __restrict__ F, const int32_t* __restrict__ q_list,
+                            const int32_t* __restrict__ slot_list, int cov_mode, double* __restrict__ A64,
+                            double* __restrict__ W64, float* __restrict__ A32, float* __restrict__ rho,
+                            double* __restrict__ work, int* __restrict__ status) {
+    const int e0 = blockIdx.x;
+    const int q = q_list[e0];
+    const int slot = slot_list[e0];
+    const int n = nfit;
+    double* L = work + (size_t)e0 * n * n;
+    double* W = W64 + (size_t)slot * n * n;
+    double* A = A64 + (size_t)slot * n * n;
+    const double* s = S + (int64_t)q * nf;
+    if (cov_mode == 2) {  // identity test mode
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const double v = (e / n == e % n) ? 1.0 : 0.0;
+            W[e] = v;
+            A[e] = v;
+            A32[(size_t)slot * n * n + e] = (float)v;
+        }
+        if (threadIdx.x == 0) rho[slot] = 1.0f;
+        return;
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = 0.0;
+    __syncthreads();
+    if (coll == nullptr) {
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e / n, m = e % n;
+            if (m > i) continue;
+            double v = (s[i] * F[i * nf + m]) * s[m];
+            if (i == m) v += s[i];
+            L[e] = v;
+        }
+    } else {
+        // row j of the fit-space matrix is owned by one thread: no races
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            for (int i = 0; i < nf; ++i) {
+                if (coll[i] != j) continue;
+                for (int m = 0; m < nf; ++m) {
+                    const int l = coll[m];
+                    if (l > j) continue;
+                    double v = (s[i] * F[i * nf + m]) * s[m];
+                    if (i == m) v += s[i];
+                    L[j * n + l] += v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const bool ok = chol_inplace(L, n);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(status, kDevNotSpd);
+        return;
+    }
+    // W = L^-1 (lower): column c by one thread, forward substitution
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int i = 0; i < c; ++i) W[i * n + c] = 0.0;
+        W[c * n + c] = 1.0 / L[c * n + c];
+        for (int i = c + 1; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = c; k < i; ++k) acc = fma(L[i * n + k], W[k * n + c], acc);
+            W[i * n + c] = -acc / L[i * n + i];
+        }
+    }
+    __syncthreads();
+    // A = W^T W: A_ij = sum_{k >= max(i,j)} W_ki W_kj
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        if (j > i) continue;
+        double acc = 0.0;
+        for (int k = i; k < n; ++k) acc = fma(W[k * n + i], W[k * n + j], acc);
+        A[i * n + j] = acc;
+        A[j * n + i] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) A32[(size_t)slot * n * n + e] = (float)A[e];
+    // rho = max_i sum_j |A_ij| (an upper bound of the spectral norm of |A|), rounded up
+    __shared__ double s_rho;
+    if (threadIdx.x == 0) s_rho = 0.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double r = 0.0;
+        for (int j = 0; j < n; ++j) r += fabs(A[i * n + j]);
+        atomicMax((unsigned long long*)&s_rho, (unsigned long long)__double_as_longlong(r));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) rho[slot] = __double2float_ru(s_rho * (1.0 + 1e-9));
+}
+
+// q_g = s~_g^T A s~_g in binary64, one thread per g
+__global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, const double* __restrict__ A64,
+                         const int32_t* __restrict__ slots, int64_t ldq, double* __restrict__ Q64) {
+    const int slot = slots[blockIdx.y];
+    const double* A = A64 + (size_t)slot * nfit * nfit;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+        const double* s = Sc + g * nfit;
+        double q = 0.0;
+        for (int i = 0; i < nfit; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < nfit; ++j) t = fma(A[i * nfit + j], s[j], t);
+            q = fma(s[i], t, q);
+        }
+        Q64[(size_t)slot * ldq + g] = q;
+    }
+}
+
+// binary32 q_g with its rounding bound; s~_g held in registers (NMAX >= nfit,
+// NMAX a multiple of 4), A staged in shared memory with rows padded to NMAX.
+template <int NMAX>
+__global__ void k_qvec32(const float* __restrict__ Sc32, const float* __restrict__ nrm, int64_t G, int64_t G_pad,
+                         int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
+                         const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb) {
+    __shared__ __align__(16) float sA[NMAX * NMAX];
+    const int slot = slots[blockIdx.y];
+    const float* A = A32 + (size_t)slot * nfit * nfit;
+    for (int e = threadIdx.x; e < NMAX * NMAX; e += blockDim.x) {
+        const int i = e / NMAX, j = e % NMAX;
+        sA[e] = (i < nfit && j < nfit) ? A[i * nfit + j] : 0.0f;
+    }
+    __syncthreads();
+    const float r = rho[slot];
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G_pad; g += (int64_t)gridDim.x * blockDim.x) {
+        float qc = 0.0f, qb = 3.0e38f;
+        if (g < G) {
+            float s[NMAX];
+#pragma unroll
+            for (int j = 0; j < NMAX; ++j) s[j] = (j < nfit) ? Sc32[g * nfit + j] : 0.0f;
+            float q = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NMAX; ++i) {
+                const float4* Ai = reinterpret_cast<const float4*>(sA + i * NMAX);
+                float t = 0.0f;
+#pragma unroll
+                for (int j4 = 0; j4 < NMAX / 4; ++j4) {
+                    const float4 a4 = Ai[j4];
+                    t = fmaf(a4.x, s[4 * j4 + 0], t);
+                    t = fmaf(a4.y, s[4 * j4 + 1], t);
+                    t = fmaf(a4.z, s[4 * j4 + 2], t);
+                    t = fmaf(a4.w, s[4 * j4 + 3], t);
+                }
+                q = fmaf(s[i], t, q);
+            }
+            const float n = nrm[g];
+            // |q^ - q| <= (nfit+4) 2^-24 rho |s|^2 + 2^-23 |q^|   (A rounded to binary32, dot products, final rounding)
+            const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + 1.1920929e-07f * fabsf(q));
+            qc = q;
+            qb = __fsub_rd(q, beta);
+        }
+        Qc[(size_t)slot * G_pad + g] = qc;
+        Qb[(size_t)slot * G_pad + g] = qb;
+    }
+}
+
+__global__ void k_qvec32_generic(const float* __restrict__ Sc32, const float* __restrict__ nrm, int64_t G,
+                                 int64_t G_pad, int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
+                                 const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb) {
+    const int slot = slots[blockIdx.y];
+    const float* A = A32 + (size_t)slot * nfit * nfit;
+    const float r = rho[slot];
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G_pad; g += (int64_t)gridDim.x * blockDim.x) {
+        float qc = 0.0f, qb = 3.0e38f;
+        if (g < G) {
+            const float* s = Sc32 + g * nfit;
+            float q = 0.0f;
+            for (int i = 0; i < nfit; ++i) {
+                float t = 0.0f;
+                for (int j = 0; j < nfit; ++j) t = fmaf(A[i * nfit + j], s[j], t);
+                q = fmaf(s[i], t, q);
+            }
+            const float n = nrm[g];
+            const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + 1.1920929e-07f * fabsf(q));
+            qc = q;
+            qb = __fsub_rd(q, beta);
+        }
+        Qc[(size_t)slot * G_pad + g] = qc;
+        Qb[(size_t)slot * G_pad + g] = qb;
+    }
+}
+
+// -------------------------------------------------------------- fake data ---
+
+// One thread per universe: z from Philox/Box-Muller, lam_i = max(0, s_i +
+// sum_{j<=i} L_ij z_j) accumulated with fma in j order, n_i = Poisson(lam_i)
+// from bin i's own stream, fit bin = sum of its full bins in i order.
+__global__ void __launch_bounds__(128) k_fake_data(const float* __restrict__ L32, const float* __restrict__ s32,
+                                                    int nf, const int32_t* __restrict__ coll, int nfit,
+                                                    const int64_t* __restrict__ ps, int U, uint32_t k0,
+                                                    uint32_t k1, int gauss, float* __restrict__ d) {
+    const int ip = blockIdx.y;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= U) return;
+    const uint32_t p = (uint32_t)ps[ip];
+    const float* L = L32 + (size_t)ip * nf * nf;
+    const float* s = s32 + (size_t)ip * nf;
+    float z[kMaxBins + 4];
+    for (int j = 0; 4 * j < nf; ++j) {
+        float zz[4];
+        normal_block((uint32_t)j, (uint32_t)u, p, k0, k1, zz);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) z[4 * j + h] = zz[h];
+    }
+    float dfit[kMaxBins];
+    for (int j = 0; j < nfit; ++j) dfit[j] = 0.0f;
+    for (int i = 0; i < nf; ++i) {
+        const float* Li = L + (size_t)i * nf;
+        float acc = 0.0f;
+        for (int j = 0; j <= i; ++j) acc = __fmaf_rn(__ldg(Li + j), z[j], acc);
+        float lam = __fadd_rn(__ldg(s + i), acc);
+        float v;
+        if (gauss) {
+            v = lam;
+        } else {
+            if (!(lam > 0.0f)) lam = 0.0f;
+            UniformStream st;
+            st.init(k0, k1, (uint32_t)u, p, (uint32_t)i);
+            v = (float)poisson(lam, st);
+        }
+        const int jf = coll ? coll[i] : i;
+        dfit[jf] = __fadd_rn(dfit[jf], v);
+    }
+    float* o = d + ((size_t)ip * U + u) * nfit;
+    for (int j = 0; j < nfit; ++j) o[j] = dfit[j];
+}
+
+// ------------------------------------------------------- bookkeeping -------
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_iota_i32(int32_t* p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+
+__global__ void k_mark_used(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ cur,
+                            uint8_t* __restrict__ flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[cur[active[i]]] = 1;
+}
+
+__global__ void k_compact_flags(uint8_t* __restrict__ flag, int64_t G, int32_t* __restrict__ list,
+                                int32_t* __restrict__ count) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    if (flag[g]) {
+        flag[g] = 0;
+        list[atomicAdd(count, 1)] = (int32_t)g;
+    }
+}
+
+__global__ void k_lookup_slots(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ cur,
+                               const int32_t* __restrict__ slot_of, int32_t* __restrict__ uslot) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) uslot[i] = slot_of[cur[active[i]]];
+}
+
+__global__ void k_set_slots(const int32_t* __restrict__ q, const int32_t* __restrict__ s, int n,
+                            int32_t* __restrict__ slot_of) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) slot_of[q[i]] = s[i];
+}
+
+// ------------------------------------------------------ plain fp64 scan -----
+
+// One warp per universe: y = A (d - v), then chi2_g - c = q_g - 2 y.s~_g for
+// every g, first minimum in index order.
+__global__ void __launch_bounds__(256) k_scan64(const int32_t* __restrict__ list, int64_t n,
+                                                 const int32_t* __restrict__ uslot, const float* __restrict__ d,
+                                                 const double* __restrict__ centre, const double* __restrict__ Sc,
+                                                 int64_t G, int nfit, const double* __restrict__ A64,
+                                                 const double* __restrict__ Q64, int64_t ldq,
+                                                 int32_t* __restrict__ best) {
+    __shared__ double sy[8][kMaxBins];
+    __shared__ double sd[8][kMaxBins];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = blockIdx.x * 8LL + w;
+    if (i >= n) return;
+    const int u = list[i];
+    const int slot = uslot[i];
+    const double* A = A64 + (size_t)slot * nfit * nfit;
+    for (int j = lane; j < nfit; j += 32) sd[w][j] = (double)d[(size_t)u * nfit + j] - centre[j];
+    __syncwarp();
+    for (int r = lane; r < nfit; r += 32) {
+        double t = 0.0;
+        for (int j = 0; j < nfit; ++j) t = fma(A[r * nfit + j], sd[w][j], t);
+        sy[w][r] = t;
+    }
+    __syncwarp();
+    const double* Q = Q64 + (size_t)slot * ldq;
+    double bv = DBL_MAX;
+    int32_t bg = INT32_MAX;
+    for (int64_t g = lane; g < G; g += 32) {
+        const double* s = Sc + g * nfit;
+        double dot = 0.0;
+        for (int j = 0; j < nfit; ++j) dot = fma(sy[w][j], s[j], dot);
+        const double v = fma(-2.0, dot, Q[g]);
+        if (v < bv) {
+            bv = v;
+            bg = (int32_t)g;
+        }
+    }
+    warp_argmin(bv, bg);
+    if (lane == 0) best[u] = bg;
+}
+
+// ------------------------------------------------------ mixed: grouping -----
+
+__global__ void k_count_slots(const int32_t* __restrict__ uslot, int64_t n, int32_t* __restrict__ cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[uslot[i]], 1);
+}
+
+// exclusive scan of ceil(cnt/BM) over slots (single CTA), writes the tile count
+__global__ void k_tile_scan(const int32_t* __restrict__ cnt, int n_slots, int32_t* __restrict__ base,
+                            int32_t* __restrict__ n_tiles) {
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int start = 0; start < n_slots; start += blockDim.x) {
+        const int s = start + threadIdx.x;
+        const int32_t v = (s < n_slots) ? (cnt[s] + kBM - 1) / kBM : 0;
+        int32_t x = v;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int32_t t = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const int32_t excl = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+        if (s < n_slots) base[s] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_tiles = carry;
+}
+
+__global__ void k_tile_slots(const int32_t* __restrict__ cnt, const int32_t* __restrict__ base, int n_slots,
+                             int32_t* __restrict__ tile_slot) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slots) return;
+    const int nt = (cnt[s] + kBM - 1) / kBM;
+    for (int t = 0; t < nt; ++t) tile_slot[base[s] + t] = s;
+}
+
+__global__ void k_scatter_tiles(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ uslot,
+                                const int32_t* __restrict__ base, int32_t* __restrict__ fill,
+                                int32_t* __restrict__ tile_univ) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = uslot[i];
+    const int pos = atomicAdd(&fill[s], 1);
+    tile_univ[(int64_t)(base[s] + pos / kBM) * kBM + pos % kBM] = active[i];
+}
+
+// ---------------------------------------------------------- mixed: y prep ---
+
+__device__ __forceinline__ int64_t ytile_offset(int64_t t, int r, int c, int K) {
+    // A-operand image of one BM-row tile: [2K/8 chunks][BM/8 row groups][8 rows][8 cols] bf16
+    return t * (int64_t)(2 * K * kBM) + (int64_t)(c >> 3) * (kBM * 8) + (r >> 3) * 64 + (r & 7) * 8 + (c & 7);
+}
+
+// One CTA per tile, one thread per row: y^ = A (d - v) in binary32, Y = -2 y^
+// split into bf16 hi + lo, and the error-bound coefficient alpha in the spare
+// column so that the screen directly yields a lower bound of chi2_g - c_u.
+__global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_slot,
+                                                const int32_t* __restrict__ tile_univ, const float* __restrict__ d,
+                                                const double* __restrict__ centre, int nfit, int K,
+                                                const float* __restrict__ A32, const float* __restrict__ rho,
+                                                uint16_t* __restrict__ Yt, float* __restrict__ alpha) {
+    extern __shared__ float sA[];
+    const int64_t t = blockIdx.x;
+    const int slot = tile_slot[t];
+    for (int e = threadIdx.x; e < nfit * nfit; e += blockDim.x) sA[e] = A32[(size_t)slot * nfit * nfit + e];
+    __syncthreads();
+    const int r = threadIdx.x;
+    const int u = tile_univ[t * kBM + r];
+    for (int c = 0; c < 2 * K; ++c) Yt[ytile_offset(t, r, c, K)] = 0;
+    if (u < 0) {
+        alpha[t * kBM + r] = 0.0f;
+        return;
+    }
+    float dt[kMaxBins];
+    float dn2 = 0.0f;
+    for (int j = 0; j < nfit; ++j) {
+        dt[j] = (float)((double)d[(size_t)u * nfit + j] - centre[j]);
+        dn2 = fmaf(dt[j], dt[j], dn2);
+    }
+    float yn2 = 0.0f;
+    for (int i = 0; i < nfit; ++i) {
+        float y = 0.0f;
+        for (int j = 0; j < nfit; ++j) y = fmaf(sA[i * nfit + j], dt[j], y);
+        const float Y = -2.0f * y;
+        yn2 = fmaf(Y, Y, yn2);
+        const __nv_bfloat16 h = __float2bfloat16_rn(Y);
+        const __nv_bfloat16 l = __float2bfloat16_rn(Y - __bfloat162float(h));
+        Yt[ytile_offset(t, r, i, K)] = __bfloat16_as_ushort(h);
+        Yt[ytile_offset(t, r, K + i, K)] = __bfloat16_as_ushort(l);
+    }
+    // |computed - exact| of -2 y.s~_g  <=  alpha * |s~_g|:
+    //   2 |y - y^| |s~|            with |y - y^| <= (nfit+2) 2^-24 rho |d~|
+    //   3.03 2^-16 |Y| |s~|        dropped lo*lo products and the two split residuals
+    //   (3K+2) 2^-23 1.02 |Y| |s~| binary32 accumulation of the products
+    const float dn = sqrtf(dn2) * 1.0001f, yn = sqrtf(yn2) * 1.0001f;
+    const float c_split = 3.03f * 1.52587890625e-05f + (float)(3 * K + 2) * 1.1920929e-07f * 1.02f;
+    const float a = 1.05f * (2.0f * (float)(nfit + 2) * 5.9604645e-08f * rho[slot] * dn + c_split * yn);
+    alpha[t * kBM + r] = a;
+    Yt[ytile_offset(t, r, nfit, K)] = __bfloat16_as_ushort(__float2bfloat16_rd(-a));
+}
+
+// ------------------------------------------------------- mixed: decision ----
+
+// ||W r||^2 with r = s_g - d, W lower triangular (A = W^T W): residual form.
+__device__ double chi2_resid_thread(const double* __restrict__ W, const double* __restrict__ sg,
+                                    const float* __restrict__ du, int n) {
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int j = 0; j <= i; ++j) t = fma(W[i * n + j], sg[j] - (double)du[j], t);
+        acc = fma(t, t, acc);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kBM) k_decide(const int32_t* __restrict__ tile_slot,
+                                                 const int32_t* __restrict__ tile_univ, int topk,
+                                                 const float* __restrict__ cval, const int32_t* __restrict__ cidx,
+                                                 const float* __restrict__ alpha, const float* __restrict__ nrm,
+                                                 const float* __restrict__ Qc, const float* __restrict__ Qb,
+                                                 int64_t G_pad, const float* __restrict__ d,
+                                                 const double* __restrict__ centre, const double* __restrict__ Sfit,
+                                                 int nfit, const double* __restrict__ W64, int32_t* __restrict__ best,
+                                                 int32_t* __restrict__ fb_list, int32_t* __restrict__ n_fb,
+                                                 unsigned long long* __restrict__ counters) {
+    const int64_t t = blockIdx.x;
+    const int r = threadIdx.x;
+    const int u = tile_univ[t * kBM + r];
+    if (u < 0) return;
+    const int slot = tile_slot[t];
+    const int64_t row = t * kBM + r;
+    const float a = alpha[row];
+    float lb[kMaxTopK], ub[kMaxTopK];
+    int32_t gi[kMaxTopK];
+    int nvalid = 0;
+    float min_ub = FLT_MAX;
+    for (int j = 0; j < topk; ++j) {
+        gi[j] = cidx[row * topk + j];
+        lb[j] = cval[row * topk + j];
+        if (gi[j] < 0) continue;
+        ++nvalid;
+        const int64_t q = (int64_t)slot * G_pad + gi[j];
+        const float eps = fmaf(a, nrm[gi[j]], Qc[q] - Qb[q]);
+        ub[j] = lb[j] + 2.0f * eps + 4.7683716e-07f * (fabsf(lb[j]) + fabsf(Qc[q]) + 1.0f);
+        min_ub = fminf(min_ub, ub[j]);
+    }
+    // every grid point outside the list has a lower bound >= tau (the k-th kept value)
+    const bool full = (nvalid == topk);
+    const float tau = full ? lb[topk - 1] - 4.7683716e-07f * (fabsf(lb[topk - 1]) + 1.0f) : FLT_MAX;
+    int nR = 0;
+    for (int j = 0; j < topk; ++j)
+        if (gi[j] >= 0 && lb[j] <= min_ub) ++nR;
+    if (nR == 1 && ub[0] < tau) {
+        best[u] = gi[0];
+        atomicAdd(&counters[0], 1ull);
+        return;
+    }
+    // binary64 residual-form chi2 of the candidates that can still be the minimum
+    const double* W = W64 + (size_t)slot * nfit * nfit;
+    const float* du = d + (size_t)u * nfit;
+    double bchi = DBL_MAX;
+    int32_t bg = INT32_MAX;
+    for (int j = 0; j < topk; ++j) {
+        if (gi[j] < 0 || lb[j] > min_ub) continue;
+        const double c = chi2_resid_thread(W, Sfit + (int64_t)gi[j] * nfit, du, nfit);
+        if (c < bchi || (c == bchi && gi[j] < bg)) {
+            bchi = c;
+            bg = gi[j];
+        }
+    }
+    bool ok = !full;
+    if (full) {
+        // c_u = |W (d - v)|^2; certified iff every outside point's lower bound exceeds chi2_min - c_u
+        double cu = 0.0;
+        for (int i = 0; i < nfit; ++i) {
+            double tt = 0.0;
+            for (int j = 0; j <= i; ++j) tt = fma(W[i * nfit + j], (double)du[j] - centre[j], tt);
+            cu = fma(tt, tt, cu);
+        }
+        const double sig_min = bchi - cu;
+        ok = (double)tau > sig_min + 1e-9 * (fabs(bchi) + fabs(cu));
+    }
+    if (ok) {
+        best[u] = bg;
+        atomicAdd(&counters[1], 1ull);
+    } else {
+        fb_list[atomicAdd(n_fb, 1)] = u;
+        atomicAdd(&counters[2], 1ull);
+    }
+}
+
+// ---------------------------------------------------------- finishing -------
+
+// One warp per finishing universe: chi2_p and chi2_min in residual form under
+// the last scan's covariance (A = W^T W), dchi2 = chi2_p - chi2_min.
+__global__ void __launch_bounds__(256) k_finish(const int32_t* __restrict__ list, int64_t n,
+                                                 const int32_t* __restrict__ uslot, const int32_t* __restrict__ best,
+                                                 const int32_t* __restrict__ p_of, int U, const float* __restrict__ d,
+                                                 const double* __restrict__ Sfit, int nfit,
+                                                 const double* __restrict__ W64, double* __restrict__ dchi2,
+                                                 double* __restrict__ chi2min) {
+    __shared__ double rp[8][kMaxBins], rm[8][kMaxBins];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = blockIdx.x * 8LL + w;
+    if (i >= n) return;
+    const int u = list[i];
+    const int slot = uslot[i];
+    const int p = p_of[u / U];
+    const int g = best[u];
+    const float* du = d + (size_t)u * nfit;
+    for (int j = lane; j < nfit; j += 32) {
+        rp[w][j] = Sfit[(int64_t)p * nfit + j] - (double)du[j];
+        rm[w][j] = Sfit[(int64_t)g * nfit + j] - (double)du[j];
+    }
+    __syncwarp();
+    const double* W = W64 + (size_t)slot * nfit * nfit;
+    double cp = 0.0, cm = 0.0;
+    for (int r = lane; r < nfit; r += 32) {
+        double tp = 0.0, tm = 0.0;
+        for (int j = 0; j <= r; ++j) {
+            const double wv = W[r * nfit + j];
+            tp = fma(wv, rp[w][j], tp);
+            tm = fma(wv, rm[w][j], tm);
+        }
+        cp = fma(tp, tp, cp);
+        cm = fma(tm, tm, cm);
+    }
+    cp = warp_sum(cp);
+    cm = warp_sum(cm);
+    if (lane == 0) {
+        dchi2[u] = (p == g) ? 0.0 : cp - cm;
+        if (chi2min) chi2min[u] = cm;
+    }
+}
+
+__global__ void k_advance(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ best,
+                          int32_t* __restrict__ cur, int8_t* __restrict__ nscan, int scan_no, int max_iter,
+                          int32_t* __restrict__ next_active, int32_t* __restrict__ n_next,
+                          int32_t* __restrict__ fin, int32_t* __restrict__ n_fin) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int u = active[i];
+    if (best[u] == cur[u] || scan_no >= max_iter) {
+        nscan[u] = (int8_t)scan_no;
+        fin[atomicAdd(n_fin, 1)] = u;
+    } else {
+        cur[u] = best[u];
+        next_active[atomicAdd(n_next, 1)] = u;
+    }
+}
+
+// ---------------------------------------------------------- quantiles -------
+
+// One CTA per row: bitonic sort in shared memory, then numpy's "linear" rule.
+__global__ void k_quantiles(const double* __restrict__ x, int n, int npow2, const double* __restrict__ probs,
+                            int nq, double* __restrict__ out) {
+    extern __shared__ double sx[];
+    const int row = blockIdx.x;
+    for (int i = threadIdx.x; i < npow2; i += blockDim.x) sx[i] = (i < n) ? x[(size_t)row * n + i] : DBL_MAX;
+    __syncthreads();
+    for (int k = 2; k <= npow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = ((i & k) == 0);
+                    const double a = sx[i], b = sx[ixj];
+                    if ((a > b) == up) {
+                        sx[i] = b;
+                        sx[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const double h = (double)(n - 1) * probs[q];
+        int lo = (int)floor(h);
+        if (lo < 0) lo = 0;
+        if (lo > n - 1) lo = n - 1;
+        const int hi = lo + 1 < n ? lo + 1 : n - 1;
+        const double f = h - lo;
+        out[(size_t)row * nq + q] = sx[lo] + f * (sx[hi] - sx[lo]);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers ----
+
+void launch_collapse(const double* S, int64_t G, int nf, const int32_t* coll, int nfit, double* out,
+                     cudaStream_t st) {
+    k_collapse<<<blocks_for(G, 128), 128, 0, st>>>(S, G, nf, coll, nfit, out);
+}
+
+void launch_centre(const double* S_fit, int64_t G, int nfit, double* centre, double*, cudaStream_t st) {
+    k_centre<<<nfit, kThreads, 0, st>>>(S_fit, G, nfit, centre);
+}
+
+void launch_centred(const double* S_fit, const double* centre, int64_t G, int64_t G_pad, int nfit, int K,
+                    double* Sc, float* Sc32, float* nrm, uint16_t* Bt, cudaStream_t st) {
+    cudaMemsetAsync(Bt, 0, (size_t)G_pad * 2 * K * sizeof(uint16_t), st);
+    k_centred<<<blocks_for(G, 128), 128, 0, st>>>(S_fit, centre, G, nfit, K, Sc, Sc32, nrm, Bt);
+}
+
+void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps, int P, int gauss, double* L64,
+                     float* L32, float* s32, double*, int* status, cudaStream_t st) {
+    if (P <= 0) return;
+    k_chol_sys<<<P, 256, 0, st>>>(S, nf, F, ps, gauss, L64, L32, s32, status);
+}
+
+void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, const double* F, const int32_t* q_list,
+                      const int32_t* slot_list, int n, int cov_mode, double* A64, double* W64, float* A32,
+                      float* rho, double* work, int* status, cudaStream_t st) {
+    if (n <= 0) return;
+    k_build_cov<<<n, 256, 0, st>>>(S, nf, nfit, coll, F, q_list, slot_list, cov_mode, A64, W64, A32, rho, work,
+                                   status);
+}
+
+void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
+                   int64_t ldq, double* Q64, cudaStream_t st) {
+    if (n <= 0) return;
+    dim3 grid(blocks_for(G, 128) < 64 ? blocks_for(G, 128) : 64, n);
+    k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, A64, slots, ldq, Q64);
+}
+
+void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad, int nfit, const float* A32,
+                   const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, cudaStream_t st) {
+    if (n <= 0) return;
+    unsigned gx = blocks_for(G_pad, 128);
+    if (gx > 128) gx = 128;
+    dim3 grid(gx, n);
+    if (nfit <= 16)
+        k_qvec32<16><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+    else if (nfit <= 32)
+        k_qvec32<32><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+    else if (nfit <= 48)
+        k_qvec32<48><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+    else if (nfit <= 64)
+        k_qvec32<64><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+    else
+        k_qvec32_generic<<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+}
+
+void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* coll, int nfit, const int64_t* ps,
+                      int P, int U, uint64_t seed, int gauss, float* d, cudaStream_t st) {
+    if (P <= 0 || U <= 0) return;
+    dim3 grid((U + 127) / 128, P);
+    k_fake_data<<<grid, 128, 0, st>>>(L32, s32, nf, coll, nfit, ps, U, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                       gauss, d);
+}
+
+void launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t st) {
+    if (n <= 0) return;
+    unsigned b = blocks_for(n);
+    if (b > 4096) b = 4096;
+    k_fill_i32<<<b, kThreads, 0, st>>>(p, n, v);
+}
+
+void launch_iota_i32(int32_t* p, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    unsigned b = blocks_for(n);
+    if (b > 4096) b = 4096;
+    k_iota_i32<<<b, kThreads, 0, st>>>(p, n);
+}
+
+void launch_mark_used(const int32_t* active, int64_t n, const int32_t* cur, uint8_t* flag, cudaStream_t st) {
+    if (n <= 0) return;
+    k_mark_used<<<blocks_for(n), kThreads, 0, st>>>(active, n, cur, flag);
+}
+
+void launch_compact_flags(uint8_t* flag, int64_t G, int32_t* list, int32_t* count, cudaStream_t st) {
+    k_compact_flags<<<blocks_for(G), kThreads, 0, st>>>(flag, G, list, count);
+}
+
+void launch_lookup_slots(const int32_t* active, int64_t n, const int32_t* cur, const int32_t* slot_of,
+                         int32_t* uslot, cudaStream_t st) {
+    if (n <= 0) return;
+    k_lookup_slots<<<blocks_for(n), kThreads, 0, st>>>(active, n, cur, slot_of, uslot);
+}
+
+void launch_set_slots(const int32_t* q, const int32_t* s, int n, int32_t* slot_of, cudaStream_t st) {
+    if (n <= 0) return;
+    k_set_slots<<<blocks_for(n), kThreads, 0, st>>>(q, s, n, slot_of);
+}
+
+void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* centre,
+                   const double* Sc, int64_t G, int nfit, const double* A64, const double* Q64, int64_t ldq,
+                   int32_t* best, cudaStream_t st) {
+    if (n <= 0) return;
+    k_scan64<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, d, centre, Sc, G, nfit, A64, Q64, ldq, best);
+}
+
+void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_slots, int32_t* cnt,
+                  int32_t* tile_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* tile_slot, int32_t* tile_univ,
+                  int64_t max_tiles, cudaStream_t st) {
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n_slots, st);
+    cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)n_slots, st);
+    launch_fill_i32(tile_univ, max_tiles * kBM, -1, st);
+    if (n > 0) k_count_slots<<<blocks_for(n), kThreads, 0, st>>>(uslot, n, cnt);
+    k_tile_scan<<<1, 1024, 0, st>>>(cnt, n_slots, tile_base, n_tiles_dev);
+    k_tile_slots<<<blocks_for(n_slots), kThreads, 0, st>>>(cnt, tile_base, n_slots, tile_slot);
+    if (n > 0) k_scatter_tiles<<<blocks_for(n), kThreads, 0, st>>>(active, n, uslot, tile_base, fill, tile_univ);
+}
+
+void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
+                  const double* centre, int nfit, int K, const float* A32, const float* rho, uint16_t* Yt,
+                  float* alpha, cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    const size_t smem = (size_t)nfit * nfit * sizeof(float);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_yprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_yprep<<<(unsigned)n_tiles, kBM, (size_t)nfit * nfit * sizeof(float), st>>>(tile_slot, tile_univ, d, centre,
+                                                                                  nfit, K, A32, rho, Yt, alpha);
+}
+
+void launch_decide(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, int topk, const float* cv,
+                   const int32_t* ci, const float* alpha, const float* nrm, const float* Qc, const float* Qb,
+                   int64_t G_pad, const float* d, const double* centre, const double* Sfit, int nfit,
+                   const double* W64, int32_t* best, int32_t* fb, int32_t* n_fb, unsigned long long* counters,
+                   cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    k_decide<<<(unsigned)n_tiles, kBM, 0, st>>>(tile_slot, tile_univ, topk, cv, ci, alpha, nrm, Qc, Qb, G_pad, d,
+                                                centre, Sfit, nfit, W64, best, fb, n_fb, counters);
+}
+
+void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const int32_t* best, const int32_t* p_of,
+                   int U, const float* d, const double* Sfit, int nfit, const double* W64, double* dchi2,
+                   double* chi2min, cudaStream_t st) {
+    if (n <= 0) return;
+    k_finish<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, best, p_of, U, d, Sfit, nfit, W64, dchi2,
+                                                      chi2min);
+}
+
+void launch_advance(const int32_t* active, int64_t n, const int32_t* best, int32_t* cur, int8_t* nscan, int scan_no,
+                    int max_iter, int32_t* next_active, int32_t* n_next, int32_t* fin, int32_t* n_fin,
+                    cudaStream_t st) {
+    if (n <= 0) return;
+    k_advance<<<blocks_for(n), kThreads, 0, st>>>(active, n, best, cur, nscan, scan_no, max_iter, next_active, n_next,
+                                                  fin, n_fin);
+}
+
+void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st) {
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    const size_t smem = (size_t)p2 * sizeof(double);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_quantiles<<<rows, 512, smem, st>>>(x, n, p2, probs, nq, out);
+}
+
+}  // namespace fcdev

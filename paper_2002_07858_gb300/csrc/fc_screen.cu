@@ -1,0 +1,404 @@
+// fc_screen.cu -- tensor-core chi2 screen (§2 steps 3-4 over the whole grid).
+//
+// For a tile of BM = 128 universes that share one inverse covariance A and a
+// tile of BN = 256 grid points, the screen value
+//
+//     LB_{u,g} = qb_g + sum_k Y_{u,k} S_{g,k}
+//              ~ (q_g - 2 y_u . s~_g) - alpha_u |s~_g| - beta_g   <=  chi2_g - c_u
+//
+// is a lower bound of chi2_g(d_u) minus a per-universe constant, where
+// y_u = A (d_u - v), s~_g = s_g - v, q_g = s~_g^T A s~_g, c_u = (d_u - v)^T A (d_u - v)
+// (Eq. 1 expanded around the centre v).  Y = -2 y and s~ are split into BF16
+// hi + lo parts and multiplied as hi*hi + lo*hi + hi*lo on tcgen05 (kind::f16,
+// FP32 accumulation in TMEM); one spare K column carries -alpha_u x |s~_g|,
+// the error bound of that product.  The epilogue adds qb_g (q_g lowered by its
+// rounding bound) and keeps, per universe, the TOPK smallest (LB, g) pairs with
+// the lowest index first among equal values -- the strict "<" of Algorithm 1.
+// The U x G score matrix never leaves the SM.
+//
+// Roles (one CTA per SM, persistent over universe tiles):
+//   warp 0      bulk-async (TMA) copies: Y tile, then S~ tile + qb slice per stage
+//   warp 1      TMEM allocation; one lane issues tcgen05.mma and commits
+//   warps 2..5  epilogue: tcgen05.ld -> + qb -> running top-k; 128 rows
+// Every mbarrier wait is bounded (about 2 s of %globaltimer); on timeout the
+// kernel records kDevTimeout, waits for its own copies and MMAs, frees TMEM
+// and returns.
+#include <cuda_runtime.h>
+#include <float.h>
+
+#include <cstdint>
+
+#include "fc_internal.cuh"
+
+namespace fcdev {
+namespace {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+// Bounded wait on a phase parity; false on timeout or when another role aborted.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (abort_flag && *abort_flag) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand without swizzle: 8x8 core matrices of 16-byte rows; LBO steps
+// along K between the two core matrices of a K=16 slice, SBO steps 8 rows.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, M = BM, N = BN
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
+
+template <int K, int STAGES>
+struct ScreenSmem {
+    static constexpr uint32_t kYBytes = 2u * K * kBM * 2u;   // hi + lo, bf16
+    static constexpr uint32_t kBBytes = 2u * K * kBN * 2u;
+    static constexpr uint32_t kQBytes = kBN * 4u;
+    static constexpr uint32_t kAChunk = kBM * 16u;           // one 8-column slab of the A image
+    static constexpr uint32_t kBChunk = kBN * 16u;
+    static constexpr uint32_t kOffY = 0;
+    static constexpr uint32_t kOffB = 2 * kYBytes;
+    static constexpr uint32_t kOffQ = kOffB + STAGES * kBBytes;
+    static constexpr uint32_t kOffBar = kOffQ + STAGES * kQBytes;
+    static constexpr uint32_t kNumBars = 2 + 2 + STAGES + STAGES + 2 + 2 + 1;
+    static constexpr uint32_t kBytes = kOffBar + kNumBars * 8 + 16 + 1024;
+};
+
+template <int K, int TOPK, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const float* __restrict__ Qb,
+             const int32_t* __restrict__ tile_slot, int64_t n_tiles, int64_t G, int64_t G_pad,
+             float* __restrict__ cand_val, int32_t* __restrict__ cand_idx, int* __restrict__ status) {
+    using L = ScreenSmem<K, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_addr(smem);
+    uint64_t* bars = (uint64_t*)(smem + L::kOffBar);
+    uint32_t* tmem_holder = (uint32_t*)(smem + L::kOffBar + L::kNumBars * 8);
+    volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+    auto bar = [&](int i) { return smem_addr(&bars[i]); };
+    // barrier indices
+    const int Y_FULL = 0, Y_EMPTY = 2, B_FULL = 4, B_EMPTY = 4 + STAGES, T_FULL = 4 + 2 * STAGES,
+              T_EMPTY = 6 + 2 * STAGES, DONE = 8 + 2 * STAGES;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar(Y_FULL + i), 1);
+            mbar_init(bar(Y_EMPTY + i), 1);
+            mbar_init(bar(T_FULL + i), 1);
+            mbar_init(bar(T_EMPTY + i), 4);
+        }
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(bar(B_FULL + s), 1);
+            mbar_init(bar(B_EMPTY + s), 1 + 4);
+        }
+        mbar_init(bar(DONE), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(tmem_holder)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+    const int n_gt = (int)(G_pad / kBN);
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- producer
+        int y_par[2] = {-1, -1}, b_par[STAGES];
+        for (int s = 0; s < STAGES; ++s) b_par[s] = -1;
+        bool ok = true;
+        int it = 0;
+        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
+            const int yb = it & 1;
+            const uint32_t yph = (it >> 1) & 1;
+            if (!mbar_wait(bar(Y_EMPTY + yb), yph ^ 1, abort_flag)) { ok = false; break; }
+            mbar_expect_tx(bar(Y_FULL + yb), L::kYBytes);
+            bulk_g2s(sbase + L::kOffY + yb * L::kYBytes, Yt + item * (int64_t)(L::kYBytes / 2), L::kYBytes,
+                     bar(Y_FULL + yb));
+            y_par[yb] = (int)yph;
+            const float* qrow = Qb + (int64_t)tile_slot[item] * G_pad;
+            for (int j = 0; j < n_gt; ++j) {
+                const int64_t seq = (int64_t)it * n_gt + j;
+                const int s = (int)(seq % STAGES);
+                const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
+                if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag)) { ok = false; break; }
+                mbar_expect_tx(bar(B_FULL + s), L::kBBytes + L::kQBytes);
+                bulk_g2s(sbase + L::kOffB + s * L::kBBytes, Bt + (int64_t)j * (L::kBBytes / 2), L::kBBytes,
+                         bar(B_FULL + s));
+                bulk_g2s(sbase + L::kOffQ + s * L::kQBytes, qrow + (int64_t)j * kBN, L::kQBytes, bar(B_FULL + s));
+                b_par[s] = (int)ph;
+            }
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicOr(status, kDevTimeout);
+            // let every copy this thread issued land before the CTA can exit
+            for (int i = 0; i < 2; ++i)
+                if (y_par[i] >= 0) mbar_wait(bar(Y_FULL + i), (uint32_t)y_par[i], nullptr);
+            for (int s = 0; s < STAGES; ++s)
+                if (b_par[s] >= 0) mbar_wait(bar(B_FULL + s), (uint32_t)b_par[s], nullptr);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // --------------------------------------------------------------- MMA
+        bool ok = true;
+        int it = 0;
+        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
+            const int yb = it & 1;
+            if (!mbar_wait(bar(Y_FULL + yb), (it >> 1) & 1, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a0 = sbase + L::kOffY + yb * L::kYBytes;
+            for (int j = 0; j < n_gt; ++j) {
+                const int64_t seq = (int64_t)it * n_gt + j;
+                const int s = (int)(seq % STAGES);
+                const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
+                const int ab = (int)(seq & 1);
+                const uint32_t aph = (uint32_t)((seq >> 1) & 1);
+                if (!mbar_wait(bar(T_EMPTY + ab), aph ^ 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t b0 = sbase + L::kOffB + s * L::kBBytes;
+                const uint32_t d = tmem_base + (uint32_t)(ab * kBN);
+#pragma unroll
+                for (int kk = 0; kk < K / 16; ++kk) {
+                    const uint64_t a_hi = smem_desc(a0 + (2 * kk) * L::kAChunk, L::kAChunk, 128);
+                    const uint64_t a_lo = smem_desc(a0 + (K / 8 + 2 * kk) * L::kAChunk, L::kAChunk, 128);
+                    const uint64_t b_hi = smem_desc(b0 + (2 * kk) * L::kBChunk, L::kBChunk, 128);
+                    const uint64_t b_lo = smem_desc(b0 + (K / 8 + 2 * kk) * L::kBChunk, L::kBChunk, 128);
+                    mma_bf16(d, a_hi, b_hi, kk > 0 ? 1u : 0u);
+                    mma_bf16(d, a_lo, b_hi, 1u);
+                    mma_bf16(d, a_hi, b_lo, 1u);
+                }
+                mma_commit(bar(B_EMPTY + s));
+                mma_commit(bar(T_FULL + ab));
+            }
+            if (ok) mma_commit(bar(Y_EMPTY + yb));
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicOr(status, kDevTimeout);
+        }
+        // every MMA issued above has completed once DONE flips
+        mma_commit(bar(DONE));
+        mbar_wait(bar(DONE), 0, nullptr);
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------- epilogue
+        const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+        const int row = quad * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        bool ok = true;
+        int it = 0;
+        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
+            float vals[TOPK];
+            int32_t idx[TOPK];
+#pragma unroll
+            for (int t = 0; t < TOPK; ++t) {
+                vals[t] = FLT_MAX;
+                idx[t] = -1;
+            }
+            for (int j = 0; j < n_gt; ++j) {
+                const int64_t seq = (int64_t)it * n_gt + j;
+                const int s = (int)(seq % STAGES);
+                const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
+                const int ab = (int)(seq & 1);
+                const uint32_t aph = (uint32_t)((seq >> 1) & 1);
+                if (!mbar_wait(bar(T_FULL + ab), aph, abort_flag)) { ok = false; }
+                if (ok && !mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; }
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                tc_fence_after();
+                const float* qs = (const float*)(smem + L::kOffQ + s * L::kQBytes);
+                const int64_t gbase = (int64_t)j * kBN;
+#pragma unroll 1
+                for (int c0 = 0; c0 < kBN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tmem_base + lane_base + (uint32_t)(ab * kBN + c0), v);
+                    const float4* q4 = reinterpret_cast<const float4*>(qs + c0);
+                    float m = FLT_MAX;
+#pragma unroll
+                    for (int i4 = 0; i4 < 8; ++i4) {
+                        const float4 qq = q4[i4];
+                        v[4 * i4 + 0] += qq.x;
+                        v[4 * i4 + 1] += qq.y;
+                        v[4 * i4 + 2] += qq.z;
+                        v[4 * i4 + 3] += qq.w;
+                        m = fminf(m, fminf(fminf(v[4 * i4 + 0], v[4 * i4 + 1]), fminf(v[4 * i4 + 2], v[4 * i4 + 3])));
+                    }
+                    if (m < vals[TOPK - 1]) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float x = v[i];
+                            const int64_t g = gbase + c0 + i;
+                            if (x < vals[TOPK - 1] && g < G) {
+                                float cx = x;
+                                int32_t cg = (int32_t)g;
+#pragma unroll
+                                for (int t = 0; t < TOPK; ++t) {
+                                    const bool sw = cx < vals[t];
+                                    const float tv = vals[t];
+                                    const int32_t ti = idx[t];
+                                    vals[t] = sw ? cx : tv;
+                                    idx[t] = sw ? cg : ti;
+                                    cx = sw ? tv : cx;
+                                    cg = sw ? ti : cg;
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(bar(T_EMPTY + ab));
+                    mbar_arrive(bar(B_EMPTY + s));
+                }
+            }
+            if (!ok) break;
+            const int64_t orow = item * kBM + row;
+#pragma unroll
+            for (int t = 0; t < TOPK; ++t) {
+                cand_val[orow * TOPK + t] = vals[t];
+                cand_idx[orow * TOPK + t] = idx[t];
+            }
+        }
+        if (!ok && lane == 0) {
+            *abort_flag = 1;
+            atomicOr(status, kDevTimeout);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+template <int K, int TOPK, int STAGES>
+void run_screen(const uint16_t* Yt, const uint16_t* Bt, const float* Qb, const int32_t* tile_slot, int64_t n_tiles,
+                int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm, cudaStream_t st) {
+    using L = ScreenSmem<K, STAGES>;
+    static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
+    auto kern = k_screen<K, TOPK, STAGES>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
+    int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, 192, L::kBytes, st>>>(Yt, Bt, Qb, tile_slot, n_tiles, G, G_pad, cv, ci, status);
+}
+
+}  // namespace
+
+bool launch_screen(int K, int topk, const uint16_t* Yt, const uint16_t* Bt, const float* Qb, const int32_t* tile_slot,
+                   int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
+                   cudaStream_t st) {
+    if (n_tiles <= 0) return true;
+#define FC_SCREEN_CASE(KK, TT, SS)                                                                    \
+    if (K == KK && topk == TT) {                                                                      \
+        run_screen<KK, TT, SS>(Yt, Bt, Qb, tile_slot, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
+        return true;                                                                                  \
+    }
+    FC_SCREEN_CASE(16, 8, 4)
+    FC_SCREEN_CASE(32, 8, 4)
+    FC_SCREEN_CASE(48, 8, 3)
+    FC_SCREEN_CASE(64, 8, 2)
+    FC_SCREEN_CASE(16, 16, 4)
+    FC_SCREEN_CASE(32, 16, 4)
+    FC_SCREEN_CASE(48, 16, 3)
+    FC_SCREEN_CASE(64, 16, 2)
+#undef FC_SCREEN_CASE
+    return false;
+}
+
+}  // namespace fcdev

@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bars (per step of §2 / Algorithm 1):
+  fake data and the systematic Cholesky factor ....... bit for bit
+  plain binary64 path .................................. |ddchi2| <= 1e-9 max(|dchi2|, 1), same best fit
+  tensor-core screen + binary64 rescoring ............. |ddchi2| <= 1e-4, best fit identical except
+                                                         near-ties, 68/90/95% quantiles within rel 1e-3
+"""
+import numpy as np
+import pytest
+from scipy import spatial
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL_PLAIN = 1e-9
+TOL_MIXED = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import paper_2002_07858_gb300 as m
+
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(fc):
+    c = fc.fc_create(0)
+    yield c
+    fc.fc_destroy(c)
+
+
+_grids = {}
+
+
+def grid(fc, ctx, w):
+    key = (w.name, id(ctx))
+    if key not in _grids:
+        gid = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+        fc.fc_set_frac_cov(ctx, gid, w.F)
+        _grids[key] = gid
+    return _grids[key]
+
+
+@pytest.fixture(scope="module")
+def w1():
+    return workloads.cfg1()
+
+
+@pytest.fixture(scope="module")
+def w2():
+    return workloads.cfg2()
+
+
+def _cfg2_points(w2, n):
+    rng = np.random.default_rng(42)
+    return np.sort(rng.choice(w2.G, n, replace=False)).astype(np.int64)
+
+
+# ------------------------------------------------------------------ a2 / a3 --
+
+@pytest.mark.parametrize("which,p", [("cfg1", 312), ("cfg1", 0), ("cfg2", 1234), ("cfg2", 9999)])
+def test_systematic_cholesky_bit_exact(fc, ctx, w1, w2, which, p):
+    w = w1 if which == "cfg1" else w2
+    gid = grid(fc, ctx, w)
+    _, L = fc.fc_covariance(ctx, gid, p, w.n_fit, w.n_full, want_A=False)
+    np.testing.assert_array_equal(L, oracle.chol_sys(w.S[p], w.F))
+
+
+@pytest.mark.parametrize("which,q", [("cfg1", 312), ("cfg1", 624), ("cfg2", 5000), ("cfg2", 17)])
+def test_inverse_covariance(fc, ctx, w1, w2, which, q):
+    w = w1 if which == "cfg1" else w2
+    gid = grid(fc, ctx, w)
+    A, _ = fc.fc_covariance(ctx, gid, q, w.n_fit, w.n_full, want_L=False)
+    ref = oracle.inv_cov(w.S[q], w.F, w.collapse, w.n_fit)
+    assert np.max(np.abs(A - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_fake_data_bit_exact_cfg1(fc, ctx, w1):
+    gid = grid(fc, ctx, w1)
+    got = fc.fc_fake_data(ctx, gid, w1.points, w1.seed, 1000, w1.n_fit)
+    ref = oracle.fake_data(w1.S, w1.F, w1.points, w1.seed, 1000)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_fake_data_bit_exact_cfg2(fc, ctx, w2):
+    gid = grid(fc, ctx, w2)
+    pts = _cfg2_points(w2, 64)
+    got = fc.fc_fake_data(ctx, gid, pts, 7, 1000, w2.n_fit)
+    ref = oracle.fake_data(w2.S, w2.F, pts, 7, 1000, collapse=w2.collapse, n_fit=w2.n_fit)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_fake_data_bit_exact_gauss_and_seed(fc, ctx, w1):
+    gid = grid(fc, ctx, w1)
+    for seed in (0, 1, 0xDEADBEEFCAFE):
+        got = fc.fc_fake_data(ctx, gid, np.array([3, 312, 600]), seed, 300, w1.n_fit, fluct=fc.FC_FLUCT_GAUSS)
+        ref = oracle.fake_data(w1.S, w1.F, [3, 312, 600], seed, 300, fluct=oracle.FLUCT_GAUSS)
+        np.testing.assert_array_equal(got, ref)
+
+
+# -------------------------------------------------------------- full path ---
+
+def _compare(d, b, n, od, ob, on, tol, exact_index):
+    err = np.abs(d - od) / np.maximum(np.abs(od), 1.0)
+    assert np.all(np.isfinite(d))
+    assert err.max() <= tol, f"max rel err {err.max():.3e}"
+    mism = (b != ob)
+    if exact_index:
+        assert not mism.any(), f"{mism.sum()} best-fit mismatches"
+        np.testing.assert_array_equal(n, on)
+    return mism.mean()
+
+
+def test_plain_fp64_cfg1(fc, ctx, w1):
+    gid = grid(fc, ctx, w1)
+    d, b, n = fc.fc_run_points(ctx, gid, w1.points, w1.seed, w1.U, opts=dict(precision=fc.FC_PREC_FP64))
+    od, ob, on = oracle.run_workload(w1)
+    _compare(d, b, n, od, ob, on, TOL_PLAIN, exact_index=True)
+
+
+def test_mixed_cfg1(fc, ctx, w1):
+    gid = grid(fc, ctx, w1)
+    d, b, n = fc.fc_run_points(ctx, gid, w1.points, w1.seed, w1.U, opts=dict(precision=fc.FC_PREC_MIXED))
+    st = fc.fc_get_stats(ctx)
+    od, ob, on = oracle.run_workload(w1)
+    frac = _compare(d, b, n, od, ob, on, TOL_MIXED, exact_index=False)
+    assert frac < 0.01
+    q = np.array([0.68, 0.90, 0.95])
+    qg, qo = np.quantile(d[0], q), np.quantile(od[0], q)
+    assert np.all(np.abs(qg - qo) <= 1e-3 * np.abs(qo))
+    assert st["screened"] + st["rescored"] + st["fallback"] == st["scans"]
+
+
+@pytest.mark.parametrize("topk", [8, 16])
+def test_mixed_cfg2_subset(fc, ctx, w2, topk):
+    gid = grid(fc, ctx, w2)
+    pts = _cfg2_points(w2, 8)
+    U = 250
+    d, b, n = fc.fc_run_points(ctx, gid, pts, 11, U, opts=dict(precision=fc.FC_PREC_MIXED, top_k=topk))
+    st = fc.fc_get_stats(ctx)
+    od, ob, on = oracle.run_points(w2.S, w2.F, pts, 11, U, collapse=w2.collapse, n_fit=w2.n_fit)
+    frac = _compare(d, b, n, od, ob, on, TOL_MIXED, exact_index=False)
+    assert frac < 0.02
+    q = np.array([0.68, 0.90, 0.95])
+    qg, qo = np.quantile(d, q, axis=1), np.quantile(od, q, axis=1)
+    assert np.all(np.abs(qg - qo) <= 1e-3 * np.maximum(np.abs(qo), 1e-3))
+    print("cfg2 subset stats", st)
+
+
+def test_plain_fp64_cfg2_subset(fc, ctx, w2):
+    gid = grid(fc, ctx, w2)
+    pts = _cfg2_points(w2, 3)
+    d, b, n = fc.fc_run_points(ctx, gid, pts, 5, 100, opts=dict(precision=fc.FC_PREC_FP64))
+    od, ob, on = oracle.run_points(w2.S, w2.F, pts, 5, 100, collapse=w2.collapse, n_fit=w2.n_fit)
+    _compare(d, b, n, od, ob, on, TOL_PLAIN, exact_index=True)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_identity_covariance_nearest_neighbour(fc, ctx, w1, prec):
+    gid = grid(fc, ctx, w1)
+    d, b, n = fc.fc_run_points(ctx, gid, w1.points, 3, 400, opts=dict(precision=prec, cov=fc.FC_COV_IDENTITY))
+    od, ob, on, fk = oracle.run_workload(w1, U=400, cov=oracle.COV_IDENTITY, want_fake=True)
+    _compare(d, b, n, od, ob, on, TOL_PLAIN if prec == 0 else TOL_MIXED, exact_index=(prec == 0))
+    dist, idx = spatial.cKDTree(w1.S).query(fk[0].astype(np.float64), k=2)
+    clear = dist[:, 1] ** 2 - dist[:, 0] ** 2 > 1e-3
+    np.testing.assert_array_equal(b[0][clear], idx[clear, 0])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fixed_covariance(fc, ctx, w1, prec):
+    gid = grid(fc, ctx, w1)
+    d, b, n = fc.fc_run_points(ctx, gid, w1.points, 9, 500, opts=dict(precision=prec, cov=fc.FC_COV_FIXED))
+    od, ob, on = oracle.run_workload(w1, U=500, cov=oracle.COV_FIXED)
+    _compare(d, b, n, od, ob, on, TOL_PLAIN if prec == 0 else TOL_MIXED, exact_index=(prec == 0))
+    assert np.all(n == 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_scan_entry(fc, ctx, w1, prec):
+    gid = grid(fc, ctx, w1)
+    rng = np.random.default_rng(5)
+    fk = oracle.fake_data(w1.S, w1.F, [312], 21, 300)[0]
+    qcov = rng.integers(0, w1.G, 300)
+    best, chi2 = fc.fc_scan(ctx, gid, fk, qcov, precision=prec)
+    for u in range(0, 300, 7):
+        A = oracle.inv_cov(w1.S[qcov[u]], w1.F)
+        c = oracle.scan(w1.S, A, fk[u].astype(np.float64))
+        assert abs(chi2[u] - c.min()) <= 1e-9 * max(1.0, c.min())
+        if prec == 0:
+            assert best[u] == int(np.argmin(c))
+        else:
+            assert c[best[u]] - c.min() < TOL_MIXED
+
+
+def test_batch_composition_invariance(fc, ctx, w2):
+    gid = grid(fc, ctx, w2)
+    pts = _cfg2_points(w2, 5)
+    d_all, b_all, _ = fc.fc_run_points(ctx, gid, pts, 17, 200)
+    d_one, b_one, _ = fc.fc_run_points(ctx, gid, pts[3:4], 17, 200)
+    d_rev, _, _ = fc.fc_run_points(ctx, gid, pts[::-1].copy(), 17, 200)
+    np.testing.assert_array_equal(d_all[3], d_one[0])
+    np.testing.assert_array_equal(b_all[3], b_one[0])
+    np.testing.assert_array_equal(d_all[::-1], d_rev)
+
+
+def test_ragged_universe_count(fc, ctx, w1):
+    gid = grid(fc, ctx, w1)
+    d, b, n = fc.fc_run_points(ctx, gid, np.array([312, 5]), 1, 77)
+    od, ob, on = oracle.run_points(w1.S, w1.F, [312, 5], 1, 77)
+    _compare(d, b, n, od, ob, on, TOL_MIXED, exact_index=False)
+
+
+def test_quantiles(fc, ctx):
+    rng = np.random.default_rng(0)
+    x = rng.chisquare(2, (7, 1000))
+    p = np.array([0.0, 0.5, 0.68, 0.9, 0.95, 1.0])
+    np.testing.assert_allclose(fc.fc_quantiles(ctx, x, p), np.quantile(x, p, axis=1).T, rtol=1e-14)
+
+
+def test_empty_and_errors(fc, ctx, w1):
+    gid = grid(fc, ctx, w1)
+    d, b, n = fc.fc_run_points(ctx, gid, np.array([312]), 0, 0)
+    assert d.size == 0
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_run_points(ctx, 12345, np.array([1]), 0, 10)
+    assert e.value.status == fc.FC_ERR_NOT_FOUND
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_run_points(ctx, gid, np.array([w1.G]), 0, 10)
+    assert e.value.status == fc.FC_ERR_ARG
+    g2 = fc.fc_load_grid(ctx, w1.S)
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_run_points(ctx, g2, np.array([1]), 0, 10)
+    assert e.value.status == fc.FC_ERR_STATE
+    fc.fc_unload_grid(ctx, g2)
+    bad = w1.S.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_load_grid(ctx, bad)
+    assert e.value.status == fc.FC_ERR_ARG
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_run_points(ctx, gid, np.array([1]), 0, 10, opts=dict(max_iter=0))
+    assert e.value.status == fc.FC_ERR_ARG
+
+
+def test_serving_matches_synchronous(fc, ctx, w1, w2):
+    g1, g2 = grid(fc, ctx, w1), grid(fc, ctx, w2)
+    pts2 = _cfg2_points(w2, 3)
+    ref1 = fc.fc_run_points(ctx, g1, w1.points, 4, 300)[0]
+    ref2 = fc.fc_run_points(ctx, g2, pts2, 4, 150)[0]
+    jobs = []
+    for _ in range(3):
+        jobs.append((fc.fc_submit(ctx, g1, w1.points, 4, 300), ref1))
+        jobs.append((fc.fc_submit(ctx, g2, pts2, 4, 150), ref2))
+    import time
+    pending = list(jobs)
+    t0 = time.time()
+    while pending and time.time() - t0 < 120:
+        keep = []
+        for (t, outs), ref in pending:
+            st, lat = fc.fc_poll(ctx, t)
+            if st == fc.FC_PENDING:
+                keep.append(((t, outs), ref))
+            else:
+                np.testing.assert_array_equal(outs[0], ref)
+                assert lat > 0
+        pending = keep
+        time.sleep(0.01)
+    assert not pending
