@@ -74,16 +74,21 @@ typedef struct {
     int32_t cov;        /* FC_COV_*   (default FC_COV_ITERATE)                       */
 } fc_opts;
 
-/* Per-context counters of the last fc_run_points call (and totals). */
+/* Counters and stage timings of the last synchronous call on a context.
+ * Stage times are CUDA-event intervals on the context stream around each
+ * stage's kernels, summed over scans (milliseconds). */
 typedef struct {
-    int64_t universes;        /* universes fitted                                   */
-    int64_t scans;            /* universe-scans performed (sum of nscans)           */
-    int64_t chi2_evals;       /* universes x G per scan actually performed          */
-    int64_t distinct_cov;     /* covariances built and inverted                     */
-    int64_t screened;         /* universe-scans decided by the tensor-core screen   */
-    int64_t rescored;         /* universe-scans that needed binary64 rescoring      */
+    int64_t universes;        /* universes fitted                                     */
+    int64_t scans;            /* universe-scans performed (sum of nscans)             */
+    int64_t chi2_evals;       /* universe-scans x G: chi2 values the scans decided on */
+    int64_t distinct_cov;     /* covariances built and inverted                       */
+    int64_t screened;         /* universe-scans decided by the tensor-core screen     */
+    int64_t rescored;         /* universe-scans that needed binary64 rescoring        */
     int64_t fallback;         /* universe-scans whose certificate failed -> fp64 scan */
-    double  ms_fake, ms_cov, ms_screen, ms_rescore, ms_total;  /* stage times       */
+    int64_t kernel_launches;  /* CUDA kernels launched by the call                    */
+    int64_t screen_launches;  /* launches of the tensor-core screen kernel             */
+    double  screen_flops;     /* algorithmic flops of those launches: 2 N_fit per eval */
+    double  ms_fake, ms_cov, ms_prep, ms_screen, ms_rescore, ms_fallback, ms_scan64, ms_finish, ms_total;
 } fc_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -265,8 +265,8 @@ def run_points(S, F, points, seed: int, U: int, collapse=None, n_fit=None, max_i
     return dchi2, best, ns
 
 
-def run_workload(w, U: int | None = None, points=None, nthreads: int | None = None, **kw):
+def run_workload(w, U: int | None = None, points=None, nthreads: int | None = None, seed: int | None = None, **kw):
     """Convenience: oracle.run_points on a workloads.Workload."""
     pts = w.points if points is None else points
-    return run_points(w.S, w.F, pts, w.seed, w.U if U is None else U, collapse=w.collapse, n_fit=w.n_fit,
-                      max_iter=w.max_iter, nthreads=nthreads, **kw)
+    return run_points(w.S, w.F, pts, w.seed if seed is None else seed, w.U if U is None else U,
+                      collapse=w.collapse, n_fit=w.n_fit, max_iter=w.max_iter, nthreads=nthreads, **kw)

@@ -31,6 +31,8 @@
 
 using namespace fcdev;
 
+std::atomic<long long> fcdev::g_launches{0};
+
 namespace {
 
 thread_local std::string t_last_error;
@@ -119,6 +121,7 @@ struct fc_ctx {
     std::map<std::string, Scratch> scratch;
     int* status_dev = nullptr;
     unsigned long long* counters_dev = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // stage timers
     fc_stats stats{};
     std::mutex api_mu;  // serialises device work of this context
     // serving
@@ -217,6 +220,18 @@ fc_status check_status(fc_ctx* c) {
         if (st & kDevNotSpd) return fail(FC_ERR_NOT_SPD, "covariance matrix is not positive definite");
         return fail(FC_ERR_CUDA, "device reported error flags " + std::to_string(st));
     }
+    return FC_OK;
+}
+
+// Stage timing: an event pair on the context stream around a stage's kernels.
+void stage_begin(fc_ctx* c) { cudaEventRecord(c->ev_a, c->stream); }
+
+fc_status stage_end(fc_ctx* c, double* acc_ms) {
+    cudaEventRecord(c->ev_b, c->stream);
+    FC_TRY(sync(c));
+    float ms = 0.0f;
+    FC_CUDA(cudaEventElapsedTime(&ms, c->ev_a, c->ev_b));
+    *acc_ms += ms;
     return FC_OK;
 }
 
@@ -425,6 +440,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
     for (int scan_no = 1; scan_no <= max_iter && n_active > 0; ++scan_no) {
         // ---- covariances for this scan
         std::vector<int32_t> qs, slots;
+        stage_begin(c);
         if (o.cov == FC_COV_IDENTITY) {
             FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, &slots));
             launch_fill_i32(uslot, n_active, slots[0], c->stream);
@@ -433,12 +449,15 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, nullptr));
             launch_lookup_slots(active, n_active, cur, g->slot_of, uslot, c->stream);
         }
+        FC_TRY(stage_end(c, &c->stats.ms_cov));
         c->stats.chi2_evals += n_active * g->G;
         c->stats.scans += n_active;
         // ---- scan: best32[u] for every active universe
         if (!mixed) {
+            stage_begin(c);
             launch_scan64(active, n_active, uslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
                           c->stream);
+            FC_TRY(stage_end(c, &c->stats.ms_scan64));
         } else {
             const int64_t n_slots = g->n_slots;
             const int64_t max_tiles = n_active / kBM + std::min<int64_t>(n_slots, n_active) + 1;
@@ -457,18 +476,26 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_TRY(scratch(c, "cval", (size_t)max_tiles * kBM * topk, &cval));
             FC_TRY(scratch(c, "cidx", (size_t)max_tiles * kBM * topk, &cidx));
             FC_TRY(scratch(c, "fb", (size_t)n_active, &fb));
+            stage_begin(c);
             launch_group(active, n_active, uslot, (int)n_slots, tcnt, tbase, tfill, cnts, tslot, tuniv, max_tiles,
                          c->stream);
             int32_t n_tiles = 0;
             FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts, 4, cudaMemcpyDeviceToHost, c->stream));
             FC_TRY(sync(c));
             launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, Yt, alpha, c->stream);
+            FC_TRY(stage_end(c, &c->stats.ms_prep));
+            stage_begin(c);
             if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb, tslot, n_tiles, g->G, g->G_pad, cval, cidx,
                                c->status_dev, c->n_sm, c->stream))
                 return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
+            FC_TRY(stage_end(c, &c->stats.ms_screen));
+            c->stats.screen_launches += 1;
+            c->stats.screen_flops += 2.0 * g->nfit * (double)n_active * (double)g->G;
+            stage_begin(c);
             FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
             launch_decide(tslot, tuniv, n_tiles, topk, cval, cidx, alpha, g->nrm, g->Qc, g->Qb, g->G_pad, d,
                           g->centre, g->S_fit, g->nfit, g->W64, best32, fb, cnts + 1, c->counters_dev, c->stream);
+            FC_TRY(stage_end(c, &c->stats.ms_rescore));
             FC_TRY(check_status(c));
             int32_t n_fb = 0;
             FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -481,7 +508,8 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 } else {
                     int32_t* fcur = nullptr;
                     FC_TRY(scratch(c, "fcur", (size_t)n_fb, &fcur));
-                    k_gather_cur<<<nb(n_fb), 256, 0, c->stream>>>(fb, n_fb, cur, fcur);
+                    count_launch();
+    k_gather_cur<<<nb(n_fb), 256, 0, c->stream>>>(fb, n_fb, cur, fcur);
                     fq.resize(n_fb);
                     FC_CUDA(cudaMemcpyAsync(fq.data(), fcur, (size_t)n_fb * 4, cudaMemcpyDeviceToHost, c->stream));
                     FC_TRY(sync(c));
@@ -495,8 +523,10 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                     launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
                 else
                     launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
+                stage_begin(c);
                 launch_scan64(fb, n_fb, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
                               c->stream);
+                FC_TRY(stage_end(c, &c->stats.ms_fallback));
             }
         }
         // ---- advance: converged or exhausted universes finish under this scan's A
@@ -513,8 +543,10 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 launch_fill_i32(fslot, hc[1], g->ident_slot, c->stream);
             else
                 launch_lookup_slots(fin, hc[1], cur, g->slot_of, fslot, c->stream);
+            stage_begin(c);
             launch_finish(fin, hc[1], fslot, best32, p_of, U, d, g->S_fit, g->nfit, g->W64, dchi2, chi2min,
                           c->stream);
+            FC_TRY(stage_end(c, &c->stats.ms_finish));
         }
         std::swap(active, next);
         std::swap(c->scratch["active"], c->scratch["next"]);
@@ -555,6 +587,7 @@ fc_status run_points_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t
     for (int64_t p : hps)
         if (p < 0 || p >= g->G) return fail(FC_ERR_ARG, "true point index out of range");
     c->stats = fc_stats{};
+    const long long launches0 = g_launches.load();
     cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -601,7 +634,9 @@ fc_status run_points_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t
     } else {
         FC_TRY(scratch(c, "dchi2", (size_t)n, &dchi2_dev));
     }
+    count_launch();
     k_init_cur<<<nb(n), 256, 0, c->stream>>>(ps_dev, n, U, cur);
+    count_launch();
     k_ps32<<<nb(P), 256, 0, c->stream>>>(ps_dev, P, p_of);
     FC_TRY(scan_loop(c, g, n, U, o, d, cur, p_of, best32, ns, dchi2_dev, chi2min));
     if (!dev_out) FC_TRY(copy_out(c, dchi2, dchi2_dev, (size_t)n * 8));
@@ -612,7 +647,8 @@ fc_status run_points_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t
         } else {
             FC_TRY(scratch(c, "best64", (size_t)n, &b64));
         }
-        k_widen<<<nb(n), 256, 0, c->stream>>>(best32, n, b64);
+        count_launch();
+    k_widen<<<nb(n), 256, 0, c->stream>>>(best32, n, b64);
         if (b64 != bestfit) FC_TRY(copy_out(c, bestfit, b64, (size_t)n * 8));
     }
     if (nscans) FC_TRY(copy_out(c, nscans, ns, (size_t)n));
@@ -624,6 +660,7 @@ fc_status run_points_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t
     c->stats.ms_fake = t_fake;
     c->stats.ms_total = t_all;
     c->stats.universes = n;
+    c->stats.kernel_launches = g_launches.load() - launches0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
@@ -711,6 +748,8 @@ fc_status fc_create(fc_ctx** out, int device, size_t hbm_budget_bytes, void* cud
         FC_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
+    FC_CUDA(cudaEventCreate(&c->ev_a));
+    FC_CUDA(cudaEventCreate(&c->ev_b));
     FC_TRY(dalloc_t(c.get(), &c->status_dev, 1));
     FC_TRY(dalloc_t(c.get(), &c->counters_dev, 4));
     FC_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream));
@@ -732,6 +771,8 @@ fc_status fc_destroy(fc_ctx* c) {
     for (auto& kv : c->allocs) cudaFree(kv.first);
     c->allocs.clear();
     if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->ev_a) cudaEventDestroy(c->ev_a);
+    if (c->ev_b) cudaEventDestroy(c->ev_b);
     delete c;
     return FC_OK;
 }
@@ -835,7 +876,15 @@ fc_status fc_set_frac_cov(fc_ctx* c, int32_t grid_id, const double* F, int32_t n
             if (std::fabs(a - b) > 1e-12 * (std::fabs(a) + std::fabs(b)) + 1e-300)
                 return fail(FC_ERR_ARG, "F must be symmetric");
         }
-    free_cache(c, g);
+    // a new F invalidates every cached covariance; keep the storage
+    if (g->cap) {
+        g->n_slots = 0;
+        g->ident_slot = -1;
+        std::fill(g->slot_host.begin(), g->slot_host.end(), -1);
+        std::fill(g->q32_ready.begin(), g->q32_ready.end(), 0);
+        std::fill(g->q64_ready.begin(), g->q64_ready.end(), 0);
+        launch_fill_i32(g->slot_of, g->G, -1, c->stream);
+    }
     if (!g->F) FC_TRY(dalloc_t(c, &g->F, (size_t)nf * nf));
     FC_CUDA(cudaMemcpyAsync(g->F, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
     FC_TRY(sync(c));
@@ -956,13 +1005,16 @@ fc_status fc_scan(fc_ctx* c, int32_t grid_id, const float* d, const int64_t* q_c
     FC_TRY(copy_in(c, dd, d, (size_t)U * g->nfit * 4));
     FC_CUDA(cudaMemcpyAsync(q64, hq.data(), (size_t)U * 8, cudaMemcpyHostToDevice, c->stream));
     // every universe is its own "point" block (U = 1): p_of = its covariance index
+    count_launch();
     k_init_cur<<<nb(U), 256, 0, c->stream>>>(q64, U, 1, cur);
     int32_t* p_of = nullptr;
     FC_TRY(scratch(c, "scan_pof", (size_t)U, &p_of));
+    count_launch();
     k_ps32<<<nb(U), 256, 0, c->stream>>>(q64, U, p_of);
     FC_TRY(scan_loop(c, g, U, 1, o, dd, cur, p_of, best32, ns, dchi2, cm));
     int64_t* b64 = nullptr;
     FC_TRY(scratch(c, "best64", (size_t)U, &b64));
+    count_launch();
     k_widen<<<nb(U), 256, 0, c->stream>>>(best32, U, b64);
     FC_TRY(copy_out(c, best, b64, (size_t)U * 8));
     if (chi2_min) FC_TRY(copy_out(c, chi2_min, cm, (size_t)U * 8));

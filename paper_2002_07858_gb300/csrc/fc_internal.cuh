@@ -2,9 +2,14 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 namespace fcdev {
+
+// Number of kernels this library has launched (for the launch count of a run).
+extern std::atomic<long long> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Screen tile shape: BM universes (TMEM lanes) x BN grid points (TMEM columns).
 constexpr int kBM = 128;

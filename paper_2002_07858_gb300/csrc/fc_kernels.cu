@@ -841,22 +841,26 @@ __global__ void k_quantiles(const double* __restrict__ x, int n, int npow2, cons
 
 void launch_collapse(const double* S, int64_t G, int nf, const int32_t* coll, int nfit, double* out,
                      cudaStream_t st) {
+    count_launch();
     k_collapse<<<blocks_for(G, 128), 128, 0, st>>>(S, G, nf, coll, nfit, out);
 }
 
 void launch_centre(const double* S_fit, int64_t G, int nfit, double* centre, double*, cudaStream_t st) {
+    count_launch();
     k_centre<<<nfit, kThreads, 0, st>>>(S_fit, G, nfit, centre);
 }
 
 void launch_centred(const double* S_fit, const double* centre, int64_t G, int64_t G_pad, int nfit, int K,
                     double* Sc, float* Sc32, float* nrm, uint16_t* Bt, cudaStream_t st) {
     cudaMemsetAsync(Bt, 0, (size_t)G_pad * 2 * K * sizeof(uint16_t), st);
+    count_launch();
     k_centred<<<blocks_for(G, 128), 128, 0, st>>>(S_fit, centre, G, nfit, K, Sc, Sc32, nrm, Bt);
 }
 
 void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps, int P, int gauss, double* L64,
                      float* L32, float* s32, double*, int* status, cudaStream_t st) {
     if (P <= 0) return;
+    count_launch();
     k_chol_sys<<<P, 256, 0, st>>>(S, nf, F, ps, gauss, L64, L32, s32, status);
 }
 
@@ -864,6 +868,7 @@ void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, co
                       const int32_t* slot_list, int n, int cov_mode, double* A64, double* W64, float* A32,
                       float* rho, double* work, int* status, cudaStream_t st) {
     if (n <= 0) return;
+    count_launch();
     k_build_cov<<<n, 256, 0, st>>>(S, nf, nfit, coll, F, q_list, slot_list, cov_mode, A64, W64, A32, rho, work,
                                    status);
 }
@@ -872,6 +877,7 @@ void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, con
                    int64_t ldq, double* Q64, cudaStream_t st) {
     if (n <= 0) return;
     dim3 grid(blocks_for(G, 128) < 64 ? blocks_for(G, 128) : 64, n);
+    count_launch();
     k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, A64, slots, ldq, Q64);
 }
 
@@ -881,6 +887,7 @@ void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad
     unsigned gx = blocks_for(G_pad, 128);
     if (gx > 128) gx = 128;
     dim3 grid(gx, n);
+    count_launch();
     if (nfit <= 16)
         k_qvec32<16><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
     else if (nfit <= 32)
@@ -897,6 +904,7 @@ void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t*
                       int P, int U, uint64_t seed, int gauss, float* d, cudaStream_t st) {
     if (P <= 0 || U <= 0) return;
     dim3 grid((U + 127) / 128, P);
+    count_launch();
     k_fake_data<<<grid, 128, 0, st>>>(L32, s32, nf, coll, nfit, ps, U, (uint32_t)seed, (uint32_t)(seed >> 32),
                                        gauss, d);
 }
@@ -905,6 +913,7 @@ void launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t st) {
     if (n <= 0) return;
     unsigned b = blocks_for(n);
     if (b > 4096) b = 4096;
+    count_launch();
     k_fill_i32<<<b, kThreads, 0, st>>>(p, n, v);
 }
 
@@ -912,26 +921,31 @@ void launch_iota_i32(int32_t* p, int64_t n, cudaStream_t st) {
     if (n <= 0) return;
     unsigned b = blocks_for(n);
     if (b > 4096) b = 4096;
+    count_launch();
     k_iota_i32<<<b, kThreads, 0, st>>>(p, n);
 }
 
 void launch_mark_used(const int32_t* active, int64_t n, const int32_t* cur, uint8_t* flag, cudaStream_t st) {
     if (n <= 0) return;
+    count_launch();
     k_mark_used<<<blocks_for(n), kThreads, 0, st>>>(active, n, cur, flag);
 }
 
 void launch_compact_flags(uint8_t* flag, int64_t G, int32_t* list, int32_t* count, cudaStream_t st) {
+    count_launch();
     k_compact_flags<<<blocks_for(G), kThreads, 0, st>>>(flag, G, list, count);
 }
 
 void launch_lookup_slots(const int32_t* active, int64_t n, const int32_t* cur, const int32_t* slot_of,
                          int32_t* uslot, cudaStream_t st) {
     if (n <= 0) return;
+    count_launch();
     k_lookup_slots<<<blocks_for(n), kThreads, 0, st>>>(active, n, cur, slot_of, uslot);
 }
 
 void launch_set_slots(const int32_t* q, const int32_t* s, int n, int32_t* slot_of, cudaStream_t st) {
     if (n <= 0) return;
+    count_launch();
     k_set_slots<<<blocks_for(n), kThreads, 0, st>>>(q, s, n, slot_of);
 }
 
@@ -939,6 +953,7 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const f
                    const double* Sc, int64_t G, int nfit, const double* A64, const double* Q64, int64_t ldq,
                    int32_t* best, cudaStream_t st) {
     if (n <= 0) return;
+    count_launch();
     k_scan64<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, d, centre, Sc, G, nfit, A64, Q64, ldq, best);
 }
 
@@ -948,10 +963,18 @@ void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_
     cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n_slots, st);
     cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)n_slots, st);
     launch_fill_i32(tile_univ, max_tiles * kBM, -1, st);
-    if (n > 0) k_count_slots<<<blocks_for(n), kThreads, 0, st>>>(uslot, n, cnt);
+    if (n > 0) {
+        count_launch();
+        k_count_slots<<<blocks_for(n), kThreads, 0, st>>>(uslot, n, cnt);
+    }
+    count_launch();
     k_tile_scan<<<1, 1024, 0, st>>>(cnt, n_slots, tile_base, n_tiles_dev);
+    count_launch();
     k_tile_slots<<<blocks_for(n_slots), kThreads, 0, st>>>(cnt, tile_base, n_slots, tile_slot);
-    if (n > 0) k_scatter_tiles<<<blocks_for(n), kThreads, 0, st>>>(active, n, uslot, tile_base, fill, tile_univ);
+    if (n > 0) {
+        count_launch();
+        k_scatter_tiles<<<blocks_for(n), kThreads, 0, st>>>(active, n, uslot, tile_base, fill, tile_univ);
+    }
 }
 
 void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
@@ -960,6 +983,7 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
     if (n_tiles <= 0) return;
     const size_t smem = (size_t)nfit * nfit * sizeof(float);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_yprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
     k_yprep<<<(unsigned)n_tiles, kBM, (size_t)nfit * nfit * sizeof(float), st>>>(tile_slot, tile_univ, d, centre,
                                                                                   nfit, K, A32, rho, Yt, alpha);
 }
@@ -970,6 +994,7 @@ void launch_decide(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n
                    const double* W64, int32_t* best, int32_t* fb, int32_t* n_fb, unsigned long long* counters,
                    cudaStream_t st) {
     if (n_tiles <= 0) return;
+    count_launch();
     k_decide<<<(unsigned)n_tiles, kBM, 0, st>>>(tile_slot, tile_univ, topk, cv, ci, alpha, nrm, Qc, Qb, G_pad, d,
                                                 centre, Sfit, nfit, W64, best, fb, n_fb, counters);
 }
@@ -978,6 +1003,7 @@ void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const i
                    int U, const float* d, const double* Sfit, int nfit, const double* W64, double* dchi2,
                    double* chi2min, cudaStream_t st) {
     if (n <= 0) return;
+    count_launch();
     k_finish<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, best, p_of, U, d, Sfit, nfit, W64, dchi2,
                                                       chi2min);
 }
@@ -986,6 +1012,7 @@ void launch_advance(const int32_t* active, int64_t n, const int32_t* best, int32
                     int max_iter, int32_t* next_active, int32_t* n_next, int32_t* fin, int32_t* n_fin,
                     cudaStream_t st) {
     if (n <= 0) return;
+    count_launch();
     k_advance<<<blocks_for(n), kThreads, 0, st>>>(active, n, best, cur, nscan, scan_no, max_iter, next_active, n_next,
                                                   fin, n_fin);
 }
@@ -995,6 +1022,7 @@ void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, d
     while (p2 < n) p2 <<= 1;
     const size_t smem = (size_t)p2 * sizeof(double);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_quantiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
     k_quantiles<<<rows, 512, smem, st>>>(x, n, p2, probs, nq, out);
 }
 

@@ -375,6 +375,7 @@ void run_screen(const uint16_t* Yt, const uint16_t* Bt, const float* Qb, const i
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
+    count_launch();
     kern<<<(unsigned)grid, 192, L::kBytes, st>>>(Yt, Bt, Qb, tile_slot, n_tiles, G, G_pad, cv, ci, status);
 }
 

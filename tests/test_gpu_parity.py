@@ -164,7 +164,7 @@ def test_plain_fp64_cfg2_subset(fc, ctx, w2):
 def test_identity_covariance_nearest_neighbour(fc, ctx, w1, prec):
     gid = grid(fc, ctx, w1)
     d, b, n = fc.fc_run_points(ctx, gid, w1.points, 3, 400, opts=dict(precision=prec, cov=fc.FC_COV_IDENTITY))
-    od, ob, on, fk = oracle.run_workload(w1, U=400, cov=oracle.COV_IDENTITY, want_fake=True)
+    od, ob, on, fk = oracle.run_workload(w1, U=400, seed=3, cov=oracle.COV_IDENTITY, want_fake=True)
     _compare(d, b, n, od, ob, on, TOL_PLAIN if prec == 0 else TOL_MIXED, exact_index=(prec == 0))
     dist, idx = spatial.cKDTree(w1.S).query(fk[0].astype(np.float64), k=2)
     clear = dist[:, 1] ** 2 - dist[:, 0] ** 2 > 1e-3
@@ -175,7 +175,7 @@ def test_identity_covariance_nearest_neighbour(fc, ctx, w1, prec):
 def test_fixed_covariance(fc, ctx, w1, prec):
     gid = grid(fc, ctx, w1)
     d, b, n = fc.fc_run_points(ctx, gid, w1.points, 9, 500, opts=dict(precision=prec, cov=fc.FC_COV_FIXED))
-    od, ob, on = oracle.run_workload(w1, U=500, cov=oracle.COV_FIXED)
+    od, ob, on = oracle.run_workload(w1, U=500, seed=9, cov=oracle.COV_FIXED)
     _compare(d, b, n, od, ob, on, TOL_PLAIN if prec == 0 else TOL_MIXED, exact_index=(prec == 0))
     assert np.all(n == 1)
 
