@@ -96,6 +96,7 @@ struct Grid {
     float* rho = nullptr;
     float* Qc = nullptr;             // [cap][G_pad] (mixed)
     float* Qb = nullptr;
+    uint16_t* Qb3 = nullptr;         // [cap][G_pad][8] bf16 q-step rows of the screen
     double* Q64 = nullptr;           // [cap][G]   (plain)
     std::vector<uint8_t> q32_ready, q64_ready;
     int busy = 0;                    // queued jobs referencing the grid
@@ -248,6 +249,7 @@ void free_cache(fc_ctx* c, Grid* g) {
     dfree(c, g->rho); g->rho = nullptr;
     dfree(c, g->Qc); g->Qc = nullptr;
     dfree(c, g->Qb); g->Qb = nullptr;
+    dfree(c, g->Qb3); g->Qb3 = nullptr;
     dfree(c, g->Q64); g->Q64 = nullptr;
     g->cap = 0;
     g->n_slots = 0;
@@ -284,6 +286,7 @@ fc_status ensure_q32_storage(fc_ctx* c, Grid* g) {
     if (g->Qc) return FC_OK;
     FC_TRY(dalloc_t(c, &g->Qc, (size_t)g->cap * g->G_pad));
     FC_TRY(dalloc_t(c, &g->Qb, (size_t)g->cap * g->G_pad));
+    FC_TRY(dalloc_t(c, &g->Qb3, (size_t)g->cap * g->G_pad * 8));
     return FC_OK;
 }
 
@@ -348,7 +351,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
         FC_TRY(ensure_q32_storage(c, g));
         FC_CUDA(cudaMemcpyAsync(ds, q32_list.data(), q32_list.size() * 4, cudaMemcpyHostToDevice, c->stream));
         launch_qvec32(g->Sc32, g->nrm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(), g->Qc,
-                      g->Qb, c->stream);
+                      g->Qb, g->Qb3, c->stream);
         FC_TRY(sync(c));
     }
     if (!q64_list.empty()) {
@@ -437,6 +440,49 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
     launch_iota_i32(active, n, c->stream);
     int64_t n_active = n;
     FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 3 * sizeof(unsigned long long), c->stream));
+    // exact binary64 scan for `list`, then advance / finish them
+    auto exact_scan = [&](const int32_t* list, int64_t cnt, int scan_no) -> fc_status {
+        std::vector<int32_t> fq;
+        int32_t* fslot = nullptr;
+        FC_TRY(scratch(c, "fslot", (size_t)cnt, &fslot));
+        if (o.cov == FC_COV_IDENTITY) {
+            FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
+            launch_fill_i32(fslot, cnt, g->ident_slot, c->stream);
+        } else {
+            int32_t* fcur = nullptr;
+            FC_TRY(scratch(c, "fcur", (size_t)cnt, &fcur));
+            count_launch();
+            k_gather_cur<<<nb(cnt), 256, 0, c->stream>>>(list, (int)cnt, cur, fcur);
+            fq.resize(cnt);
+            FC_CUDA(cudaMemcpyAsync(fq.data(), fcur, (size_t)cnt * 4, cudaMemcpyDeviceToHost, c->stream));
+            FC_TRY(sync(c));
+            std::sort(fq.begin(), fq.end());
+            fq.erase(std::unique(fq.begin(), fq.end()), fq.end());
+            FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
+            launch_lookup_slots(list, cnt, cur, g->slot_of, fslot, c->stream);
+        }
+        stage_begin(c);
+        launch_scan64(list, cnt, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32, c->stream);
+        FC_TRY(stage_end(c, mixed ? &c->stats.ms_fallback : &c->stats.ms_scan64));
+        // finishing universes keep cur (the covariance of this scan); others move to their minimum
+        launch_advance(list, cnt, best32, cur, nscan, scan_no, max_iter, next, cnts + 2, fin, cnts + 3, c->stream);
+        int32_t n_fin = 0;
+        FC_CUDA(cudaMemcpyAsync(&n_fin, cnts + 3, 4, cudaMemcpyDeviceToHost, c->stream));
+        FC_TRY(sync(c));
+        if (n_fin > 0) {
+            int32_t* finslot = nullptr;
+            FC_TRY(scratch(c, "finslot", (size_t)n_fin, &finslot));
+            if (o.cov == FC_COV_IDENTITY)
+                launch_fill_i32(finslot, n_fin, g->ident_slot, c->stream);
+            else
+                launch_lookup_slots(fin, n_fin, cur, g->slot_of, finslot, c->stream);
+            stage_begin(c);
+            launch_finish(fin, n_fin, finslot, best32, p_of, U, d, g->S_fit, g->nfit, g->W64, dchi2, chi2min,
+                          c->stream);
+            FC_TRY(stage_end(c, &c->stats.ms_finish));
+        }
+        return FC_OK;
+    };
     for (int scan_no = 1; scan_no <= max_iter && n_active > 0; ++scan_no) {
         // ---- covariances for this scan
         std::vector<int32_t> qs, slots;
@@ -452,12 +498,9 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
         FC_TRY(stage_end(c, &c->stats.ms_cov));
         c->stats.chi2_evals += n_active * g->G;
         c->stats.scans += n_active;
-        // ---- scan: best32[u] for every active universe
+        FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 12, c->stream));  // n_fb, n_next, n_fin
         if (!mixed) {
-            stage_begin(c);
-            launch_scan64(active, n_active, uslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
-                          c->stream);
-            FC_TRY(stage_end(c, &c->stats.ms_scan64));
+            FC_TRY(exact_scan(active, n_active, scan_no));
         } else {
             const int64_t n_slots = g->n_slots;
             const int64_t max_tiles = n_active / kBM + std::min<int64_t>(n_slots, n_active) + 1;
@@ -485,72 +528,57 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, Yt, alpha, c->stream);
             FC_TRY(stage_end(c, &c->stats.ms_prep));
             stage_begin(c);
-            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb, tslot, n_tiles, g->G, g->G_pad, cval, cidx,
+            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb3, tslot, n_tiles, g->G, g->G_pad, cval, cidx,
                                c->status_dev, c->n_sm, c->stream))
                 return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
             FC_TRY(stage_end(c, &c->stats.ms_screen));
             c->stats.screen_launches += 1;
             c->stats.screen_flops += 2.0 * g->nfit * (double)n_active * (double)g->G;
+            ResolveArgs ra;
+            ra.tile_slot = tslot;
+            ra.tile_univ = tuniv;
+            ra.topk = topk;
+            ra.cval = cval;
+            ra.cidx = cidx;
+            ra.alpha = alpha;
+            ra.nrm = g->nrm;
+            ra.Qc = g->Qc;
+            ra.Qb = g->Qb;
+            ra.G_pad = g->G_pad;
+            ra.d = d;
+            ra.centre = g->centre;
+            ra.S_fit = g->S_fit;
+            ra.nfit = g->nfit;
+            ra.W64 = g->W64;
+            ra.cur = cur;
+            ra.p_of = p_of;
+            ra.U = U;
+            ra.scan_no = scan_no;
+            ra.max_iter = max_iter;
+            ra.best = best32;
+            ra.nscan = nscan;
+            ra.dchi2 = dchi2;
+            ra.chi2min = chi2min;
+            ra.next = next;
+            ra.n_next = cnts + 2;
+            ra.fb = fb;
+            ra.n_fb = cnts + 1;
+            ra.counters = c->counters_dev;
             stage_begin(c);
-            FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
-            launch_decide(tslot, tuniv, n_tiles, topk, cval, cidx, alpha, g->nrm, g->Qc, g->Qb, g->G_pad, d,
-                          g->centre, g->S_fit, g->nfit, g->W64, best32, fb, cnts + 1, c->counters_dev, c->stream);
+            launch_resolve(ra, n_tiles, c->stream);
             FC_TRY(stage_end(c, &c->stats.ms_rescore));
             FC_TRY(check_status(c));
             int32_t n_fb = 0;
             FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
             FC_TRY(sync(c));
-            if (n_fb > 0) {
-                // certificate failed: exact binary64 scan for these universes
-                std::vector<int32_t> fq;
-                if (o.cov == FC_COV_IDENTITY) {
-                    FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
-                } else {
-                    int32_t* fcur = nullptr;
-                    FC_TRY(scratch(c, "fcur", (size_t)n_fb, &fcur));
-                    count_launch();
-    k_gather_cur<<<nb(n_fb), 256, 0, c->stream>>>(fb, n_fb, cur, fcur);
-                    fq.resize(n_fb);
-                    FC_CUDA(cudaMemcpyAsync(fq.data(), fcur, (size_t)n_fb * 4, cudaMemcpyDeviceToHost, c->stream));
-                    FC_TRY(sync(c));
-                    std::sort(fq.begin(), fq.end());
-                    fq.erase(std::unique(fq.begin(), fq.end()), fq.end());
-                    FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
-                }
-                int32_t* fslot = nullptr;
-                FC_TRY(scratch(c, "fslot", (size_t)n_fb, &fslot));
-                if (o.cov == FC_COV_IDENTITY)
-                    launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
-                else
-                    launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
-                stage_begin(c);
-                launch_scan64(fb, n_fb, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
-                              c->stream);
-                FC_TRY(stage_end(c, &c->stats.ms_fallback));
-            }
+            if (n_fb > 0) FC_TRY(exact_scan(fb, n_fb, scan_no));
         }
-        // ---- advance: converged or exhausted universes finish under this scan's A
-        FC_CUDA(cudaMemsetAsync(cnts + 2, 0, 8, c->stream));
-        launch_advance(active, n_active, best32, cur, nscan, scan_no, max_iter, next, cnts + 2, fin, cnts + 3,
-                       c->stream);
-        int32_t hc[2] = {0, 0};
-        FC_CUDA(cudaMemcpyAsync(hc, cnts + 2, 8, cudaMemcpyDeviceToHost, c->stream));
+        int32_t n_next = 0;
+        FC_CUDA(cudaMemcpyAsync(&n_next, cnts + 2, 4, cudaMemcpyDeviceToHost, c->stream));
         FC_TRY(sync(c));
-        if (hc[1] > 0) {
-            int32_t* fslot = nullptr;
-            FC_TRY(scratch(c, "finslot", (size_t)hc[1], &fslot));
-            if (o.cov == FC_COV_IDENTITY)
-                launch_fill_i32(fslot, hc[1], g->ident_slot, c->stream);
-            else
-                launch_lookup_slots(fin, hc[1], cur, g->slot_of, fslot, c->stream);
-            stage_begin(c);
-            launch_finish(fin, hc[1], fslot, best32, p_of, U, d, g->S_fit, g->nfit, g->W64, dchi2, chi2min,
-                          c->stream);
-            FC_TRY(stage_end(c, &c->stats.ms_finish));
-        }
         std::swap(active, next);
         std::swap(c->scratch["active"], c->scratch["next"]);
-        n_active = hc[0];
+        n_active = n_next;
         FC_TRY(check_status(c));
     }
     unsigned long long cn[3] = {0, 0, 0};

@@ -48,7 +48,8 @@ void launch_build_cov(const double* S_full, int nf, int nfit, const int32_t* col
 void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
                    int64_t ldq, double* Q64, cudaStream_t st);
 void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad, int nfit, const float* A32,
-                   const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, cudaStream_t st);
+                   const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
+                   cudaStream_t st);
 
 // ---- fake data (a3) ----
 void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* collapse, int nfit,
@@ -77,15 +78,41 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                   const double* centre, int nfit, int K, const float* A32, const float* rho, uint16_t* Ytiles,
                   float* alpha, cudaStream_t st);
 // returns false if the padded K has no compiled screen instance
-bool launch_screen(int K, int topk, const uint16_t* Ytiles, const uint16_t* Btiles, const float* Qb,
+bool launch_screen(int K, int topk, const uint16_t* Ytiles, const uint16_t* Btiles, const uint16_t* Qb3,
                    const int32_t* tile_slot, int64_t n_tiles, int64_t G, int64_t G_pad, float* cand_val,
                    int32_t* cand_idx, int* status, int n_sm, cudaStream_t st);
-// decides the argmin from candidates; writes best[u] or flags fallback
-void launch_decide(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, int topk,
-                   const float* cand_val, const int32_t* cand_idx, const float* alpha, const float* nrm,
-                   const float* Qc, const float* Qb, int64_t G_pad, const float* d, const double* centre,
-                   const double* S_fit, int nfit, const double* W64, int32_t* best, int32_t* fallback_list,
-                   int32_t* n_fallback, unsigned long long* counters, cudaStream_t st);
+// Resolution of one mixed-path scan per screen tile (see k_resolve).
+struct ResolveArgs {
+    const int32_t* tile_slot;
+    const int32_t* tile_univ;
+    int topk;
+    const float* cval;
+    const int32_t* cidx;
+    const float* alpha;
+    const float* nrm;
+    const float* Qc;
+    const float* Qb;
+    int64_t G_pad;
+    const float* d;
+    const double* centre;
+    const double* S_fit;
+    int nfit;
+    const double* W64;
+    int32_t* cur;          // [n] covariance grid index, advanced for continuing universes
+    const int32_t* p_of;   // true point per block of U universes
+    int U;
+    int scan_no, max_iter;
+    int32_t* best;         // [n]
+    int8_t* nscan;         // [n]
+    double* dchi2;         // [n]
+    double* chi2min;       // [n] nullable
+    int32_t* next;         // next active list
+    int32_t* n_next;
+    int32_t* fb;           // fallback list
+    int32_t* n_fb;
+    unsigned long long* counters;  // screened, rescored, fallback
+};
+void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st);
 
 // ---- final residual-form chi2 and dchi2 ----
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot_of_list, const int32_t* best,

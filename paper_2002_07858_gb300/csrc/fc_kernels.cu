@@ -330,12 +330,46 @@ __global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, con
     }
 }
 
+// Relative slack on q_g: its own binary32 rounding plus its share of the
+// screen's binary32 accumulation.  The q-step enters the tensor-core
+// accumulator first and 3K products follow; bounding every add as a truncated
+// binary32 add of the running sum gives (3K + 3) 2^-23 |q| (K = padded N_fit).
+__device__ __forceinline__ float q_rel_slack(int nfit) {
+    const int K = ((nfit + 1 + 15) / 16) * 16;
+    return (float)(3 * K + 5) * 1.1920929e-07f;
+}
+
+// qb as a sum of three bf16 (hi + mid + lo <= qb, residual <= 2^-24 |qb|): the
+// B-operand row of the screen's q-step, [hi, mid, lo, 0, 0, 0, 0, 0].
+__device__ __forceinline__ void store_qb3(uint16_t* o, float qb) {
+    uint16_t h = 0, m = 0, l = 0;
+    if (qb < 1.0e38f) {
+        const __nv_bfloat16 bh = __float2bfloat16_rn(qb);
+        const float r1 = qb - __bfloat162float(bh);
+        const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(bm);
+        const __nv_bfloat16 bl = __float2bfloat16_rd(r2);
+        h = __bfloat16_as_ushort(bh);
+        m = __bfloat16_as_ushort(bm);
+        l = __bfloat16_as_ushort(bl);
+    } else {
+        h = __bfloat16_as_ushort(__float2bfloat16_rn(3.0e38f));  // padding rows: never a candidate
+    }
+    uint4 v;
+    v.x = (uint32_t)h | ((uint32_t)m << 16);
+    v.y = (uint32_t)l;
+    v.z = 0;
+    v.w = 0;
+    *reinterpret_cast<uint4*>(o) = v;
+}
+
 // binary32 q_g with its rounding bound; s~_g held in registers (NMAX >= nfit,
 // NMAX a multiple of 4), A staged in shared memory with rows padded to NMAX.
 template <int NMAX>
 __global__ void k_qvec32(const float* __restrict__ Sc32, const float* __restrict__ nrm, int64_t G, int64_t G_pad,
                          int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
-                         const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb) {
+                         const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb,
+                         uint16_t* __restrict__ Qb3) {
     __shared__ __align__(16) float sA[NMAX * NMAX];
     const int slot = slots[blockIdx.y];
     const float* A = A32 + (size_t)slot * nfit * nfit;
@@ -368,18 +402,20 @@ __global__ void k_qvec32(const float* __restrict__ Sc32, const float* __restrict
             }
             const float n = nrm[g];
             // |q^ - q| <= (nfit+4) 2^-24 rho |s|^2 + 2^-23 |q^|   (A rounded to binary32, dot products, final rounding)
-            const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + 1.1920929e-07f * fabsf(q));
+            const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + q_rel_slack(nfit) * fabsf(q));
             qc = q;
             qb = __fsub_rd(q, beta);
         }
         Qc[(size_t)slot * G_pad + g] = qc;
         Qb[(size_t)slot * G_pad + g] = qb;
+        store_qb3(Qb3 + ((size_t)slot * G_pad + g) * 8, qb);
     }
 }
 
 __global__ void k_qvec32_generic(const float* __restrict__ Sc32, const float* __restrict__ nrm, int64_t G,
                                  int64_t G_pad, int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
-                                 const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb) {
+                                 const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb,
+                                 uint16_t* __restrict__ Qb3) {
     const int slot = slots[blockIdx.y];
     const float* A = A32 + (size_t)slot * nfit * nfit;
     const float r = rho[slot];
@@ -394,12 +430,13 @@ __global__ void k_qvec32_generic(const float* __restrict__ Sc32, const float* __
                 q = fmaf(s[i], t, q);
             }
             const float n = nrm[g];
-            const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + 1.1920929e-07f * fabsf(q));
+            const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + q_rel_slack(nfit) * fabsf(q));
             qc = q;
             qb = __fsub_rd(q, beta);
         }
         Qc[(size_t)slot * G_pad + g] = qc;
         Qb[(size_t)slot * G_pad + g] = qb;
+        store_qb3(Qb3 + ((size_t)slot * G_pad + g) * 8, qb);
     }
 }
 
@@ -649,93 +686,193 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     Yt[ytile_offset(t, r, nfit, K)] = __bfloat16_as_ushort(__float2bfloat16_rd(-a));
 }
 
-// ------------------------------------------------------- mixed: decision ----
+// ------------------------------------------------------- mixed: resolution --
 
-// ||W r||^2 with r = s_g - d, W lower triangular (A = W^T W): residual form.
-__device__ double chi2_resid_thread(const double* __restrict__ W, const double* __restrict__ sg,
-                                    const float* __restrict__ du, int n) {
+// Residual form ||W r||^2, r = s - d, A = W^T W (W lower triangular), binary64.
+__device__ double resid_chi2(const double* __restrict__ W, int n, const double* __restrict__ s,
+                             const float* __restrict__ du) {
+    double r[kMaxBins];
+    for (int j = 0; j < n; ++j) r[j] = s[j] - (double)du[j];
     double acc = 0.0;
     for (int i = 0; i < n; ++i) {
+        const double* Wi = W + i * n;
         double t = 0.0;
-        for (int j = 0; j <= i; ++j) t = fma(W[i * n + j], sg[j] - (double)du[j], t);
+        for (int j = 0; j <= i; ++j) t = fma(Wi[j], r[j], t);
         acc = fma(t, t, acc);
     }
     return acc;
 }
 
-__global__ void __launch_bounds__(kBM) k_decide(const int32_t* __restrict__ tile_slot,
-                                                 const int32_t* __restrict__ tile_univ, int topk,
-                                                 const float* __restrict__ cval, const int32_t* __restrict__ cidx,
-                                                 const float* __restrict__ alpha, const float* __restrict__ nrm,
-                                                 const float* __restrict__ Qc, const float* __restrict__ Qb,
-                                                 int64_t G_pad, const float* __restrict__ d,
-                                                 const double* __restrict__ centre, const double* __restrict__ Sfit,
-                                                 int nfit, const double* __restrict__ W64, int32_t* __restrict__ best,
-                                                 int32_t* __restrict__ fb_list, int32_t* __restrict__ n_fb,
-                                                 unsigned long long* __restrict__ counters) {
+constexpr int kResolveMaxN = 64;      // W staged in shared memory up to this N_fit
+constexpr int kItemCu = kMaxTopK;     // item codes beyond the candidates
+constexpr int kItemP = kMaxTopK + 1;
+constexpr int kItemMin = kMaxTopK + 2;
+constexpr int kItemCodes = kMaxTopK + 3;
+
+// One CTA per screen tile (the 128 universes share one covariance), one thread
+// per universe:
+//  1. from the screen's lower bounds LB and upper bounds UB = LB + 2 eps of
+//     its candidates, accept the first candidate when it is the only one that
+//     can still be the minimum and its UB is below every outside bound tau;
+//  2. otherwise evaluate the binary64 residual-form chi2 of every candidate
+//     that can still be the minimum (and c_u = |W (d - v)|^2 when the
+//     certificate needs it), all lanes of the CTA sharing W in shared memory;
+//     take the first minimum and certify it against tau, else hand the
+//     universe to the exact fallback scan;
+//  3. universes whose minimum repeats their covariance index (or that used
+//     their last scan) get chi2_p and chi2_min in residual form and finish
+//     with dchi2; the others move their covariance index to the minimum.
+__global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
+    extern __shared__ double sW[];
+    __shared__ int s_nitem, s_nnext, s_nfb, s_cnt[3];
+    __shared__ int s_base_next, s_base_fb;
+    __shared__ uint16_t s_item[kBM * kItemCodes];
+    __shared__ double s_res[kBM][kItemCodes];
+    __shared__ int32_t s_g[kBM][kItemCodes];
+    __shared__ int32_t s_u[kBM];
     const int64_t t = blockIdx.x;
     const int r = threadIdx.x;
-    const int u = tile_univ[t * kBM + r];
-    if (u < 0) return;
-    const int slot = tile_slot[t];
+    const int n = a.nfit;
+    const int slot = a.tile_slot[t];
+    const double* Wg = a.W64 + (size_t)slot * n * n;
+    const bool staged = (n <= kResolveMaxN);
+    if (staged)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sW[e] = Wg[e];
+    const double* W = staged ? sW : Wg;
+    if (r == 0) {
+        s_nitem = 0;
+        s_nnext = 0;
+        s_nfb = 0;
+        s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    }
+    const int u = a.tile_univ[t * kBM + r];
+    s_u[r] = u;
     const int64_t row = t * kBM + r;
-    const float a = alpha[row];
+    const int topk = a.topk;
+    __syncthreads();
+
+    // ---- 1. screen decision
+    int state = 0;  // 0 padding, 1 decided, 2 rescoring, 3 fallback
+    int32_t g_best = -1;
+    double chi2_min = 0.0;
+    bool have_min = false;
     float lb[kMaxTopK], ub[kMaxTopK];
-    int32_t gi[kMaxTopK];
-    int nvalid = 0;
-    float min_ub = FLT_MAX;
-    for (int j = 0; j < topk; ++j) {
-        gi[j] = cidx[row * topk + j];
-        lb[j] = cval[row * topk + j];
-        if (gi[j] < 0) continue;
-        ++nvalid;
-        const int64_t q = (int64_t)slot * G_pad + gi[j];
-        const float eps = fmaf(a, nrm[gi[j]], Qc[q] - Qb[q]);
-        ub[j] = lb[j] + 2.0f * eps + 4.7683716e-07f * (fabsf(lb[j]) + fabsf(Qc[q]) + 1.0f);
-        min_ub = fminf(min_ub, ub[j]);
-    }
-    // every grid point outside the list has a lower bound >= tau (the k-th kept value)
-    const bool full = (nvalid == topk);
-    const float tau = full ? lb[topk - 1] - 4.7683716e-07f * (fabsf(lb[topk - 1]) + 1.0f) : FLT_MAX;
-    int nR = 0;
-    for (int j = 0; j < topk; ++j)
-        if (gi[j] >= 0 && lb[j] <= min_ub) ++nR;
-    if (nR == 1 && ub[0] < tau) {
-        best[u] = gi[0];
-        atomicAdd(&counters[0], 1ull);
-        return;
-    }
-    // binary64 residual-form chi2 of the candidates that can still be the minimum
-    const double* W = W64 + (size_t)slot * nfit * nfit;
-    const float* du = d + (size_t)u * nfit;
-    double bchi = DBL_MAX;
-    int32_t bg = INT32_MAX;
-    for (int j = 0; j < topk; ++j) {
-        if (gi[j] < 0 || lb[j] > min_ub) continue;
-        const double c = chi2_resid_thread(W, Sfit + (int64_t)gi[j] * nfit, du, nfit);
-        if (c < bchi || (c == bchi && gi[j] < bg)) {
-            bchi = c;
-            bg = gi[j];
+    bool full = false;
+    float tau = FLT_MAX, min_ub = FLT_MAX;
+    if (u >= 0) {
+        const float al = a.alpha[row];
+        int nvalid = 0;
+        for (int j = 0; j < topk; ++j) {
+            const int32_t gj = a.cidx[row * topk + j];
+            s_g[r][j] = gj;
+            lb[j] = a.cval[row * topk + j];
+            ub[j] = FLT_MAX;
+            if (gj < 0) continue;
+            ++nvalid;
+            const int64_t q = (int64_t)slot * a.G_pad + gj;
+            const float eps = fmaf(al, a.nrm[gj], a.Qc[q] - a.Qb[q]);
+            ub[j] = lb[j] + 2.0f * eps + 4.7683716e-07f * (fabsf(lb[j]) + fabsf(a.Qc[q]) + 1.0f);
+            min_ub = fminf(min_ub, ub[j]);
+        }
+        // every grid point outside the list has LB >= tau (the k-th kept value)
+        full = (nvalid == topk);
+        tau = full ? lb[topk - 1] - 4.7683716e-07f * (fabsf(lb[topk - 1]) + 1.0f) : FLT_MAX;
+        int nR = 0;
+        for (int j = 0; j < topk; ++j)
+            if (s_g[r][j] >= 0 && lb[j] <= min_ub) ++nR;
+        if (nR == 1 && ub[0] < tau) {
+            state = 1;
+            g_best = s_g[r][0];
+        } else {
+            state = 2;
+            for (int j = 0; j < topk; ++j)
+                if (s_g[r][j] >= 0 && lb[j] <= min_ub) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + j);
+            if (full && !(min_ub < tau)) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemCu);
         }
     }
-    bool ok = !full;
-    if (full) {
-        // c_u = |W (d - v)|^2; certified iff every outside point's lower bound exceeds chi2_min - c_u
-        double cu = 0.0;
-        for (int i = 0; i < nfit; ++i) {
-            double tt = 0.0;
-            for (int j = 0; j <= i; ++j) tt = fma(W[i * nfit + j], (double)du[j] - centre[j], tt);
-            cu = fma(tt, tt, cu);
-        }
-        const double sig_min = bchi - cu;
-        ok = (double)tau > sig_min + 1e-9 * (fabs(bchi) + fabs(cu));
+    __syncthreads();
+    // ---- 2. binary64 residual-form rescoring of the open candidates
+    for (int it = threadIdx.x; it < s_nitem; it += blockDim.x) {
+        const int code = s_item[it];
+        const int rr = code / kItemCodes, j = code % kItemCodes;
+        const float* du = a.d + (size_t)s_u[rr] * n;
+        const double* sv = (j == kItemCu) ? a.centre : a.S_fit + (int64_t)s_g[rr][j] * n;
+        s_res[rr][j] = resid_chi2(W, n, sv, du);
     }
-    if (ok) {
-        best[u] = bg;
-        atomicAdd(&counters[1], 1ull);
-    } else {
-        fb_list[atomicAdd(n_fb, 1)] = u;
-        atomicAdd(&counters[2], 1ull);
+    __syncthreads();
+    if (state == 2) {
+        double bchi = DBL_MAX;
+        int32_t bg = INT32_MAX;
+        for (int j = 0; j < topk; ++j) {
+            if (s_g[r][j] < 0 || lb[j] > min_ub) continue;
+            const double c = s_res[r][j];
+            if (c < bchi || (c == bchi && s_g[r][j] < bg)) {
+                bchi = c;
+                bg = s_g[r][j];
+            }
+        }
+        bool ok = !full || (min_ub < tau);
+        if (!ok) {
+            const double cu = s_res[r][kItemCu];
+            ok = (double)tau > (bchi - cu) + 1e-9 * (fabs(bchi) + fabs(cu));
+        }
+        if (ok) {
+            state = 1;
+            g_best = bg;
+            chi2_min = bchi;
+            have_min = true;
+            atomicAdd(&s_cnt[1], 1);
+        } else {
+            state = 3;
+            atomicAdd(&s_cnt[2], 1);
+        }
+    } else if (state == 1) {
+        atomicAdd(&s_cnt[0], 1);
+    }
+    __syncthreads();
+    if (r == 0) s_nitem = 0;
+    __syncthreads();
+    // ---- 3. finish converged / exhausted universes, advance the others
+    bool finishing = false;
+    int32_t p = -1;
+    if (state == 1) {
+        a.best[u] = g_best;
+        finishing = (g_best == a.cur[u]) || (a.scan_no >= a.max_iter);
+        if (finishing) {
+            p = a.p_of[u / a.U];
+            s_g[r][kItemP] = p;
+            s_g[r][kItemMin] = g_best;
+            if (p != g_best) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemP);
+            if (!have_min) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemMin);
+        } else {
+            a.cur[u] = g_best;
+        }
+    }
+    const bool to_next = (state == 1 && !finishing);
+    const int my_next = to_next ? atomicAdd(&s_nnext, 1) : -1;
+    const int my_fb = (state == 3) ? atomicAdd(&s_nfb, 1) : -1;
+    __syncthreads();
+    if (r == 0) {
+        s_base_next = s_nnext ? atomicAdd(a.n_next, s_nnext) : 0;
+        s_base_fb = s_nfb ? atomicAdd(a.n_fb, s_nfb) : 0;
+        if (s_cnt[0]) atomicAdd(&a.counters[0], (unsigned long long)s_cnt[0]);
+        if (s_cnt[1]) atomicAdd(&a.counters[1], (unsigned long long)s_cnt[1]);
+        if (s_cnt[2]) atomicAdd(&a.counters[2], (unsigned long long)s_cnt[2]);
+    }
+    for (int it = threadIdx.x; it < s_nitem; it += blockDim.x) {
+        const int code = s_item[it];
+        const int rr = code / kItemCodes, j = code % kItemCodes;
+        const float* du = a.d + (size_t)s_u[rr] * n;
+        s_res[rr][j] = resid_chi2(W, n, a.S_fit + (int64_t)s_g[rr][j] * n, du);
+    }
+    __syncthreads();
+    if (to_next) a.next[s_base_next + my_next] = u;
+    if (state == 3) a.fb[s_base_fb + my_fb] = u;
+    if (finishing) {
+        const double cmin = have_min ? chi2_min : s_res[r][kItemMin];
+        a.dchi2[u] = (p == g_best) ? 0.0 : s_res[r][kItemP] - cmin;
+        if (a.chi2min) a.chi2min[u] = cmin;
+        a.nscan[u] = (int8_t)a.scan_no;
     }
 }
 
@@ -882,22 +1019,23 @@ void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, con
 }
 
 void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad, int nfit, const float* A32,
-                   const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, cudaStream_t st) {
+                   const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
+                   cudaStream_t st) {
     if (n <= 0) return;
     unsigned gx = blocks_for(G_pad, 128);
     if (gx > 128) gx = 128;
     dim3 grid(gx, n);
     count_launch();
     if (nfit <= 16)
-        k_qvec32<16><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+        k_qvec32<16><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 32)
-        k_qvec32<32><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+        k_qvec32<32><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 48)
-        k_qvec32<48><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+        k_qvec32<48><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 64)
-        k_qvec32<64><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+        k_qvec32<64><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else
-        k_qvec32_generic<<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb);
+        k_qvec32_generic<<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
 }
 
 void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* coll, int nfit, const int64_t* ps,
@@ -988,15 +1126,17 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                                                                                   nfit, K, A32, rho, Yt, alpha);
 }
 
-void launch_decide(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, int topk, const float* cv,
-                   const int32_t* ci, const float* alpha, const float* nrm, const float* Qc, const float* Qb,
-                   int64_t G_pad, const float* d, const double* centre, const double* Sfit, int nfit,
-                   const double* W64, int32_t* best, int32_t* fb, int32_t* n_fb, unsigned long long* counters,
-                   cudaStream_t st) {
+void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
     if (n_tiles <= 0) return;
+    const size_t smem = a.nfit <= kResolveMaxN ? (size_t)a.nfit * a.nfit * sizeof(double) : 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kResolveMaxN * kResolveMaxN * (int)sizeof(double));
+        attr = true;
+    }
     count_launch();
-    k_decide<<<(unsigned)n_tiles, kBM, 0, st>>>(tile_slot, tile_univ, topk, cv, ci, alpha, nrm, Qc, Qb, G_pad, d,
-                                                centre, Sfit, nfit, W64, best, fb, n_fb, counters);
+    k_resolve<<<(unsigned)n_tiles, kBM, smem, st>>>(a);
 }
 
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const int32_t* best, const int32_t* p_of,

@@ -11,15 +11,19 @@
 // (Eq. 1 expanded around the centre v).  Y = -2 y and s~ are split into BF16
 // hi + lo parts and multiplied as hi*hi + lo*hi + hi*lo on tcgen05 (kind::f16,
 // FP32 accumulation in TMEM); one spare K column carries -alpha_u x |s~_g|,
-// the error bound of that product.  The epilogue adds qb_g (q_g lowered by its
-// rounding bound) and keeps, per universe, the TOPK smallest (LB, g) pairs with
-// the lowest index first among equal values -- the strict "<" of Algorithm 1.
-// The U x G score matrix never leaves the SM.
+// the error bound of that product.  A first K-step multiplies a constant
+// operand [1, 1, 1, 0...] with [qb_hi, qb_mid, qb_lo, 0...] (q_g lowered by its
+// rounding bound, split in three BF16) so the accumulator starts at qb_g and
+// the epilogue reads finished lower bounds.  It keeps, per universe, the TOPK
+// smallest (LB, g) pairs with the lowest index first among equal values --
+// the strict "<" of Algorithm 1.  The U x G score matrix never leaves the SM.
 //
 // Roles (one CTA per SM, persistent over universe tiles):
-//   warp 0      bulk-async (TMA) copies: Y tile, then S~ tile + qb slice per stage
+//   warp 0      bulk-async (TMA) copies: Y tile, then S~ tile + qb rows per stage
 //   warp 1      TMEM allocation; one lane issues tcgen05.mma and commits
-//   warps 2..5  epilogue: tcgen05.ld -> + qb -> running top-k; 128 rows
+//   warps 2..9  epilogue: two warps per TMEM lane quadrant, each owning half of
+//               the BN columns; tcgen05.ld double-buffered in registers, running
+//               top-k, the two halves merged through shared memory per tile row
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); on timeout the
 // kernel records kDevTimeout, waits for its own copies and MMAs, frees TMEM
 // and returns.
@@ -114,8 +118,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// Asynchronous 32-column TMEM load (one lane = one row); the registers are only
+// valid after tmem_wait() on the same buffer.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -126,34 +131,86 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// tcgen05.wait::ld; the buffer's registers are in-out operands so no use of
+// them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]),
+                   "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
+                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ void named_bar(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// (value, index) insertion into a sorted list, lexicographic order
+template <int TOPK>
+__device__ __forceinline__ void topk_insert(float (&vals)[TOPK], int32_t (&idx)[TOPK], float x, int32_t g) {
+    float cx = x;
+    int32_t cg = g;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int t = 0; t < TOPK; ++t) {
+        const bool sw = cx < vals[t] || (cx == vals[t] && cg < idx[t]);
+        const float tv = vals[t];
+        const int32_t ti = idx[t];
+        vals[t] = sw ? cx : tv;
+        idx[t] = sw ? cg : ti;
+        cx = sw ? tv : cx;
+        cg = sw ? ti : cg;
+    }
+}
+
+// 32 lower bounds of one row (columns g0..g0+31, increasing): running top-k.
+template <int TOPK>
+__device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[TOPK], const uint32_t (&r)[32],
+                                           int64_t g0, int64_t G) {
+    float m = __uint_as_float(r[0]);
+#pragma unroll
+    for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
+    if (m < vals[TOPK - 1]) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float x = __uint_as_float(r[i]);
+            if (x < vals[TOPK - 1] && g0 + i < G) topk_insert<TOPK>(vals, idx, x, (int32_t)(g0 + i));
+        }
+    }
 }
 
 constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
+constexpr int kEpiWarps = 8;
+constexpr int kHalfCols = kBN / 2;
 
-template <int K, int STAGES>
+template <int K, int STAGES, int TOPK>
 struct ScreenSmem {
     static constexpr uint32_t kYBytes = 2u * K * kBM * 2u;   // hi + lo, bf16
     static constexpr uint32_t kBBytes = 2u * K * kBN * 2u;
-    static constexpr uint32_t kQBytes = kBN * 4u;
+    static constexpr uint32_t kQBytes = kBN * 16u;           // one 8-column slab of q-step rows
     static constexpr uint32_t kAChunk = kBM * 16u;           // one 8-column slab of the A image
     static constexpr uint32_t kBChunk = kBN * 16u;
     static constexpr uint32_t kOffY = 0;
     static constexpr uint32_t kOffB = 2 * kYBytes;
     static constexpr uint32_t kOffQ = kOffB + STAGES * kBBytes;
-    static constexpr uint32_t kOffBar = kOffQ + STAGES * kQBytes;
+    static constexpr uint32_t kOffOnes = kOffQ + STAGES * kQBytes;   // A slab of the q-step: [1,1,1,0..] per row
+    static constexpr uint32_t kOffZero = kOffOnes + kAChunk;         // second slab of the q-step, all zero
+    static constexpr uint32_t kOffMerge = kOffZero + kBChunk;        // [BM][TOPK] (value, index) of half 1
+    static constexpr uint32_t kOffBar = kOffMerge + kBM * TOPK * 8;
     static constexpr uint32_t kNumBars = 2 + 2 + STAGES + STAGES + 2 + 2 + 1;
     static constexpr uint32_t kBytes = kOffBar + kNumBars * 8 + 16 + 1024;
 };
 
 template <int K, int TOPK, int STAGES>
-__global__ void __launch_bounds__(192, 1)
-    k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const float* __restrict__ Qb,
+__global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
+    k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
              const int32_t* __restrict__ tile_slot, int64_t n_tiles, int64_t G, int64_t G_pad,
              float* __restrict__ cand_val, int32_t* __restrict__ cand_idx, int* __restrict__ status) {
-    using L = ScreenSmem<K, STAGES>;
+    using L = ScreenSmem<K, STAGES, TOPK>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_addr(smem);
@@ -161,21 +218,31 @@ __global__ void __launch_bounds__(192, 1)
     uint32_t* tmem_holder = (uint32_t*)(smem + L::kOffBar + L::kNumBars * 8);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
     auto bar = [&](int i) { return smem_addr(&bars[i]); };
-    // barrier indices
     const int Y_FULL = 0, Y_EMPTY = 2, B_FULL = 4, B_EMPTY = 4 + STAGES, T_FULL = 4 + 2 * STAGES,
               T_EMPTY = 6 + 2 * STAGES, DONE = 8 + 2 * STAGES;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // constant q-step operand slabs (generic-proxy writes, fenced for the tensor core below)
+    {
+        uint32_t* ones = (uint32_t*)(smem + L::kOffOnes);
+        for (int i = threadIdx.x; i < (int)(L::kAChunk / 4); i += blockDim.x) {
+            const int w = i & 3;  // 4 words per 16-byte row: bf16 pairs (1,1), (1,0), (0,0), (0,0)
+            ones[i] = (w == 0) ? 0x3F803F80u : (w == 1 ? 0x00003F80u : 0u);
+        }
+        uint32_t* zero = (uint32_t*)(smem + L::kOffZero);
+        for (int i = threadIdx.x; i < (int)(L::kBChunk / 4); i += blockDim.x) zero[i] = 0u;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(bar(Y_FULL + i), 1);
             mbar_init(bar(Y_EMPTY + i), 1);
             mbar_init(bar(T_FULL + i), 1);
-            mbar_init(bar(T_EMPTY + i), 4);
+            mbar_init(bar(T_EMPTY + i), kEpiWarps);
         }
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(bar(B_FULL + s), 1);
-            mbar_init(bar(B_EMPTY + s), 1 + 4);
+            mbar_init(bar(B_EMPTY + s), 1);
         }
         mbar_init(bar(DONE), 1);
         *abort_flag = 0;
@@ -208,7 +275,7 @@ __global__ void __launch_bounds__(192, 1)
             bulk_g2s(sbase + L::kOffY + yb * L::kYBytes, Yt + item * (int64_t)(L::kYBytes / 2), L::kYBytes,
                      bar(Y_FULL + yb));
             y_par[yb] = (int)yph;
-            const float* qrow = Qb + (int64_t)tile_slot[item] * G_pad;
+            const uint16_t* qrow = Qb3 + (int64_t)tile_slot[item] * G_pad * 8;
             for (int j = 0; j < n_gt; ++j) {
                 const int64_t seq = (int64_t)it * n_gt + j;
                 const int s = (int)(seq % STAGES);
@@ -217,7 +284,7 @@ __global__ void __launch_bounds__(192, 1)
                 mbar_expect_tx(bar(B_FULL + s), L::kBBytes + L::kQBytes);
                 bulk_g2s(sbase + L::kOffB + s * L::kBBytes, Bt + (int64_t)j * (L::kBBytes / 2), L::kBBytes,
                          bar(B_FULL + s));
-                bulk_g2s(sbase + L::kOffQ + s * L::kQBytes, qrow + (int64_t)j * kBN, L::kQBytes, bar(B_FULL + s));
+                bulk_g2s(sbase + L::kOffQ + s * L::kQBytes, qrow + (int64_t)j * kBN * 8, L::kQBytes, bar(B_FULL + s));
                 b_par[s] = (int)ph;
             }
         }
@@ -234,6 +301,7 @@ __global__ void __launch_bounds__(192, 1)
         // --------------------------------------------------------------- MMA
         bool ok = true;
         int it = 0;
+        const uint64_t a_q = smem_desc(sbase + L::kOffOnes, L::kOffZero - L::kOffOnes, 128);
         for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
             const int yb = it & 1;
             if (!mbar_wait(bar(Y_FULL + yb), (it >> 1) & 1, abort_flag)) { ok = false; break; }
@@ -249,14 +317,17 @@ __global__ void __launch_bounds__(192, 1)
                 if (!mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t b0 = sbase + L::kOffB + s * L::kBBytes;
+                const uint32_t qs = L::kOffQ + s * L::kQBytes;
                 const uint32_t d = tmem_base + (uint32_t)(ab * kBN);
+                // q-step: accumulator <- qb_g
+                mma_bf16(d, a_q, smem_desc(sbase + qs, L::kOffZero - qs, 128), 0u);
 #pragma unroll
                 for (int kk = 0; kk < K / 16; ++kk) {
                     const uint64_t a_hi = smem_desc(a0 + (2 * kk) * L::kAChunk, L::kAChunk, 128);
                     const uint64_t a_lo = smem_desc(a0 + (K / 8 + 2 * kk) * L::kAChunk, L::kAChunk, 128);
                     const uint64_t b_hi = smem_desc(b0 + (2 * kk) * L::kBChunk, L::kBChunk, 128);
                     const uint64_t b_lo = smem_desc(b0 + (K / 8 + 2 * kk) * L::kBChunk, L::kBChunk, 128);
-                    mma_bf16(d, a_hi, b_hi, kk > 0 ? 1u : 0u);
+                    mma_bf16(d, a_hi, b_hi, 1u);
                     mma_bf16(d, a_lo, b_hi, 1u);
                     mma_bf16(d, a_hi, b_lo, 1u);
                 }
@@ -274,83 +345,81 @@ __global__ void __launch_bounds__(192, 1)
         mbar_wait(bar(DONE), 0, nullptr);
     } else if (warp >= 2) {
         // ---------------------------------------------------------- epilogue
-        const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+        const int quad = warp & 3;           // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;    // which half of the BN columns
         const int row = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+        float* mval = (float*)(smem + L::kOffMerge);
+        int32_t* midx = (int32_t*)(smem + L::kOffMerge + kBM * TOPK * 4);
         bool ok = true;
         int it = 0;
-        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
+        for (int64_t item = blockIdx.x; item < n_tiles; item += gridDim.x, ++it) {
             float vals[TOPK];
             int32_t idx[TOPK];
 #pragma unroll
             for (int t = 0; t < TOPK; ++t) {
                 vals[t] = FLT_MAX;
-                idx[t] = -1;
+                idx[t] = INT32_MAX;
             }
-            for (int j = 0; j < n_gt; ++j) {
+            for (int j = 0; ok && j < n_gt; ++j) {
                 const int64_t seq = (int64_t)it * n_gt + j;
-                const int s = (int)(seq % STAGES);
-                const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
                 const int ab = (int)(seq & 1);
                 const uint32_t aph = (uint32_t)((seq >> 1) & 1);
-                if (!mbar_wait(bar(T_FULL + ab), aph, abort_flag)) { ok = false; }
-                if (ok && !mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; }
-                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
-                tc_fence_after();
-                const float* qs = (const float*)(smem + L::kOffQ + s * L::kQBytes);
-                const int64_t gbase = (int64_t)j * kBN;
-#pragma unroll 1
-                for (int c0 = 0; c0 < kBN; c0 += 32) {
-                    float v[32];
-                    tmem_ld32(tmem_base + lane_base + (uint32_t)(ab * kBN + c0), v);
-                    const float4* q4 = reinterpret_cast<const float4*>(qs + c0);
-                    float m = FLT_MAX;
-#pragma unroll
-                    for (int i4 = 0; i4 < 8; ++i4) {
-                        const float4 qq = q4[i4];
-                        v[4 * i4 + 0] += qq.x;
-                        v[4 * i4 + 1] += qq.y;
-                        v[4 * i4 + 2] += qq.z;
-                        v[4 * i4 + 3] += qq.w;
-                        m = fminf(m, fminf(fminf(v[4 * i4 + 0], v[4 * i4 + 1]), fminf(v[4 * i4 + 2], v[4 * i4 + 3])));
-                    }
-                    if (m < vals[TOPK - 1]) {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const float x = v[i];
-                            const int64_t g = gbase + c0 + i;
-                            if (x < vals[TOPK - 1] && g < G) {
-                                float cx = x;
-                                int32_t cg = (int32_t)g;
-#pragma unroll
-                                for (int t = 0; t < TOPK; ++t) {
-                                    const bool sw = cx < vals[t];
-                                    const float tv = vals[t];
-                                    const int32_t ti = idx[t];
-                                    vals[t] = sw ? cx : tv;
-                                    idx[t] = sw ? cg : ti;
-                                    cx = sw ? tv : cx;
-                                    cg = sw ? ti : cg;
-                                }
-                            }
-                        }
-                    }
-                    __syncwarp();
+                bool w_ok = mbar_wait(bar(T_FULL + ab), aph, abort_flag);
+                if (!__all_sync(0xffffffffu, w_ok)) {
+                    ok = false;
+                    if (lane == 0) *abort_flag = 1;
+                    break;
                 }
+                tc_fence_after();
+                const uint32_t tb = tmem_base + lane_base + (uint32_t)(ab * kBN + half * kHalfCols);
+                const int64_t g0 = (int64_t)j * kBN + half * kHalfCols;
+                uint32_t ra[32], rb[32];
+                tmem_ld32(tb + 0, ra);
+                tmem_wait(ra);
+                tmem_ld32(tb + 32, rb);
+                topk_chunk<TOPK>(vals, idx, ra, g0 + 0, G);
+                __syncwarp();
+                tmem_wait(rb);
+                tmem_ld32(tb + 64, ra);
+                topk_chunk<TOPK>(vals, idx, rb, g0 + 32, G);
+                __syncwarp();
+                tmem_wait(ra);
+                tmem_ld32(tb + 96, rb);
+                topk_chunk<TOPK>(vals, idx, ra, g0 + 64, G);
+                __syncwarp();
+                tmem_wait(rb);
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(bar(T_EMPTY + ab));
-                    mbar_arrive(bar(B_EMPTY + s));
+                if (lane == 0) mbar_arrive(bar(T_EMPTY + ab));
+                topk_chunk<TOPK>(vals, idx, rb, g0 + 96, G);
+                __syncwarp();
+            }
+            // both halves of a row reach here even after a timeout, so the pair barrier cannot hang
+            if (half == 1) {
+#pragma unroll
+                for (int t = 0; t < TOPK; ++t) {
+                    mval[row * TOPK + t] = vals[t];
+                    midx[row * TOPK + t] = idx[t];
                 }
             }
-            if (!ok) break;
-            const int64_t orow = item * kBM + row;
+            named_bar(1 + quad, 64);
+            if (half == 0) {
 #pragma unroll
-            for (int t = 0; t < TOPK; ++t) {
-                cand_val[orow * TOPK + t] = vals[t];
-                cand_idx[orow * TOPK + t] = idx[t];
+                for (int t = 0; t < TOPK; ++t) {
+                    const float x = mval[row * TOPK + t];
+                    if (x < vals[TOPK - 1] || (x == vals[TOPK - 1] && midx[row * TOPK + t] < idx[TOPK - 1]))
+                        topk_insert<TOPK>(vals, idx, x, midx[row * TOPK + t]);
+                }
+                const int64_t orow = item * kBM + row;
+#pragma unroll
+                for (int t = 0; t < TOPK; ++t) {
+                    cand_val[orow * TOPK + t] = vals[t];
+                    cand_idx[orow * TOPK + t] = (idx[t] == INT32_MAX) ? -1 : idx[t];
+                }
             }
+            named_bar(1 + quad, 64);
+            if (!ok) break;
         }
         if (!ok && lane == 0) {
             *abort_flag = 1;
@@ -367,36 +436,38 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 template <int K, int TOPK, int STAGES>
-void run_screen(const uint16_t* Yt, const uint16_t* Bt, const float* Qb, const int32_t* tile_slot, int64_t n_tiles,
-                int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm, cudaStream_t st) {
-    using L = ScreenSmem<K, STAGES>;
+void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
+                int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
+                cudaStream_t st) {
+    using L = ScreenSmem<K, STAGES, TOPK>;
     static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
     auto kern = k_screen<K, TOPK, STAGES>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
-    kern<<<(unsigned)grid, 192, L::kBytes, st>>>(Yt, Bt, Qb, tile_slot, n_tiles, G, G_pad, cv, ci, status);
+    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, n_tiles, G, G_pad, cv,
+                                                                   ci, status);
 }
 
 }  // namespace
 
-bool launch_screen(int K, int topk, const uint16_t* Yt, const uint16_t* Bt, const float* Qb, const int32_t* tile_slot,
+bool launch_screen(int K, int topk, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
                    int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
                    cudaStream_t st) {
     if (n_tiles <= 0) return true;
 #define FC_SCREEN_CASE(KK, TT, SS)                                                                    \
     if (K == KK && topk == TT) {                                                                      \
-        run_screen<KK, TT, SS>(Yt, Bt, Qb, tile_slot, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
+        run_screen<KK, TT, SS>(Yt, Bt, Qb3, tile_slot, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
         return true;                                                                                  \
     }
     FC_SCREEN_CASE(16, 8, 4)
-    FC_SCREEN_CASE(32, 8, 4)
-    FC_SCREEN_CASE(48, 8, 3)
+    FC_SCREEN_CASE(32, 8, 3)
+    FC_SCREEN_CASE(48, 8, 2)
     FC_SCREEN_CASE(64, 8, 2)
     FC_SCREEN_CASE(16, 16, 4)
-    FC_SCREEN_CASE(32, 16, 4)
-    FC_SCREEN_CASE(48, 16, 3)
+    FC_SCREEN_CASE(32, 16, 3)
+    FC_SCREEN_CASE(48, 16, 2)
     FC_SCREEN_CASE(64, 16, 2)
 #undef FC_SCREEN_CASE
     return false;
