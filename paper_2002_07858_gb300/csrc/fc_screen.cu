@@ -168,16 +168,21 @@ __device__ __forceinline__ void topk_insert(float (&vals)[TOPK], int32_t (&idx)[
 }
 
 // 32 lower bounds of one row (columns g0..g0+31, increasing): running top-k.
+// Fast path: a min over the 32 values and one compare.  The rare slow path
+// parks the values in this warp's shared scratch ([i][lane]) and walks them in
+// a rolled loop, keeping the kernel small enough for the instruction cache.
 template <int TOPK>
 __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[TOPK], const uint32_t (&r)[32],
-                                           int64_t g0, int64_t G) {
+                                           int64_t g0, int64_t G, float* scratch, int lane) {
     float m = __uint_as_float(r[0]);
 #pragma unroll
     for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
     if (m < vals[TOPK - 1]) {
 #pragma unroll
+        for (int i = 0; i < 32; ++i) scratch[i * 32 + lane] = __uint_as_float(r[i]);
+#pragma unroll 1
         for (int i = 0; i < 32; ++i) {
-            const float x = __uint_as_float(r[i]);
+            const float x = scratch[i * 32 + lane];
             if (x < vals[TOPK - 1] && g0 + i < G) topk_insert<TOPK>(vals, idx, x, (int32_t)(g0 + i));
         }
     }
@@ -187,7 +192,7 @@ constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
 constexpr int kEpiWarps = 8;
 constexpr int kHalfCols = kBN / 2;
 
-template <int K, int STAGES, int TOPK>
+template <int K, int STAGES, int YBUF>
 struct ScreenSmem {
     static constexpr uint32_t kYBytes = 2u * K * kBM * 2u;   // hi + lo, bf16
     static constexpr uint32_t kBBytes = 2u * K * kBN * 2u;
@@ -195,22 +200,24 @@ struct ScreenSmem {
     static constexpr uint32_t kAChunk = kBM * 16u;           // one 8-column slab of the A image
     static constexpr uint32_t kBChunk = kBN * 16u;
     static constexpr uint32_t kOffY = 0;
-    static constexpr uint32_t kOffB = 2 * kYBytes;
+    static constexpr uint32_t kOffB = YBUF * kYBytes;
     static constexpr uint32_t kOffQ = kOffB + STAGES * kBBytes;
     static constexpr uint32_t kOffOnes = kOffQ + STAGES * kQBytes;   // A slab of the q-step: [1,1,1,0..] per row
     static constexpr uint32_t kOffZero = kOffOnes + kAChunk;         // second slab of the q-step, all zero
-    static constexpr uint32_t kOffMerge = kOffZero + kBChunk;        // [BM][TOPK] (value, index) of half 1
-    static constexpr uint32_t kOffBar = kOffMerge + kBM * TOPK * 8;
+    // per epilogue warp 4 KB: slow-path scratch inside a tile, top-k hand-over at the end of a row tile
+    static constexpr uint32_t kOffScratch = kOffZero + kBChunk;
+    static constexpr uint32_t kOffBar = kOffScratch + kEpiWarps * 4096;
     static constexpr uint32_t kNumBars = 2 + 2 + STAGES + STAGES + 2 + 2 + 1;
     static constexpr uint32_t kBytes = kOffBar + kNumBars * 8 + 16 + 1024;
 };
 
-template <int K, int TOPK, int STAGES>
+template <int K, int TOPK, int STAGES, int YBUF>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
              const int32_t* __restrict__ tile_slot, int64_t n_tiles, int64_t G, int64_t G_pad,
              float* __restrict__ cand_val, int32_t* __restrict__ cand_idx, int* __restrict__ status) {
-    using L = ScreenSmem<K, STAGES, TOPK>;
+    using L = ScreenSmem<K, STAGES, YBUF>;
+    static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_addr(smem);
@@ -268,8 +275,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         bool ok = true;
         int it = 0;
         for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
-            const int yb = it & 1;
-            const uint32_t yph = (it >> 1) & 1;
+            const int yb = it % YBUF;
+            const uint32_t yph = (it / YBUF) & 1;
             if (!mbar_wait(bar(Y_EMPTY + yb), yph ^ 1, abort_flag)) { ok = false; break; }
             mbar_expect_tx(bar(Y_FULL + yb), L::kYBytes);
             bulk_g2s(sbase + L::kOffY + yb * L::kYBytes, Yt + item * (int64_t)(L::kYBytes / 2), L::kYBytes,
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             *abort_flag = 1;
             atomicOr(status, kDevTimeout);
             // let every copy this thread issued land before the CTA can exit
-            for (int i = 0; i < 2; ++i)
+            for (int i = 0; i < YBUF; ++i)
                 if (y_par[i] >= 0) mbar_wait(bar(Y_FULL + i), (uint32_t)y_par[i], nullptr);
             for (int s = 0; s < STAGES; ++s)
                 if (b_par[s] >= 0) mbar_wait(bar(B_FULL + s), (uint32_t)b_par[s], nullptr);
@@ -303,8 +310,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         int it = 0;
         const uint64_t a_q = smem_desc(sbase + L::kOffOnes, L::kOffZero - L::kOffOnes, 128);
         for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
-            const int yb = it & 1;
-            if (!mbar_wait(bar(Y_FULL + yb), (it >> 1) & 1, abort_flag)) { ok = false; break; }
+            const int yb = it % YBUF;
+            if (!mbar_wait(bar(Y_FULL + yb), (it / YBUF) & 1, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const uint32_t a0 = sbase + L::kOffY + yb * L::kYBytes;
             for (int j = 0; j < n_gt; ++j) {
@@ -349,8 +356,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         const int half = (warp - 2) >> 2;    // which half of the BN columns
         const int row = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        float* mval = (float*)(smem + L::kOffMerge);
-        int32_t* midx = (int32_t*)(smem + L::kOffMerge + kBM * TOPK * 4);
+        float* scratch = (float*)(smem + L::kOffScratch + (warp - 2) * 4096);
+        // hand-over area of this row's half-1 warp (warp + 4 for a half-0 warp)
+        float* mval = (float*)(smem + L::kOffScratch + (half ? warp - 2 : warp + 2) * 4096);
+        int32_t* midx = (int32_t*)(mval + TOPK * 32);
         bool ok = true;
         int it = 0;
         for (int64_t item = blockIdx.x; item < n_tiles; item += gridDim.x, ++it) {
@@ -378,38 +387,39 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 tmem_ld32(tb + 0, ra);
                 tmem_wait(ra);
                 tmem_ld32(tb + 32, rb);
-                topk_chunk<TOPK>(vals, idx, ra, g0 + 0, G);
+                topk_chunk<TOPK>(vals, idx, ra, g0 + 0, G, scratch, lane);
                 __syncwarp();
                 tmem_wait(rb);
                 tmem_ld32(tb + 64, ra);
-                topk_chunk<TOPK>(vals, idx, rb, g0 + 32, G);
+                topk_chunk<TOPK>(vals, idx, rb, g0 + 32, G, scratch, lane);
                 __syncwarp();
                 tmem_wait(ra);
                 tmem_ld32(tb + 96, rb);
-                topk_chunk<TOPK>(vals, idx, ra, g0 + 64, G);
+                topk_chunk<TOPK>(vals, idx, ra, g0 + 64, G, scratch, lane);
                 __syncwarp();
                 tmem_wait(rb);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(T_EMPTY + ab));
-                topk_chunk<TOPK>(vals, idx, rb, g0 + 96, G);
+                topk_chunk<TOPK>(vals, idx, rb, g0 + 96, G, scratch, lane);
                 __syncwarp();
             }
             // both halves of a row reach here even after a timeout, so the pair barrier cannot hang
             if (half == 1) {
 #pragma unroll
                 for (int t = 0; t < TOPK; ++t) {
-                    mval[row * TOPK + t] = vals[t];
-                    midx[row * TOPK + t] = idx[t];
+                    mval[t * 32 + lane] = vals[t];
+                    midx[t * 32 + lane] = idx[t];
                 }
             }
             named_bar(1 + quad, 64);
             if (half == 0) {
-#pragma unroll
+#pragma unroll 1
                 for (int t = 0; t < TOPK; ++t) {
-                    const float x = mval[row * TOPK + t];
-                    if (x < vals[TOPK - 1] || (x == vals[TOPK - 1] && midx[row * TOPK + t] < idx[TOPK - 1]))
-                        topk_insert<TOPK>(vals, idx, x, midx[row * TOPK + t]);
+                    const float x = mval[t * 32 + lane];
+                    const int32_t xi = midx[t * 32 + lane];
+                    if (x < vals[TOPK - 1] || (x == vals[TOPK - 1] && xi < idx[TOPK - 1]))
+                        topk_insert<TOPK>(vals, idx, x, xi);
                 }
                 const int64_t orow = item * kBM + row;
 #pragma unroll
@@ -435,13 +445,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     }
 }
 
-template <int K, int TOPK, int STAGES>
+template <int K, int TOPK, int STAGES, int YBUF>
 void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
                 int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
                 cudaStream_t st) {
-    using L = ScreenSmem<K, STAGES, TOPK>;
+    using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
-    auto kern = k_screen<K, TOPK, STAGES>;
+    auto kern = k_screen<K, TOPK, STAGES, YBUF>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
@@ -456,19 +466,19 @@ bool launch_screen(int K, int topk, const uint16_t* Yt, const uint16_t* Bt, cons
                    int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
                    cudaStream_t st) {
     if (n_tiles <= 0) return true;
-#define FC_SCREEN_CASE(KK, TT, SS)                                                                    \
-    if (K == KK && topk == TT) {                                                                      \
-        run_screen<KK, TT, SS>(Yt, Bt, Qb3, tile_slot, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
-        return true;                                                                                  \
+#define FC_SCREEN_CASE(KK, TT, SS, YY)                                                                    \
+    if (K == KK && topk == TT) {                                                                          \
+        run_screen<KK, TT, SS, YY>(Yt, Bt, Qb3, tile_slot, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
+        return true;                                                                                      \
     }
-    FC_SCREEN_CASE(16, 8, 4)
-    FC_SCREEN_CASE(32, 8, 3)
-    FC_SCREEN_CASE(48, 8, 2)
-    FC_SCREEN_CASE(64, 8, 2)
-    FC_SCREEN_CASE(16, 16, 4)
-    FC_SCREEN_CASE(32, 16, 3)
-    FC_SCREEN_CASE(48, 16, 2)
-    FC_SCREEN_CASE(64, 16, 2)
+    FC_SCREEN_CASE(16, 8, 4, 2)
+    FC_SCREEN_CASE(32, 8, 3, 2)
+    FC_SCREEN_CASE(48, 8, 2, 2)
+    FC_SCREEN_CASE(64, 8, 2, 1)
+    FC_SCREEN_CASE(16, 16, 4, 2)
+    FC_SCREEN_CASE(32, 16, 3, 2)
+    FC_SCREEN_CASE(48, 16, 2, 2)
+    FC_SCREEN_CASE(64, 16, 2, 1)
 #undef FC_SCREEN_CASE
     return false;
 }
