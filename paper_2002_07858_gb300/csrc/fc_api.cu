@@ -507,7 +507,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
                     *fb = nullptr;
             uint16_t* Yt = nullptr;
-            float *alpha = nullptr, *cval = nullptr;
+            float *alpha = nullptr, *cval = nullptr, *tau0 = nullptr;
             int32_t* cidx = nullptr;
             FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
             FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
@@ -516,6 +516,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_TRY(scratch(c, "tuniv", (size_t)max_tiles * kBM, &tuniv));
             FC_TRY(scratch(c, "Yt", (size_t)max_tiles * kBM * 2 * g->K, &Yt));
             FC_TRY(scratch(c, "alpha", (size_t)max_tiles * kBM, &alpha));
+            FC_TRY(scratch(c, "tau0", (size_t)max_tiles * kBM, &tau0));
             FC_TRY(scratch(c, "cval", (size_t)max_tiles * kBM * topk, &cval));
             FC_TRY(scratch(c, "cidx", (size_t)max_tiles * kBM * topk, &cidx));
             FC_TRY(scratch(c, "fb", (size_t)n_active, &fb));
@@ -525,10 +526,11 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             int32_t n_tiles = 0;
             FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts, 4, cudaMemcpyDeviceToHost, c->stream));
             FC_TRY(sync(c));
-            launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, Yt, alpha, c->stream);
+            launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32, g->nrm,
+                         g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, c->stream);
             FC_TRY(stage_end(c, &c->stats.ms_prep));
             stage_begin(c);
-            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb3, tslot, n_tiles, g->G, g->G_pad, cval, cidx,
+            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb3, tslot, tau0, n_tiles, g->G, g->G_pad, cval, cidx,
                                c->status_dev, c->n_sm, c->stream))
                 return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
             FC_TRY(stage_end(c, &c->stats.ms_screen));

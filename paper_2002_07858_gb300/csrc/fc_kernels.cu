@@ -641,11 +641,18 @@ __device__ __forceinline__ int64_t ytile_offset(int64_t t, int r, int c, int K) 
 // One CTA per tile, one thread per row: y^ = A (d - v) in binary32, Y = -2 y^
 // split into bf16 hi + lo, and the error-bound coefficient alpha in the spare
 // column so that the screen directly yields a lower bound of chi2_g - c_u.
+// It also evaluates the row's screen value at its own covariance point q
+// (= cur[u]) with an upper bound UB_q: no grid point with LB >= UB_q can be the
+// minimum, so tau0 = UB_q seeds the screen's top-k threshold.
 __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_slot,
                                                 const int32_t* __restrict__ tile_univ, const float* __restrict__ d,
                                                 const double* __restrict__ centre, int nfit, int K,
                                                 const float* __restrict__ A32, const float* __restrict__ rho,
-                                                uint16_t* __restrict__ Yt, float* __restrict__ alpha) {
+                                                const int32_t* __restrict__ cur, const float* __restrict__ Sc32,
+                                                const float* __restrict__ nrm, const float* __restrict__ Qc,
+                                                const float* __restrict__ Qb, int64_t G_pad,
+                                                uint16_t* __restrict__ Yt, float* __restrict__ alpha,
+                                                float* __restrict__ tau0) {
     extern __shared__ float sA[];
     const int64_t t = blockIdx.x;
     const int slot = tile_slot[t];
@@ -656,20 +663,25 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     for (int c = 0; c < 2 * K; ++c) Yt[ytile_offset(t, r, c, K)] = 0;
     if (u < 0) {
         alpha[t * kBM + r] = 0.0f;
+        tau0[t * kBM + r] = -FLT_MAX;  // padding rows keep no candidate
         return;
     }
+    const int q = cur[u];
+    const float* sq = Sc32 + (int64_t)q * nfit;
     float dt[kMaxBins];
     float dn2 = 0.0f;
     for (int j = 0; j < nfit; ++j) {
         dt[j] = (float)((double)d[(size_t)u * nfit + j] - centre[j]);
         dn2 = fmaf(dt[j], dt[j], dn2);
     }
-    float yn2 = 0.0f;
+    float yn2 = 0.0f, dot = 0.0f, adot = 0.0f;
     for (int i = 0; i < nfit; ++i) {
         float y = 0.0f;
         for (int j = 0; j < nfit; ++j) y = fmaf(sA[i * nfit + j], dt[j], y);
         const float Y = -2.0f * y;
         yn2 = fmaf(Y, Y, yn2);
+        dot = fmaf(Y, sq[i], dot);
+        adot = fmaf(fabsf(Y), fabsf(sq[i]), adot);
         const __nv_bfloat16 h = __float2bfloat16_rn(Y);
         const __nv_bfloat16 l = __float2bfloat16_rn(Y - __bfloat162float(h));
         Yt[ytile_offset(t, r, i, K)] = __bfloat16_as_ushort(h);
@@ -684,6 +696,14 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     const float a = 1.05f * (2.0f * (float)(nfit + 2) * 5.9604645e-08f * rho[slot] * dn + c_split * yn);
     alpha[t * kBM + r] = a;
     Yt[ytile_offset(t, r, nfit, K)] = __bfloat16_as_ushort(__float2bfloat16_rd(-a));
+    // probe at q: sigma^ = q^_q + Y.s~_q (binary32), |sigma^ - sigma| <= 2|y - y^||s~_q| + |q^ - q|
+    //   + (nfit+1) 2^-24 (sum |Y_i s~_i| + |q^|) + 2^-24 |sigma^|   (all inside eps below)
+    const int64_t qi = (int64_t)slot * G_pad + q;
+    const float qc = Qc[qi];
+    const float sig = qc + dot;
+    const float eps = a * nrm[q] + (qc - Qb[qi]) +
+                      (float)(nfit + 2) * 5.9604645e-08f * (adot + fabsf(qc)) + 1.1920929e-07f * (fabsf(sig) + 1.0f);
+    tau0[t * kBM + r] = (sig + 2.0f * eps) * 1.0000005f + 1.0e-6f + 4.7683716e-07f * fabsf(sig);
 }
 
 // ------------------------------------------------------- mixed: resolution --
@@ -774,13 +794,17 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
             ub[j] = lb[j] + 2.0f * eps + 4.7683716e-07f * (fabsf(lb[j]) + fabsf(a.Qc[q]) + 1.0f);
             min_ub = fminf(min_ub, ub[j]);
         }
-        // every grid point outside the list has LB >= tau (the k-th kept value)
+        // every grid point outside the list has LB >= the k-th kept value; an
+        // empty slot holds the seed tau0 = UB of the row's probe, so a list that is
+        // not full holds every point that can be the minimum
         full = (nvalid == topk);
-        tau = full ? lb[topk - 1] - 4.7683716e-07f * (fabsf(lb[topk - 1]) + 1.0f) : FLT_MAX;
+        tau = lb[topk - 1] - 4.7683716e-07f * (fabsf(lb[topk - 1]) + 1.0f);
         int nR = 0;
         for (int j = 0; j < topk; ++j)
             if (s_g[r][j] >= 0 && lb[j] <= min_ub) ++nR;
-        if (nR == 1 && ub[0] < tau) {
+        if (nvalid == 0) {
+            state = 3;  // nothing below the seed: only possible with non-finite data
+        } else if (nR == 1 && ub[0] < tau) {
             state = 1;
             g_best = s_g[r][0];
         } else {
@@ -828,6 +852,8 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         }
     } else if (state == 1) {
         atomicAdd(&s_cnt[0], 1);
+    } else if (state == 3) {
+        atomicAdd(&s_cnt[2], 1);
     }
     __syncthreads();
     if (r == 0) s_nitem = 0;
@@ -1116,14 +1142,16 @@ void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_
 }
 
 void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
-                  const double* centre, int nfit, int K, const float* A32, const float* rho, uint16_t* Yt,
-                  float* alpha, cudaStream_t st) {
+                  const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
+                  const float* Sc32, const float* nrm, const float* Qc, const float* Qb, int64_t G_pad,
+                  uint16_t* Yt, float* alpha, float* tau0, cudaStream_t st) {
     if (n_tiles <= 0) return;
     const size_t smem = (size_t)nfit * nfit * sizeof(float);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_yprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
     k_yprep<<<(unsigned)n_tiles, kBM, (size_t)nfit * nfit * sizeof(float), st>>>(tile_slot, tile_univ, d, centre,
-                                                                                  nfit, K, A32, rho, Yt, alpha);
+                                                                                  nfit, K, A32, rho, cur, Sc32, nrm,
+                                                                                  Qc, Qb, G_pad, Yt, alpha, tau0);
 }
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {

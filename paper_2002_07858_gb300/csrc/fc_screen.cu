@@ -167,10 +167,11 @@ __device__ __forceinline__ void topk_insert(float (&vals)[TOPK], int32_t (&idx)[
     }
 }
 
-// 32 lower bounds of one row (columns g0..g0+31, increasing): running top-k.
-// Fast path: a min over the 32 values and one compare.  The rare slow path
-// parks the values in this warp's shared scratch ([i][lane]) and walks them in
-// a rolled loop, keeping the kernel small enough for the instruction cache.
+// 32 lower bounds of one row (columns g0..g0+31): running top-k.  Fast path:
+// a min over the 32 values and one compare.  The slow path marks the values
+// below the current k-th one in a bit mask, parks them in this warp's shared
+// scratch ([i][lane]) and inserts the marked ones in a rolled loop, keeping
+// the kernel small enough for the instruction cache.
 template <int TOPK>
 __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[TOPK], const uint32_t (&r)[32],
                                            int64_t g0, int64_t G, float* scratch, int lane) {
@@ -178,12 +179,21 @@ __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[T
 #pragma unroll
     for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
     if (m < vals[TOPK - 1]) {
+        const float tau = vals[TOPK - 1];
+        uint32_t mask = 0;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) scratch[i * 32 + lane] = __uint_as_float(r[i]);
-#pragma unroll 1
         for (int i = 0; i < 32; ++i) {
+            const float x = __uint_as_float(r[i]);
+            mask |= (x < tau ? 1u : 0u) << i;
+            scratch[i * 32 + lane] = x;
+        }
+        const int64_t lim = G - g0;
+        if (lim < 32) mask &= (lim <= 0) ? 0u : ((1u << lim) - 1u);
+        while (mask) {
+            const int i = __ffs(mask) - 1;
+            mask &= mask - 1;
             const float x = scratch[i * 32 + lane];
-            if (x < vals[TOPK - 1] && g0 + i < G) topk_insert<TOPK>(vals, idx, x, (int32_t)(g0 + i));
+            if (x < vals[TOPK - 1]) topk_insert<TOPK>(vals, idx, x, (int32_t)(g0 + i));
         }
     }
 }
@@ -214,8 +224,8 @@ struct ScreenSmem {
 template <int K, int TOPK, int STAGES, int YBUF>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
-             const int32_t* __restrict__ tile_slot, int64_t n_tiles, int64_t G, int64_t G_pad,
-             float* __restrict__ cand_val, int32_t* __restrict__ cand_idx, int* __restrict__ status) {
+             const int32_t* __restrict__ tile_slot, const float* __restrict__ tau0, int64_t n_tiles, int64_t G,
+             int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx, int* __restrict__ status) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
@@ -363,11 +373,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         bool ok = true;
         int it = 0;
         for (int64_t item = blockIdx.x; item < n_tiles; item += gridDim.x, ++it) {
+            // seeded with the row's certified upper bound: larger values can never be the minimum
+            const float seed = tau0[item * kBM + row];
             float vals[TOPK];
             int32_t idx[TOPK];
 #pragma unroll
             for (int t = 0; t < TOPK; ++t) {
-                vals[t] = FLT_MAX;
+                vals[t] = seed;
                 idx[t] = INT32_MAX;
             }
             for (int j = 0; ok && j < n_gt; ++j) {
@@ -447,8 +459,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 
 template <int K, int TOPK, int STAGES, int YBUF>
 void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
-                int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
-                cudaStream_t st) {
+                const float* tau0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status,
+                int n_sm, cudaStream_t st) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
     auto kern = k_screen<K, TOPK, STAGES, YBUF>;
@@ -456,28 +468,28 @@ void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, con
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
-    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, n_tiles, G, G_pad, cv,
-                                                                   ci, status);
+    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, n_tiles, G, G_pad,
+                                                                   cv, ci, status);
 }
 
 }  // namespace
 
 bool launch_screen(int K, int topk, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
-                   int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
+                   const float* tau0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
                    cudaStream_t st) {
     if (n_tiles <= 0) return true;
 #define FC_SCREEN_CASE(KK, TT, SS, YY)                                                                    \
     if (K == KK && topk == TT) {                                                                          \
-        run_screen<KK, TT, SS, YY>(Yt, Bt, Qb3, tile_slot, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
+        run_screen<KK, TT, SS, YY>(Yt, Bt, Qb3, tile_slot, tau0, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
         return true;                                                                                      \
     }
     FC_SCREEN_CASE(16, 8, 4, 2)
     FC_SCREEN_CASE(32, 8, 3, 2)
-    FC_SCREEN_CASE(48, 8, 2, 2)
+    FC_SCREEN_CASE(48, 8, 3, 1)
     FC_SCREEN_CASE(64, 8, 2, 1)
     FC_SCREEN_CASE(16, 16, 4, 2)
     FC_SCREEN_CASE(32, 16, 3, 2)
-    FC_SCREEN_CASE(48, 16, 2, 2)
+    FC_SCREEN_CASE(48, 16, 3, 1)
     FC_SCREEN_CASE(64, 16, 2, 1)
 #undef FC_SCREEN_CASE
     return false;
