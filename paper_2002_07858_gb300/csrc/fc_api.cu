@@ -517,6 +517,8 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_TRY(scratch(c, "Yt", (size_t)max_tiles * kBM * 2 * g->K, &Yt));
             FC_TRY(scratch(c, "alpha", (size_t)max_tiles * kBM, &alpha));
             FC_TRY(scratch(c, "tau0", (size_t)max_tiles * kBM, &tau0));
+            int32_t* tj0 = nullptr;
+            FC_TRY(scratch(c, "tile_j0", (size_t)max_tiles, &tj0));
             FC_TRY(scratch(c, "cval", (size_t)max_tiles * kBM * topk, &cval));
             FC_TRY(scratch(c, "cidx", (size_t)max_tiles * kBM * topk, &cidx));
             FC_TRY(scratch(c, "fb", (size_t)n_active, &fb));
@@ -527,10 +529,10 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts, 4, cudaMemcpyDeviceToHost, c->stream));
             FC_TRY(sync(c));
             launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32, g->nrm,
-                         g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, c->stream);
+                         g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
             FC_TRY(stage_end(c, &c->stats.ms_prep));
             stage_begin(c);
-            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb3, tslot, tau0, n_tiles, g->G, g->G_pad, cval, cidx,
+            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G, g->G_pad, cval, cidx,
                                c->status_dev, c->n_sm, c->stream))
                 return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
             FC_TRY(stage_end(c, &c->stats.ms_screen));

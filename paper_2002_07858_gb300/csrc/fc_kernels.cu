@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
                                                 const float* __restrict__ nrm, const float* __restrict__ Qc,
                                                 const float* __restrict__ Qb, int64_t G_pad,
                                                 uint16_t* __restrict__ Yt, float* __restrict__ alpha,
-                                                float* __restrict__ tau0) {
+                                                float* __restrict__ tau0, int32_t* __restrict__ tile_j0) {
     extern __shared__ float sA[];
     const int64_t t = blockIdx.x;
     const int slot = tile_slot[t];
@@ -660,6 +660,8 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     __syncthreads();
     const int r = threadIdx.x;
     const int u = tile_univ[t * kBM + r];
+    // the screen walks this tile's grid tiles starting at the one holding row 0's q
+    if (r == 0) tile_j0[t] = (u >= 0) ? cur[u] / kBN : 0;
     for (int c = 0; c < 2 * K; ++c) Yt[ytile_offset(t, r, c, K)] = 0;
     if (u < 0) {
         alpha[t * kBM + r] = 0.0f;
@@ -668,6 +670,7 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     }
     const int q = cur[u];
     const float* sq = Sc32 + (int64_t)q * nfit;
+
     float dt[kMaxBins];
     float dn2 = 0.0f;
     for (int j = 0; j < nfit; ++j) {
@@ -1144,14 +1147,15 @@ void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_
 void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
                   const float* Sc32, const float* nrm, const float* Qc, const float* Qb, int64_t G_pad,
-                  uint16_t* Yt, float* alpha, float* tau0, cudaStream_t st) {
+                  uint16_t* Yt, float* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st) {
     if (n_tiles <= 0) return;
     const size_t smem = (size_t)nfit * nfit * sizeof(float);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_yprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
     k_yprep<<<(unsigned)n_tiles, kBM, (size_t)nfit * nfit * sizeof(float), st>>>(tile_slot, tile_univ, d, centre,
                                                                                   nfit, K, A32, rho, cur, Sc32, nrm,
-                                                                                  Qc, Qb, G_pad, Yt, alpha, tau0);
+                                                                                  Qc, Qb, G_pad, Yt, alpha, tau0,
+                                                                                  tile_j0);
 }
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {

@@ -168,32 +168,33 @@ __device__ __forceinline__ void topk_insert(float (&vals)[TOPK], int32_t (&idx)[
 }
 
 // 32 lower bounds of one row (columns g0..g0+31): running top-k.  Fast path:
-// a min over the 32 values and one compare.  The slow path marks the values
-// below the current k-th one in a bit mask, parks them in this warp's shared
-// scratch ([i][lane]) and inserts the marked ones in a rolled loop, keeping
-// the kernel small enough for the instruction cache.
+// a min over the 32 values and one compare.  If exactly one value is at or
+// below the current k-th one it is that minimum and is inserted directly;
+// with several, they are parked in this warp's shared scratch ([i][lane]) and
+// inserted in a rolled loop (small code for the instruction cache).
 template <int TOPK>
 __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[TOPK], const uint32_t (&r)[32],
                                            int64_t g0, int64_t G, float* scratch, int lane) {
     float m = __uint_as_float(r[0]);
 #pragma unroll
     for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
-    if (m < vals[TOPK - 1]) {
+    if (m <= vals[TOPK - 1]) {
         const float tau = vals[TOPK - 1];
         uint32_t mask = 0;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const float x = __uint_as_float(r[i]);
-            mask |= (x < tau ? 1u : 0u) << i;
-            scratch[i * 32 + lane] = x;
-        }
+        for (int i = 0; i < 32; ++i) mask |= (__uint_as_float(r[i]) <= tau ? 1u : 0u) << i;
         const int64_t lim = G - g0;
         if (lim < 32) mask &= (lim <= 0) ? 0u : ((1u << lim) - 1u);
-        while (mask) {
-            const int i = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const float x = scratch[i * 32 + lane];
-            if (x < vals[TOPK - 1]) topk_insert<TOPK>(vals, idx, x, (int32_t)(g0 + i));
+        if (__popc(mask) == 1) {
+            topk_insert<TOPK>(vals, idx, m, (int32_t)(g0 + __ffs(mask) - 1));
+        } else if (mask) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) scratch[i * 32 + lane] = __uint_as_float(r[i]);
+            while (mask) {
+                const int i = __ffs(mask) - 1;
+                mask &= mask - 1;
+                topk_insert<TOPK>(vals, idx, scratch[i * 32 + lane], (int32_t)(g0 + i));
+            }
         }
     }
 }
@@ -224,8 +225,9 @@ struct ScreenSmem {
 template <int K, int TOPK, int STAGES, int YBUF>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
-             const int32_t* __restrict__ tile_slot, const float* __restrict__ tau0, int64_t n_tiles, int64_t G,
-             int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx, int* __restrict__ status) {
+             const int32_t* __restrict__ tile_slot, const float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
+             int64_t n_tiles, int64_t G, int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
+             int* __restrict__ status) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
@@ -293,8 +295,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                      bar(Y_FULL + yb));
             y_par[yb] = (int)yph;
             const uint16_t* qrow = Qb3 + (int64_t)tile_slot[item] * G_pad * 8;
-            for (int j = 0; j < n_gt; ++j) {
-                const int64_t seq = (int64_t)it * n_gt + j;
+            const int j0 = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
+            for (int jj = 0; jj < n_gt; ++jj) {
+                const int j = (j0 + jj) % n_gt;
+                const int64_t seq = (int64_t)it * n_gt + jj;
                 const int s = (int)(seq % STAGES);
                 const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
                 if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag)) { ok = false; break; }
@@ -324,8 +328,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             if (!mbar_wait(bar(Y_FULL + yb), (it / YBUF) & 1, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const uint32_t a0 = sbase + L::kOffY + yb * L::kYBytes;
-            for (int j = 0; j < n_gt; ++j) {
-                const int64_t seq = (int64_t)it * n_gt + j;
+            for (int jj = 0; jj < n_gt; ++jj) {
+                const int64_t seq = (int64_t)it * n_gt + jj;
                 const int s = (int)(seq % STAGES);
                 const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
                 const int ab = (int)(seq & 1);
@@ -382,8 +386,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 vals[t] = seed;
                 idx[t] = INT32_MAX;
             }
-            for (int j = 0; ok && j < n_gt; ++j) {
-                const int64_t seq = (int64_t)it * n_gt + j;
+            const int j0 = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
+            for (int jj = 0; ok && jj < n_gt; ++jj) {
+                const int j = (j0 + jj) % n_gt;
+                const int64_t seq = (int64_t)it * n_gt + jj;
                 const int ab = (int)(seq & 1);
                 const uint32_t aph = (uint32_t)((seq >> 1) & 1);
                 bool w_ok = mbar_wait(bar(T_FULL + ab), aph, abort_flag);
@@ -459,7 +465,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 
 template <int K, int TOPK, int STAGES, int YBUF>
 void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
-                const float* tau0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status,
+                const float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status,
                 int n_sm, cudaStream_t st) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
@@ -468,19 +474,20 @@ void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, con
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
-    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, n_tiles, G, G_pad,
-                                                                   cv, ci, status);
+    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles,
+                                                                   G, G_pad, cv, ci, status);
 }
 
 }  // namespace
 
 bool launch_screen(int K, int topk, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
-                   const float* tau0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status, int n_sm,
+                   const float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv,
+                   int32_t* ci, int* status, int n_sm,
                    cudaStream_t st) {
     if (n_tiles <= 0) return true;
 #define FC_SCREEN_CASE(KK, TT, SS, YY)                                                                    \
     if (K == KK && topk == TT) {                                                                          \
-        run_screen<KK, TT, SS, YY>(Yt, Bt, Qb3, tile_slot, tau0, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
+        run_screen<KK, TT, SS, YY>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
         return true;                                                                                      \
     }
     FC_SCREEN_CASE(16, 8, 4, 2)
