@@ -190,6 +190,27 @@ FC_API fc_status fc_poll(fc_ctx* ctx, uint64_t ticket, double* latency_ms);
 /* Cancel a queued or running job; it finishes with FC_ERR_CANCELLED. */
 FC_API fc_status fc_cancel(fc_ctx* ctx, uint64_t ticket);
 
+/* Fake data exactly as fc_fake_data produces it, for callers that cannot
+ * allocate device memory when they need it: work recorded into a CUDA graph by
+ * stream capture, code running inside another framework's allocator callback,
+ * or request paths that must not allocate after start-up.  The paper has no
+ * counterpart; it is a deployment variant of §2 step 2.
+ * All pointers are device memory: S [G][N_full] float64, collapse [N_full]
+ * int32 (NULL = identity, then N_fit == N_full), F [N_full][N_full] float64,
+ * ps [P] int64, output d [P][U][N_fit] float32.  Work runs on cuda_stream
+ * (NULL = legacy default stream); the call returns after it finished.
+ * No cudaMalloc / cudaFree: the only scratch is a 16 MiB file-scope device
+ * array held by every device that loads the library until the process exits.
+ * Limit: 256 + P * N_full^2 * 12 + P * N_full * 4 <= 16 MiB (e.g. P <= 172
+ * points at N_full = 90); larger P gives FC_ERR_ARG -- split the points.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * race.  Errors: FC_ERR_ARG, FC_ERR_NOT_SPD, FC_ERR_CUDA (fc_last_error(NULL)). */
+FC_API fc_status fc_fake_data_noalloc(const double* S, int64_t G, int32_t N_full, const int32_t* collapse,
+                                      int32_t N_fit, const double* F, const int64_t* ps, int32_t P, uint64_t seed,
+                                      int32_t U, int32_t fluct, float* d, void* cuda_stream);
+
 /* Counters of the last synchronous run on this context. */
 FC_API fc_status fc_get_stats(fc_ctx* ctx, fc_stats* out);
 

@@ -27,7 +27,7 @@ _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_
 
 EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set_frac_cov", "fc_unload_grid",
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
-           "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error"]
+           "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc"]
 
 
 class FCError(RuntimeError):
@@ -97,6 +97,7 @@ def load(build: bool = False):
         "fc_cancel": (st, [vp, u64]),
         "fc_get_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
         "fc_last_error": (ctypes.c_char_p, [vp]),
+        "fc_fake_data_noalloc": (st, [vp, i64, i32, vp, i32, vp, vp, i32, u64, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -274,6 +275,18 @@ def fc_get_stats(ctx) -> dict:
     s = fc_stats()
     _check(load().fc_get_stats(ctx, ctypes.byref(s)), ctx)
     return s.as_dict()
+
+
+def fc_fake_data_noalloc(S, F, ps, seed: int, U: int, d, collapse=None, n_fit: int | None = None,
+                         fluct: int = FC_FLUCT_POISSON_SYS, cuda_stream: int | None = None):
+    """Fake data into the caller's device buffer d [P][U][N_fit] without any device allocation.
+
+    S, F, ps, collapse and d must be CUDA tensors (device memory)."""
+    G, nf = int(S.shape[0]), int(S.shape[1])
+    nfit = nf if n_fit is None else int(n_fit)
+    _check(load().fc_fake_data_noalloc(_ptr(S), G, nf, _ptr(collapse), nfit, _ptr(F), _ptr(ps), int(ps.shape[0]),
+                                       seed, U, fluct, _ptr(d), cuda_stream))
+    return d
 
 
 def fc_last_error(ctx=None) -> str:

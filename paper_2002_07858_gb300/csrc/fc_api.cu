@@ -34,8 +34,12 @@ using namespace fcdev;
 std::atomic<long long> fcdev::g_launches{0};
 
 namespace {
-
 thread_local std::string t_last_error;
+}  // namespace
+
+void fcdev::record_error(const char* msg) { t_last_error = msg ? msg : ""; }
+
+namespace {
 
 fc_status fail(fc_status st, const std::string& msg) {
     t_last_error = msg;

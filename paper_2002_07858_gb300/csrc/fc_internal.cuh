@@ -7,6 +7,9 @@
 
 namespace fcdev {
 
+// Message returned by fc_last_error() for the calling thread.
+void record_error(const char* msg);
+
 // Number of kernels this library has launched (for the launch count of a run).
 extern std::atomic<long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
