@@ -536,11 +536,13 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                          g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
             FC_TRY(stage_end(c, &c->stats.ms_prep));
             stage_begin(c);
-            if (!launch_screen(g->K, topk, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G, g->G_pad, cval, cidx,
-                               c->status_dev, c->n_sm, c->stream))
-                return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
+            for (int pass = 0; pass < 2; ++pass)
+                if (!launch_screen(g->K, topk, pass == 0, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
+                                   g->G_pad, cval, cidx, c->status_dev, g->Qc, g->Qb, g->nrm, alpha, g->Sc32,
+                                   g->nfit, c->n_sm, c->stream))
+                    return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
             FC_TRY(stage_end(c, &c->stats.ms_screen));
-            c->stats.screen_launches += 1;
+            c->stats.screen_launches += 2;
             c->stats.screen_flops += 2.0 * g->nfit * (double)n_active * (double)g->G;
             ResolveArgs ra;
             ra.tile_slot = tslot;

@@ -81,11 +81,14 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
                   const float* Sc32, const float* nrm, const float* Qc, const float* Qb, int64_t G_pad,
                   uint16_t* Ytiles, float* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st);
-// returns false if the padded K has no compiled screen instance
-bool launch_screen(int K, int topk, const uint16_t* Ytiles, const uint16_t* Btiles, const uint16_t* Qb3,
-                   const int32_t* tile_slot, const float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
-                   int64_t G_pad, float* cand_val,
-                   int32_t* cand_idx, int* status, int n_sm, cudaStream_t st);
+// Tensor-core screen of BM-row tiles (see fc_screen.cu).  min_only = the first
+// pass, which tightens tau0 in place; otherwise the top-k pass.  Returns false
+// if the padded K has no compiled instance.
+bool launch_screen(int K, int topk, bool min_only, const uint16_t* Ytiles, const uint16_t* Btiles,
+                   const uint16_t* Qb3, const int32_t* tile_slot, float* tau0, const int32_t* tile_j0,
+                   int64_t n_tiles, int64_t G, int64_t G_pad, float* cand_val, int32_t* cand_idx, int* status,
+                   const float* Qc, const float* Qb, const float* nrm, const float* alpha, const float* Sc32,
+                   int nfit, int n_sm, cudaStream_t st);
 // Resolution of one mixed-path scan per screen tile (see k_resolve).
 struct ResolveArgs {
     const int32_t* tile_slot;

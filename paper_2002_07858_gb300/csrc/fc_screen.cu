@@ -199,6 +199,63 @@ __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[T
     }
 }
 
+// Screen modes: the first pass (MIN_ONLY) uses only the hi*hi products, keeps
+// each row's minimum and turns it into a certified upper bound that tightens
+// the row's seed tau0 in place; the second pass keeps the full top-k.
+struct ProbeArgs {
+    const float* Qc;
+    const float* Qb;
+    const float* nrm;
+    const float* alpha;
+    const float* Sc32;
+    int nfit;
+};
+
+// First pass: running minimum of a row.  The index is recovered only when the
+// chunk improves the minimum (rare after the first tiles).
+__device__ __forceinline__ void min_chunk(float& bv, int32_t& bi, const uint32_t (&r)[32], int64_t g0, int64_t G) {
+    float m = __uint_as_float(r[0]);
+#pragma unroll
+    for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
+    if (m < bv) {
+        int ii = 31;
+#pragma unroll
+        for (int i = 31; i >= 0; --i) ii = (__uint_as_float(r[i]) == m) ? i : ii;
+        if (g0 + ii < G) {
+            bv = m;
+            bi = (int32_t)(g0 + ii);
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t ytile_elem(int64_t t, int r, int c, int K) {
+    return t * (int64_t)(2 * K * kBM) + (int64_t)(c >> 3) * (kBM * 8) + (r >> 3) * 64 + (r & 7) * 8 + (c & 7);
+}
+
+// Certified upper bound of sigma_g = chi2_g - c_u for one row at grid point g:
+// sigma^ = q^_g + Y.s~_g in binary32 with Y = hi + lo from the row's A image
+// (|Y_hl - Y| <= 2^-16 |Y|, inside alpha), plus every error term of the screen.
+__device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item, int row, int slot, int32_t g,
+                                   int64_t G_pad, const ProbeArgs& pa) {
+    const int n = pa.nfit;
+    const int K = ((n + 1 + 15) / 16) * 16;
+    const float* sg = pa.Sc32 + (int64_t)g * n;
+    float dot = 0.0f, adot = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        const float h = __uint_as_float((uint32_t)Yt[ytile_elem(item, row, i, K)] << 16);
+        const float l = __uint_as_float((uint32_t)Yt[ytile_elem(item, row, K + i, K)] << 16);
+        const float y = h + l;
+        dot = fmaf(y, sg[i], dot);
+        adot = fmaf(fabsf(y), fabsf(sg[i]), adot);
+    }
+    const int64_t qi = (int64_t)slot * G_pad + g;
+    const float qc = pa.Qc[qi];
+    const float sig = qc + dot;
+    const float eps = pa.alpha[item * kBM + row] * pa.nrm[g] + (qc - pa.Qb[qi]) +
+                      (float)(n + 2) * 5.9604645e-08f * (adot + fabsf(qc)) + 1.1920929e-07f * (fabsf(sig) + 1.0f);
+    return (sig + 2.0f * eps) * 1.0000005f + 1.0e-6f + 4.7683716e-07f * fabsf(sig);
+}
+
 constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
 constexpr int kEpiWarps = 8;
 constexpr int kHalfCols = kBN / 2;
@@ -222,12 +279,12 @@ struct ScreenSmem {
     static constexpr uint32_t kBytes = kOffBar + kNumBars * 8 + 16 + 1024;
 };
 
-template <int K, int TOPK, int STAGES, int YBUF>
+template <int K, int TOPK, int STAGES, int YBUF, bool MIN_ONLY>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
-             const int32_t* __restrict__ tile_slot, const float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
+             const int32_t* __restrict__ tile_slot, float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
              int64_t n_tiles, int64_t G, int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
-             int* __restrict__ status) {
+             int* __restrict__ status, ProbeArgs pa) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
@@ -349,8 +406,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                     const uint64_t b_hi = smem_desc(b0 + (2 * kk) * L::kBChunk, L::kBChunk, 128);
                     const uint64_t b_lo = smem_desc(b0 + (K / 8 + 2 * kk) * L::kBChunk, L::kBChunk, 128);
                     mma_bf16(d, a_hi, b_hi, 1u);
-                    mma_bf16(d, a_lo, b_hi, 1u);
-                    mma_bf16(d, a_hi, b_lo, 1u);
+                    if (!MIN_ONLY) {
+                        mma_bf16(d, a_lo, b_hi, 1u);
+                        mma_bf16(d, a_hi, b_lo, 1u);
+                    }
                 }
                 mma_commit(bar(B_EMPTY + s));
                 mma_commit(bar(T_FULL + ab));
@@ -386,6 +445,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 vals[t] = seed;
                 idx[t] = INT32_MAX;
             }
+            float bv = FLT_MAX;       // MIN_ONLY: running minimum of the row and its index
+            int32_t bi = INT32_MAX;
             const int j0 = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
             for (int jj = 0; ok && jj < n_gt; ++jj) {
                 const int j = (j0 + jj) % n_gt;
@@ -402,48 +463,70 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 const uint32_t tb = tmem_base + lane_base + (uint32_t)(ab * kBN + half * kHalfCols);
                 const int64_t g0 = (int64_t)j * kBN + half * kHalfCols;
                 uint32_t ra[32], rb[32];
+                auto chunk = [&](const uint32_t(&r)[32], int64_t gc) {
+                    if (MIN_ONLY)
+                        min_chunk(bv, bi, r, gc, G);
+                    else
+                        topk_chunk<TOPK>(vals, idx, r, gc, G, scratch, lane);
+                };
                 tmem_ld32(tb + 0, ra);
                 tmem_wait(ra);
                 tmem_ld32(tb + 32, rb);
-                topk_chunk<TOPK>(vals, idx, ra, g0 + 0, G, scratch, lane);
+                chunk(ra, g0 + 0);
                 __syncwarp();
                 tmem_wait(rb);
                 tmem_ld32(tb + 64, ra);
-                topk_chunk<TOPK>(vals, idx, rb, g0 + 32, G, scratch, lane);
+                chunk(rb, g0 + 32);
                 __syncwarp();
                 tmem_wait(ra);
                 tmem_ld32(tb + 96, rb);
-                topk_chunk<TOPK>(vals, idx, ra, g0 + 64, G, scratch, lane);
+                chunk(ra, g0 + 64);
                 __syncwarp();
                 tmem_wait(rb);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(T_EMPTY + ab));
-                topk_chunk<TOPK>(vals, idx, rb, g0 + 96, G, scratch, lane);
+                chunk(rb, g0 + 96);
                 __syncwarp();
             }
             // both halves of a row reach here even after a timeout, so the pair barrier cannot hang
             if (half == 1) {
+                if (MIN_ONLY) {
+                    mval[lane] = bv;
+                    midx[lane] = bi;
+                } else {
 #pragma unroll
-                for (int t = 0; t < TOPK; ++t) {
-                    mval[t * 32 + lane] = vals[t];
-                    midx[t * 32 + lane] = idx[t];
+                    for (int t = 0; t < TOPK; ++t) {
+                        mval[t * 32 + lane] = vals[t];
+                        midx[t * 32 + lane] = idx[t];
+                    }
                 }
             }
             named_bar(1 + quad, 64);
             if (half == 0) {
-#pragma unroll 1
-                for (int t = 0; t < TOPK; ++t) {
-                    const float x = mval[t * 32 + lane];
-                    const int32_t xi = midx[t * 32 + lane];
-                    if (x < vals[TOPK - 1] || (x == vals[TOPK - 1] && xi < idx[TOPK - 1]))
-                        topk_insert<TOPK>(vals, idx, x, xi);
-                }
                 const int64_t orow = item * kBM + row;
+                if (MIN_ONLY) {
+                    const float x = mval[lane];
+                    const int32_t xi = midx[lane];
+                    if (x < bv || (x == bv && xi < bi)) {
+                        bv = x;
+                        bi = xi;
+                    }
+                    if (ok && bi != INT32_MAX && seed > -FLT_MAX)
+                        tau0[orow] = fminf(seed, probe_upper_bound(Yt, item, row, tile_slot[item], bi, G_pad, pa));
+                } else {
+#pragma unroll 1
+                    for (int t = 0; t < TOPK; ++t) {
+                        const float x = mval[t * 32 + lane];
+                        const int32_t xi = midx[t * 32 + lane];
+                        if (x < vals[TOPK - 1] || (x == vals[TOPK - 1] && xi < idx[TOPK - 1]))
+                            topk_insert<TOPK>(vals, idx, x, xi);
+                    }
 #pragma unroll
-                for (int t = 0; t < TOPK; ++t) {
-                    cand_val[orow * TOPK + t] = vals[t];
-                    cand_idx[orow * TOPK + t] = (idx[t] == INT32_MAX) ? -1 : idx[t];
+                    for (int t = 0; t < TOPK; ++t) {
+                        cand_val[orow * TOPK + t] = vals[t];
+                        cand_idx[orow * TOPK + t] = (idx[t] == INT32_MAX) ? -1 : idx[t];
+                    }
                 }
             }
             named_bar(1 + quad, 64);
@@ -463,32 +546,38 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     }
 }
 
-template <int K, int TOPK, int STAGES, int YBUF>
-void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
-                const float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int* status,
-                int n_sm, cudaStream_t st) {
+template <int K, int TOPK, int STAGES, int YBUF, bool MIN_ONLY>
+void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot, float* tau0,
+                const int32_t* tile_j0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci,
+                int* status, const ProbeArgs& pa, int n_sm, cudaStream_t st) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
-    auto kern = k_screen<K, TOPK, STAGES, YBUF>;
+    auto kern = k_screen<K, TOPK, STAGES, YBUF, MIN_ONLY>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
     kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles,
-                                                                   G, G_pad, cv, ci, status);
+                                                                   G, G_pad, cv, ci, status, pa);
 }
 
 }  // namespace
 
-bool launch_screen(int K, int topk, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot,
-                   const float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv,
-                   int32_t* ci, int* status, int n_sm,
-                   cudaStream_t st) {
+bool launch_screen(int K, int topk, bool min_only, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
+                   const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
+                   int64_t G_pad, float* cv, int32_t* ci, int* status, const float* Qc, const float* Qb,
+                   const float* nrm, const float* alpha, const float* Sc32, int nfit, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
-#define FC_SCREEN_CASE(KK, TT, SS, YY)                                                                    \
-    if (K == KK && topk == TT) {                                                                          \
-        run_screen<KK, TT, SS, YY>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, status, n_sm, st); \
-        return true;                                                                                      \
+    const ProbeArgs pa{Qc, Qb, nrm, alpha, Sc32, nfit};
+#define FC_SCREEN_CASE(KK, TT, SS, YY)                                                                          \
+    if (K == KK && topk == TT) {                                                                                \
+        if (min_only)                                                                                           \
+            run_screen<KK, TT, SS, YY, true>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci,  \
+                                             status, pa, n_sm, st);                                             \
+        else                                                                                                    \
+            run_screen<KK, TT, SS, YY, false>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, \
+                                              status, pa, n_sm, st);                                            \
+        return true;                                                                                            \
     }
     FC_SCREEN_CASE(16, 8, 4, 2)
     FC_SCREEN_CASE(32, 8, 3, 2)
