@@ -84,7 +84,8 @@ typedef struct {
     int64_t distinct_cov;     /* covariances built and inverted                       */
     int64_t screened;         /* universe-scans decided by the tensor-core screen     */
     int64_t rescored;         /* universe-scans that needed binary64 rescoring        */
-    int64_t fallback;         /* universe-scans whose certificate failed -> fp64 scan */
+    int64_t rescreened;       /* universe-scans whose first certificate failed -> second screen round */
+    int64_t fallback;         /* universe-scans whose certificates failed twice -> exact fp64 scan */
     int64_t kernel_launches;  /* CUDA kernels launched by the call                    */
     int64_t screen_launches;  /* launches of the tensor-core screen kernel             */
     double  screen_flops;     /* algorithmic flops of those launches: 2 N_fit per eval */

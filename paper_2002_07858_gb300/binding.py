@@ -44,7 +44,7 @@ class fc_opts(ctypes.Structure):
 class fc_stats(ctypes.Structure):
     _fields_ = [("universes", ctypes.c_int64), ("scans", ctypes.c_int64), ("chi2_evals", ctypes.c_int64),
                 ("distinct_cov", ctypes.c_int64), ("screened", ctypes.c_int64), ("rescored", ctypes.c_int64),
-                ("fallback", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("rescreened", ctypes.c_int64), ("fallback", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("screen_launches", ctypes.c_int64), ("screen_flops", ctypes.c_double)] + [
         (n, ctypes.c_double) for n in ("ms_fake", "ms_cov", "ms_prep", "ms_screen", "ms_rescore", "ms_fallback",
                                        "ms_scan64", "ms_finish", "ms_total")]

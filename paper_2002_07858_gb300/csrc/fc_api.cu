@@ -443,7 +443,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
     FC_TRY(scratch(c, "cnts", 8, &cnts));
     launch_iota_i32(active, n, c->stream);
     int64_t n_active = n;
-    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 3 * sizeof(unsigned long long), c->stream));
+    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 6 * sizeof(unsigned long long), c->stream));
     // exact binary64 scan for `list`, then advance / finish them
     auto exact_scan = [&](const int32_t* list, int64_t cnt, int scan_no) -> fc_status {
         std::vector<int32_t> fq;
@@ -502,86 +502,110 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
         FC_TRY(stage_end(c, &c->stats.ms_cov));
         c->stats.chi2_evals += n_active * g->G;
         c->stats.scans += n_active;
-        FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 12, c->stream));  // n_fb, n_next, n_fin
+        FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 20, c->stream));  // n_fb, n_next, n_fin, n_fb2, n_tiles2
         if (!mixed) {
             FC_TRY(exact_scan(active, n_active, scan_no));
         } else {
-            const int64_t n_slots = g->n_slots;
-            const int64_t max_tiles = n_active / kBM + std::min<int64_t>(n_slots, n_active) + 1;
-            int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
-                    *fb = nullptr;
-            uint16_t* Yt = nullptr;
-            float *alpha = nullptr, *cval = nullptr, *tau0 = nullptr;
-            int32_t* cidx = nullptr;
-            FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
-            FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
-            FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
-            FC_TRY(scratch(c, "tslot", (size_t)max_tiles, &tslot));
-            FC_TRY(scratch(c, "tuniv", (size_t)max_tiles * kBM, &tuniv));
-            FC_TRY(scratch(c, "Yt", (size_t)max_tiles * kBM * 2 * g->K, &Yt));
-            FC_TRY(scratch(c, "alpha", (size_t)max_tiles * kBM, &alpha));
-            FC_TRY(scratch(c, "tau0", (size_t)max_tiles * kBM, &tau0));
-            int32_t* tj0 = nullptr;
-            FC_TRY(scratch(c, "tile_j0", (size_t)max_tiles, &tj0));
-            FC_TRY(scratch(c, "cval", (size_t)max_tiles * kBM * topk, &cval));
-            FC_TRY(scratch(c, "cidx", (size_t)max_tiles * kBM * topk, &cidx));
+            int32_t *fb = nullptr, *fb2 = nullptr, *fslot = nullptr;
+            float* thr = nullptr;
             FC_TRY(scratch(c, "fb", (size_t)n_active, &fb));
-            stage_begin(c);
-            launch_group(active, n_active, uslot, (int)n_slots, tcnt, tbase, tfill, cnts, tslot, tuniv, max_tiles,
-                         c->stream);
-            int32_t n_tiles = 0;
-            FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts, 4, cudaMemcpyDeviceToHost, c->stream));
-            FC_TRY(sync(c));
-            launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32, g->nrm,
-                         g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
-            FC_TRY(stage_end(c, &c->stats.ms_prep));
-            stage_begin(c);
-            for (int pass = 0; pass < 2; ++pass)
-                if (!launch_screen(g->K, topk, pass == 0, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
-                                   g->G_pad, cval, cidx, c->status_dev, g->Qc, g->Qb, g->nrm, alpha, g->Sc32,
-                                   g->nfit, c->n_sm, c->stream))
-                    return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
-            FC_TRY(stage_end(c, &c->stats.ms_screen));
-            c->stats.screen_launches += 2;
-            c->stats.screen_flops += 2.0 * g->nfit * (double)n_active * (double)g->G;
-            ResolveArgs ra;
-            ra.tile_slot = tslot;
-            ra.tile_univ = tuniv;
-            ra.topk = topk;
-            ra.cval = cval;
-            ra.cidx = cidx;
-            ra.alpha = alpha;
-            ra.nrm = g->nrm;
-            ra.Qc = g->Qc;
-            ra.Qb = g->Qb;
-            ra.G_pad = g->G_pad;
-            ra.d = d;
-            ra.centre = g->centre;
-            ra.S_fit = g->S_fit;
-            ra.nfit = g->nfit;
-            ra.W64 = g->W64;
-            ra.cur = cur;
-            ra.p_of = p_of;
-            ra.U = U;
-            ra.scan_no = scan_no;
-            ra.max_iter = max_iter;
-            ra.best = best32;
-            ra.nscan = nscan;
-            ra.dchi2 = dchi2;
-            ra.chi2min = chi2min;
-            ra.next = next;
-            ra.n_next = cnts + 2;
-            ra.fb = fb;
-            ra.n_fb = cnts + 1;
-            ra.counters = c->counters_dev;
-            stage_begin(c);
-            launch_resolve(ra, n_tiles, c->stream);
-            FC_TRY(stage_end(c, &c->stats.ms_rescore));
-            FC_TRY(check_status(c));
+            FC_TRY(scratch(c, "fb2", (size_t)n_active, &fb2));
+            FC_TRY(scratch(c, "fbslot", (size_t)n_active, &fslot));
+            FC_TRY(scratch(c, "thr", (size_t)n, &thr));
+            // one certified screen round over `list` (grouped into tiles by covariance slot)
+            auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
+                                    int32_t* fb_out, int32_t* n_fb_out) -> fc_status {
+                const int64_t n_slots = g->n_slots;
+                const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
+                const std::string sfx = round ? "2" : "";
+                int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
+                        *tj0 = nullptr, *cidx = nullptr;
+                uint16_t* Yt = nullptr;
+                float *alpha = nullptr, *cval = nullptr, *tau0 = nullptr;
+                FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
+                FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
+                FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
+                FC_TRY(scratch(c, ("tslot" + sfx).c_str(), (size_t)max_tiles, &tslot));
+                FC_TRY(scratch(c, ("tuniv" + sfx).c_str(), (size_t)max_tiles * kBM, &tuniv));
+                FC_TRY(scratch(c, ("Yt" + sfx).c_str(), (size_t)max_tiles * kBM * 2 * g->K, &Yt));
+                FC_TRY(scratch(c, ("alpha" + sfx).c_str(), (size_t)max_tiles * kBM, &alpha));
+                FC_TRY(scratch(c, ("tau0" + sfx).c_str(), (size_t)max_tiles * kBM, &tau0));
+                FC_TRY(scratch(c, ("tile_j0" + sfx).c_str(), (size_t)max_tiles, &tj0));
+                FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * rtopk, &cval));
+                FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * rtopk, &cidx));
+                stage_begin(c);
+                launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
+                             c->stream);
+                int32_t n_tiles = 0;
+                FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
+                FC_TRY(sync(c));
+                launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
+                             g->nrm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
+                if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
+                FC_TRY(stage_end(c, &c->stats.ms_prep));
+                stage_begin(c);
+                // round 0: min-only pass to tighten the seeds, then the top-k pass; round 1 is seeded already
+                for (int pass = round ? 1 : 0; pass < 2; ++pass) {
+                    if (!launch_screen(g->K, rtopk, pass == 0, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
+                                       g->G_pad, cval, cidx, c->status_dev, g->Qc, g->Qb, g->nrm, alpha, g->Sc32,
+                                       g->nfit, c->n_sm, c->stream))
+                        return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
+                    c->stats.screen_launches += 1;
+                }
+                FC_TRY(stage_end(c, &c->stats.ms_screen));
+                c->stats.screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
+                ResolveArgs ra;
+                ra.tile_slot = tslot;
+                ra.tile_univ = tuniv;
+                ra.topk = rtopk;
+                ra.cval = cval;
+                ra.cidx = cidx;
+                ra.alpha = alpha;
+                ra.nrm = g->nrm;
+                ra.Qc = g->Qc;
+                ra.Qb = g->Qb;
+                ra.G_pad = g->G_pad;
+                ra.d = d;
+                ra.centre = g->centre;
+                ra.S_fit = g->S_fit;
+                ra.nfit = g->nfit;
+                ra.W64 = g->W64;
+                ra.cur = cur;
+                ra.p_of = p_of;
+                ra.U = U;
+                ra.scan_no = scan_no;
+                ra.max_iter = max_iter;
+                ra.best = best32;
+                ra.nscan = nscan;
+                ra.dchi2 = dchi2;
+                ra.chi2min = chi2min;
+                ra.next = next;
+                ra.n_next = cnts + 2;
+                ra.fb = fb_out;
+                ra.n_fb = n_fb_out;
+                ra.counters = c->counters_dev + 3 * round;
+                ra.thr = round ? nullptr : thr;
+                stage_begin(c);
+                launch_resolve(ra, n_tiles, c->stream);
+                FC_TRY(stage_end(c, &c->stats.ms_rescore));
+                return check_status(c);
+            };
+            FC_TRY(screen_round(0, active, n_active, uslot, topk, fb, cnts + 1));
             int32_t n_fb = 0;
             FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
             FC_TRY(sync(c));
-            if (n_fb > 0) FC_TRY(exact_scan(fb, n_fb, scan_no));
+            if (n_fb > 0) {
+                // second certified round for the universes whose certificate failed
+                if (o.cov == FC_COV_IDENTITY)
+                    launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
+                else
+                    launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
+                FC_TRY(screen_round(1, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4));
+                int32_t n_fb2 = 0;
+                FC_CUDA(cudaMemcpyAsync(&n_fb2, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
+                FC_TRY(sync(c));
+                if (n_fb2 > 0) FC_TRY(exact_scan(fb2, n_fb2, scan_no));
+            }
         }
         int32_t n_next = 0;
         FC_CUDA(cudaMemcpyAsync(&n_next, cnts + 2, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -591,12 +615,13 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
         n_active = n_next;
         FC_TRY(check_status(c));
     }
-    unsigned long long cn[3] = {0, 0, 0};
+    unsigned long long cn[6] = {0, 0, 0, 0, 0, 0};
     FC_CUDA(cudaMemcpyAsync(cn, c->counters_dev, sizeof(cn), cudaMemcpyDeviceToHost, c->stream));
     FC_TRY(sync(c));
-    c->stats.screened += (int64_t)cn[0];
-    c->stats.rescored += (int64_t)cn[1];
-    c->stats.fallback += (int64_t)cn[2];
+    c->stats.screened += (int64_t)(cn[0] + cn[3]);
+    c->stats.rescored += (int64_t)(cn[1] + cn[4]);
+    c->stats.rescreened += (int64_t)cn[2];
+    c->stats.fallback += (int64_t)cn[5];
     return FC_OK;
 }
 
@@ -789,7 +814,7 @@ fc_status fc_create(fc_ctx** out, int device, size_t hbm_budget_bytes, void* cud
     FC_CUDA(cudaEventCreate(&c->ev_a));
     FC_CUDA(cudaEventCreate(&c->ev_b));
     FC_TRY(dalloc_t(c.get(), &c->status_dev, 1));
-    FC_TRY(dalloc_t(c.get(), &c->counters_dev, 4));
+    FC_TRY(dalloc_t(c.get(), &c->counters_dev, 8));
     FC_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream));
     FC_CUDA(cudaStreamSynchronize(c->stream));
     *out = c.release();

@@ -118,8 +118,11 @@ struct ResolveArgs {
     int32_t* n_next;
     int32_t* fb;           // fallback list
     int32_t* n_fb;
-    unsigned long long* counters;  // screened, rescored, fallback
+    unsigned long long* counters;  // screened, rescored, handed on
+    float* thr;            // [n] nullable: for handed-on universes, an upper bound of min_g (chi2_g - c_u)
 };
+// tau0[row] = min(tau0[row], thr[u]) for the rows of the tiles
+void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st);
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st);
 
 // ---- final residual-form chi2 and dchi2 ----

@@ -852,11 +852,19 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         } else {
             state = 3;
             atomicAdd(&s_cnt[2], 1);
+            // every grid point that can still be the minimum has LB <= sigma* = chi2_min - c_u of the
+            // best candidate found: a second screen seeded with sigma* (rounded up) lists all of them
+            if (a.thr) {
+                const double cu = s_res[r][kItemCu];
+                const double sig = (bchi - cu) + 1e-9 * (fabs(bchi) + fabs(cu));
+                a.thr[u] = __double2float_ru(sig) + 4.7683716e-07f * (fabsf((float)sig) + 1.0f);
+            }
         }
     } else if (state == 1) {
         atomicAdd(&s_cnt[0], 1);
     } else if (state == 3) {
         atomicAdd(&s_cnt[2], 1);
+        if (a.thr) a.thr[u] = FLT_MAX;
     }
     __syncthreads();
     if (r == 0) s_nitem = 0;
@@ -903,6 +911,14 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         if (a.chi2min) a.chi2min[u] = cmin;
         a.nscan[u] = (int8_t)a.scan_no;
     }
+}
+
+__global__ void k_min_tau(const int32_t* __restrict__ tile_univ, int64_t n_rows, const float* __restrict__ thr,
+                          float* __restrict__ tau0) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    const int u = tile_univ[i];
+    if (u >= 0) tau0[i] = fminf(tau0[i], thr[u]);
 }
 
 // ---------------------------------------------------------- finishing -------
@@ -1156,6 +1172,12 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                                                                                   nfit, K, A32, rho, cur, Sc32, nrm,
                                                                                   Qc, Qb, G_pad, Yt, alpha, tau0,
                                                                                   tile_j0);
+}
+
+void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    count_launch();
+    k_min_tau<<<blocks_for(n_tiles * kBM), kThreads, 0, st>>>(tile_univ, n_tiles * kBM, thr, tau0);
 }
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
