@@ -443,7 +443,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
     FC_TRY(scratch(c, "cnts", 8, &cnts));
     launch_iota_i32(active, n, c->stream);
     int64_t n_active = n;
-    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 6 * sizeof(unsigned long long), c->stream));
+    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 9 * sizeof(unsigned long long), c->stream));
     // exact binary64 scan for `list`, then advance / finish them
     auto exact_scan = [&](const int32_t* list, int64_t cnt, int scan_no) -> fc_status {
         std::vector<int32_t> fq;
@@ -515,9 +515,10 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             // one certified screen round over `list` (grouped into tiles by covariance slot)
             auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
                                     int32_t* fb_out, int32_t* n_fb_out) -> fc_status {
+                const bool listing = (round == 2);
                 const int64_t n_slots = g->n_slots;
                 const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
-                const std::string sfx = round ? "2" : "";
+                const std::string sfx = round ? std::to_string(round + 1) : "";
                 int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
                         *tj0 = nullptr, *cidx = nullptr;
                 uint16_t* Yt = nullptr;
@@ -531,8 +532,11 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 FC_TRY(scratch(c, ("alpha" + sfx).c_str(), (size_t)max_tiles * kBM, &alpha));
                 FC_TRY(scratch(c, ("tau0" + sfx).c_str(), (size_t)max_tiles * kBM, &tau0));
                 FC_TRY(scratch(c, ("tile_j0" + sfx).c_str(), (size_t)max_tiles, &tj0));
-                FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * rtopk, &cval));
-                FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * rtopk, &cidx));
+                const size_t per_row = listing ? 2 * kListCap : rtopk;
+                int32_t* ccount = nullptr;
+                FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cval));
+                FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cidx));
+                FC_TRY(scratch(c, "ccount", (size_t)max_tiles * kBM * 2, &ccount));
                 stage_begin(c);
                 launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
                              c->stream);
@@ -544,11 +548,13 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
                 FC_TRY(stage_end(c, &c->stats.ms_prep));
                 stage_begin(c);
-                // round 0: min-only pass to tighten the seeds, then the top-k pass; round 1 is seeded already
+                // round 0: min-only pass to tighten the seeds, then the top-k pass; later rounds are seeded
+                // already (round 1: top-k, round 2: every point at or below the seed)
                 for (int pass = round ? 1 : 0; pass < 2; ++pass) {
-                    if (!launch_screen(g->K, rtopk, pass == 0, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
-                                       g->G_pad, cval, cidx, c->status_dev, g->Qc, g->Qb, g->nrm, alpha, g->Sc32,
-                                       g->nfit, c->n_sm, c->stream))
+                    const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
+                    if (!launch_screen(g->K, rtopk, mode, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
+                                       g->G_pad, cval, cidx, ccount, c->status_dev, g->Qc, g->Qb, g->nrm, alpha,
+                                       g->Sc32, g->nfit, c->n_sm, c->stream))
                         return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
                     c->stats.screen_launches += 1;
                 }
@@ -584,9 +590,12 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 ra.fb = fb_out;
                 ra.n_fb = n_fb_out;
                 ra.counters = c->counters_dev + 3 * round;
-                ra.thr = round ? nullptr : thr;
+                ra.thr = thr;
                 stage_begin(c);
-                launch_resolve(ra, n_tiles, c->stream);
+                if (listing)
+                    launch_resolve_list(ra, ccount, n_tiles, c->stream);
+                else
+                    launch_resolve(ra, n_tiles, c->stream);
                 FC_TRY(stage_end(c, &c->stats.ms_rescore));
                 return check_status(c);
             };
@@ -604,7 +613,19 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 int32_t n_fb2 = 0;
                 FC_CUDA(cudaMemcpyAsync(&n_fb2, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
                 FC_TRY(sync(c));
-                if (n_fb2 > 0) FC_TRY(exact_scan(fb2, n_fb2, scan_no));
+                if (n_fb2 > 0) {
+                    // third round: list every point that can still be the minimum
+                    if (o.cov == FC_COV_IDENTITY)
+                        launch_fill_i32(fslot, n_fb2, g->ident_slot, c->stream);
+                    else
+                        launch_lookup_slots(fb2, n_fb2, cur, g->slot_of, fslot, c->stream);
+                    FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
+                    FC_TRY(screen_round(2, fb2, n_fb2, fslot, kMaxTopK, fb, cnts + 1));
+                    int32_t n_fb3 = 0;
+                    FC_CUDA(cudaMemcpyAsync(&n_fb3, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+                    FC_TRY(sync(c));
+                    if (n_fb3 > 0) FC_TRY(exact_scan(fb, n_fb3, scan_no));
+                }
             }
         }
         int32_t n_next = 0;
@@ -615,13 +636,14 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
         n_active = n_next;
         FC_TRY(check_status(c));
     }
-    unsigned long long cn[6] = {0, 0, 0, 0, 0, 0};
+    // [0..2] round 1: screened, rescored, handed on; [3..5] round 2 likewise; [6] listed, [7] list overflow
+    unsigned long long cn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     FC_CUDA(cudaMemcpyAsync(cn, c->counters_dev, sizeof(cn), cudaMemcpyDeviceToHost, c->stream));
     FC_TRY(sync(c));
     c->stats.screened += (int64_t)(cn[0] + cn[3]);
-    c->stats.rescored += (int64_t)(cn[1] + cn[4]);
-    c->stats.rescreened += (int64_t)cn[2];
-    c->stats.fallback += (int64_t)cn[5];
+    c->stats.rescored += (int64_t)(cn[1] + cn[4] + cn[6]);
+    c->stats.rescreened += (int64_t)(cn[2] + cn[5]);
+    c->stats.fallback += (int64_t)cn[7];
     return FC_OK;
 }
 
@@ -814,7 +836,7 @@ fc_status fc_create(fc_ctx** out, int device, size_t hbm_budget_bytes, void* cud
     FC_CUDA(cudaEventCreate(&c->ev_a));
     FC_CUDA(cudaEventCreate(&c->ev_b));
     FC_TRY(dalloc_t(c.get(), &c->status_dev, 1));
-    FC_TRY(dalloc_t(c.get(), &c->counters_dev, 8));
+    FC_TRY(dalloc_t(c.get(), &c->counters_dev, 16));
     FC_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->stream));
     FC_CUDA(cudaStreamSynchronize(c->stream));
     *out = c.release();

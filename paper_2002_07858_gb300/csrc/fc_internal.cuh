@@ -81,12 +81,15 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
                   const float* Sc32, const float* nrm, const float* Qc, const float* Qb, int64_t G_pad,
                   uint16_t* Ytiles, float* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st);
-// Tensor-core screen of BM-row tiles (see fc_screen.cu).  min_only = the first
-// pass, which tightens tau0 in place; otherwise the top-k pass.  Returns false
-// if the padded K has no compiled instance.
-bool launch_screen(int K, int topk, bool min_only, const uint16_t* Ytiles, const uint16_t* Btiles,
-                   const uint16_t* Qb3, const int32_t* tile_slot, float* tau0, const int32_t* tile_j0,
-                   int64_t n_tiles, int64_t G, int64_t G_pad, float* cand_val, int32_t* cand_idx, int* status,
+// Tensor-core screen of BM-row tiles (see fc_screen.cu).  mode: kScreenTopK,
+// kScreenMin (first pass; tightens tau0 in place) or kScreenList (every point
+// with LB <= tau0, kListCap per half row; cand_count > kListCap = overflow).
+// Returns false if the padded K has no compiled instance.
+constexpr int kScreenTopK = 0, kScreenMin = 1, kScreenList = 2;
+constexpr int kListCap = 64;
+bool launch_screen(int K, int topk, int mode, const uint16_t* Ytiles, const uint16_t* Btiles, const uint16_t* Qb3,
+                   const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
+                   int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
                    const float* Qc, const float* Qb, const float* nrm, const float* alpha, const float* Sc32,
                    int nfit, int n_sm, cudaStream_t st);
 // Resolution of one mixed-path scan per screen tile (see k_resolve).
@@ -123,6 +126,9 @@ struct ResolveArgs {
 };
 // tau0[row] = min(tau0[row], thr[u]) for the rows of the tiles
 void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st);
+// Third round: binary64 residual chi2 of every listed candidate of each row
+// (complete lists certify the minimum); overflowing rows go to `fb`.
+void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, cudaStream_t st);
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st);
 
 // ---- final residual-form chi2 and dchi2 ----

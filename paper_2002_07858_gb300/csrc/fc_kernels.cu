@@ -913,6 +913,80 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
     }
 }
 
+// Third round: every grid point whose screen lower bound is at or below the
+// row's seed (an upper bound of the minimum) is listed, so the binary64
+// residual-form minimum over a complete list is the minimum of the scan.
+// One warp per row, W in shared memory; lanes split the list, then the first
+// minimum (lowest index among equal values) is taken across the warp.  The row
+// then finishes (dchi2) or advances exactly as in k_resolve; rows whose list
+// overflowed go to the exact scan.
+__global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32_t* __restrict__ cand_count) {
+    extern __shared__ double sW[];
+    const int64_t t = blockIdx.x;
+    const int n = a.nfit;
+    const int slot = a.tile_slot[t];
+    const double* Wg = a.W64 + (size_t)slot * n * n;
+    const bool staged = (n <= kResolveMaxN);
+    if (staged)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sW[e] = Wg[e];
+    __syncthreads();
+    const double* W = staged ? sW : Wg;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < kBM; r += blockDim.x >> 5) {
+        const int u = a.tile_univ[t * kBM + r];
+        if (u < 0) continue;
+        const int64_t row = t * kBM + r;
+        const int n0 = cand_count[row * 2], n1 = cand_count[row * 2 + 1];
+        if (n0 > kListCap || n1 > kListCap || n0 + n1 == 0) {
+            if (lane == 0) {
+                a.fb[atomicAdd(a.n_fb, 1)] = u;
+                atomicAdd(&a.counters[1], 1ull);
+            }
+            continue;
+        }
+        const float* du = a.d + (size_t)u * n;
+        double bv = DBL_MAX;
+        int32_t bg = INT32_MAX;
+        for (int k = lane; k < n0 + n1; k += 32) {
+            const int64_t e = (row * 2 + (k < n0 ? 0 : 1)) * (int64_t)kListCap + (k < n0 ? k : k - n0);
+            const int32_t g = a.cidx[e];
+            const double c = resid_chi2(W, n, a.S_fit + (int64_t)g * n, du);
+            if (c < bv || (c == bv && g < bg)) {
+                bv = c;
+                bg = g;
+            }
+        }
+        warp_argmin(bv, bg);
+        const int32_t cur_u = a.cur[u];
+        const bool finishing = (bg == cur_u) || (a.scan_no >= a.max_iter);
+        if (finishing) {
+            const int p = a.p_of[u / a.U];
+            double cp = 0.0;
+            if (p != bg) {
+                // chi2_p in residual form, rows of W split over the lanes
+                for (int i = lane; i < n; i += 32) {
+                    double tt = 0.0;
+                    for (int j = 0; j <= i; ++j) tt = fma(W[i * n + j], a.S_fit[(int64_t)p * n + j] - (double)du[j], tt);
+                    cp = fma(tt, tt, cp);
+                }
+                cp = warp_sum(cp);
+            }
+            if (lane == 0) {
+                a.best[u] = bg;
+                a.dchi2[u] = (p == bg) ? 0.0 : cp - bv;
+                if (a.chi2min) a.chi2min[u] = bv;
+                a.nscan[u] = (int8_t)a.scan_no;
+                atomicAdd(&a.counters[0], 1ull);
+            }
+        } else if (lane == 0) {
+            a.best[u] = bg;
+            a.cur[u] = bg;
+            a.next[atomicAdd(a.n_next, 1)] = u;
+            atomicAdd(&a.counters[0], 1ull);
+        }
+    }
+}
+
 __global__ void k_min_tau(const int32_t* __restrict__ tile_univ, int64_t n_rows, const float* __restrict__ thr,
                           float* __restrict__ tau0) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1178,6 +1252,13 @@ void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr,
     if (n_tiles <= 0) return;
     count_launch();
     k_min_tau<<<blocks_for(n_tiles * kBM), kThreads, 0, st>>>(tile_univ, n_tiles * kBM, thr, tau0);
+}
+
+void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, cudaStream_t st) {
+    if (n_tiles <= 0) return;
+    const size_t smem = a.nfit <= kResolveMaxN ? (size_t)a.nfit * a.nfit * sizeof(double) : 0;
+    count_launch();
+    k_resolve_list<<<(unsigned)n_tiles, 256, smem, st>>>(a, cand_count);
 }
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {

@@ -199,9 +199,11 @@ __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[T
     }
 }
 
-// Screen modes: the first pass (MIN_ONLY) uses only the hi*hi products, keeps
-// each row's minimum and turns it into a certified upper bound that tightens
-// the row's seed tau0 in place; the second pass keeps the full top-k.
+// Screen modes: kModeMin (first pass) uses only the hi*hi products, keeps each
+// row's minimum and turns it into a certified upper bound that tightens the
+// row's seed tau0 in place; kModeTopK keeps the full top-k; kModeList lists
+// every grid point whose lower bound is at or below the seed (kListCap per
+// half row, the count says whether the list overflowed).
 struct ProbeArgs {
     const float* Qc;
     const float* Qb;
@@ -210,6 +212,34 @@ struct ProbeArgs {
     const float* Sc32;
     int nfit;
 };
+
+constexpr int kModeTopK = 0;
+constexpr int kModeMin = 1;
+constexpr int kModeList = 2;
+
+// List mode: append every value at or below the seed (and its grid index).
+__device__ __forceinline__ void list_chunk(int32_t& n, float* __restrict__ lval, int32_t* __restrict__ lidx, float seed,
+                                           const uint32_t (&r)[32], int64_t g0, int64_t G) {
+    float m = __uint_as_float(r[0]);
+#pragma unroll
+    for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
+    if (m <= seed) {
+        uint32_t mask = 0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) mask |= (__uint_as_float(r[i]) <= seed ? 1u : 0u) << i;
+        const int64_t lim = G - g0;
+        if (lim < 32) mask &= (lim <= 0) ? 0u : ((1u << lim) - 1u);
+        while (mask) {
+            const int i = __ffs(mask) - 1;
+            mask &= mask - 1;
+            if (n < kListCap) {
+                lidx[n] = (int32_t)(g0 + i);
+                lval[n] = m;  // a lower bound of the entry (the chunk minimum); only the index is used
+            }
+            ++n;
+        }
+    }
+}
 
 // First pass: running minimum of a row.  The index is recovered only when the
 // chunk improves the minimum (rare after the first tiles).
@@ -279,12 +309,12 @@ struct ScreenSmem {
     static constexpr uint32_t kBytes = kOffBar + kNumBars * 8 + 16 + 1024;
 };
 
-template <int K, int TOPK, int STAGES, int YBUF, bool MIN_ONLY>
+template <int K, int TOPK, int STAGES, int YBUF, int MODE>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
              const int32_t* __restrict__ tile_slot, float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
              int64_t n_tiles, int64_t G, int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
-             int* __restrict__ status, ProbeArgs pa) {
+             int32_t* __restrict__ cand_count, int* __restrict__ status, ProbeArgs pa) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
@@ -406,7 +436,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                     const uint64_t b_hi = smem_desc(b0 + (2 * kk) * L::kBChunk, L::kBChunk, 128);
                     const uint64_t b_lo = smem_desc(b0 + (K / 8 + 2 * kk) * L::kBChunk, L::kBChunk, 128);
                     mma_bf16(d, a_hi, b_hi, 1u);
-                    if (!MIN_ONLY) {
+                    if (MODE != kModeMin) {
                         mma_bf16(d, a_lo, b_hi, 1u);
                         mma_bf16(d, a_hi, b_lo, 1u);
                     }
@@ -445,8 +475,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 vals[t] = seed;
                 idx[t] = INT32_MAX;
             }
-            float bv = FLT_MAX;       // MIN_ONLY: running minimum of the row and its index
+            float bv = FLT_MAX;       // kModeMin: running minimum of the row and its index
             int32_t bi = INT32_MAX;
+            int32_t nlist = 0;        // kModeList: entries found by this half row
+            const int64_t lbase = ((item * kBM + row) * 2 + half) * (int64_t)kListCap;
             const int j0 = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
             for (int jj = 0; ok && jj < n_gt; ++jj) {
                 const int j = (j0 + jj) % n_gt;
@@ -464,8 +496,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 const int64_t g0 = (int64_t)j * kBN + half * kHalfCols;
                 uint32_t ra[32], rb[32];
                 auto chunk = [&](const uint32_t(&r)[32], int64_t gc) {
-                    if (MIN_ONLY)
+                    if (MODE == kModeMin)
                         min_chunk(bv, bi, r, gc, G);
+                    else if (MODE == kModeList)
+                        list_chunk(nlist, cand_val + lbase, cand_idx + lbase, seed, r, gc, G);
                     else
                         topk_chunk<TOPK>(vals, idx, r, gc, G, scratch, lane);
                 };
@@ -489,9 +523,14 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 chunk(rb, g0 + 96);
                 __syncwarp();
             }
+            if (MODE == kModeList) {
+                cand_count[(item * kBM + row) * 2 + half] = ok ? nlist : kListCap + 1;
+                if (!ok) break;
+                continue;
+            }
             // both halves of a row reach here even after a timeout, so the pair barrier cannot hang
             if (half == 1) {
-                if (MIN_ONLY) {
+                if (MODE == kModeMin) {
                     mval[lane] = bv;
                     midx[lane] = bi;
                 } else {
@@ -505,7 +544,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             named_bar(1 + quad, 64);
             if (half == 0) {
                 const int64_t orow = item * kBM + row;
-                if (MIN_ONLY) {
+                if (MODE == kModeMin) {
                     const float x = mval[lane];
                     const int32_t xi = midx[lane];
                     if (x < bv || (x == bv && xi < bi)) {
@@ -546,38 +585,40 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     }
 }
 
-template <int K, int TOPK, int STAGES, int YBUF, bool MIN_ONLY>
+template <int K, int TOPK, int STAGES, int YBUF, int MODE>
 void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot, float* tau0,
                 const int32_t* tile_j0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci,
-                int* status, const ProbeArgs& pa, int n_sm, cudaStream_t st) {
+                int32_t* cc, int* status, const ProbeArgs& pa, int n_sm, cudaStream_t st) {
     using L = ScreenSmem<K, STAGES, YBUF>;
     static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
-    auto kern = k_screen<K, TOPK, STAGES, YBUF, MIN_ONLY>;
+    auto kern = k_screen<K, TOPK, STAGES, YBUF, MODE>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
     kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles,
-                                                                   G, G_pad, cv, ci, status, pa);
+                                                                   G, G_pad, cv, ci, cc, status, pa);
 }
 
 }  // namespace
 
-bool launch_screen(int K, int topk, bool min_only, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
+bool launch_screen(int K, int topk, int mode, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
                    const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
-                   int64_t G_pad, float* cv, int32_t* ci, int* status, const float* Qc, const float* Qb,
+                   int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const float* Qc, const float* Qb,
                    const float* nrm, const float* alpha, const float* Sc32, int nfit, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
     const ProbeArgs pa{Qc, Qb, nrm, alpha, Sc32, nfit};
-#define FC_SCREEN_CASE(KK, TT, SS, YY)                                                                          \
-    if (K == KK && topk == TT) {                                                                                \
-        if (min_only)                                                                                           \
-            run_screen<KK, TT, SS, YY, true>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci,  \
-                                             status, pa, n_sm, st);                                             \
-        else                                                                                                    \
-            run_screen<KK, TT, SS, YY, false>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, \
-                                              status, pa, n_sm, st);                                            \
-        return true;                                                                                            \
+#define FC_SCREEN_RUN(KK, TT, SS, YY, MM) \
+    run_screen<KK, TT, SS, YY, MM>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, n_sm, st)
+#define FC_SCREEN_CASE(KK, TT, SS, YY)                                   \
+    if (K == KK && topk == TT) {                                         \
+        if (mode == kModeMin)                                            \
+            FC_SCREEN_RUN(KK, TT, SS, YY, kModeMin);                     \
+        else if (mode == kModeList)                                      \
+            FC_SCREEN_RUN(KK, TT, SS, YY, kModeList);                    \
+        else                                                             \
+            FC_SCREEN_RUN(KK, TT, SS, YY, kModeTopK);                    \
+        return true;                                                     \
     }
     FC_SCREEN_CASE(16, 8, 4, 2)
     FC_SCREEN_CASE(32, 8, 3, 2)
@@ -588,6 +629,7 @@ bool launch_screen(int K, int topk, bool min_only, const uint16_t* Yt, const uin
     FC_SCREEN_CASE(48, 16, 3, 1)
     FC_SCREEN_CASE(64, 16, 2, 1)
 #undef FC_SCREEN_CASE
+#undef FC_SCREEN_RUN
     return false;
 }
 
