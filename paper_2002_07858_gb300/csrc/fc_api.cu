@@ -548,9 +548,11 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
                 FC_TRY(stage_end(c, &c->stats.ms_prep));
                 stage_begin(c);
-                // round 0: min-only pass to tighten the seeds, then the top-k pass; later rounds are seeded
-                // already (round 1: top-k, round 2: every point at or below the seed)
-                for (int pass = round ? 1 : 0; pass < 2; ++pass) {
+                // round 0 of the first scan: min-only pass to tighten the seeds (the probe at the true point
+                // is loose there), then the top-k pass.  Later scans probe at the previous minimum, and later
+                // rounds are seeded by the best binary64 value (round 1: top-k, round 2: list).
+                const bool min_pass = (round == 0 && scan_no == 1);
+                for (int pass = min_pass ? 0 : 1; pass < 2; ++pass) {
                     const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
                     if (!launch_screen(g->K, rtopk, mode, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
                                        g->G_pad, cval, cidx, ccount, c->status_dev, g->Qc, g->Qb, g->nrm, alpha,

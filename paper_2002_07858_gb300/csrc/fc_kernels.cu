@@ -638,6 +638,17 @@ __device__ __forceinline__ int64_t ytile_offset(int64_t t, int r, int c, int K) 
     return t * (int64_t)(2 * K * kBM) + (int64_t)(c >> 3) * (kBM * 8) + (r >> 3) * 64 + (r & 7) * 8 + (c & 7);
 }
 
+constexpr int kMaxScreenK = 64;
+
+// element i of a register array of packed bf16 pairs (i a loop index: the
+// compiler resolves the selection with predicated moves, no local memory)
+__device__ __forceinline__ void put_bf16(uint32_t (&w)[kMaxScreenK / 2], int i, uint16_t v) {
+#pragma unroll
+    for (int c = 0; c < kMaxScreenK / 2; ++c) {
+        if (c == (i >> 1)) w[c] = (i & 1) ? ((w[c] & 0x0000FFFFu) | ((uint32_t)v << 16)) : ((w[c] & 0xFFFF0000u) | v);
+    }
+}
+
 // One CTA per tile, one thread per row: y^ = A (d - v) in binary32, Y = -2 y^
 // split into bf16 hi + lo, and the error-bound coefficient alpha in the spare
 // column so that the screen directly yields a lower bound of chi2_g - c_u.
@@ -662,8 +673,23 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     const int u = tile_univ[t * kBM + r];
     // the screen walks this tile's grid tiles starting at the one holding row 0's q
     if (r == 0) tile_j0[t] = (u >= 0) ? cur[u] / kBN : 0;
-    for (int c = 0; c < 2 * K; ++c) Yt[ytile_offset(t, r, c, K)] = 0;
+    // the row's A-image entries, written as 16-byte runs (8 bf16 of one core-matrix row)
+    uint32_t hw[kMaxScreenK / 2], lw[kMaxScreenK / 2];
+#pragma unroll
+    for (int c = 0; c < kMaxScreenK / 2; ++c) hw[c] = lw[c] = 0u;
+    auto store_row = [&]() {
+#pragma unroll
+        for (int c8 = 0; c8 < kMaxScreenK / 8; ++c8) {
+            if (c8 * 8 >= K) break;
+            uint4 vh, vl;
+            vh.x = hw[4 * c8]; vh.y = hw[4 * c8 + 1]; vh.z = hw[4 * c8 + 2]; vh.w = hw[4 * c8 + 3];
+            vl.x = lw[4 * c8]; vl.y = lw[4 * c8 + 1]; vl.z = lw[4 * c8 + 2]; vl.w = lw[4 * c8 + 3];
+            *reinterpret_cast<uint4*>(Yt + ytile_offset(t, r, c8 * 8, K)) = vh;
+            *reinterpret_cast<uint4*>(Yt + ytile_offset(t, r, K + c8 * 8, K)) = vl;
+        }
+    };
     if (u < 0) {
+        store_row();
         alpha[t * kBM + r] = 0.0f;
         tau0[t * kBM + r] = -FLT_MAX;  // padding rows keep no candidate
         return;
@@ -687,8 +713,8 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
         adot = fmaf(fabsf(Y), fabsf(sq[i]), adot);
         const __nv_bfloat16 h = __float2bfloat16_rn(Y);
         const __nv_bfloat16 l = __float2bfloat16_rn(Y - __bfloat162float(h));
-        Yt[ytile_offset(t, r, i, K)] = __bfloat16_as_ushort(h);
-        Yt[ytile_offset(t, r, K + i, K)] = __bfloat16_as_ushort(l);
+        put_bf16(hw, i, __bfloat16_as_ushort(h));
+        put_bf16(lw, i, __bfloat16_as_ushort(l));
     }
     // |computed - exact| of -2 y.s~_g  <=  alpha * |s~_g|:
     //   2 |y - y^| |s~|            with |y - y^| <= (nfit+2) 2^-24 rho |d~|
@@ -698,7 +724,8 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     const float c_split = 3.03f * 1.52587890625e-05f + (float)(3 * K + 2) * 1.1920929e-07f * 1.02f;
     const float a = 1.05f * (2.0f * (float)(nfit + 2) * 5.9604645e-08f * rho[slot] * dn + c_split * yn);
     alpha[t * kBM + r] = a;
-    Yt[ytile_offset(t, r, nfit, K)] = __bfloat16_as_ushort(__float2bfloat16_rd(-a));
+    put_bf16(hw, nfit, __bfloat16_as_ushort(__float2bfloat16_rd(-a)));
+    store_row();
     // probe at q: sigma^ = q^_q + Y.s~_q (binary32), |sigma^ - sigma| <= 2|y - y^||s~_q| + |q^ - q|
     //   + (nfit+1) 2^-24 (sum |Y_i s~_i| + |q^|) + 2^-24 |sigma^|   (all inside eps below)
     const int64_t qi = (int64_t)slot * G_pad + q;
