@@ -1168,7 +1168,8 @@ void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
                    cudaStream_t st) {
     if (n <= 0) return;
-    unsigned gx = blocks_for(G_pad, 128);
+    // ~16 grid points per thread so each block's staging of A is amortised
+    unsigned gx = blocks_for(G_pad, 128 * 16);
     if (gx > 128) gx = 128;
     dim3 grid(gx, n);
     count_launch();
