@@ -449,7 +449,16 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
         std::vector<int32_t> fq;
         int32_t* fslot = nullptr;
         FC_TRY(scratch(c, "fslot", (size_t)cnt, &fslot));
-        if (o.cov == FC_COV_IDENTITY) {
+        if (mixed) {
+            // the mixed path's last resort: residual form for every g, no binary64 q-vectors
+            if (o.cov == FC_COV_IDENTITY)
+                launch_fill_i32(fslot, cnt, g->ident_slot, c->stream);
+            else
+                launch_lookup_slots(list, cnt, cur, g->slot_of, fslot, c->stream);
+            stage_begin(c);
+            launch_scan_resid(list, cnt, fslot, d, g->S_fit, g->G, g->nfit, g->W64, best32, c->stream);
+            FC_TRY(stage_end(c, &c->stats.ms_fallback));
+        } else if (o.cov == FC_COV_IDENTITY) {
             FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
             launch_fill_i32(fslot, cnt, g->ident_slot, c->stream);
         } else {
@@ -465,9 +474,12 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
             launch_lookup_slots(list, cnt, cur, g->slot_of, fslot, c->stream);
         }
-        stage_begin(c);
-        launch_scan64(list, cnt, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32, c->stream);
-        FC_TRY(stage_end(c, mixed ? &c->stats.ms_fallback : &c->stats.ms_scan64));
+        if (!mixed) {
+            stage_begin(c);
+            launch_scan64(list, cnt, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
+                          c->stream);
+            FC_TRY(stage_end(c, &c->stats.ms_scan64));
+        }
         // finishing universes keep cur (the covariance of this scan); others move to their minimum
         launch_advance(list, cnt, best32, cur, nscan, scan_no, max_iter, next, cnts + 2, fin, cnts + 3, c->stream);
         int32_t n_fin = 0;

@@ -72,6 +72,10 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot_of_list,
                    const double* centre, const double* Sc, int64_t G, int nfit, const double* A64,
                    const double* Q64, int64_t ldq, int32_t* best, cudaStream_t st);
 
+// exact residual-form scan (one CTA per listed universe), no q-vectors needed
+void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* Sfit,
+                       int64_t G, int nfit, const double* W64, int32_t* best, cudaStream_t st);
+
 // ---- mixed path: grouping, y prep, screen, decision ----
 // counting sort of active universes by slot into BM-row tiles
 void launch_group(const int32_t* active, int64_t n_active, const int32_t* uslot, int n_slots, int32_t* cnt,

@@ -20,6 +20,7 @@ namespace fcdev {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kResolveMaxN = 64;  // a fit-space matrix is staged in shared memory up to this N_fit
 
 inline unsigned blocks_for(int64_t n, int t = kThreads) {
     int64_t b = (n + t - 1) / t;
@@ -45,6 +46,21 @@ __device__ __forceinline__ void warp_argmin(double& v, int32_t& g) {
             g = og;
         }
     }
+}
+
+// Residual form ||W r||^2, r = s - d, A = W^T W (W lower triangular), binary64.
+__device__ double resid_chi2(const double* __restrict__ W, int n, const double* __restrict__ s,
+                             const float* __restrict__ du) {
+    double r[kMaxBins];
+    for (int j = 0; j < n; ++j) r[j] = s[j] - (double)du[j];
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double* Wi = W + i * n;
+        double t = 0.0;
+        for (int j = 0; j <= i; ++j) t = fma(Wi[j], r[j], t);
+        acc = fma(t, t, acc);
+    }
+    return acc;
 }
 
 // ---------------------------------------------------------------- ingest ---
@@ -165,8 +181,10 @@ __global__ void k_centred(const double* __restrict__ Sfit, const double* __restr
 
 // ------------------------------------------------------------ covariances ---
 
-// Cholesky in place on the lower triangle of a row-major n x n matrix held in
-// global memory; every element's sum runs k = 0..j-1 with separately rounded
+constexpr int kCholSmemN = 110;  // n*n doubles <= 96.8 KB of shared memory
+
+// Cholesky in place on the lower triangle of a row-major n x n matrix (shared
+// or global memory); every element's sum runs k = 0..j-1 with separately rounded
 // multiply and subtract, so the factor is reproducible bit for bit.
 __device__ bool chol_inplace(double* L, int n) {
     __shared__ double s_d;
@@ -204,9 +222,13 @@ __device__ bool chol_inplace(double* L, int n) {
 __global__ void k_chol_sys(const double* __restrict__ S, int nf, const double* __restrict__ F,
                            const int64_t* __restrict__ ps, int gauss, double* __restrict__ L64,
                            float* __restrict__ L32, float* __restrict__ s32, int* __restrict__ status) {
+    extern __shared__ double sL[];
     const int ip = blockIdx.x;
     const double* s = S + ps[ip] * nf;
-    double* L = L64 + (size_t)ip * nf * nf;
+    double* Lg = L64 + (size_t)ip * nf * nf;
+    // factor in shared memory when it fits (the dependent sums then run at shared-memory latency)
+    const bool staged = (nf <= kCholSmemN);
+    double* L = staged ? sL : Lg;
     for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) {
         const int i = e / nf, j = e % nf;
         if (j <= i) {
@@ -218,7 +240,10 @@ __global__ void k_chol_sys(const double* __restrict__ S, int nf, const double* _
     __syncthreads();
     const bool ok = chol_inplace(L, nf);
     if (!ok && threadIdx.x == 0) atomicOr(status, kDevNotSpd);
-    for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) L32[(size_t)ip * nf * nf + e] = __double2float_rn(L[e]);
+    for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) {
+        if (staged) Lg[e] = L[e];
+        L32[(size_t)ip * nf * nf + e] = __double2float_rn(L[e]);
+    }
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s32[(size_t)ip * nf + i] = __double2float_rn(s[i]);
 }
 
@@ -229,18 +254,21 @@ __global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, cons
                             const int32_t* __restrict__ slot_list, int cov_mode, double* __restrict__ A64,
                             double* __restrict__ W64, float* __restrict__ A32, float* __restrict__ rho,
                             double* __restrict__ work, int* __restrict__ status) {
+    extern __shared__ double sLW[];
     const int e0 = blockIdx.x;
     const int q = q_list[e0];
     const int slot = slot_list[e0];
     const int n = nfit;
-    double* L = work + (size_t)e0 * n * n;
-    double* W = W64 + (size_t)slot * n * n;
+    const bool staged = (n <= kResolveMaxN);
+    double* L = staged ? sLW : work + (size_t)e0 * n * n;
+    double* Wg = W64 + (size_t)slot * n * n;
+    double* W = staged ? sLW + n * n : Wg;
     double* A = A64 + (size_t)slot * n * n;
     const double* s = S + (int64_t)q * nf;
     if (cov_mode == 2) {  // identity test mode
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const double v = (e / n == e % n) ? 1.0 : 0.0;
-            W[e] = v;
+            Wg[e] = v;
             A[e] = v;
             A32[(size_t)slot * n * n + e] = (float)v;
         }
@@ -298,6 +326,8 @@ __global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, cons
         A[i * n + j] = acc;
         A[j * n + i] = acc;
     }
+    if (staged)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) Wg[e] = W[e];
     __syncthreads();
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) A32[(size_t)slot * n * n + e] = (float)A[e];
     // rho = max_i sum_j |A_ij| (an upper bound of the spectral norm of |A|), rounded up
@@ -568,6 +598,49 @@ __global__ void __launch_bounds__(256) k_scan64(const int32_t* __restrict__ list
     if (lane == 0) best[u] = bg;
 }
 
+// Exact residual-form scan (Algorithm 2 for every g) of the universes in
+// `list`: one CTA per universe, W of its covariance in shared memory, the
+// threads split the grid, first minimum in index order.  Used when all
+// certified screen rounds failed, so it never needs binary64 q-vectors.
+__global__ void __launch_bounds__(256) k_scan_resid(const int32_t* __restrict__ list, const int32_t* __restrict__ uslot,
+                                                     const float* __restrict__ d, const double* __restrict__ Sfit,
+                                                     int64_t G, int nfit, const double* __restrict__ W64,
+                                                     int32_t* __restrict__ best) {
+    extern __shared__ double sW[];
+    __shared__ double rv[8];
+    __shared__ int32_t rg[8];
+    const int i = blockIdx.x;
+    const int u = list[i];
+    const double* Wg = W64 + (size_t)uslot[i] * nfit * nfit;
+    const bool staged = (nfit <= kResolveMaxN);
+    if (staged)
+        for (int e = threadIdx.x; e < nfit * nfit; e += blockDim.x) sW[e] = Wg[e];
+    __syncthreads();
+    const double* W = staged ? sW : Wg;
+    const float* du = d + (size_t)u * nfit;
+    double bv = DBL_MAX;
+    int32_t bg = INT32_MAX;
+    for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
+        const double c = resid_chi2(W, nfit, Sfit + g * nfit, du);
+        if (c < bv) {
+            bv = c;
+            bg = (int32_t)g;
+        }
+    }
+    warp_argmin(bv, bg);
+    if ((threadIdx.x & 31) == 0) {
+        rv[threadIdx.x >> 5] = bv;
+        rg[threadIdx.x >> 5] = bg;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        bv = threadIdx.x < (blockDim.x >> 5) ? rv[threadIdx.x] : DBL_MAX;
+        bg = threadIdx.x < (blockDim.x >> 5) ? rg[threadIdx.x] : INT32_MAX;
+        warp_argmin(bv, bg);
+        if (threadIdx.x == 0) best[u] = bg;
+    }
+}
+
 // ------------------------------------------------------ mixed: grouping -----
 
 __global__ void k_count_slots(const int32_t* __restrict__ uslot, int64_t n, int32_t* __restrict__ cnt) {
@@ -738,22 +811,6 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
 
 // ------------------------------------------------------- mixed: resolution --
 
-// Residual form ||W r||^2, r = s - d, A = W^T W (W lower triangular), binary64.
-__device__ double resid_chi2(const double* __restrict__ W, int n, const double* __restrict__ s,
-                             const float* __restrict__ du) {
-    double r[kMaxBins];
-    for (int j = 0; j < n; ++j) r[j] = s[j] - (double)du[j];
-    double acc = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double* Wi = W + i * n;
-        double t = 0.0;
-        for (int j = 0; j <= i; ++j) t = fma(Wi[j], r[j], t);
-        acc = fma(t, t, acc);
-    }
-    return acc;
-}
-
-constexpr int kResolveMaxN = 64;      // W staged in shared memory up to this N_fit
 constexpr int kItemCu = kMaxTopK;     // item codes beyond the candidates
 constexpr int kItemP = kMaxTopK + 1;
 constexpr int kItemMin = kMaxTopK + 2;
@@ -1144,7 +1201,14 @@ void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps
                      float* L32, float* s32, double*, int* status, cudaStream_t st) {
     if (P <= 0) return;
     count_launch();
-    k_chol_sys<<<P, 256, 0, st>>>(S, nf, F, ps, gauss, L64, L32, s32, status);
+    const size_t smem = nf <= kCholSmemN ? (size_t)nf * nf * sizeof(double) : 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_chol_sys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kCholSmemN * kCholSmemN * (int)sizeof(double));
+        attr = true;
+    }
+    k_chol_sys<<<P, 256, smem, st>>>(S, nf, F, ps, gauss, L64, L32, s32, status);
 }
 
 void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, const double* F, const int32_t* q_list,
@@ -1152,8 +1216,15 @@ void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, co
                       float* rho, double* work, int* status, cudaStream_t st) {
     if (n <= 0) return;
     count_launch();
-    k_build_cov<<<n, 256, 0, st>>>(S, nf, nfit, coll, F, q_list, slot_list, cov_mode, A64, W64, A32, rho, work,
-                                   status);
+    const size_t smem = nfit <= kResolveMaxN ? 2 * (size_t)nfit * nfit * sizeof(double) : 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_build_cov, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * kResolveMaxN * kResolveMaxN * (int)sizeof(double));
+        attr = true;
+    }
+    k_build_cov<<<n, 256, smem, st>>>(S, nf, nfit, coll, F, q_list, slot_list, cov_mode, A64, W64, A32, rho, work,
+                                      status);
 }
 
 void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
@@ -1240,6 +1311,14 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const f
     if (n <= 0) return;
     count_launch();
     k_scan64<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, d, centre, Sc, G, nfit, A64, Q64, ldq, best);
+}
+
+void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* Sfit,
+                       int64_t G, int nfit, const double* W64, int32_t* best, cudaStream_t st) {
+    if (n <= 0) return;
+    const size_t smem = nfit <= kResolveMaxN ? (size_t)nfit * nfit * sizeof(double) : 0;
+    count_launch();
+    k_scan_resid<<<(unsigned)n, 256, smem, st>>>(list, uslot, d, Sfit, G, nfit, W64, best);
 }
 
 void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_slots, int32_t* cnt,
