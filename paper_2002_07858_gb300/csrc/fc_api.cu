@@ -455,8 +455,15 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 launch_fill_i32(fslot, cnt, g->ident_slot, c->stream);
             else
                 launch_lookup_slots(list, cnt, cur, g->slot_of, fslot, c->stream);
+            // enough CTAs to cover the GPU about four times, each at least 1024 grid points
+            int nsp = (int)std::max<int64_t>(1, (4 * (int64_t)c->n_sm + cnt - 1) / cnt);
+            nsp = (int)std::min<int64_t>(nsp, std::max<int64_t>(1, g->G / 1024));
+            double* pv = nullptr;
+            int32_t* pg = nullptr;
+            FC_TRY(scratch(c, "fb_pv", (size_t)cnt * nsp, &pv));
+            FC_TRY(scratch(c, "fb_pg", (size_t)cnt * nsp, &pg));
             stage_begin(c);
-            launch_scan_resid(list, cnt, fslot, d, g->S_fit, g->G, g->nfit, g->W64, best32, c->stream);
+            launch_scan_resid(list, cnt, fslot, d, g->S_fit, g->G, g->nfit, g->W64, pv, pg, nsp, best32, c->stream);
             FC_TRY(stage_end(c, &c->stats.ms_fallback));
         } else if (o.cov == FC_COV_IDENTITY) {
             FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));

@@ -16,7 +16,7 @@ inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_
 
 // Screen tile shape: BM universes (TMEM lanes) x BN grid points (TMEM columns).
 constexpr int kBM = 128;
-constexpr int kBN = 256;
+constexpr int kBN = 128;
 constexpr int kMaxTopK = 16;
 constexpr int kMaxBins = 200;
 
@@ -74,7 +74,8 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot_of_list,
 
 // exact residual-form scan (one CTA per listed universe), no q-vectors needed
 void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* Sfit,
-                       int64_t G, int nfit, const double* W64, int32_t* best, cudaStream_t st);
+                       int64_t G, int nfit, const double* W64, double* part_v, int32_t* part_g, int nsp,
+                       int32_t* best, cudaStream_t st);
 
 // ---- mixed path: grouping, y prep, screen, decision ----
 // counting sort of active universes by slot into BM-row tiles

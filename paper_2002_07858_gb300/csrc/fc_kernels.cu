@@ -187,27 +187,40 @@ constexpr int kCholSmemN = 110;  // n*n doubles <= 96.8 KB of shared memory
 // or global memory); every element's sum runs k = 0..j-1 with separately rounded
 // multiply and subtract, so the factor is reproducible bit for bit.
 __device__ bool chol_inplace(double* L, int n) {
+    // Right-looking form: after column k is final, every trailing element
+    // (i >= j > k) subtracts L_ik L_jk.  Each element therefore still sees its
+    // terms in increasing k with a separately rounded multiply and subtract --
+    // the same sequence as the left-looking sum -- while the dependency chain
+    // shrinks to one step per column.
     __shared__ double s_d;
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
+    for (int k = 0; k < n; ++k) {
         if (threadIdx.x == 0) {
-            double acc = L[j * n + j];
-            for (int k = 0; k < j; ++k) acc = __dsub_rn(acc, __dmul_rn(L[j * n + k], L[j * n + k]));
+            double acc = L[k * n + k];
             if (!(acc > 0.0)) {
                 s_bad = 1;
                 acc = 1.0;
             }
             s_d = __dsqrt_rn(acc);
-            L[j * n + j] = s_d;
+            L[k * n + k] = s_d;
         }
         __syncthreads();
-        const double dj = s_d;
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            double a = L[i * n + j];
-            for (int k = 0; k < j; ++k) a = __dsub_rn(a, __dmul_rn(L[i * n + k], L[j * n + k]));
-            L[i * n + j] = __ddiv_rn(a, dj);
+        const double dk = s_d;
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) L[i * n + k] = __ddiv_rn(L[i * n + k], dk);
+        __syncthreads();
+        // trailing update of the lower triangle, rows i > k, columns k < j <= i
+        const int m = n - k - 1;
+        const int cnt = m * (m + 1) / 2;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            // e -> (a, b) with 0 <= b <= a < m
+            int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while ((a + 1) * (a + 2) / 2 <= e) ++a;
+            while (a * (a + 1) / 2 > e) --a;
+            const int b = e - a * (a + 1) / 2;
+            const int i = k + 1 + a, jj = k + 1 + b;
+            L[i * n + jj] = __dsub_rn(L[i * n + jj], __dmul_rn(L[i * n + k], L[jj * n + k]));
         }
         __syncthreads();
     }
@@ -599,17 +612,18 @@ __global__ void __launch_bounds__(256) k_scan64(const int32_t* __restrict__ list
 }
 
 // Exact residual-form scan (Algorithm 2 for every g) of the universes in
-// `list`: one CTA per universe, W of its covariance in shared memory, the
-// threads split the grid, first minimum in index order.  Used when all
-// certified screen rounds failed, so it never needs binary64 q-vectors.
+// `list`, used when all certified screen rounds failed, so it never needs
+// binary64 q-vectors.  Grid (universe, split): each CTA stages W of the
+// universe's covariance in shared memory and scans every split-th grid point;
+// k_scan_resid_reduce takes the first minimum over the splits.
 __global__ void __launch_bounds__(256) k_scan_resid(const int32_t* __restrict__ list, const int32_t* __restrict__ uslot,
                                                      const float* __restrict__ d, const double* __restrict__ Sfit,
                                                      int64_t G, int nfit, const double* __restrict__ W64,
-                                                     int32_t* __restrict__ best) {
+                                                     double* __restrict__ part_v, int32_t* __restrict__ part_g) {
     extern __shared__ double sW[];
     __shared__ double rv[8];
     __shared__ int32_t rg[8];
-    const int i = blockIdx.x;
+    const int i = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
     const int u = list[i];
     const double* Wg = W64 + (size_t)uslot[i] * nfit * nfit;
     const bool staged = (nfit <= kResolveMaxN);
@@ -620,7 +634,7 @@ __global__ void __launch_bounds__(256) k_scan_resid(const int32_t* __restrict__ 
     const float* du = d + (size_t)u * nfit;
     double bv = DBL_MAX;
     int32_t bg = INT32_MAX;
-    for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
+    for (int64_t g = (int64_t)sp * blockDim.x + threadIdx.x; g < G; g += (int64_t)nsp * blockDim.x) {
         const double c = resid_chi2(W, nfit, Sfit + g * nfit, du);
         if (c < bv) {
             bv = c;
@@ -637,8 +651,29 @@ __global__ void __launch_bounds__(256) k_scan_resid(const int32_t* __restrict__ 
         bv = threadIdx.x < (blockDim.x >> 5) ? rv[threadIdx.x] : DBL_MAX;
         bg = threadIdx.x < (blockDim.x >> 5) ? rg[threadIdx.x] : INT32_MAX;
         warp_argmin(bv, bg);
-        if (threadIdx.x == 0) best[u] = bg;
+        if (threadIdx.x == 0) {
+            part_v[(size_t)i * nsp + sp] = bv;
+            part_g[(size_t)i * nsp + sp] = bg;
+        }
     }
+}
+
+__global__ void k_scan_resid_reduce(const int32_t* __restrict__ list, int64_t n, int nsp,
+                                    const double* __restrict__ part_v, const int32_t* __restrict__ part_g,
+                                    int32_t* __restrict__ best) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double bv = DBL_MAX;
+    int32_t bg = INT32_MAX;
+    for (int sp = 0; sp < nsp; ++sp) {
+        const double v = part_v[i * nsp + sp];
+        const int32_t g = part_g[i * nsp + sp];
+        if (v < bv || (v == bv && g < bg)) {
+            bv = v;
+            bg = g;
+        }
+    }
+    best[list[i]] = bg;
 }
 
 // ------------------------------------------------------ mixed: grouping -----
@@ -1314,11 +1349,14 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const f
 }
 
 void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* Sfit,
-                       int64_t G, int nfit, const double* W64, int32_t* best, cudaStream_t st) {
+                       int64_t G, int nfit, const double* W64, double* part_v, int32_t* part_g, int nsp,
+                       int32_t* best, cudaStream_t st) {
     if (n <= 0) return;
     const size_t smem = nfit <= kResolveMaxN ? (size_t)nfit * nfit * sizeof(double) : 0;
-    count_launch();
-    k_scan_resid<<<(unsigned)n, 256, smem, st>>>(list, uslot, d, Sfit, G, nfit, W64, best);
+    count_launch(2);
+    k_scan_resid<<<dim3((unsigned)n, (unsigned)nsp), 256, smem, st>>>(list, uslot, d, Sfit, G, nfit, W64, part_v,
+                                                                      part_g);
+    k_scan_resid_reduce<<<blocks_for(n), kThreads, 0, st>>>(list, n, nsp, part_v, part_g, best);
 }
 
 void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_slots, int32_t* cnt,
