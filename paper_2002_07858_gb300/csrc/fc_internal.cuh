@@ -16,7 +16,7 @@ inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_
 
 // Screen tile shape: BM universes (TMEM lanes) x BN grid points (TMEM columns).
 constexpr int kBM = 128;
-constexpr int kBN = 128;
+constexpr int kBN = 256;
 constexpr int kMaxTopK = 16;
 constexpr int kMaxBins = 200;
 

@@ -286,8 +286,7 @@ __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item
     return (sig + 2.0f * eps) * 1.0000005f + 1.0e-6f + 4.7683716e-07f * fabsf(sig);
 }
 
-constexpr int kNumAcc = 4;                // TMEM accumulator buffers
-constexpr int kTmemCols = kNumAcc * kBN;  // 512 columns
+constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
 constexpr int kEpiWarps = 8;
 constexpr int kHalfCols = kBN / 2;
 
@@ -306,7 +305,7 @@ struct ScreenSmem {
     // per epilogue warp 4 KB: slow-path scratch inside a tile, top-k hand-over at the end of a row tile
     static constexpr uint32_t kOffScratch = kOffZero + kBChunk;
     static constexpr uint32_t kOffBar = kOffScratch + kEpiWarps * 4096;
-    static constexpr uint32_t kNumBars = 2 + 2 + STAGES + STAGES + kNumAcc + kNumAcc + 1;
+    static constexpr uint32_t kNumBars = 2 + 2 + STAGES + STAGES + 2 + 2 + 1;
     static constexpr uint32_t kBytes = kOffBar + kNumBars * 8 + 16 + 1024;
 };
 
@@ -326,7 +325,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
     auto bar = [&](int i) { return smem_addr(&bars[i]); };
     const int Y_FULL = 0, Y_EMPTY = 2, B_FULL = 4, B_EMPTY = 4 + STAGES, T_FULL = 4 + 2 * STAGES,
-              T_EMPTY = 4 + 2 * STAGES + kNumAcc, DONE = 4 + 2 * STAGES + 2 * kNumAcc;
+              T_EMPTY = 6 + 2 * STAGES, DONE = 8 + 2 * STAGES;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // constant q-step operand slabs (generic-proxy writes, fenced for the tensor core below)
@@ -344,8 +343,6 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(bar(Y_FULL + i), 1);
             mbar_init(bar(Y_EMPTY + i), 1);
-        }
-        for (int i = 0; i < kNumAcc; ++i) {
             mbar_init(bar(T_FULL + i), 1);
             mbar_init(bar(T_EMPTY + i), kEpiWarps);
         }
@@ -422,8 +419,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 const int64_t seq = (int64_t)it * n_gt + jj;
                 const int s = (int)(seq % STAGES);
                 const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
-                const int ab = (int)(seq % kNumAcc);
-                const uint32_t aph = (uint32_t)((seq / kNumAcc) & 1);
+                const int ab = (int)(seq & 1);
+                const uint32_t aph = (uint32_t)((seq >> 1) & 1);
                 if (!mbar_wait(bar(T_EMPTY + ab), aph ^ 1, abort_flag)) { ok = false; break; }
                 if (!mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; break; }
                 tc_fence_after();
@@ -486,8 +483,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             for (int jj = 0; ok && jj < n_gt; ++jj) {
                 const int j = (j0 + jj) % n_gt;
                 const int64_t seq = (int64_t)it * n_gt + jj;
-                const int ab = (int)(seq % kNumAcc);
-                const uint32_t aph = (uint32_t)((seq / kNumAcc) & 1);
+                const int ab = (int)(seq & 1);
+                const uint32_t aph = (uint32_t)((seq >> 1) & 1);
                 bool w_ok = mbar_wait(bar(T_FULL + ab), aph, abort_flag);
                 if (!__all_sync(0xffffffffu, w_ok)) {
                     ok = false;
@@ -506,18 +503,24 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                     else
                         topk_chunk<TOPK>(vals, idx, r, gc, G, scratch, lane);
                 };
-                static_assert(kHalfCols == 64, "two 32-column chunks per warp and tile");
                 tmem_ld32(tb + 0, ra);
-                tmem_ld32(tb + 32, rb);
                 tmem_wait(ra);
+                tmem_ld32(tb + 32, rb);
+                chunk(ra, g0 + 0);
+                __syncwarp();
                 tmem_wait(rb);
-                // both chunks are in registers: hand the accumulator back before filtering
+                tmem_ld32(tb + 64, ra);
+                chunk(rb, g0 + 32);
+                __syncwarp();
+                tmem_wait(ra);
+                tmem_ld32(tb + 96, rb);
+                chunk(ra, g0 + 64);
+                __syncwarp();
+                tmem_wait(rb);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(T_EMPTY + ab));
-                chunk(ra, g0 + 0);
-                __syncwarp();
-                chunk(rb, g0 + 32);
+                chunk(rb, g0 + 96);
                 __syncwarp();
             }
             if (MODE == kModeList) {
@@ -617,14 +620,14 @@ bool launch_screen(int K, int topk, int mode, const uint16_t* Yt, const uint16_t
             FC_SCREEN_RUN(KK, TT, SS, YY, kModeTopK);                    \
         return true;                                                     \
     }
-    FC_SCREEN_CASE(16, 8, 8, 2)
-    FC_SCREEN_CASE(32, 8, 8, 2)
-    FC_SCREEN_CASE(48, 8, 5, 2)
-    FC_SCREEN_CASE(64, 8, 3, 2)
-    FC_SCREEN_CASE(16, 16, 8, 2)
-    FC_SCREEN_CASE(32, 16, 8, 2)
-    FC_SCREEN_CASE(48, 16, 5, 2)
-    FC_SCREEN_CASE(64, 16, 3, 2)
+    FC_SCREEN_CASE(16, 8, 4, 2)
+    FC_SCREEN_CASE(32, 8, 3, 2)
+    FC_SCREEN_CASE(48, 8, 3, 1)
+    FC_SCREEN_CASE(64, 8, 2, 1)
+    FC_SCREEN_CASE(16, 16, 4, 2)
+    FC_SCREEN_CASE(32, 16, 3, 2)
+    FC_SCREEN_CASE(48, 16, 3, 1)
+    FC_SCREEN_CASE(64, 16, 2, 1)
 #undef FC_SCREEN_CASE
 #undef FC_SCREEN_RUN
     return false;
