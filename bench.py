@@ -321,6 +321,24 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_once(args):
+    """One untimed FC job (for profilers): the configured points x universes, stats printed as JSON."""
+    import numpy as np
+
+    import paper_2002_07858_gb300 as fc
+    import workloads
+
+    fc.load()
+    w = workloads.cfg2(U=args.universes)
+    pts = np.linspace(0, w.G - 1, args.points).round().astype(np.int64) if args.points else w.points
+    ctx = fc.fc_create(0)
+    gid = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+    fc.fc_set_frac_cov(ctx, gid, w.F)
+    fc.fc_run_points(ctx, gid, pts, 1, w.U, dict(precision=args.precision, top_k=args.top_k))
+    print(json.dumps({"once": {"points": int(len(pts)), "universes": w.U, **fc.fc_get_stats(ctx)}}), flush=True)
+    fc.fc_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,8 +352,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--once", action="store_true", help="run one untimed job and print its stats (for profilers)")
+    ap.add_argument("--precision", type=int, default=1, help="with --once: 1 = mixed, 0 = plain fp64")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.once:
+        run_once(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)
