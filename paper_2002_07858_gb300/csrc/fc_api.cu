@@ -84,7 +84,7 @@ struct Grid {
     double* centre = nullptr;   // [nfit]
     double* Sc = nullptr;       // [G][nfit] centred
     float* Sc32 = nullptr;      // [G][nfit]
-    float* nrm = nullptr;       // [G]
+    float4* gnorm = nullptr;    // [G] |s~|, |S_lo|, |r_S|
     uint16_t* Bt = nullptr;     // screen B image [G_pad/BN][2K/8][BN/8][8][8]
     int32_t* collapse = nullptr;
     double* F = nullptr;
@@ -354,7 +354,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
     if (!q32_list.empty()) {
         FC_TRY(ensure_q32_storage(c, g));
         FC_CUDA(cudaMemcpyAsync(ds, q32_list.data(), q32_list.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        launch_qvec32(g->Sc32, g->nrm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(), g->Qc,
+        launch_qvec32(g->Sc32, g->gnorm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(), g->Qc,
                       g->Qb, g->Qb3, c->stream);
         FC_TRY(sync(c));
     }
@@ -541,7 +541,8 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
                         *tj0 = nullptr, *cidx = nullptr;
                 uint16_t* Yt = nullptr;
-                float *alpha = nullptr, *cval = nullptr, *tau0 = nullptr;
+                float *cval = nullptr, *tau0 = nullptr;
+                float4* alpha = nullptr;
                 FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
                 FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
                 FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
@@ -563,7 +564,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
                 FC_TRY(sync(c));
                 launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
-                             g->nrm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
+                             g->gnorm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
                 if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
                 FC_TRY(stage_end(c, &c->stats.ms_prep));
                 stage_begin(c);
@@ -574,7 +575,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 for (int pass = min_pass ? 0 : 1; pass < 2; ++pass) {
                     const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
                     if (!launch_screen(g->K, rtopk, mode, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
-                                       g->G_pad, cval, cidx, ccount, c->status_dev, g->Qc, g->Qb, g->nrm, alpha,
+                                       g->G_pad, cval, cidx, ccount, c->status_dev, g->Qc, g->Qb, g->gnorm, alpha,
                                        g->Sc32, g->nfit, c->n_sm, c->stream))
                         return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
                     c->stats.screen_launches += 1;
@@ -588,7 +589,7 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
                 ra.cval = cval;
                 ra.cidx = cidx;
                 ra.alpha = alpha;
-                ra.nrm = g->nrm;
+                ra.gnorm = g->gnorm;
                 ra.Qc = g->Qc;
                 ra.Qb = g->Qb;
                 ra.G_pad = g->G_pad;
@@ -919,7 +920,7 @@ fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const 
     fc_status st = FC_OK;
     auto cleanup = [&](fc_status s) {
         dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
-        dfree(c, g->nrm); dfree(c, g->Bt); dfree(c, g->collapse);
+        dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse);
         return s;
     };
     if ((st = dalloc_t(c, &g->S_full, (size_t)G * nf)) != FC_OK) return cleanup(st);
@@ -927,7 +928,7 @@ fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const 
     if ((st = dalloc_t(c, &g->centre, (size_t)nfit)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->Sc, (size_t)G * nfit)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->Sc32, (size_t)G * nfit)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->nrm, (size_t)G)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->gnorm, (size_t)G)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->Bt, (size_t)g->G_pad * 2 * g->K)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->collapse, (size_t)nf)) != FC_OK) return cleanup(st);
     if ((st = copy_in(c, g->S_full, S, (size_t)G * nf * 8)) != FC_OK) return cleanup(st);
@@ -952,7 +953,7 @@ fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const 
     }
     launch_collapse(g->S_full, G, nf, ident ? nullptr : g->collapse, nfit, g->S_fit, c->stream);
     launch_centre(g->S_fit, G, nfit, g->centre, nullptr, c->stream);
-    launch_centred(g->S_fit, g->centre, G, g->G_pad, nfit, g->K, g->Sc, g->Sc32, g->nrm, g->Bt, c->stream);
+    launch_centred(g->S_fit, g->centre, G, g->G_pad, nfit, g->K, g->Sc, g->Sc32, g->gnorm, g->Bt, c->stream);
     if ((st = sync(c)) != FC_OK) return cleanup(st);
     {
         std::lock_guard<std::mutex> lq(c->q_mu);
@@ -1014,7 +1015,7 @@ fc_status fc_unload_grid(fc_ctx* c, int32_t grid_id) {
     cudaStreamSynchronize(c->stream);
     free_cache(c, g);
     dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
-    dfree(c, g->nrm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->F);
+    dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->F);
     return FC_OK;
 }
 

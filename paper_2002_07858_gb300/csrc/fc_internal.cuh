@@ -28,16 +28,24 @@ enum : int {
     kDevBadIndex = 4,
 };
 
-// Padded fit dimension of the tensor-core screen: at least one spare column
-// (it carries the error-bound term), rounded up to the MMA K-step of 16.
-inline int screen_k(int nfit) { return ((nfit + 1 + 15) / 16) * 16; }
+// Padded fit dimension of the tensor-core screen: three spare columns (they
+// carry the error-bound terms), rounded up to the MMA K-step of 16.
+__host__ __device__ inline int screen_k(int nfit) { return ((nfit + 3 + 15) / 16) * 16; }
+
+// Error-bound coefficients.  Per grid point g (gnorm): |s~_g|, |S_lo,g|, |r_S,g|
+// (r_S = s~ - S_hi - S_lo); per universe row (alpha): a_acc (binary32
+// accumulation, y^ rounding and |r_Y| with |s~|), |Y_lo|, |Y_hi + Y_lo|.  The
+// screen's products are within dot(alpha, gnorm) of -2 y.s~_g.
+__device__ __forceinline__ float bound_dot(const float4& a, const float4& n) {
+    return 1.0001f * fmaf(a.x, n.x, fmaf(a.y, n.y, a.z * n.z));
+}
 
 // ---- ingest (a1) ----
 void launch_collapse(const double* S_full, int64_t G, int nf, const int32_t* collapse, int nfit, double* S_fit,
                      cudaStream_t st);
 void launch_centre(const double* S_fit, int64_t G, int nfit, double* centre, double* work, cudaStream_t st);
 void launch_centred(const double* S_fit, const double* centre, int64_t G, int64_t G_pad, int nfit, int K,
-                    double* Sc, float* Sc32, float* nrm, uint16_t* Btiles, cudaStream_t st);
+                    double* Sc, float* Sc32, float4* gnorm, uint16_t* Btiles, cudaStream_t st);
 
 // ---- covariances (a2) ----
 // L_p (binary64 and binary32 copies) for every true point; gauss adds diag(s).
@@ -50,7 +58,7 @@ void launch_build_cov(const double* S_full, int nf, int nfit, const int32_t* col
 // q_g = s~_g^T A s~_g for slots: binary64 (plain) or binary32 central + lower bound (mixed).
 void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
                    int64_t ldq, double* Q64, cudaStream_t st);
-void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad, int nfit, const float* A32,
+void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
                    cudaStream_t st);
 
@@ -84,8 +92,8 @@ void launch_group(const int32_t* active, int64_t n_active, const int32_t* uslot,
                   int64_t max_tiles, cudaStream_t st);
 void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
-                  const float* Sc32, const float* nrm, const float* Qc, const float* Qb, int64_t G_pad,
-                  uint16_t* Ytiles, float* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st);
+                  const float* Sc32, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
+                  uint16_t* Ytiles, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st);
 // Tensor-core screen of BM-row tiles (see fc_screen.cu).  mode: kScreenTopK,
 // kScreenMin (first pass; tightens tau0 in place) or kScreenList (every point
 // with LB <= tau0, kListCap per half row; cand_count > kListCap = overflow).
@@ -95,7 +103,7 @@ constexpr int kListCap = 64;
 bool launch_screen(int K, int topk, int mode, const uint16_t* Ytiles, const uint16_t* Btiles, const uint16_t* Qb3,
                    const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
-                   const float* Qc, const float* Qb, const float* nrm, const float* alpha, const float* Sc32,
+                   const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
                    int nfit, int n_sm, cudaStream_t st);
 // Resolution of one mixed-path scan per screen tile (see k_resolve).
 struct ResolveArgs {
@@ -104,8 +112,8 @@ struct ResolveArgs {
     int topk;
     const float* cval;
     const int32_t* cidx;
-    const float* alpha;
-    const float* nrm;
+    const float4* alpha;
+    const float4* gnorm;
     const float* Qc;
     const float* Qb;
     int64_t G_pad;

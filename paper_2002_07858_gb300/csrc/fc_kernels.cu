@@ -157,11 +157,11 @@ __device__ __forceinline__ int64_t btile_offset(int64_t g, int c, int K) {
 }
 
 __global__ void k_centred(const double* __restrict__ Sfit, const double* __restrict__ centre, int64_t G, int nfit,
-                          int K, double* __restrict__ Sc, float* __restrict__ Sc32, float* __restrict__ nrm,
+                          int K, double* __restrict__ Sc, float* __restrict__ Sc32, float4* __restrict__ gnorm,
                           uint16_t* __restrict__ Bt) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= G) return;
-    double ss = 0.0;
+    double ss = 0.0, sl = 0.0, sr = 0.0;
     for (int j = 0; j < nfit; ++j) {
         const double x = Sfit[g * nfit + j] - centre[j];
         Sc[g * nfit + j] = x;
@@ -170,13 +170,21 @@ __global__ void k_centred(const double* __restrict__ Sfit, const double* __restr
         const __nv_bfloat16 h = __double2bfloat16(x);
         const double rem = x - (double)__bfloat162float(h);
         const __nv_bfloat16 l = __double2bfloat16(rem);
+        const double lo = (double)__bfloat162float(l);
+        const double res = rem - lo;  // r_S: what hi + lo leave out
+        sl = fma(lo, lo, sl);
+        sr = fma(res, res, sr);
         Bt[btile_offset(g, j, K)] = __bfloat16_as_ushort(h);
         Bt[btile_offset(g, K + j, K)] = __bfloat16_as_ushort(l);
     }
-    // norm, rounded up twice (double sqrt then float), carried by the spare column of the lo half
+    // norms rounded up (double sqrt, then float), carried by the spare columns of the lo half
     const float n = __double2float_ru(__dsqrt_ru(ss) * (1.0 + 1e-12));
-    nrm[g] = n;
+    const float nl = __double2float_ru(__dsqrt_ru(sl) * (1.0 + 1e-12));
+    const float nr = __double2float_ru(__dsqrt_ru(sr) * (1.0 + 1e-12));
+    gnorm[g] = make_float4(n, nl, nr, 0.0f);
     Bt[btile_offset(g, K + nfit, K)] = __bfloat16_as_ushort(__float2bfloat16_ru(n));
+    Bt[btile_offset(g, K + nfit + 1, K)] = __bfloat16_as_ushort(__float2bfloat16_ru(nl));
+    Bt[btile_offset(g, K + nfit + 2, K)] = __bfloat16_as_ushort(__float2bfloat16_ru(nr));
 }
 
 // ------------------------------------------------------------ covariances ---
@@ -378,7 +386,7 @@ __global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, con
 // accumulator first and 3K products follow; bounding every add as a truncated
 // binary32 add of the running sum gives (3K + 3) 2^-23 |q| (K = padded N_fit).
 __device__ __forceinline__ float q_rel_slack(int nfit) {
-    const int K = ((nfit + 1 + 15) / 16) * 16;
+    const int K = screen_k(nfit);
     return (float)(3 * K + 5) * 1.1920929e-07f;
 }
 
@@ -409,7 +417,7 @@ __device__ __forceinline__ void store_qb3(uint16_t* o, float qb) {
 // binary32 q_g with its rounding bound; s~_g held in registers (NMAX >= nfit,
 // NMAX a multiple of 4), A staged in shared memory with rows padded to NMAX.
 template <int NMAX>
-__global__ void k_qvec32(const float* __restrict__ Sc32, const float* __restrict__ nrm, int64_t G, int64_t G_pad,
+__global__ void k_qvec32(const float* __restrict__ Sc32, const float4* __restrict__ gnorm, int64_t G, int64_t G_pad,
                          int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
                          const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb,
                          uint16_t* __restrict__ Qb3) {
@@ -443,7 +451,7 @@ __global__ void k_qvec32(const float* __restrict__ Sc32, const float* __restrict
                 }
                 q = fmaf(s[i], t, q);
             }
-            const float n = nrm[g];
+            const float n = gnorm[g].x;
             // |q^ - q| <= (nfit+4) 2^-24 rho |s|^2 + 2^-23 |q^|   (A rounded to binary32, dot products, final rounding)
             const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + q_rel_slack(nfit) * fabsf(q));
             qc = q;
@@ -455,7 +463,7 @@ __global__ void k_qvec32(const float* __restrict__ Sc32, const float* __restrict
     }
 }
 
-__global__ void k_qvec32_generic(const float* __restrict__ Sc32, const float* __restrict__ nrm, int64_t G,
+__global__ void k_qvec32_generic(const float* __restrict__ Sc32, const float4* __restrict__ gnorm, int64_t G,
                                  int64_t G_pad, int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
                                  const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb,
                                  uint16_t* __restrict__ Qb3) {
@@ -472,7 +480,7 @@ __global__ void k_qvec32_generic(const float* __restrict__ Sc32, const float* __
                 for (int j = 0; j < nfit; ++j) t = fmaf(A[i * nfit + j], s[j], t);
                 q = fmaf(s[i], t, q);
             }
-            const float n = nrm[g];
+            const float n = gnorm[g].x;
             const float beta = 1.02f * ((float)(nfit + 4) * 5.9604645e-08f * r * n * n + q_rel_slack(nfit) * fabsf(q));
             qc = q;
             qb = __fsub_rd(q, beta);
@@ -768,9 +776,9 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
                                                 const double* __restrict__ centre, int nfit, int K,
                                                 const float* __restrict__ A32, const float* __restrict__ rho,
                                                 const int32_t* __restrict__ cur, const float* __restrict__ Sc32,
-                                                const float* __restrict__ nrm, const float* __restrict__ Qc,
+                                                const float4* __restrict__ gnorm, const float* __restrict__ Qc,
                                                 const float* __restrict__ Qb, int64_t G_pad,
-                                                uint16_t* __restrict__ Yt, float* __restrict__ alpha,
+                                                uint16_t* __restrict__ Yt, float4* __restrict__ alpha,
                                                 float* __restrict__ tau0, int32_t* __restrict__ tile_j0) {
     extern __shared__ float sA[];
     const int64_t t = blockIdx.x;
@@ -798,7 +806,7 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     };
     if (u < 0) {
         store_row();
-        alpha[t * kBM + r] = 0.0f;
+        alpha[t * kBM + r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         tau0[t * kBM + r] = -FLT_MAX;  // padding rows keep no candidate
         return;
     }
@@ -811,7 +819,7 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
         dt[j] = (float)((double)d[(size_t)u * nfit + j] - centre[j]);
         dn2 = fmaf(dt[j], dt[j], dn2);
     }
-    float yn2 = 0.0f, dot = 0.0f, adot = 0.0f;
+    float yn2 = 0.0f, yl2 = 0.0f, yhl2 = 0.0f, ry2 = 0.0f, dot = 0.0f, adot = 0.0f;
     for (int i = 0; i < nfit; ++i) {
         float y = 0.0f;
         for (int j = 0; j < nfit; ++j) y = fmaf(sA[i * nfit + j], dt[j], y);
@@ -820,26 +828,35 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
         dot = fmaf(Y, sq[i], dot);
         adot = fmaf(fabsf(Y), fabsf(sq[i]), adot);
         const __nv_bfloat16 h = __float2bfloat16_rn(Y);
-        const __nv_bfloat16 l = __float2bfloat16_rn(Y - __bfloat162float(h));
+        const float rem = Y - __bfloat162float(h);           // exact
+        const __nv_bfloat16 l = __float2bfloat16_rn(rem);
+        const float lo = __bfloat162float(l), hl = __bfloat162float(h) + lo;
+        const float ry = rem - lo;                            // exact: r_Y = Y - hi - lo
+        yl2 = fmaf(lo, lo, yl2);
+        yhl2 = fmaf(hl, hl, yhl2);
+        ry2 = fmaf(ry, ry, ry2);
         put_bf16(hw, i, __bfloat16_as_ushort(h));
         put_bf16(lw, i, __bfloat16_as_ushort(l));
     }
-    // |computed - exact| of -2 y.s~_g  <=  alpha * |s~_g|:
-    //   2 |y - y^| |s~|            with |y - y^| <= (nfit+2) 2^-24 rho |d~|
-    //   3.03 2^-16 |Y| |s~|        dropped lo*lo products and the two split residuals
-    //   (3K+2) 2^-23 1.02 |Y| |s~| binary32 accumulation of the products
+    // -2 y.s~_g - (hi*hi + lo*hi + hi*lo products)  =  -2 (y - y^).s~ + Y_lo.S_lo + (Y_hi + Y_lo).r_S + r_Y.s~
+    // and the binary32 accumulation of the 3K products (each add bounded as truncated, Sum|products| <= 1.02 |Y||s~|):
+    //   |error| <= [2 |y - y^| + |r_Y| + (3K+2) 1.02 2^-23 |Y|] |s~| + |Y_lo| |S_lo| + |Y_hi+Y_lo| |r_S|
+    // with |y - y^| <= (nfit+2) 2^-24 rho |d~| (A and d~ rounded to binary32, binary32 dot products).
     const float dn = sqrtf(dn2) * 1.0001f, yn = sqrtf(yn2) * 1.0001f;
-    const float c_split = 3.03f * 1.52587890625e-05f + (float)(3 * K + 2) * 1.1920929e-07f * 1.02f;
-    const float a = 1.05f * (2.0f * (float)(nfit + 2) * 5.9604645e-08f * rho[slot] * dn + c_split * yn);
-    alpha[t * kBM + r] = a;
-    put_bf16(hw, nfit, __bfloat16_as_ushort(__float2bfloat16_rd(-a)));
+    const float a_acc = 1.02f * (2.0f * (float)(nfit + 2) * 5.9604645e-08f * rho[slot] * dn +
+                                 (float)(3 * K + 2) * 1.1920929e-07f * 1.02f * yn + sqrtf(ry2));
+    const float4 al = make_float4(a_acc, 1.0001f * sqrtf(yl2), 1.0001f * sqrtf(yhl2), 0.0f);
+    alpha[t * kBM + r] = al;
+    put_bf16(hw, nfit, __bfloat16_as_ushort(__float2bfloat16_rd(-al.x)));
+    put_bf16(hw, nfit + 1, __bfloat16_as_ushort(__float2bfloat16_rd(-al.y)));
+    put_bf16(hw, nfit + 2, __bfloat16_as_ushort(__float2bfloat16_rd(-al.z)));
     store_row();
     // probe at q: sigma^ = q^_q + Y.s~_q (binary32), |sigma^ - sigma| <= 2|y - y^||s~_q| + |q^ - q|
     //   + (nfit+1) 2^-24 (sum |Y_i s~_i| + |q^|) + 2^-24 |sigma^|   (all inside eps below)
     const int64_t qi = (int64_t)slot * G_pad + q;
     const float qc = Qc[qi];
     const float sig = qc + dot;
-    const float eps = a * nrm[q] + (qc - Qb[qi]) +
+    const float eps = bound_dot(al, gnorm[q]) + (qc - Qb[qi]) +
                       (float)(nfit + 2) * 5.9604645e-08f * (adot + fabsf(qc)) + 1.1920929e-07f * (fabsf(sig) + 1.0f);
     tau0[t * kBM + r] = (sig + 2.0f * eps) * 1.0000005f + 1.0e-6f + 4.7683716e-07f * fabsf(sig);
 }
@@ -902,7 +919,7 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
     bool full = false;
     float tau = FLT_MAX, min_ub = FLT_MAX;
     if (u >= 0) {
-        const float al = a.alpha[row];
+        const float4 al = a.alpha[row];
         int nvalid = 0;
         for (int j = 0; j < topk; ++j) {
             const int32_t gj = a.cidx[row * topk + j];
@@ -912,7 +929,7 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
             if (gj < 0) continue;
             ++nvalid;
             const int64_t q = (int64_t)slot * a.G_pad + gj;
-            const float eps = fmaf(al, a.nrm[gj], a.Qc[q] - a.Qb[q]);
+            const float eps = bound_dot(al, a.gnorm[gj]) + (a.Qc[q] - a.Qb[q]);
             ub[j] = lb[j] + 2.0f * eps + 4.7683716e-07f * (fabsf(lb[j]) + fabsf(a.Qc[q]) + 1.0f);
             min_ub = fminf(min_ub, ub[j]);
         }
@@ -1226,10 +1243,10 @@ void launch_centre(const double* S_fit, int64_t G, int nfit, double* centre, dou
 }
 
 void launch_centred(const double* S_fit, const double* centre, int64_t G, int64_t G_pad, int nfit, int K,
-                    double* Sc, float* Sc32, float* nrm, uint16_t* Bt, cudaStream_t st) {
+                    double* Sc, float* Sc32, float4* gnorm, uint16_t* Bt, cudaStream_t st) {
     cudaMemsetAsync(Bt, 0, (size_t)G_pad * 2 * K * sizeof(uint16_t), st);
     count_launch();
-    k_centred<<<blocks_for(G, 128), 128, 0, st>>>(S_fit, centre, G, nfit, K, Sc, Sc32, nrm, Bt);
+    k_centred<<<blocks_for(G, 128), 128, 0, st>>>(S_fit, centre, G, nfit, K, Sc, Sc32, gnorm, Bt);
 }
 
 void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps, int P, int gauss, double* L64,
@@ -1270,7 +1287,7 @@ void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, con
     k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, A64, slots, ldq, Q64);
 }
 
-void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad, int nfit, const float* A32,
+void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
                    cudaStream_t st) {
     if (n <= 0) return;
@@ -1280,15 +1297,15 @@ void launch_qvec32(const float* Sc32, const float* nrm, int64_t G, int64_t G_pad
     dim3 grid(gx, n);
     count_launch();
     if (nfit <= 16)
-        k_qvec32<16><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<16><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 32)
-        k_qvec32<32><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<32><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 48)
-        k_qvec32<48><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<48><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 64)
-        k_qvec32<64><<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<64><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else
-        k_qvec32_generic<<<grid, 128, 0, st>>>(Sc32, nrm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32_generic<<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
 }
 
 void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* coll, int nfit, const int64_t* ps,
@@ -1381,14 +1398,14 @@ void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_
 
 void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
-                  const float* Sc32, const float* nrm, const float* Qc, const float* Qb, int64_t G_pad,
-                  uint16_t* Yt, float* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st) {
+                  const float* Sc32, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
+                  uint16_t* Yt, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st) {
     if (n_tiles <= 0) return;
     const size_t smem = (size_t)nfit * nfit * sizeof(float);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_yprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
     k_yprep<<<(unsigned)n_tiles, kBM, (size_t)nfit * nfit * sizeof(float), st>>>(tile_slot, tile_univ, d, centre,
-                                                                                  nfit, K, A32, rho, cur, Sc32, nrm,
+                                                                                  nfit, K, A32, rho, cur, Sc32, gnorm,
                                                                                   Qc, Qb, G_pad, Yt, alpha, tau0,
                                                                                   tile_j0);
 }

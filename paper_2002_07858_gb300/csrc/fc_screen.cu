@@ -207,8 +207,8 @@ __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[T
 struct ProbeArgs {
     const float* Qc;
     const float* Qb;
-    const float* nrm;
-    const float* alpha;
+    const float4* gnorm;
+    const float4* alpha;
     const float* Sc32;
     int nfit;
 };
@@ -268,7 +268,7 @@ __device__ __forceinline__ int64_t ytile_elem(int64_t t, int r, int c, int K) {
 __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item, int row, int slot, int32_t g,
                                    int64_t G_pad, const ProbeArgs& pa) {
     const int n = pa.nfit;
-    const int K = ((n + 1 + 15) / 16) * 16;
+    const int K = screen_k(n);
     const float* sg = pa.Sc32 + (int64_t)g * n;
     float dot = 0.0f, adot = 0.0f;
     for (int i = 0; i < n; ++i) {
@@ -281,7 +281,7 @@ __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item
     const int64_t qi = (int64_t)slot * G_pad + g;
     const float qc = pa.Qc[qi];
     const float sig = qc + dot;
-    const float eps = pa.alpha[item * kBM + row] * pa.nrm[g] + (qc - pa.Qb[qi]) +
+    const float eps = bound_dot(pa.alpha[item * kBM + row], pa.gnorm[g]) + (qc - pa.Qb[qi]) +
                       (float)(n + 2) * 5.9604645e-08f * (adot + fabsf(qc)) + 1.1920929e-07f * (fabsf(sig) + 1.0f);
     return (sig + 2.0f * eps) * 1.0000005f + 1.0e-6f + 4.7683716e-07f * fabsf(sig);
 }
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 tc_fence_after();
                 const uint32_t tb = tmem_base + lane_base + (uint32_t)(ab * kBN + half * kHalfCols);
                 const int64_t g0 = (int64_t)j * kBN + half * kHalfCols;
-                uint32_t ra[32], rb[32];
+                uint32_t r0[32], r1[32], r2[32], r3[32];
                 auto chunk = [&](const uint32_t(&r)[32], int64_t gc) {
                     if (MODE == kModeMin)
                         min_chunk(bv, bi, r, gc, G);
@@ -503,24 +503,26 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                     else
                         topk_chunk<TOPK>(vals, idx, r, gc, G, scratch, lane);
                 };
-                tmem_ld32(tb + 0, ra);
-                tmem_wait(ra);
-                tmem_ld32(tb + 32, rb);
-                chunk(ra, g0 + 0);
-                __syncwarp();
-                tmem_wait(rb);
-                tmem_ld32(tb + 64, ra);
-                chunk(rb, g0 + 32);
-                __syncwarp();
-                tmem_wait(ra);
-                tmem_ld32(tb + 96, rb);
-                chunk(ra, g0 + 64);
-                __syncwarp();
-                tmem_wait(rb);
+                // the warp's 128 columns go to registers at once, so the accumulator is
+                // handed back to the MMA after one load latency, before any filtering
+                tmem_ld32(tb + 0, r0);
+                tmem_ld32(tb + 32, r1);
+                tmem_ld32(tb + 64, r2);
+                tmem_ld32(tb + 96, r3);
+                tmem_wait(r0);
+                tmem_wait(r1);
+                tmem_wait(r2);
+                tmem_wait(r3);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(T_EMPTY + ab));
-                chunk(rb, g0 + 96);
+                chunk(r0, g0 + 0);
+                __syncwarp();
+                chunk(r1, g0 + 32);
+                __syncwarp();
+                chunk(r2, g0 + 64);
+                __syncwarp();
+                chunk(r3, g0 + 96);
                 __syncwarp();
             }
             if (MODE == kModeList) {
@@ -605,9 +607,9 @@ void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, con
 bool launch_screen(int K, int topk, int mode, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
                    const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const float* Qc, const float* Qb,
-                   const float* nrm, const float* alpha, const float* Sc32, int nfit, int n_sm, cudaStream_t st) {
+                   const float4* gnorm, const float4* alpha, const float* Sc32, int nfit, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
-    const ProbeArgs pa{Qc, Qb, nrm, alpha, Sc32, nfit};
+    const ProbeArgs pa{Qc, Qb, gnorm, alpha, Sc32, nfit};
 #define FC_SCREEN_RUN(KK, TT, SS, YY, MM) \
     run_screen<KK, TT, SS, YY, MM>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, n_sm, st)
 #define FC_SCREEN_CASE(KK, TT, SS, YY)                                   \
