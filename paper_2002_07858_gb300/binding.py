@@ -245,12 +245,17 @@ def fc_quantiles(ctx, x, probs):
     return out
 
 
-def fc_submit(ctx, grid_id: int, ps, seed: int, U: int, opts=None, dchi2=None, bestfit=None, nscans=None):
+def fc_submit(ctx, grid_id: int, ps, seed: int, U: int, opts=None, dchi2=None, bestfit=None, nscans=None,
+              want_bestfit: bool = False, want_nscans: bool = False):
     """Queue a job; the output arrays (returned) must stay alive until fc_poll reports it done."""
     ps = _host(ps, np.int64)
     P = int(ps.shape[0])
     if dchi2 is None:
         dchi2 = np.empty((P, U), np.float64)
+    if bestfit is None and want_bestfit:
+        bestfit = np.empty((P, U), np.int64)
+    if nscans is None and want_nscans:
+        nscans = np.empty((P, U), np.int8)
     j = fc_job()
     j.grid_id, j.ps, j.P, j.seed, j.U = grid_id, _ptr(ps), P, seed, U
     j.opts = _opts(opts)

@@ -111,7 +111,57 @@ struct Scratch {
     size_t bytes = 0;
 };
 
-struct JobRec;
+// Served job: a copy of the caller's arguments and its completion state.
+struct JobRec {
+    fc_job job;
+    std::vector<int64_t> ps;
+    std::atomic<int> state{FC_PENDING};
+    std::atomic<bool> cancelled{false};
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+// A lane holds the per-universe state of every job that runs with the same
+// grid and scan options (precision, top-k bucket, identity or data
+// covariance).  Jobs own contiguous universe ranges of the lane; one call of
+// scan_once advances every active universe of every job by one scan, whatever
+// scan each is on, so a job admitted between two scans joins the next one
+// (continuous batching).  A job is complete when its last universe finishes.
+
+constexpr int kLaneJobs = 1024;  // jobs resident in one lane at a time
+
+// Where a job's results go when it completes.
+struct LaneJob {
+    std::shared_ptr<JobRec> jr;  // null for synchronous calls
+    int32_t slot = -1;
+    int64_t base = 0, n = 0;
+    double* dchi2 = nullptr;     // caller outputs (host or device), nullable
+    int64_t* best = nullptr;
+    int8_t* nscans = nullptr;
+    double* chi2min = nullptr;
+    bool done = false;
+    fc_status status = FC_OK;
+};
+
+struct Lane {
+    Grid* g = nullptr;
+    fc_opts o{};           // precision, top_k and cov; max_iter and fluct are per job
+    int64_t cap = 0;       // universes
+    int nfit = 0;
+    float* d = nullptr;    // [cap][nfit] data
+    int32_t *cur = nullptr, *pt = nullptr, *best = nullptr, *job_of = nullptr;
+    int8_t *nscan = nullptr, *maxit = nullptr;
+    double *dchi2 = nullptr, *chi2min = nullptr;
+    float* thr = nullptr;
+    int32_t *active = nullptr, *next = nullptr, *fin = nullptr, *uslot = nullptr;
+    int32_t *fb = nullptr, *fb2 = nullptr, *fbslot = nullptr;
+    int32_t* job_left = nullptr;  // [kLaneJobs]
+    uint8_t* job_dead = nullptr;  // [kLaneJobs]
+    int64_t n_active = 0;
+    int64_t n_first = 0;          // universes admitted since the last scan
+    std::map<int64_t, int64_t> free_ranges;  // start -> length
+    std::vector<int32_t> free_jobs;
+    std::vector<std::shared_ptr<LaneJob>> jobs;  // indexed by job slot
+};
 
 struct fc_ctx {
     int device = 0;
@@ -127,7 +177,11 @@ struct fc_ctx {
     int* status_dev = nullptr;
     unsigned long long* counters_dev = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;  // stage timers
-    fc_stats stats{};
+    fc_stats stats{};              // last synchronous call
+    fc_stats serve_stats{};        // everything the serving worker ran
+    fc_stats* acc = &stats;        // where the running work counts
+    Lane sync_lane;                // synchronous calls
+    std::vector<std::unique_ptr<Lane>> lanes;  // serving (worker thread only)
     std::mutex api_mu;  // serialises device work of this context
     // serving
     std::mutex q_mu;
@@ -348,7 +402,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
                          (int)new_q.size(), cov_mode == FC_COV_IDENTITY ? 2 : 0, g->A64, g->W64, g->A32, g->rho,
                          work, c->status_dev, c->stream);
         if (cov_mode != FC_COV_IDENTITY) launch_set_slots(dq, ds, (int)new_q.size(), g->slot_of, c->stream);
-        c->stats.distinct_cov += (int64_t)new_q.size();
+        c->acc->distinct_cov += (int64_t)new_q.size();
         FC_TRY(check_status(c));
     }
     if (!q32_list.empty()) {
@@ -378,16 +432,6 @@ fc_status validate_opts(const fc_opts* o, const Grid* g) {
     return FC_OK;
 }
 
-__global__ void k_init_cur(const int64_t* __restrict__ ps, int64_t n, int U, int32_t* __restrict__ cur) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) cur[i] = (int32_t)ps[i / U];
-}
-
-__global__ void k_ps32(const int64_t* __restrict__ ps, int P, int32_t* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P) out[i] = (int32_t)ps[i];
-}
-
 __global__ void k_widen(const int32_t* __restrict__ a, int64_t n, int64_t* __restrict__ b) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = a[i];
@@ -397,6 +441,35 @@ __global__ void k_gather_cur(const int32_t* __restrict__ list, int n, const int3
                              int32_t* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = cur[list[i]];
+}
+
+// State of a newly admitted job's universes base .. base+n-1: universe i of
+// the job belongs to true point ps[i / U]; its first covariance is that point's
+// (§2 step 3 starts from M at the true point).  The universes are appended to
+// the lane's active list at `tail`.
+__global__ void k_lane_admit(const int64_t* __restrict__ ps, int64_t n, int U, int64_t base, int8_t max_iter,
+                             int32_t job, int32_t* __restrict__ cur, int32_t* __restrict__ pt,
+                             int8_t* __restrict__ nscan, int8_t* __restrict__ maxit, int32_t* __restrict__ job_of,
+                             int32_t* __restrict__ tail) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t u = base + i;
+    const int32_t p = (int32_t)ps[i / U];
+    cur[u] = p;
+    pt[u] = p;
+    nscan[u] = 0;
+    maxit[u] = max_iter;
+    job_of[u] = job;
+    tail[i] = (int32_t)u;
+}
+
+// Drop the universes of cancelled jobs from an active list.
+__global__ void k_drop_jobs(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ job_of,
+                            const uint8_t* __restrict__ dead, int32_t* __restrict__ out, int32_t* __restrict__ n_out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t u = active[i];
+    if (!dead[job_of[u]]) out[atomicAdd(n_out, 1)] = u;
 }
 
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -425,27 +498,165 @@ fc_status distinct_cur(fc_ctx* c, Grid* g, const int32_t* active, int64_t n_acti
     return FC_OK;
 }
 
-// The per-scan loop shared by fc_run_points and fc_scan.
-//   d      [n][nfit] fake (or caller) data on the device
-//   cur    [n] covariance grid index per universe (updated in place)
-//   p_of   [n / U] true point per block of U universes (int32)
-// Outputs (device): best32 [n], nscan [n], dchi2 [n], chi2min [n].
-fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, const float* d, int32_t* cur,
-                    const int32_t* p_of, int32_t* best32, int8_t* nscan, double* dchi2, double* chi2min) {
-    const int max_iter = (o.cov == FC_COV_ITERATE) ? o.max_iter : 1;
+// ------------------------------------------------------------------ lanes ---
+
+void lane_free(fc_ctx* c, Lane* L) {
+    for (void* p : {(void*)L->d, (void*)L->cur, (void*)L->pt, (void*)L->best, (void*)L->job_of, (void*)L->nscan,
+                    (void*)L->maxit, (void*)L->dchi2, (void*)L->chi2min, (void*)L->thr, (void*)L->active,
+                    (void*)L->next, (void*)L->fin, (void*)L->uslot, (void*)L->fb, (void*)L->fb2, (void*)L->fbslot,
+                    (void*)L->job_left, (void*)L->job_dead})
+        dfree(c, p);
+    *L = Lane{};
+}
+
+void lane_reset(Lane* L) {
+    L->n_active = 0;
+    L->n_first = 0;
+    L->free_ranges.clear();
+    L->free_ranges[0] = L->cap;
+    L->free_jobs.clear();
+    for (int j = kLaneJobs - 1; j >= 0; --j) L->free_jobs.push_back(j);
+    L->jobs.assign(kLaneJobs, nullptr);
+}
+
+fc_status lane_alloc(fc_ctx* c, Lane* L, Grid* g, const fc_opts& o, int64_t cap) {
+    lane_free(c, L);
+    L->g = g;
+    L->o = o;
+    L->cap = cap;
+    L->nfit = g->nfit;
+    fc_status st = FC_OK;
+    auto A = [&](auto** p, size_t count) {
+        if (st == FC_OK) st = dalloc_t(c, p, count);
+    };
+    A(&L->d, (size_t)cap * g->nfit);
+    A(&L->cur, cap);
+    A(&L->pt, cap);
+    A(&L->best, cap);
+    A(&L->job_of, cap);
+    A(&L->nscan, cap);
+    A(&L->maxit, cap);
+    A(&L->dchi2, cap);
+    A(&L->chi2min, cap);
+    A(&L->thr, cap);
+    A(&L->active, cap);
+    A(&L->next, cap);
+    A(&L->fin, cap);
+    A(&L->uslot, cap);
+    A(&L->fb, cap);
+    A(&L->fb2, cap);
+    A(&L->fbslot, cap);
+    A(&L->job_left, kLaneJobs);
+    A(&L->job_dead, kLaneJobs);
+    if (st != FC_OK) {
+        lane_free(c, L);
+        return st;
+    }
+    FC_CUDA(cudaMemsetAsync(L->job_dead, 0, kLaneJobs, c->stream));
+    lane_reset(L);
+    return FC_OK;
+}
+
+bool lane_reserve(Lane* L, int64_t n, int64_t* base) {
+    if (L->free_jobs.empty()) return false;
+    for (auto it = L->free_ranges.begin(); it != L->free_ranges.end(); ++it) {
+        if (it->second >= n) {
+            *base = it->first;
+            const int64_t rest = it->second - n;
+            L->free_ranges.erase(it);
+            if (rest) L->free_ranges[*base + n] = rest;
+            return true;
+        }
+    }
+    return false;
+}
+
+void lane_release(Lane* L, int64_t base, int64_t n) {
+    auto it = L->free_ranges.emplace(base, n).first;
+    auto nx = std::next(it);
+    if (nx != L->free_ranges.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        L->free_ranges.erase(nx);
+    }
+    if (it != L->free_ranges.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            L->free_ranges.erase(it);
+        }
+    }
+}
+
+bool lane_idle(const Lane* L) { return L->free_jobs.size() == (size_t)kLaneJobs; }
+
+// Admit a job into reserved range [base, base+n): data (fake, from the job's
+// seed, or the caller's), per-universe state, active-list entries.  On error
+// nothing of the job is left in the lane.
+//   ps_dev  [P] true points (device)      d_in  caller data [n][nfit] or NULL
+fc_status lane_admit(fc_ctx* c, Lane* L, const std::shared_ptr<LaneJob>& J, const int64_t* ps_host, int32_t P,
+                     int32_t U, uint64_t seed, int fluct, int max_iter, const float* d_in) {
+    Grid* g = L->g;
+    const int64_t n = J->n;
+    int64_t* ps_dev = nullptr;
+    FC_TRY(scratch(c, "ps", (size_t)P, &ps_dev));
+    FC_CUDA(cudaMemcpyAsync(ps_dev, ps_host, (size_t)P * 8, cudaMemcpyHostToDevice, c->stream));
+    float* dst = L->d + (size_t)J->base * g->nfit;
+    if (d_in) {
+        FC_TRY(copy_in(c, dst, d_in, (size_t)n * g->nfit * sizeof(float)));
+    } else {
+        double* L64 = nullptr;
+        float *L32 = nullptr, *s32 = nullptr;
+        FC_TRY(scratch(c, "L64", (size_t)P * g->nf * g->nf, &L64));
+        FC_TRY(scratch(c, "L32", (size_t)P * g->nf * g->nf, &L32));
+        FC_TRY(scratch(c, "s32", (size_t)P * g->nf, &s32));
+        launch_chol_sys(g->S_full, g->nf, g->F, ps_dev, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
+                        c->status_dev, c->stream);
+        FC_TRY(check_status(c));
+        launch_fake_data(L32, s32, g->nf, g->identity_collapse ? nullptr : g->collapse, g->nfit, ps_dev, P, U, seed,
+                         fluct == FC_FLUCT_GAUSS, dst, c->stream);
+    }
+    count_launch();
+    k_lane_admit<<<nb(n), 256, 0, c->stream>>>(ps_dev, n, U, J->base, (int8_t)max_iter, J->slot, L->cur, L->pt,
+                                               L->nscan, L->maxit, L->job_of, L->active + L->n_active);
+    launch_fill_i32(L->job_left + J->slot, 1, (int32_t)n, c->stream);
+    FC_CUDA(cudaGetLastError());
+    L->jobs[J->slot] = J;
+    L->n_active += n;
+    L->n_first += n;
+    return FC_OK;
+}
+
+// One scan (§2 steps 3-5) of every active universe of the lane: covariances
+// at each universe's current index, the scan itself (plain binary64, or the
+// tensor-core screen with certified binary64 resolution), and the advance /
+// finish bookkeeping.  Universes that finish get dchi2 and leave the active
+// list; the others continue from their new minimum in the next call.
+fc_status scan_once(fc_ctx* c, Lane* L) {
+    Grid* g = L->g;
+    const fc_opts& o = L->o;
+    fc_stats* S = c->acc;
+    const int64_t n_active = L->n_active;
+    if (n_active == 0) return FC_OK;
     const bool mixed = (o.precision == FC_PREC_MIXED);
     const int topk = o.top_k <= 8 ? 8 : 16;
-    int32_t *active = nullptr, *next = nullptr, *fin = nullptr, *uslot = nullptr, *cnts = nullptr;
-    FC_TRY(scratch(c, "active", (size_t)n, &active));
-    FC_TRY(scratch(c, "next", (size_t)n, &next));
-    FC_TRY(scratch(c, "fin", (size_t)n, &fin));
-    FC_TRY(scratch(c, "uslot", (size_t)n, &uslot));
+    // The probe at the true point is a loose first seed; when most universes
+    // are on their first scan a min-only pass tightens the seeds first.
+    const bool first_heavy = 2 * L->n_first >= n_active;
+    L->n_first = 0;
+    int32_t *active = L->active, *next = L->next, *fin = L->fin, *uslot = L->uslot, *cur = L->cur;
+    const float* d = L->d;
+    int32_t* cnts = nullptr;
     FC_TRY(scratch(c, "cnts", 8, &cnts));
-    launch_iota_i32(active, n, c->stream);
-    int64_t n_active = n;
+    UniverseState us;
+    us.cur = L->cur;
+    us.pt = L->pt;
+    us.nscan = L->nscan;
+    us.maxit = L->maxit;
+    us.job_of = L->job_of;
+    us.job_left = L->job_left;
     FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 9 * sizeof(unsigned long long), c->stream));
     // exact binary64 scan for `list`, then advance / finish them
-    auto exact_scan = [&](const int32_t* list, int64_t cnt, int scan_no) -> fc_status {
+    auto exact_scan = [&](const int32_t* list, int64_t cnt) -> fc_status {
         std::vector<int32_t> fq;
         int32_t* fslot = nullptr;
         FC_TRY(scratch(c, "fslot", (size_t)cnt, &fslot));
@@ -463,8 +674,9 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_TRY(scratch(c, "fb_pv", (size_t)cnt * nsp, &pv));
             FC_TRY(scratch(c, "fb_pg", (size_t)cnt * nsp, &pg));
             stage_begin(c);
-            launch_scan_resid(list, cnt, fslot, d, g->S_fit, g->G, g->nfit, g->W64, pv, pg, nsp, best32, c->stream);
-            FC_TRY(stage_end(c, &c->stats.ms_fallback));
+            launch_scan_resid(list, cnt, fslot, d, g->S_fit, g->G, g->nfit, g->W64, pv, pg, nsp, L->best,
+                              c->stream);
+            FC_TRY(stage_end(c, &S->ms_fallback));
         } else if (o.cov == FC_COV_IDENTITY) {
             FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
             launch_fill_i32(fslot, cnt, g->ident_slot, c->stream);
@@ -483,12 +695,12 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
         }
         if (!mixed) {
             stage_begin(c);
-            launch_scan64(list, cnt, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, best32,
+            launch_scan64(list, cnt, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, L->best,
                           c->stream);
-            FC_TRY(stage_end(c, &c->stats.ms_scan64));
+            FC_TRY(stage_end(c, &S->ms_scan64));
         }
         // finishing universes keep cur (the covariance of this scan); others move to their minimum
-        launch_advance(list, cnt, best32, cur, nscan, scan_no, max_iter, next, cnts + 2, fin, cnts + 3, c->stream);
+        launch_advance(list, cnt, L->best, us, next, cnts + 2, fin, cnts + 3, c->stream);
         int32_t n_fin = 0;
         FC_CUDA(cudaMemcpyAsync(&n_fin, cnts + 3, 4, cudaMemcpyDeviceToHost, c->stream));
         FC_TRY(sync(c));
@@ -500,14 +712,14 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             else
                 launch_lookup_slots(fin, n_fin, cur, g->slot_of, finslot, c->stream);
             stage_begin(c);
-            launch_finish(fin, n_fin, finslot, best32, p_of, U, d, g->S_fit, g->nfit, g->W64, dchi2, chi2min,
+            launch_finish(fin, n_fin, finslot, L->best, us, d, g->S_fit, g->nfit, g->W64, L->dchi2, L->chi2min,
                           c->stream);
-            FC_TRY(stage_end(c, &c->stats.ms_finish));
+            FC_TRY(stage_end(c, &S->ms_finish));
         }
         return FC_OK;
     };
-    for (int scan_no = 1; scan_no <= max_iter && n_active > 0; ++scan_no) {
-        // ---- covariances for this scan
+    // ---- covariances for this scan
+    {
         std::vector<int32_t> qs, slots;
         stage_begin(c);
         if (o.cov == FC_COV_IDENTITY) {
@@ -518,304 +730,489 @@ fc_status scan_loop(fc_ctx* c, Grid* g, int64_t n, int U, const fc_opts& o, cons
             FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, nullptr));
             launch_lookup_slots(active, n_active, cur, g->slot_of, uslot, c->stream);
         }
-        FC_TRY(stage_end(c, &c->stats.ms_cov));
-        c->stats.chi2_evals += n_active * g->G;
-        c->stats.scans += n_active;
-        FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 20, c->stream));  // n_fb, n_next, n_fin, n_fb2, n_tiles2
-        if (!mixed) {
-            FC_TRY(exact_scan(active, n_active, scan_no));
-        } else {
-            int32_t *fb = nullptr, *fb2 = nullptr, *fslot = nullptr;
-            float* thr = nullptr;
-            FC_TRY(scratch(c, "fb", (size_t)n_active, &fb));
-            FC_TRY(scratch(c, "fb2", (size_t)n_active, &fb2));
-            FC_TRY(scratch(c, "fbslot", (size_t)n_active, &fslot));
-            FC_TRY(scratch(c, "thr", (size_t)n, &thr));
-            // one certified screen round over `list` (grouped into tiles by covariance slot)
-            auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
-                                    int32_t* fb_out, int32_t* n_fb_out) -> fc_status {
-                const bool listing = (round == 2);
-                const int64_t n_slots = g->n_slots;
-                const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
-                const std::string sfx = round ? std::to_string(round + 1) : "";
-                int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
-                        *tj0 = nullptr, *cidx = nullptr;
-                uint16_t* Yt = nullptr;
-                float *cval = nullptr, *tau0 = nullptr;
-                float4* alpha = nullptr;
-                FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
-                FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
-                FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
-                FC_TRY(scratch(c, ("tslot" + sfx).c_str(), (size_t)max_tiles, &tslot));
-                FC_TRY(scratch(c, ("tuniv" + sfx).c_str(), (size_t)max_tiles * kBM, &tuniv));
-                FC_TRY(scratch(c, ("Yt" + sfx).c_str(), (size_t)max_tiles * kBM * 2 * g->K, &Yt));
-                FC_TRY(scratch(c, ("alpha" + sfx).c_str(), (size_t)max_tiles * kBM, &alpha));
-                FC_TRY(scratch(c, ("tau0" + sfx).c_str(), (size_t)max_tiles * kBM, &tau0));
-                FC_TRY(scratch(c, ("tile_j0" + sfx).c_str(), (size_t)max_tiles, &tj0));
-                const size_t per_row = listing ? 2 * kListCap : rtopk;
-                int32_t* ccount = nullptr;
-                FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cval));
-                FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cidx));
-                FC_TRY(scratch(c, "ccount", (size_t)max_tiles * kBM * 2, &ccount));
-                stage_begin(c);
-                launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
-                             c->stream);
-                int32_t n_tiles = 0;
-                FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
-                FC_TRY(sync(c));
-                launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
-                             g->gnorm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
-                if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
-                FC_TRY(stage_end(c, &c->stats.ms_prep));
-                stage_begin(c);
-                // round 0 of the first scan: min-only pass to tighten the seeds (the probe at the true point
-                // is loose there), then the top-k pass.  Later scans probe at the previous minimum, and later
-                // rounds are seeded by the best binary64 value (round 1: top-k, round 2: list).
-                const bool min_pass = (round == 0 && scan_no == 1);
-                for (int pass = min_pass ? 0 : 1; pass < 2; ++pass) {
-                    const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
-                    if (!launch_screen(g->K, rtopk, mode, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G,
-                                       g->G_pad, cval, cidx, ccount, c->status_dev, g->Qc, g->Qb, g->gnorm, alpha,
-                                       g->Sc32, g->nfit, c->n_sm, c->stream))
-                        return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
-                    c->stats.screen_launches += 1;
-                }
-                FC_TRY(stage_end(c, &c->stats.ms_screen));
-                c->stats.screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
-                ResolveArgs ra;
-                ra.tile_slot = tslot;
-                ra.tile_univ = tuniv;
-                ra.topk = rtopk;
-                ra.cval = cval;
-                ra.cidx = cidx;
-                ra.alpha = alpha;
-                ra.gnorm = g->gnorm;
-                ra.Qc = g->Qc;
-                ra.Qb = g->Qb;
-                ra.G_pad = g->G_pad;
-                ra.d = d;
-                ra.centre = g->centre;
-                ra.S_fit = g->S_fit;
-                ra.nfit = g->nfit;
-                ra.W64 = g->W64;
-                ra.cur = cur;
-                ra.p_of = p_of;
-                ra.U = U;
-                ra.scan_no = scan_no;
-                ra.max_iter = max_iter;
-                ra.best = best32;
-                ra.nscan = nscan;
-                ra.dchi2 = dchi2;
-                ra.chi2min = chi2min;
-                ra.next = next;
-                ra.n_next = cnts + 2;
-                ra.fb = fb_out;
-                ra.n_fb = n_fb_out;
-                ra.counters = c->counters_dev + 3 * round;
-                ra.thr = thr;
-                stage_begin(c);
-                if (listing)
-                    launch_resolve_list(ra, ccount, n_tiles, c->stream);
-                else
-                    launch_resolve(ra, n_tiles, c->stream);
-                FC_TRY(stage_end(c, &c->stats.ms_rescore));
-                return check_status(c);
-            };
-            FC_TRY(screen_round(0, active, n_active, uslot, topk, fb, cnts + 1));
-            int32_t n_fb = 0;
-            FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+        FC_TRY(stage_end(c, &S->ms_cov));
+    }
+    S->chi2_evals += n_active * g->G;
+    S->scans += n_active;
+    FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 20, c->stream));  // n_fb, n_next, n_fin, n_fb2, n_tiles2
+    if (!mixed) {
+        FC_TRY(exact_scan(active, n_active));
+    } else {
+        int32_t *fb = L->fb, *fb2 = L->fb2, *fslot = L->fbslot;
+        float* thr = L->thr;
+        // one certified screen round over `list` (grouped into tiles by covariance slot)
+        auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
+                                int32_t* fb_out, int32_t* n_fb_out) -> fc_status {
+            const bool listing = (round == 2);
+            const int64_t n_slots = g->n_slots;
+            const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
+            const std::string sfx = round ? std::to_string(round + 1) : "";
+            int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
+                    *tj0 = nullptr, *cidx = nullptr;
+            uint16_t* Yt = nullptr;
+            float *cval = nullptr, *tau0 = nullptr;
+            float4* alpha = nullptr;
+            FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
+            FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
+            FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
+            FC_TRY(scratch(c, ("tslot" + sfx).c_str(), (size_t)max_tiles, &tslot));
+            FC_TRY(scratch(c, ("tuniv" + sfx).c_str(), (size_t)max_tiles * kBM, &tuniv));
+            FC_TRY(scratch(c, ("Yt" + sfx).c_str(), (size_t)max_tiles * kBM * 2 * g->K, &Yt));
+            FC_TRY(scratch(c, ("alpha" + sfx).c_str(), (size_t)max_tiles * kBM, &alpha));
+            FC_TRY(scratch(c, ("tau0" + sfx).c_str(), (size_t)max_tiles * kBM, &tau0));
+            FC_TRY(scratch(c, ("tile_j0" + sfx).c_str(), (size_t)max_tiles, &tj0));
+            const size_t per_row = listing ? 2 * kListCap : rtopk;
+            int32_t* ccount = nullptr;
+            FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cval));
+            FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cidx));
+            FC_TRY(scratch(c, "ccount", (size_t)max_tiles * kBM * 2, &ccount));
+            stage_begin(c);
+            launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
+                         c->stream);
+            int32_t n_tiles = 0;
+            FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
             FC_TRY(sync(c));
-            if (n_fb > 0) {
-                // second certified round for the universes whose certificate failed
+            launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
+                         g->gnorm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
+            if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
+            FC_TRY(stage_end(c, &S->ms_prep));
+            stage_begin(c);
+            // round 0: a min-only pass to tighten the seeds when most rows are on their first scan (the probe
+            // at the true point is loose there; later scans probe at the previous minimum), then the top-k
+            // pass.  Later rounds are seeded by the best binary64 value (round 1: top-k, round 2: list).
+            const bool min_pass = (round == 0 && first_heavy);
+            for (int pass = min_pass ? 0 : 1; pass < 2; ++pass) {
+                const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
+                if (!launch_screen(g->K, rtopk, mode, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G, g->G_pad,
+                                   cval, cidx, ccount, c->status_dev, g->Qc, g->Qb, g->gnorm, alpha, g->Sc32,
+                                   g->nfit, c->n_sm, c->stream))
+                    return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
+                S->screen_launches += 1;
+            }
+            FC_TRY(stage_end(c, &S->ms_screen));
+            S->screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
+            ResolveArgs ra;
+            ra.tile_slot = tslot;
+            ra.tile_univ = tuniv;
+            ra.topk = rtopk;
+            ra.cval = cval;
+            ra.cidx = cidx;
+            ra.alpha = alpha;
+            ra.gnorm = g->gnorm;
+            ra.Qc = g->Qc;
+            ra.Qb = g->Qb;
+            ra.G_pad = g->G_pad;
+            ra.d = d;
+            ra.centre = g->centre;
+            ra.S_fit = g->S_fit;
+            ra.nfit = g->nfit;
+            ra.W64 = g->W64;
+            ra.cur = cur;
+            ra.pt = L->pt;
+            ra.maxit = L->maxit;
+            ra.job_of = L->job_of;
+            ra.job_left = L->job_left;
+            ra.best = L->best;
+            ra.nscan = L->nscan;
+            ra.dchi2 = L->dchi2;
+            ra.chi2min = L->chi2min;
+            ra.next = next;
+            ra.n_next = cnts + 2;
+            ra.fb = fb_out;
+            ra.n_fb = n_fb_out;
+            ra.counters = c->counters_dev + 3 * round;
+            ra.thr = thr;
+            stage_begin(c);
+            if (listing)
+                launch_resolve_list(ra, ccount, n_tiles, c->stream);
+            else
+                launch_resolve(ra, n_tiles, c->stream);
+            FC_TRY(stage_end(c, &S->ms_rescore));
+            return check_status(c);
+        };
+        FC_TRY(screen_round(0, active, n_active, uslot, topk, fb, cnts + 1));
+        int32_t n_fb = 0;
+        FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+        FC_TRY(sync(c));
+        if (n_fb > 0) {
+            // second certified round for the universes whose certificate failed
+            if (o.cov == FC_COV_IDENTITY)
+                launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
+            else
+                launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
+            FC_TRY(screen_round(1, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4));
+            int32_t n_fb2 = 0;
+            FC_CUDA(cudaMemcpyAsync(&n_fb2, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
+            FC_TRY(sync(c));
+            if (n_fb2 > 0) {
+                // third round: list every point that can still be the minimum
                 if (o.cov == FC_COV_IDENTITY)
-                    launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
+                    launch_fill_i32(fslot, n_fb2, g->ident_slot, c->stream);
                 else
-                    launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
-                FC_TRY(screen_round(1, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4));
-                int32_t n_fb2 = 0;
-                FC_CUDA(cudaMemcpyAsync(&n_fb2, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
+                    launch_lookup_slots(fb2, n_fb2, cur, g->slot_of, fslot, c->stream);
+                FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
+                FC_TRY(screen_round(2, fb2, n_fb2, fslot, kMaxTopK, fb, cnts + 1));
+                int32_t n_fb3 = 0;
+                FC_CUDA(cudaMemcpyAsync(&n_fb3, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
                 FC_TRY(sync(c));
-                if (n_fb2 > 0) {
-                    // third round: list every point that can still be the minimum
-                    if (o.cov == FC_COV_IDENTITY)
-                        launch_fill_i32(fslot, n_fb2, g->ident_slot, c->stream);
-                    else
-                        launch_lookup_slots(fb2, n_fb2, cur, g->slot_of, fslot, c->stream);
-                    FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
-                    FC_TRY(screen_round(2, fb2, n_fb2, fslot, kMaxTopK, fb, cnts + 1));
-                    int32_t n_fb3 = 0;
-                    FC_CUDA(cudaMemcpyAsync(&n_fb3, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
-                    FC_TRY(sync(c));
-                    if (n_fb3 > 0) FC_TRY(exact_scan(fb, n_fb3, scan_no));
-                }
+                if (n_fb3 > 0) FC_TRY(exact_scan(fb, n_fb3));
             }
         }
-        int32_t n_next = 0;
-        FC_CUDA(cudaMemcpyAsync(&n_next, cnts + 2, 4, cudaMemcpyDeviceToHost, c->stream));
-        FC_TRY(sync(c));
-        std::swap(active, next);
-        std::swap(c->scratch["active"], c->scratch["next"]);
-        n_active = n_next;
-        FC_TRY(check_status(c));
     }
+    int32_t n_next = 0;
+    FC_CUDA(cudaMemcpyAsync(&n_next, cnts + 2, 4, cudaMemcpyDeviceToHost, c->stream));
     // [0..2] round 1: screened, rescored, handed on; [3..5] round 2 likewise; [6] listed, [7] list overflow
     unsigned long long cn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     FC_CUDA(cudaMemcpyAsync(cn, c->counters_dev, sizeof(cn), cudaMemcpyDeviceToHost, c->stream));
     FC_TRY(sync(c));
-    c->stats.screened += (int64_t)(cn[0] + cn[3]);
-    c->stats.rescored += (int64_t)(cn[1] + cn[4] + cn[6]);
-    c->stats.rescreened += (int64_t)(cn[2] + cn[5]);
-    c->stats.fallback += (int64_t)cn[7];
+    std::swap(L->active, L->next);
+    L->n_active = n_next;
+    S->screened += (int64_t)(cn[0] + cn[3]);
+    S->rescored += (int64_t)(cn[1] + cn[4] + cn[6]);
+    S->rescreened += (int64_t)(cn[2] + cn[5]);
+    S->fallback += (int64_t)cn[7];
+    return check_status(c);
+}
+
+// Jobs of the lane whose universes have all finished: results to the
+// caller's buffers, range and job slot back to the lane.  `done` receives
+// them (in job-slot order).
+fc_status lane_harvest(fc_ctx* c, Lane* L, std::vector<std::shared_ptr<LaneJob>>* done) {
+    if (lane_idle(L)) return FC_OK;
+    std::vector<int32_t> left(kLaneJobs);
+    FC_CUDA(cudaMemcpyAsync(left.data(), L->job_left, kLaneJobs * 4, cudaMemcpyDeviceToHost, c->stream));
+    FC_TRY(sync(c));
+    for (int j = 0; j < kLaneJobs; ++j) {
+        std::shared_ptr<LaneJob> J = L->jobs[j];
+        if (!J || left[j] != 0) continue;
+        const bool cancelled = J->jr && J->jr->cancelled.load();
+        if (!cancelled) {
+            if (J->dchi2) FC_TRY(copy_out(c, J->dchi2, L->dchi2 + J->base, (size_t)J->n * 8));
+            if (J->chi2min) FC_TRY(copy_out(c, J->chi2min, L->chi2min + J->base, (size_t)J->n * 8));
+            if (J->nscans) FC_TRY(copy_out(c, J->nscans, L->nscan + J->base, (size_t)J->n));
+            if (J->best) {
+                int64_t* b64 = nullptr;
+                if (is_device_ptr(J->best)) {
+                    b64 = J->best;
+                } else {
+                    FC_TRY(scratch(c, "best64", (size_t)J->n, &b64));
+                }
+                count_launch();
+                k_widen<<<nb(J->n), 256, 0, c->stream>>>(L->best + J->base, J->n, b64);
+                if (b64 != J->best) FC_TRY(copy_out(c, J->best, b64, (size_t)J->n * 8));
+            }
+            FC_TRY(sync(c));
+        }
+        J->status = cancelled ? FC_ERR_CANCELLED : FC_OK;
+        J->done = true;
+        lane_release(L, J->base, J->n);
+        L->jobs[j] = nullptr;
+        L->free_jobs.push_back(j);
+        done->push_back(J);
+    }
     return FC_OK;
 }
 
+// Remove the universes of cancelled running jobs from the active list; they
+// complete (with FC_ERR_CANCELLED) at the next harvest.
+fc_status lane_drop_cancelled(fc_ctx* c, Lane* L) {
+    std::vector<uint8_t> dead(kLaneJobs, 0);
+    std::vector<int32_t> hit;
+    for (int j = 0; j < kLaneJobs; ++j) {
+        const auto& J = L->jobs[j];
+        if (J && J->jr && J->jr->cancelled.load()) {
+            dead[j] = 1;
+            hit.push_back(j);
+        }
+    }
+    if (hit.empty() || L->n_active == 0) return FC_OK;
+    int32_t* cnt = nullptr;
+    FC_TRY(scratch(c, "dropcnt", 1, &cnt));
+    FC_CUDA(cudaMemcpyAsync(L->job_dead, dead.data(), kLaneJobs, cudaMemcpyHostToDevice, c->stream));
+    FC_CUDA(cudaMemsetAsync(cnt, 0, 4, c->stream));
+    count_launch();
+    k_drop_jobs<<<nb(L->n_active), 256, 0, c->stream>>>(L->active, L->n_active, L->job_of, L->job_dead, L->next, cnt);
+    int32_t h = 0;
+    FC_CUDA(cudaMemcpyAsync(&h, cnt, 4, cudaMemcpyDeviceToHost, c->stream));
+    FC_CUDA(cudaMemsetAsync(L->job_dead, 0, kLaneJobs, c->stream));
+    FC_TRY(sync(c));
+    std::swap(L->active, L->next);
+    L->n_active = h;
+    for (int j : hit) launch_fill_i32(L->job_left + j, 1, 0, c->stream);
+    return FC_OK;
+}
+
+// Every job of the lane fails with `st` (a device error mid-scan cannot be
+// attributed to one job); the lane is emptied.
+void lane_fail_all(Lane* L, fc_status st, std::vector<std::shared_ptr<LaneJob>>* done) {
+    for (int j = 0; j < kLaneJobs; ++j) {
+        if (!L->jobs[j]) continue;
+        L->jobs[j]->status = st;
+        L->jobs[j]->done = true;
+        done->push_back(L->jobs[j]);
+    }
+    lane_reset(L);
+}
+
+fc_status check_points(const Grid* g, const int64_t* ps, int32_t P, std::vector<int64_t>* out) {
+    out->resize(P);
+    if (P == 0) return FC_OK;
+    if (is_device_ptr(ps)) {
+        FC_CUDA(cudaMemcpy(out->data(), ps, (size_t)P * 8, cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(out->data(), ps, (size_t)P * 8);
+    }
+    for (int64_t p : *out)
+        if (p < 0 || p >= g->G) return fail(FC_ERR_ARG, "grid index out of range");
+    return FC_OK;
+}
+
+int effective_max_iter(const fc_opts& o) { return o.cov == FC_COV_ITERATE ? o.max_iter : 1; }
+
+// The lane a synchronous call uses (kept by the context, grown on demand).
+fc_status sync_lane(fc_ctx* c, Grid* g, const fc_opts& o, int64_t n, Lane** out) {
+    Lane* L = &c->sync_lane;
+    if (L->cap < n || L->nfit < g->nfit) FC_TRY(lane_alloc(c, L, g, o, n));
+    L->g = g;
+    L->o = o;
+    lane_reset(L);
+    *out = L;
+    return FC_OK;
+}
+
+// Synchronous job through a lane of its own: admit, scan until every
+// universe finished, harvest.
+fc_status run_sync(fc_ctx* c, Grid* g, const fc_opts& o, const std::vector<int64_t>& ps, int32_t U, uint64_t seed,
+                   const float* d_in, double* dchi2, int64_t* best, int8_t* nscans, double* chi2min,
+                   cudaEvent_t ev_data) {
+    const int64_t n = (int64_t)ps.size() * U;
+    Lane* L = nullptr;
+    FC_TRY(sync_lane(c, g, o, n, &L));
+    auto J = std::make_shared<LaneJob>();
+    J->n = n;
+    J->dchi2 = dchi2;
+    J->best = best;
+    J->nscans = nscans;
+    J->chi2min = chi2min;
+    J->slot = L->free_jobs.back();
+    L->free_jobs.pop_back();
+    if (!lane_reserve(L, n, &J->base)) return fail(FC_ERR_STATE, "synchronous lane has no room");
+    fc_status st = lane_admit(c, L, J, ps.data(), (int32_t)ps.size(), U, seed, o.fluct, effective_max_iter(o), d_in);
+    if (ev_data) cudaEventRecord(ev_data, c->stream);
+    while (st == FC_OK && L->n_active > 0) st = scan_once(c, L);
+    std::vector<std::shared_ptr<LaneJob>> done;
+    if (st == FC_OK) st = lane_harvest(c, L, &done);
+    if (st == FC_OK && (done.size() != 1 || !lane_idle(L)))
+        st = fail(FC_ERR_STATE, "internal: synchronous job did not complete");
+    if (st != FC_OK) lane_reset(L);
+    return st;
+}
+
 fc_status run_points_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P, uint64_t seed, int32_t U,
-                          const fc_opts* opts_in, double* dchi2, int64_t* bestfit, int8_t* nscans,
-                          float* fake_only, int fluct_only) {
+                          const fc_opts* opts_in, double* dchi2, int64_t* bestfit, int8_t* nscans) {
     Grid* g = find_grid(c, grid_id);
     if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
     if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
     if (P < 0 || U < 0 || (P > 0 && !ps)) return fail(FC_ERR_ARG, "bad P, U or ps");
-    if (!fake_only && P > 0 && U > 0 && !dchi2) return fail(FC_ERR_ARG, "dchi2 output is required");
+    if (P > 0 && U > 0 && !dchi2) return fail(FC_ERR_ARG, "dchi2 output is required");
     fc_opts o;
     fc_default_opts(&o);
     if (opts_in) o = *opts_in;
-    if (fake_only) o.fluct = fluct_only;
     FC_TRY(validate_opts(&o, g));
     const int64_t n = (int64_t)P * U;
     if (n == 0) return FC_OK;
     if (n > (int64_t)INT32_MAX / 2) return fail(FC_ERR_ARG, "P * U too large");
-    std::vector<int64_t> hps(P);
-    if (is_device_ptr(ps)) {
-        FC_CUDA(cudaMemcpy(hps.data(), ps, (size_t)P * 8, cudaMemcpyDeviceToHost));
-    } else {
-        memcpy(hps.data(), ps, (size_t)P * 8);
-    }
-    for (int64_t p : hps)
-        if (p < 0 || p >= g->G) return fail(FC_ERR_ARG, "true point index out of range");
+    std::vector<int64_t> hps;
+    FC_TRY(check_points(g, ps, P, &hps));
     c->stats = fc_stats{};
+    c->acc = &c->stats;
     const long long launches0 = g_launches.load();
     cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventCreate(&e2);
     cudaEventRecord(e0, c->stream);
+    fc_status st = run_sync(c, g, o, hps, U, seed, nullptr, dchi2, bestfit, nscans, nullptr, e1);
+    if (st == FC_OK) {
+        cudaEventRecord(e2, c->stream);
+        st = sync(c);
+    }
+    if (st == FC_OK) {
+        float t_fake = 0, t_all = 0;
+        cudaEventElapsedTime(&t_fake, e0, e1);
+        cudaEventElapsedTime(&t_all, e0, e2);
+        c->stats.ms_fake = t_fake;
+        c->stats.ms_total = t_all;
+        c->stats.universes = n;
+        c->stats.kernel_launches = g_launches.load() - launches0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    return st;
+}
+
+// Fake data only: the systematic factors of the points, then the draws
+// straight into the caller's buffer when it is device memory.
+fc_status fake_data_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P, uint64_t seed, int32_t U,
+                         int fluct, float* out) {
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
+    if (P < 0 || U < 0 || (P > 0 && !ps)) return fail(FC_ERR_ARG, "bad P, U or ps");
+    const int64_t n = (int64_t)P * U;
+    if (n == 0) return FC_OK;
+    std::vector<int64_t> hps;
+    FC_TRY(check_points(g, ps, P, &hps));
     int64_t* ps_dev = nullptr;
     double* L64 = nullptr;
     float *L32 = nullptr, *s32 = nullptr, *d = nullptr;
-    int32_t *cur = nullptr, *p_of = nullptr, *best32 = nullptr;
-    int8_t* ns = nullptr;
-    double *dchi2_dev = nullptr, *chi2min = nullptr;
     FC_TRY(scratch(c, "ps", (size_t)P, &ps_dev));
     FC_CUDA(cudaMemcpyAsync(ps_dev, hps.data(), (size_t)P * 8, cudaMemcpyHostToDevice, c->stream));
     FC_TRY(scratch(c, "L64", (size_t)P * g->nf * g->nf, &L64));
     FC_TRY(scratch(c, "L32", (size_t)P * g->nf * g->nf, &L32));
     FC_TRY(scratch(c, "s32", (size_t)P * g->nf, &s32));
-    launch_chol_sys(g->S_full, g->nf, g->F, ps_dev, P, o.fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
+    launch_chol_sys(g->S_full, g->nf, g->F, ps_dev, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
                     c->status_dev, c->stream);
     FC_TRY(check_status(c));
-    if (fake_only && is_device_ptr(fake_only)) {
-        d = fake_only;
+    if (is_device_ptr(out)) {
+        d = out;
     } else {
         FC_TRY(scratch(c, "d", (size_t)n * g->nfit, &d));
     }
     launch_fake_data(L32, s32, g->nf, g->identity_collapse ? nullptr : g->collapse, g->nfit, ps_dev, P, U, seed,
-                     o.fluct == FC_FLUCT_GAUSS, d, c->stream);
-    cudaEventRecord(e1, c->stream);
-    if (fake_only) {
-        if (d != fake_only) FC_TRY(copy_out(c, fake_only, d, (size_t)n * g->nfit * sizeof(float)));
-        FC_TRY(sync(c));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaEventDestroy(e2);
-        return FC_OK;
-    }
-    FC_TRY(scratch(c, "cur", (size_t)n, &cur));
-    FC_TRY(scratch(c, "p_of", (size_t)P, &p_of));
-    FC_TRY(scratch(c, "best32", (size_t)n, &best32));
-    FC_TRY(scratch(c, "nscan", (size_t)n, &ns));
-    FC_TRY(scratch(c, "chi2min", (size_t)n, &chi2min));
-    const bool dev_out = is_device_ptr(dchi2);
-    if (dev_out) {
-        dchi2_dev = dchi2;
-    } else {
-        FC_TRY(scratch(c, "dchi2", (size_t)n, &dchi2_dev));
-    }
-    count_launch();
-    k_init_cur<<<nb(n), 256, 0, c->stream>>>(ps_dev, n, U, cur);
-    count_launch();
-    k_ps32<<<nb(P), 256, 0, c->stream>>>(ps_dev, P, p_of);
-    FC_TRY(scan_loop(c, g, n, U, o, d, cur, p_of, best32, ns, dchi2_dev, chi2min));
-    if (!dev_out) FC_TRY(copy_out(c, dchi2, dchi2_dev, (size_t)n * 8));
-    if (bestfit) {
-        int64_t* b64 = nullptr;
-        if (is_device_ptr(bestfit)) {
-            b64 = bestfit;
-        } else {
-            FC_TRY(scratch(c, "best64", (size_t)n, &b64));
-        }
-        count_launch();
-    k_widen<<<nb(n), 256, 0, c->stream>>>(best32, n, b64);
-        if (b64 != bestfit) FC_TRY(copy_out(c, bestfit, b64, (size_t)n * 8));
-    }
-    if (nscans) FC_TRY(copy_out(c, nscans, ns, (size_t)n));
-    cudaEventRecord(e2, c->stream);
-    FC_TRY(sync(c));
-    float t_fake = 0, t_all = 0;
-    cudaEventElapsedTime(&t_fake, e0, e1);
-    cudaEventElapsedTime(&t_all, e0, e2);
-    c->stats.ms_fake = t_fake;
-    c->stats.ms_total = t_all;
-    c->stats.universes = n;
-    c->stats.kernel_launches = g_launches.load() - launches0;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
-    return FC_OK;
+                     fluct == FC_FLUCT_GAUSS, d, c->stream);
+    if (d != out) FC_TRY(copy_out(c, out, d, (size_t)n * g->nfit * sizeof(float)));
+    return sync(c);
 }
 
 // --------------------------------------------------------------- serving ---
 
-}  // namespace
+// Lane key of a served job: jobs that agree on it share scans.
+bool same_key(int32_t grid_a, const fc_opts& a, int32_t grid_b, const fc_opts& b) {
+    return grid_a == grid_b && a.precision == b.precision && (a.top_k <= 8) == (b.top_k <= 8) &&
+           (a.cov == FC_COV_IDENTITY) == (b.cov == FC_COV_IDENTITY);
+}
 
-struct JobRec {
-    fc_job job;
-    std::vector<int64_t> ps;
-    std::atomic<int> state{FC_PENDING};
-    std::atomic<bool> cancelled{false};
-    std::chrono::steady_clock::time_point t_submit, t_done;
-    size_t reserve = 0;
-};
+bool same_lane(const Lane* L, const fc_job& j) { return L->g && same_key(L->g->id, L->o, j.grid_id, j.opts); }
 
-namespace {
+constexpr int64_t kServeLaneMin = int64_t(1) << 20;  // universes per serving lane at least
 
+void complete(fc_ctx* c, const std::shared_ptr<JobRec>& jr, fc_status st) {
+    std::lock_guard<std::mutex> lk(c->q_mu);
+    auto it = c->grids.find(jr->job.grid_id);
+    if (it != c->grids.end()) it->second->busy--;
+    jr->t_done = std::chrono::steady_clock::now();
+    jr->state.store(st);
+}
+
+// Try to admit a queued job.  Returns true when the job left the queue
+// (admitted, or completed with an error); false when its lane has no room now.
+bool serve_admit(fc_ctx* c, const std::shared_ptr<JobRec>& jr) {
+    const fc_job& jb = jr->job;
+    Grid* g = find_grid(c, jb.grid_id);
+    if (!g) {
+        complete(c, jr, FC_ERR_NOT_FOUND);
+        return true;
+    }
+    const int64_t n = (int64_t)jb.P * jb.U;
+    if (n == 0 || jr->cancelled.load()) {
+        complete(c, jr, jr->cancelled.load() ? FC_ERR_CANCELLED : FC_OK);
+        return true;
+    }
+    Lane* L = nullptr;
+    for (auto& l : c->lanes)
+        if (same_lane(l.get(), jb)) L = l.get();
+    if (!L) {
+        c->lanes.push_back(std::make_unique<Lane>());
+        L = c->lanes.back().get();
+    }
+    int64_t base = 0;
+    if (!L->cap || !lane_reserve(L, n, &base)) {
+        if (L->cap && !lane_idle(L)) return false;  // wait for running jobs of the lane to finish
+        // empty lane: (re)size it for this job, with headroom for later ones
+        fc_status st = lane_alloc(c, L, g, jb.opts, std::max(n, kServeLaneMin));
+        if (st != FC_OK) st = lane_alloc(c, L, g, jb.opts, n);
+        if (st != FC_OK) {
+            complete(c, jr, st);
+            return true;
+        }
+        lane_reserve(L, n, &base);
+    }
+    auto J = std::make_shared<LaneJob>();
+    J->jr = jr;
+    J->n = n;
+    J->base = base;
+    J->dchi2 = jb.dchi2;
+    J->best = jb.bestfit;
+    J->nscans = jb.nscans;
+    J->slot = L->free_jobs.back();
+    L->free_jobs.pop_back();
+    const fc_status st =
+        lane_admit(c, L, J, jr->ps.data(), jb.P, jb.U, jb.seed, jb.opts.fluct, effective_max_iter(jb.opts), nullptr);
+    if (st != FC_OK) {
+        lane_release(L, base, n);
+        L->free_jobs.push_back(J->slot);
+        complete(c, jr, st);
+    }
+    return true;
+}
+
+// The serving loop.  Each turn: admit queued jobs (FIFO per lane) into free
+// universe ranges, run one scan of every non-empty lane, hand back the jobs
+// that completed.  Jobs admitted in a turn join the scans of jobs that are
+// mid-iteration; a job's latency is its own universes' scans, not the batch's.
 void worker_main(fc_ctx* c) {
     cudaSetDevice(c->device);
+    std::deque<std::shared_ptr<JobRec>> waiting;
+    int64_t running = 0;  // jobs inside lanes
     for (;;) {
-        std::shared_ptr<JobRec> jr;
         {
             std::unique_lock<std::mutex> lk(c->q_mu);
-            c->q_cv.wait(lk, [&] { return c->stop || !c->queue.empty(); });
-            if (c->queue.empty() && c->stop) return;
-            jr = c->queue.front();
-            c->queue.pop_front();
+            c->q_cv.wait(lk, [&] { return c->stop || !c->queue.empty() || running > 0 || !waiting.empty(); });
+            while (!c->queue.empty()) {
+                waiting.push_back(c->queue.front());
+                c->queue.pop_front();
+            }
+            if (c->stop && waiting.empty() && running == 0) break;
         }
-        fc_status st;
-        if (jr->cancelled.load()) {
-            st = FC_ERR_CANCELLED;
-        } else {
-            std::lock_guard<std::mutex> lk(c->api_mu);
-            st = run_points_impl(c, jr->job.grid_id, jr->ps.data(), jr->job.P, jr->job.seed, jr->job.U,
-                                 &jr->job.opts, jr->job.dchi2, jr->job.bestfit, jr->job.nscans, nullptr, 0);
-            if (jr->cancelled.load()) st = FC_ERR_CANCELLED;
+        std::lock_guard<std::mutex> lk(c->api_mu);
+        c->acc = &c->serve_stats;
+        // admission, FIFO within a lane key
+        std::vector<const fc_job*> blocked;
+        for (auto it = waiting.begin(); it != waiting.end();) {
+            const fc_job& jb = (*it)->job;
+            bool skip = false;
+            for (const fc_job* b : blocked) skip = skip || same_key(b->grid_id, b->opts, jb.grid_id, jb.opts);
+            const int64_t n = (int64_t)jb.P * jb.U;
+            if (!skip && serve_admit(c, *it)) {
+                if (n > 0 && (*it)->state.load() == FC_PENDING) running++;
+                it = waiting.erase(it);
+            } else {
+                if (!skip) blocked.push_back(&jb);
+                ++it;
+            }
         }
-        {
-            std::lock_guard<std::mutex> lk(c->q_mu);
-            auto it = c->grids.find(jr->job.grid_id);
-            if (it != c->grids.end()) it->second->busy--;
-            jr->t_done = std::chrono::steady_clock::now();
-            jr->state.store(st);
+        // one scan per lane, then completions
+        for (auto& l : c->lanes) {
+            Lane* L = l.get();
+            if (lane_idle(L)) continue;
+            std::vector<std::shared_ptr<LaneJob>> done;
+            fc_status st = lane_drop_cancelled(c, L);
+            if (st == FC_OK) st = scan_once(c, L);
+            if (st == FC_OK) st = lane_harvest(c, L, &done);
+            if (st != FC_OK) lane_fail_all(L, st, &done);
+            for (auto& J : done) {
+                complete(c, J->jr, J->status);
+                running--;
+            }
         }
+        // release the memory of empty lanes when nothing waits
+        if (waiting.empty() && running == 0) {
+            for (auto& l : c->lanes) lane_free(c, l.get());
+            c->lanes.clear();
+        }
+        c->acc = &c->stats;
     }
 }
 
@@ -1013,6 +1410,15 @@ fc_status fc_unload_grid(fc_ctx* c, int32_t grid_id) {
     }
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->sync_lane.g == g) c->sync_lane.g = nullptr;
+    for (auto it = c->lanes.begin(); it != c->lanes.end();) {
+        if ((*it)->g == g) {
+            lane_free(c, it->get());
+            it = c->lanes.erase(it);
+        } else {
+            ++it;
+        }
+    }
     free_cache(c, g);
     dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
     dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->F);
@@ -1024,7 +1430,7 @@ fc_status fc_run_points(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P
     if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
     std::lock_guard<std::mutex> lk(c->api_mu);
     cudaSetDevice(c->device);
-    return run_points_impl(c, grid_id, ps, P, seed, U, opts, dchi2, bestfit, nscans, nullptr, 0);
+    return run_points_impl(c, grid_id, ps, P, seed, U, opts, dchi2, bestfit, nscans);
 }
 
 fc_status fc_run_point(fc_ctx* c, int32_t grid_id, int64_t p, uint64_t seed, int32_t U, const fc_opts* opts,
@@ -1038,10 +1444,7 @@ fc_status fc_fake_data(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P,
     if (fluct != FC_FLUCT_POISSON_SYS && fluct != FC_FLUCT_GAUSS) return fail(FC_ERR_ARG, "bad fluct");
     std::lock_guard<std::mutex> lk(c->api_mu);
     cudaSetDevice(c->device);
-    fc_opts o;
-    fc_default_opts(&o);
-    o.precision = FC_PREC_FP64;
-    return run_points_impl(c, grid_id, ps, P, seed, U, &o, nullptr, nullptr, nullptr, d, fluct);
+    return fake_data_impl(c, grid_id, ps, P, seed, U, fluct, d);
 }
 
 fc_status fc_covariance(fc_ctx* c, int32_t grid_id, int64_t q, double* A, double* L_sys) {
@@ -1089,42 +1492,12 @@ fc_status fc_scan(fc_ctx* c, int32_t grid_id, const float* d, const int64_t* q_c
     o.max_iter = 1;
     FC_TRY(validate_opts(&o, g));
     if (U == 0) return FC_OK;
-    std::vector<int64_t> hq(U);
-    if (is_device_ptr(q_cov))
-        FC_CUDA(cudaMemcpy(hq.data(), q_cov, (size_t)U * 8, cudaMemcpyDeviceToHost));
-    else
-        memcpy(hq.data(), q_cov, (size_t)U * 8);
-    for (int64_t q : hq)
-        if (q < 0 || q >= g->G) return fail(FC_ERR_ARG, "q_cov out of range");
+    std::vector<int64_t> hq;
+    FC_TRY(check_points(g, q_cov, U, &hq));
     c->stats = fc_stats{};
-    float* dd = nullptr;
-    int64_t* q64 = nullptr;
-    int32_t *cur = nullptr, *best32 = nullptr;
-    int8_t* ns = nullptr;
-    double *dchi2 = nullptr, *cm = nullptr;
-    FC_TRY(scratch(c, "d", (size_t)U * g->nfit, &dd));
-    FC_TRY(scratch(c, "scan_q", (size_t)U, &q64));
-    FC_TRY(scratch(c, "cur", (size_t)U, &cur));
-    FC_TRY(scratch(c, "best32", (size_t)U, &best32));
-    FC_TRY(scratch(c, "nscan", (size_t)U, &ns));
-    FC_TRY(scratch(c, "dchi2", (size_t)U, &dchi2));
-    FC_TRY(scratch(c, "chi2min", (size_t)U, &cm));
-    FC_TRY(copy_in(c, dd, d, (size_t)U * g->nfit * 4));
-    FC_CUDA(cudaMemcpyAsync(q64, hq.data(), (size_t)U * 8, cudaMemcpyHostToDevice, c->stream));
-    // every universe is its own "point" block (U = 1): p_of = its covariance index
-    count_launch();
-    k_init_cur<<<nb(U), 256, 0, c->stream>>>(q64, U, 1, cur);
-    int32_t* p_of = nullptr;
-    FC_TRY(scratch(c, "scan_pof", (size_t)U, &p_of));
-    count_launch();
-    k_ps32<<<nb(U), 256, 0, c->stream>>>(q64, U, p_of);
-    FC_TRY(scan_loop(c, g, U, 1, o, dd, cur, p_of, best32, ns, dchi2, cm));
-    int64_t* b64 = nullptr;
-    FC_TRY(scratch(c, "best64", (size_t)U, &b64));
-    count_launch();
-    k_widen<<<nb(U), 256, 0, c->stream>>>(best32, U, b64);
-    FC_TRY(copy_out(c, best, b64, (size_t)U * 8));
-    if (chi2_min) FC_TRY(copy_out(c, chi2_min, cm, (size_t)U * 8));
+    c->acc = &c->stats;
+    // every universe is its own point: its true point and first covariance are q_cov[u]
+    FC_TRY(run_sync(c, g, o, hq, 1, 0, d, nullptr, best, nullptr, chi2_min, nullptr));
     return sync(c);
 }
 
@@ -1174,6 +1547,11 @@ fc_status fc_submit(fc_ctx* c, const fc_job* job, uint64_t* ticket) {
     auto it = c->grids.find(job->grid_id);
     if (it == c->grids.end()) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
     const Grid* g = it->second.get();
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
+    FC_TRY(validate_opts(&jr->job.opts, g));
+    for (int64_t p : jr->ps)
+        if (p < 0 || p >= g->G) return fail(FC_ERR_ARG, "true point index out of range");
+    if ((int64_t)job->P * job->U > (int64_t)INT32_MAX / 2) return fail(FC_ERR_ARG, "P * U too large");
     // device memory this job needs at most (fake data, state, candidates); it must fit the budget
     const size_t n = (size_t)job->P * job->U;
     const size_t need = n * ((size_t)g->nfit * 4 + 64 + 16 * 8 + (size_t)g->K * 4);

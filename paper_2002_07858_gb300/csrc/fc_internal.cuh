@@ -123,11 +123,12 @@ struct ResolveArgs {
     int nfit;
     const double* W64;
     int32_t* cur;          // [n] covariance grid index, advanced for continuing universes
-    const int32_t* p_of;   // true point per block of U universes
-    int U;
-    int scan_no, max_iter;
+    const int32_t* pt;     // [n] true point of the universe
+    const int8_t* maxit;   // [n] scan limit of the universe
+    const int32_t* job_of; // [n] job of the universe
+    int32_t* job_left;     // [jobs] universes of the job still running
     int32_t* best;         // [n]
-    int8_t* nscan;         // [n]
+    int8_t* nscan;         // [n] scans done (incremented by every decided scan)
     double* dchi2;         // [n]
     double* chi2min;       // [n] nullable
     int32_t* next;         // next active list
@@ -145,13 +146,22 @@ void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st);
 
 // ---- final residual-form chi2 and dchi2 ----
+// Per-universe state of a scan: cur (covariance index), pt (true point),
+// nscan (scans done), maxit (limit), job_of / job_left (completion counting).
+struct UniverseState {
+    int32_t* cur;
+    const int32_t* pt;
+    int8_t* nscan;
+    const int8_t* maxit;
+    const int32_t* job_of;
+    int32_t* job_left;
+};
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot_of_list, const int32_t* best,
-                   const int32_t* p_of_univ_base, int U, const float* d, const double* S_fit, int nfit,
-                   const double* W64, double* dchi2, double* chi2min, cudaStream_t st);
+                   const UniverseState& us, const float* d, const double* S_fit, int nfit, const double* W64,
+                   double* dchi2, double* chi2min, cudaStream_t st);
 // advance: converged / exhausted universes -> finish list, others stay active
-void launch_advance(const int32_t* active, int64_t n_active, const int32_t* best, int32_t* cur, int8_t* nscan,
-                    int scan_no, int max_iter, int32_t* next_active, int32_t* n_next, int32_t* finish_list,
-                    int32_t* n_finish, cudaStream_t st);
+void launch_advance(const int32_t* active, int64_t n_active, const int32_t* best, const UniverseState& us,
+                    int32_t* next_active, int32_t* n_next, int32_t* finish_list, int32_t* n_finish, cudaStream_t st);
 
 // ---- quantiles ----
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st);

@@ -1010,15 +1010,16 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
     int32_t p = -1;
     if (state == 1) {
         a.best[u] = g_best;
-        finishing = (g_best == a.cur[u]) || (a.scan_no >= a.max_iter);
+        finishing = (g_best == a.cur[u]) || (a.nscan[u] + 1 >= a.maxit[u]);
         if (finishing) {
-            p = a.p_of[u / a.U];
+            p = a.pt[u];
             s_g[r][kItemP] = p;
             s_g[r][kItemMin] = g_best;
             if (p != g_best) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemP);
             if (!have_min) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemMin);
         } else {
             a.cur[u] = g_best;
+            a.nscan[u] = (int8_t)(a.nscan[u] + 1);
         }
     }
     const bool to_next = (state == 1 && !finishing);
@@ -1045,7 +1046,8 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         const double cmin = have_min ? chi2_min : s_res[r][kItemMin];
         a.dchi2[u] = (p == g_best) ? 0.0 : s_res[r][kItemP] - cmin;
         if (a.chi2min) a.chi2min[u] = cmin;
-        a.nscan[u] = (int8_t)a.scan_no;
+        a.nscan[u] = (int8_t)(a.nscan[u] + 1);
+        atomicSub(&a.job_left[a.job_of[u]], 1);
     }
 }
 
@@ -1094,9 +1096,9 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
         }
         warp_argmin(bv, bg);
         const int32_t cur_u = a.cur[u];
-        const bool finishing = (bg == cur_u) || (a.scan_no >= a.max_iter);
+        const bool finishing = (bg == cur_u) || (a.nscan[u] + 1 >= a.maxit[u]);
         if (finishing) {
-            const int p = a.p_of[u / a.U];
+            const int p = a.pt[u];
             double cp = 0.0;
             if (p != bg) {
                 // chi2_p in residual form, rows of W split over the lanes
@@ -1111,12 +1113,14 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
                 a.best[u] = bg;
                 a.dchi2[u] = (p == bg) ? 0.0 : cp - bv;
                 if (a.chi2min) a.chi2min[u] = bv;
-                a.nscan[u] = (int8_t)a.scan_no;
+                a.nscan[u] = (int8_t)(a.nscan[u] + 1);
+                atomicSub(&a.job_left[a.job_of[u]], 1);
                 atomicAdd(&a.counters[0], 1ull);
             }
         } else if (lane == 0) {
             a.best[u] = bg;
             a.cur[u] = bg;
+            a.nscan[u] = (int8_t)(a.nscan[u] + 1);
             a.next[atomicAdd(a.n_next, 1)] = u;
             atomicAdd(&a.counters[0], 1ull);
         }
@@ -1137,7 +1141,7 @@ __global__ void k_min_tau(const int32_t* __restrict__ tile_univ, int64_t n_rows,
 // the last scan's covariance (A = W^T W), dchi2 = chi2_p - chi2_min.
 __global__ void __launch_bounds__(256) k_finish(const int32_t* __restrict__ list, int64_t n,
                                                  const int32_t* __restrict__ uslot, const int32_t* __restrict__ best,
-                                                 const int32_t* __restrict__ p_of, int U, const float* __restrict__ d,
+                                                 UniverseState us, const float* __restrict__ d,
                                                  const double* __restrict__ Sfit, int nfit,
                                                  const double* __restrict__ W64, double* __restrict__ dchi2,
                                                  double* __restrict__ chi2min) {
@@ -1147,7 +1151,7 @@ __global__ void __launch_bounds__(256) k_finish(const int32_t* __restrict__ list
     if (i >= n) return;
     const int u = list[i];
     const int slot = uslot[i];
-    const int p = p_of[u / U];
+    const int p = us.pt[u];
     const int g = best[u];
     const float* du = d + (size_t)u * nfit;
     for (int j = lane; j < nfit; j += 32) {
@@ -1172,21 +1176,24 @@ __global__ void __launch_bounds__(256) k_finish(const int32_t* __restrict__ list
     if (lane == 0) {
         dchi2[u] = (p == g) ? 0.0 : cp - cm;
         if (chi2min) chi2min[u] = cm;
+        atomicSub(&us.job_left[us.job_of[u]], 1);
     }
 }
 
+// exact-path bookkeeping: a universe finishes when its minimum repeats its
+// covariance index or it used its last scan; the others move on
 __global__ void k_advance(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ best,
-                          int32_t* __restrict__ cur, int8_t* __restrict__ nscan, int scan_no, int max_iter,
-                          int32_t* __restrict__ next_active, int32_t* __restrict__ n_next,
+                          UniverseState us, int32_t* __restrict__ next_active, int32_t* __restrict__ n_next,
                           int32_t* __restrict__ fin, int32_t* __restrict__ n_fin) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int u = active[i];
-    if (best[u] == cur[u] || scan_no >= max_iter) {
-        nscan[u] = (int8_t)scan_no;
+    const int done = us.nscan[u] + 1;
+    us.nscan[u] = (int8_t)done;
+    if (best[u] == us.cur[u] || done >= us.maxit[u]) {
         fin[atomicAdd(n_fin, 1)] = u;
     } else {
-        cur[u] = best[u];
+        us.cur[u] = best[u];
         next_active[atomicAdd(n_next, 1)] = u;
     }
 }
@@ -1436,22 +1443,19 @@ void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
     k_resolve<<<(unsigned)n_tiles, kBM, smem, st>>>(a);
 }
 
-void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const int32_t* best, const int32_t* p_of,
-                   int U, const float* d, const double* Sfit, int nfit, const double* W64, double* dchi2,
-                   double* chi2min, cudaStream_t st) {
+void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const int32_t* best, const UniverseState& us,
+                   const float* d, const double* Sfit, int nfit, const double* W64, double* dchi2, double* chi2min,
+                   cudaStream_t st) {
     if (n <= 0) return;
     count_launch();
-    k_finish<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, best, p_of, U, d, Sfit, nfit, W64, dchi2,
-                                                      chi2min);
+    k_finish<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, best, us, d, Sfit, nfit, W64, dchi2, chi2min);
 }
 
-void launch_advance(const int32_t* active, int64_t n, const int32_t* best, int32_t* cur, int8_t* nscan, int scan_no,
-                    int max_iter, int32_t* next_active, int32_t* n_next, int32_t* fin, int32_t* n_fin,
-                    cudaStream_t st) {
+void launch_advance(const int32_t* active, int64_t n, const int32_t* best, const UniverseState& us,
+                    int32_t* next_active, int32_t* n_next, int32_t* fin, int32_t* n_fin, cudaStream_t st) {
     if (n <= 0) return;
     count_launch();
-    k_advance<<<blocks_for(n), kThreads, 0, st>>>(active, n, best, cur, nscan, scan_no, max_iter, next_active, n_next,
-                                                  fin, n_fin);
+    k_advance<<<blocks_for(n), kThreads, 0, st>>>(active, n, best, us, next_active, n_next, fin, n_fin);
 }
 
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st) {
