@@ -124,8 +124,7 @@ def _oracle_sample(w, target_s: float, nthreads: int, seed: int = 0, max_points:
     dt = time.perf_counter() - t0
     evals = float(ns.astype(np.int64).sum()) * w.G
     return {"value": evals / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-            "sample": f"{P} true points x {U} universes of the 100x100 grid (N 90->45), "
-                      f"{evals:.3e} chi2 evals in {dt:.1f} s",
+            "sample": f"{P} true points x {U} universes of {w.name}, {evals:.3e} chi2 evals in {dt:.1f} s",
             "universes_per_s": P * U / dt}
 
 
@@ -190,9 +189,20 @@ def run_native(args):
     rank, local_rank, ws, dist = _dist_init()
     torch.cuda.set_device(local_rank)
     fc.load()
-    w = workloads.cfg2(U=args.universes)
-    P_all = w.G if args.points is None else args.points
-    pts = np.linspace(0, w.G - 1, P_all).round().astype(np.int64) if args.points else np.arange(w.G, dtype=np.int64)
+    if args.config == "cfg3":
+        w = workloads.cfg3(U=args.universes or 500)
+        pts = w.points if args.points is None else w.points[np.linspace(0, len(w.points) - 1, args.points).astype(int)]
+        desc = (f"cfg3: D=3 64^3 grid (262144 points), N=120 (K=128), {len(pts)} seeded true points x {w.U} "
+                f"universes, <= {w.max_iter} scans, top-{args.top_k}")
+        l2 = "working set per step > L2 (screen B image 134 MB, q-vectors 6.3 MB per covariance)"
+    else:
+        w = workloads.cfg2(U=args.universes or 1000)
+        P_all = w.G if args.points is None else args.points
+        pts = (np.linspace(0, w.G - 1, P_all).round().astype(np.int64) if args.points
+               else np.arange(w.G, dtype=np.int64))
+        desc = (f"cfg2: D=2 100x100 grid, N 90->45 (pair collapse), all 1e4 true points x {w.U} universes, "
+                f"<= {w.max_iter} scans, top-{args.top_k}")
+        l2 = "working set per step > L2 (fake data 1.8 GB, screen A-tiles ~2 GB, q-vectors 0.8 GB)"
     P, U = len(pts), w.U
     n = P * U
     stream = torch.cuda.Stream()
@@ -276,8 +286,9 @@ def run_native(args):
         # ---- plain binary64 GPU fit on a sample (same metric)
         plain = None
         if not args.no_plain:
-            pp = torch.from_numpy(np.linspace(0, w.G - 1, args.plain_points).round().astype(np.int64)).to(dev)
-            m = args.plain_points * U
+            n_pp = args.plain_points if args.plain_points is not None else (1 if args.config == "cfg3" else 20)
+            pp = torch.from_numpy(np.linspace(0, w.G - 1, n_pp).round().astype(np.int64)).to(dev)
+            m = n_pp * U
             outs = (torch.empty(m, dtype=torch.float64, device=dev), torch.empty(m, dtype=torch.int64, device=dev),
                     torch.empty(m, dtype=torch.int8, device=dev))
             fc.fc_set_frac_cov(ctx, gid, w.F)
@@ -291,7 +302,7 @@ def run_native(args):
             torch.cuda.synchronize()
             st = fc.fc_get_stats(ctx)
             pv = st["chi2_evals"] / (a.elapsed_time(b) / 1e3)
-            plain = {"value": pv, "unit": UNIT, "sample": f"{args.plain_points} true points x {U} universes, "
+            plain = {"value": pv, "unit": UNIT, "sample": f"{n_pp} true points x {U} universes, "
                                                           "cold covariance cache", "mixed_speedup": value / ws / pv}
         cpu = None
         if not args.no_cpu_baseline:
@@ -301,12 +312,11 @@ def run_native(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32acc screen, f64 rescoring/cov",
                 "data": "synthetic",
-                "config": {"workload": "cfg2: D=2 100x100 grid, N 90->45 (pair collapse), all 1e4 true points x "
-                                       f"{U} universes, <= {w.max_iter} scans, top-{args.top_k}",
+                "config": {"workload": desc,
                            "global_batch": n * ws, "true_points": P, "universes_per_point": U,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "covariance_cache": "cold every step",
-                           "l2": "working set per step > L2 (fake data 1.8 GB, screen A-tiles ~2 GB, q-vectors 0.8 GB)"},
+                           "l2": l2},
                 "universes_per_s": univ / (ms / 1e3),
                 "plain_fp64_gpu": plain,
                 "stage_ms_per_step": stage,
@@ -321,6 +331,103 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def _serve_stream(fc, ctx, gids, sizes, rate, duration, seed, drain_s):
+    """Submit a cfg4 Poisson stream in real time, poll to completion; latency = submit -> done."""
+    import numpy as np
+
+    import workloads
+
+    jobs = workloads.cfg4_jobs(sizes, rate, duration, seed)
+    pending, lat, failed, evals, univ = {}, [], 0, 0, 0
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(jobs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(jobs) and jobs[i][0] <= now:
+            _, k, p, sd, U = jobs[i]
+            tk, outs = fc.fc_submit(ctx, gids[k], np.array([p], np.int64), sd, U, want_nscans=True)
+            pending[tk] = (k, U, outs)
+            i += 1
+        for tk in list(pending):
+            try:
+                st, ms = fc.fc_poll(ctx, tk)
+            except fc.FCError:
+                failed += 1
+                pending.pop(tk)
+                continue
+            if st == fc.FC_PENDING:
+                continue
+            k, U, outs = pending.pop(tk)
+            lat.append(ms)
+            evals += int(outs[2].astype(np.int64).sum()) * sizes[k]
+            univ += U
+        if now > duration + drain_s:
+            for tk in list(pending):
+                fc.fc_cancel(ctx, tk)
+            while pending:
+                for tk in list(pending):
+                    try:
+                        st, _ = fc.fc_poll(ctx, tk)
+                    except fc.FCError:
+                        st = None
+                    if st != fc.FC_PENDING:
+                        pending.pop(tk)
+                time.sleep(0.01)
+            break
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    a = np.array(lat) if lat else np.array([float("nan")])
+    return {"offered_jobs_per_s": rate, "window_s": duration, "jobs": len(jobs), "completed": len(lat),
+            "failed": failed, "dropped": len(jobs) - len(lat) - failed, "wall_s": wall,
+            "p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+            "mean_ms": float(a.mean()), "max_ms": float(a.max()),
+            "throughput_jobs_per_s": len(lat) / wall, "chi2_evals_per_s": evals / wall,
+            "universes_per_s": univ / wall}
+
+
+def run_serve(args):
+    """Serving stream (cfg4): a pool of resident grids, Poisson job arrivals, continuous batching.
+
+    Prints one JSON line with p50/p99 job latency at the offered rate (default
+    50 jobs/s, an overload on one GPU: its throughput is the saturation
+    throughput) and at half that measured throughput (utilisation < 1)."""
+    import numpy as np
+    import torch
+
+    import paper_2002_07858_gb300 as fc
+    import workloads
+
+    rank, local_rank, ws, dist = _dist_init()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    fc.load()
+    pool = workloads.cfg4_pool()
+    ctx = fc.fc_create(local_rank, 80 << 30, None)
+    gids = []
+    for w in pool:
+        g = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+        fc.fc_set_frac_cov(ctx, g, w.F)
+        gids.append(g)
+    sizes = [w.G for w in pool]
+    # warm-up: one small job per grid (scratch, lanes, a few covariances)
+    for g, G in zip(gids, sizes):
+        fc.fc_run_points(ctx, g, np.array([G // 2], np.int64), 1, 128)
+    with ClockSampler(local_rank) as clk:
+        over = _serve_stream(fc, ctx, gids, sizes, args.serve_rate, args.serve_seconds, 0, args.serve_drain)
+        low_rate = max(0.05, 0.5 * over["throughput_jobs_per_s"])
+        low = _serve_stream(fc, ctx, gids, sizes, low_rate, args.serve_seconds_low, 1, args.serve_drain)
+    line = {"metric": "p50/p99 job latency", "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "value": low["p99_ms"], "data": "synthetic",
+            "config": {"workload": "cfg4 serving stream: 8 resident grids (D 2-4, G log-U[1e3,1e6], N U{40..200}), "
+                                   "one true point per job, U log-U[100,1e4], Poisson arrivals",
+                       "grids": [w.name for w in pool], "hbm_budget_bytes": 80 << 30,
+                       "precision": "mixed (tensor-core screen + binary64 rescoring)", "max_iter": 5},
+            "overload": over, "below_saturation": low, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    fc.fc_destroy(ctx)
+
+
 def run_once(args):
     """One untimed FC job (for profilers): the configured points x universes, stats printed as JSON."""
     import numpy as np
@@ -329,8 +436,12 @@ def run_once(args):
     import workloads
 
     fc.load()
-    w = workloads.cfg2(U=args.universes)
-    pts = np.linspace(0, w.G - 1, args.points).round().astype(np.int64) if args.points else w.points
+    if args.config == "cfg3":
+        w = workloads.cfg3(U=args.universes or 500)
+        pts = w.points if args.points is None else w.points[np.linspace(0, len(w.points) - 1, args.points).astype(int)]
+    else:
+        w = workloads.cfg2(U=args.universes or 1000)
+        pts = np.linspace(0, w.G - 1, args.points).round().astype(np.int64) if args.points else w.points
     ctx = fc.fc_create(0)
     gid = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
     fc.fc_set_frac_cov(ctx, gid, w.F)
@@ -345,18 +456,27 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--universes", type=int, default=1000, help="universes per true point")
+    ap.add_argument("--config", default="cfg2", choices=["cfg2", "cfg3"],
+                    help="cfg2 (the metric's workload, default) or cfg3 (D=3, N=120, 2048 points x 500)")
+    ap.add_argument("--universes", type=int, default=None, help="universes per true point (default: the config's)")
     ap.add_argument("--points", type=int, default=None, help="true points (default: all 10^4)")
     ap.add_argument("--top-k", type=int, default=8)
-    ap.add_argument("--plain-points", type=int, default=20)
+    ap.add_argument("--plain-points", type=int, default=None, help="plain binary64 sample (default 20; cfg3: 1)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--once", action="store_true", help="run one untimed job and print its stats (for profilers)")
     ap.add_argument("--precision", type=int, default=1, help="with --once: 1 = mixed, 0 = plain fp64")
+    ap.add_argument("--serve", action="store_true", help="cfg4 serving stream: p50/p99 job latency (own JSON line)")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="offered jobs/s of the overload stream")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the overload stream")
+    ap.add_argument("--serve-seconds-low", type=float, default=20.0, help="arrival window below saturation")
+    ap.add_argument("--serve-drain", type=float, default=240.0, help="seconds after a window before cancelling")
     args = ap.parse_args()
     if args.once:
         run_once(args)
+    elif args.serve:
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -74,6 +74,21 @@ typedef struct {
     int32_t cov;        /* FC_COV_*   (default FC_COV_ITERATE)                       */
 } fc_opts;
 
+/* Kernel choices of one grid.  They change speed only: every choice gives
+ * the same dchi2, best fits and scan counts (the screen's decisions are
+ * certified and resolved in binary64).  fc_autotune picks them by timing. */
+enum { FC_QVEC_AUTO = 0,     /* tensor cores above N_fit ~ 61, binary32 SIMT below */
+       FC_QVEC_SIMT = 1,     /* q_g = s~^T A s~ in binary32, A in shared memory    */
+       FC_QVEC_TC = 2 };     /* q_g = |W s~|^2 on tcgen05 (bf16 hi/lo), K <= 128  */
+
+typedef struct {
+    int32_t qvec;           /* FC_QVEC_*                                            */
+    int32_t screen_stages;  /* screen pipeline depth, 0 = built-in choice (2..8)    */
+    int32_t screen_ybuf;    /* A-image buffers of the screen, 0 = built-in (1 or 2) */
+    int32_t cache_slots;    /* covariance-cache slots at most, 0 = as memory allows;
+                               one scan needs a slot per distinct covariance index */
+} fc_tuning;
+
 /* Counters and stage timings of the last synchronous call on a context.
  * Stage times are CUDA-event intervals on the context stream around each
  * stage's kernels, summed over scans (milliseconds). */
@@ -90,6 +105,10 @@ typedef struct {
     int64_t screen_launches;  /* launches of the tensor-core screen kernel             */
     double  screen_flops;     /* algorithmic flops of those launches: 2 N_fit per eval */
     double  ms_fake, ms_cov, ms_prep, ms_screen, ms_rescore, ms_fallback, ms_scan64, ms_finish, ms_total;
+    int64_t evicted;          /* covariance-cache slots handed to another grid index  */
+    int64_t cache_slots;      /* covariance-cache slots allocated for the grid        */
+    int64_t max_distinct_cov; /* most distinct covariance indices one scan needed     */
+    int64_t scan_waves;       /* cache-sized groups run by scans that needed more     */
 } fc_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -211,6 +230,22 @@ FC_API fc_status fc_cancel(fc_ctx* ctx, uint64_t ticket);
 FC_API fc_status fc_fake_data_noalloc(const double* S, int64_t G, int32_t N_full, const int32_t* collapse,
                                       int32_t N_fit, const double* F, const int64_t* ps, int32_t P, uint64_t seed,
                                       int32_t U, int32_t fluct, float* d, void* cuda_stream);
+
+/* Set / read the kernel choices of a loaded grid.  A choice the grid cannot
+ * use (FC_QVEC_TC above K = 128, a screen depth that does not fit in shared
+ * memory) gives FC_ERR_ARG.  Lowering cache_slots below the slots in use
+ * clears the grid's covariance cache.  fc_autotune keeps cache_slots.
+ * Errors: FC_ERR_ARG, FC_ERR_NOT_FOUND. */
+FC_API fc_status fc_set_tuning(fc_ctx* ctx, int32_t grid_id, const fc_tuning* t);
+FC_API fc_status fc_get_tuning(fc_ctx* ctx, int32_t grid_id, fc_tuning* t);
+
+/* Time the candidate kernel choices of a grid on a short synthetic run (one
+ * scan of fake universes at seeded grid points; the grid's F must be set),
+ * keep the fastest, and return it in *out (nullable).  cache_path (nullable):
+ * a text file of earlier results keyed by device, G, N_full, N_fit; a hit
+ * skips the timing, a miss appends the new result.  The covariance cache is
+ * cleared afterwards.  Errors: as fc_run_points. */
+FC_API fc_status fc_autotune(fc_ctx* ctx, int32_t grid_id, const char* cache_path, fc_tuning* out);
 
 /* Counters of the last synchronous run on this context. */
 FC_API fc_status fc_get_stats(fc_ctx* ctx, fc_stats* out);

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfc.so")
 
-SOURCES = ["fc_api.cu", "fc_kernels.cu", "fc_screen.cu", "fc_noalloc.cu"]
+SOURCES = ["fc_api.cu", "fc_kernels.cu", "fc_screen.cu", "fc_qvec.cu", "fc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -20,6 +20,7 @@ FC_ERR_TIMEOUT, FC_ERR_CANCELLED, FC_ERR_NOT_FOUND, FC_ERR_STATE = -5, -6, -7, -
 FC_PREC_FP64, FC_PREC_MIXED = 0, 1
 FC_FLUCT_POISSON_SYS, FC_FLUCT_GAUSS = 0, 1
 FC_COV_ITERATE, FC_COV_FIXED, FC_COV_IDENTITY = 0, 1, 2
+FC_QVEC_AUTO, FC_QVEC_SIMT, FC_QVEC_TC = 0, 1, 2
 
 _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_SPD", -3: "FC_ERR_BUDGET",
                  -4: "FC_ERR_CUDA", -5: "FC_ERR_TIMEOUT", -6: "FC_ERR_CANCELLED", -7: "FC_ERR_NOT_FOUND",
@@ -27,7 +28,8 @@ _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_
 
 EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set_frac_cov", "fc_unload_grid",
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
-           "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc"]
+           "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
+           "fc_set_tuning", "fc_get_tuning", "fc_autotune"]
 
 
 class FCError(RuntimeError):
@@ -47,7 +49,17 @@ class fc_stats(ctypes.Structure):
                 ("rescreened", ctypes.c_int64), ("fallback", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("screen_launches", ctypes.c_int64), ("screen_flops", ctypes.c_double)] + [
         (n, ctypes.c_double) for n in ("ms_fake", "ms_cov", "ms_prep", "ms_screen", "ms_rescore", "ms_fallback",
-                                       "ms_scan64", "ms_finish", "ms_total")]
+                                       "ms_scan64", "ms_finish", "ms_total")] + [
+        ("evicted", ctypes.c_int64), ("cache_slots", ctypes.c_int64), ("max_distinct_cov", ctypes.c_int64),
+        ("scan_waves", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fc_tuning(ctypes.Structure):
+    _fields_ = [("qvec", ctypes.c_int32), ("screen_stages", ctypes.c_int32), ("screen_ybuf", ctypes.c_int32),
+                ("cache_slots", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -96,6 +108,9 @@ def load(build: bool = False):
         "fc_poll": (st, [vp, u64, ctypes.POINTER(ctypes.c_double)]),
         "fc_cancel": (st, [vp, u64]),
         "fc_get_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
+        "fc_set_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
+        "fc_get_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
+        "fc_autotune": (st, [vp, i32, ctypes.c_char_p, ctypes.POINTER(fc_tuning)]),
         "fc_last_error": (ctypes.c_char_p, [vp]),
         "fc_fake_data_noalloc": (st, [vp, i64, i32, vp, i32, vp, vp, i32, u64, i32, i32, vp, vp]),
     }
@@ -274,6 +289,25 @@ def fc_poll(ctx, ticket: int):
 
 def fc_cancel(ctx, ticket: int):
     _check(load().fc_cancel(ctx, ticket), ctx)
+
+
+def fc_set_tuning(ctx, grid_id: int, qvec: int = 0, screen_stages: int = 0, screen_ybuf: int = 0,
+                  cache_slots: int = 0):
+    t = fc_tuning(qvec, screen_stages, screen_ybuf, cache_slots)
+    _check(load().fc_set_tuning(ctx, grid_id, ctypes.byref(t)), ctx)
+
+
+def fc_get_tuning(ctx, grid_id: int) -> dict:
+    t = fc_tuning()
+    _check(load().fc_get_tuning(ctx, grid_id, ctypes.byref(t)), ctx)
+    return t.as_dict()
+
+
+def fc_autotune(ctx, grid_id: int, cache_path: str | None = None) -> dict:
+    t = fc_tuning()
+    path = cache_path.encode() if cache_path else None
+    _check(load().fc_autotune(ctx, grid_id, path, ctypes.byref(t)), ctx)
+    return t.as_dict()
 
 
 def fc_get_stats(ctx) -> dict:

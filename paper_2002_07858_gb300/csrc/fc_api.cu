@@ -16,6 +16,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -88,21 +89,30 @@ struct Grid {
     uint16_t* Bt = nullptr;     // screen B image [G_pad/BN][2K/8][BN/8][8][8]
     int32_t* collapse = nullptr;
     double* F = nullptr;
-    // covariance cache (slot per grid index; slot `cap-1` reserved for A = I)
-    int64_t cap = 0;
-    int32_t n_slots = 0;
-    std::vector<int32_t> slot_host;  // [G]
+    // covariance cache: one slot per grid index used as a fit covariance (plus
+    // one for A = I).  Grows by doubling up to max_cap; when full, the slots
+    // least recently used by a scan are handed to new indices.
+    int64_t cap = 0;                 // slots allocated
+    int64_t max_cap = 0;             // memory-derived limit
+    int32_t n_slots = 0;             // slot ids handed out so far (high-water mark)
+    int64_t epoch = 0;               // ensure_slots calls
+    std::vector<int32_t> slot_host;  // [G] grid index -> slot or -1
+    std::vector<int32_t> slot_q;     // [cap] slot -> grid index (-2 identity)
+    std::vector<int64_t> slot_used;  // [cap] epoch of last use
     int32_t ident_slot = -1;
     int32_t* slot_of = nullptr;      // device [G]
-    double* A64 = nullptr;
-    double* W64 = nullptr;
+    double* A64 = nullptr;           // [cap][nfit][nfit]
+    double* W64 = nullptr;           // [cap][nfit][nfit]  A = W^T W, W lower triangular
     float* A32 = nullptr;
     float* rho = nullptr;
+    uint16_t* Wimg = nullptr;        // [cap][2K][K] bf16 hi/lo image of W (tensor-core q-vectors)
+    float4* wnorm = nullptr;         // [cap] Frobenius norms of W, W_lo, r_W, W_hi + W_lo
     float* Qc = nullptr;             // [cap][G_pad] (mixed)
     float* Qb = nullptr;
     uint16_t* Qb3 = nullptr;         // [cap][G_pad][8] bf16 q-step rows of the screen
     double* Q64 = nullptr;           // [cap][G]   (plain)
     std::vector<uint8_t> q32_ready, q64_ready;
+    fc_tuning tune{};                // kernel choices (all zero: built-in)
     int busy = 0;                    // queued jobs referencing the grid
 };
 
@@ -170,6 +180,7 @@ struct fc_ctx {
     size_t budget = 0;
     size_t used = 0;
     int n_sm = 148;
+    std::string dev_name;
     std::unordered_map<void*, size_t> allocs;
     std::map<int32_t, std::unique_ptr<Grid>> grids;
     int32_t next_grid = 1;
@@ -305,39 +316,94 @@ void free_cache(fc_ctx* c, Grid* g) {
     dfree(c, g->W64); g->W64 = nullptr;
     dfree(c, g->A32); g->A32 = nullptr;
     dfree(c, g->rho); g->rho = nullptr;
+    dfree(c, g->Wimg); g->Wimg = nullptr;
+    dfree(c, g->wnorm); g->wnorm = nullptr;
     dfree(c, g->Qc); g->Qc = nullptr;
     dfree(c, g->Qb); g->Qb = nullptr;
     dfree(c, g->Qb3); g->Qb3 = nullptr;
     dfree(c, g->Q64); g->Q64 = nullptr;
     g->cap = 0;
+    g->max_cap = 0;
     g->n_slots = 0;
     g->ident_slot = -1;
     g->slot_host.clear();
+    g->slot_q.clear();
+    g->slot_used.clear();
     g->q32_ready.clear();
     g->q64_ready.clear();
 }
 
-// Covariance cache: one slot per distinct grid index used as a fit covariance.
+// Forget every cached covariance (a new F); storage is kept.
+void reset_cache(fc_ctx* c, Grid* g) {
+    if (!g->cap) return;
+    g->n_slots = 0;
+    g->ident_slot = -1;
+    std::fill(g->slot_host.begin(), g->slot_host.end(), -1);
+    std::fill(g->slot_q.begin(), g->slot_q.end(), -1);
+    std::fill(g->slot_used.begin(), g->slot_used.end(), 0);
+    std::fill(g->q32_ready.begin(), g->q32_ready.end(), 0);
+    std::fill(g->q64_ready.begin(), g->q64_ready.end(), 0);
+    launch_fill_i32(g->slot_of, g->G, -1, c->stream);
+}
+
+// Device bytes one cache slot costs (covariance, W image, binary32 q-vectors,
+// binary64 q-vectors).
+size_t slot_bytes(const Grid* g) {
+    return (size_t)g->nfit * g->nfit * (8 + 8 + 4) + 4 + (size_t)4 * g->K * g->K + 16 + (size_t)g->G_pad * 24 +
+           (size_t)g->G * 8;
+}
+
+// Resize one per-slot array from `old_cap` to `new_cap` slots, keeping contents.
+template <class T>
+fc_status regrow(fc_ctx* c, T** p, size_t per_slot, int64_t old_cap, int64_t new_cap) {
+    T* q = nullptr;
+    FC_TRY(dalloc_t(c, &q, (size_t)new_cap * per_slot));
+    if (*p) {
+        FC_CUDA(cudaMemcpyAsync(q, *p, (size_t)old_cap * per_slot * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+        FC_CUDA(cudaStreamSynchronize(c->stream));
+        dfree(c, *p);
+    }
+    *p = q;
+    return FC_OK;
+}
+
+fc_status grow_cache(fc_ctx* c, Grid* g, int64_t new_cap) {
+    const int64_t old = g->cap;
+    const size_t n2 = (size_t)g->nfit * g->nfit;
+    FC_TRY(regrow(c, &g->A64, n2, old, new_cap));
+    FC_TRY(regrow(c, &g->W64, n2, old, new_cap));
+    FC_TRY(regrow(c, &g->A32, n2, old, new_cap));
+    FC_TRY(regrow(c, &g->rho, 1, old, new_cap));
+    if (g->Wimg) FC_TRY(regrow(c, &g->Wimg, (size_t)2 * g->K * g->K, old, new_cap));
+    if (g->wnorm) FC_TRY(regrow(c, &g->wnorm, 1, old, new_cap));
+    if (g->Qc) {
+        FC_TRY(regrow(c, &g->Qc, (size_t)g->G_pad, old, new_cap));
+        FC_TRY(regrow(c, &g->Qb, (size_t)g->G_pad, old, new_cap));
+        FC_TRY(regrow(c, &g->Qb3, (size_t)g->G_pad * 8, old, new_cap));
+    }
+    if (g->Q64) FC_TRY(regrow(c, &g->Q64, (size_t)g->G, old, new_cap));
+    g->cap = new_cap;
+    g->slot_q.resize(new_cap, -1);
+    g->slot_used.resize(new_cap, 0);
+    g->q32_ready.resize(new_cap, 0);
+    g->q64_ready.resize(new_cap, 0);
+    return FC_OK;
+}
+
+// Covariance cache of a grid: the limit is half of the device memory free at
+// first use (and half of what the context budget has left).
 fc_status ensure_cache(fc_ctx* c, Grid* g) {
     if (g->cap) return FC_OK;
-    const size_t per_slot = (size_t)g->nfit * g->nfit * (8 + 8 + 4) + 4;
     size_t free_b = 0, total_b = 0;
     FC_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    size_t limit = free_b / 4;
+    size_t limit = free_b / 2;
     if (c->budget) limit = std::min(limit, (c->budget > c->used ? c->budget - c->used : 0) / 2);
-    int64_t cap = std::min<int64_t>(g->G + 1, (int64_t)(limit / per_slot));
-    if (cap < 2) return fail(FC_ERR_BUDGET, "no room for the covariance cache");
-    g->cap = cap;
+    g->max_cap = std::min<int64_t>(g->G + 1, (int64_t)(limit / slot_bytes(g)));
+    if (g->max_cap < 2) return fail(FC_ERR_BUDGET, "no room for the covariance cache");
     g->slot_host.assign(g->G, -1);
-    g->q32_ready.assign(cap, 0);
-    g->q64_ready.assign(cap, 0);
     FC_TRY(dalloc_t(c, &g->slot_of, g->G));
     launch_fill_i32(g->slot_of, g->G, -1, c->stream);
-    FC_TRY(dalloc_t(c, &g->A64, (size_t)cap * g->nfit * g->nfit));
-    FC_TRY(dalloc_t(c, &g->W64, (size_t)cap * g->nfit * g->nfit));
-    FC_TRY(dalloc_t(c, &g->A32, (size_t)cap * g->nfit * g->nfit));
-    FC_TRY(dalloc_t(c, &g->rho, (size_t)cap));
-    return FC_OK;
+    return grow_cache(c, g, std::min<int64_t>(g->max_cap, 256));
 }
 
 fc_status ensure_q32_storage(fc_ctx* c, Grid* g) {
@@ -354,45 +420,110 @@ fc_status ensure_q64_storage(fc_ctx* c, Grid* g) {
     return FC_OK;
 }
 
+// q-vector kernel of a grid: the tensor-core form above K = 64 (where the
+// register-resident binary32 kernel stops) unless the grid's tuning says otherwise.
+bool use_qvec_tc(const Grid* g) {
+    if (!qvec_tc_supported(g->K)) return false;
+    if (g->tune.qvec == FC_QVEC_TC) return true;
+    if (g->tune.qvec == FC_QVEC_SIMT) return false;
+    return g->K > 64;
+}
+
 // Make sure every grid index in `qs` has a covariance slot (build + invert the
-// missing ones) and, for the given path, its q-vector.
+// missing ones) and, for the given path, its q-vector.  The slots of `qs` are
+// all resident when this returns: they are marked as used by this call, so a
+// full cache hands out only slots that this call does not need.
 fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int cov_mode, bool need_q32,
                        bool need_q64, std::vector<int32_t>* slots_out) {
     FC_TRY(ensure_cache(c, g));
-    std::vector<int32_t> new_q, new_s, q32_list, q64_list;
+    const int64_t ep = ++g->epoch;
+    std::vector<int32_t> new_q, new_s, q32_list, q64_list, evicted_q;
     if (slots_out) slots_out->clear();
+    // a slot for one more grid index: unused id, else grow, else the least recently used
+    std::vector<int32_t> lru;  // candidates for eviction, oldest first (built on first need)
+    size_t lru_pos = 0;
+    const int64_t lim = g->tune.cache_slots > 0 ? std::min<int64_t>(g->tune.cache_slots, g->max_cap) : g->max_cap;
+    auto take_slot = [&](int32_t* out) -> fc_status {
+        if (g->n_slots >= g->cap && g->cap < lim) {
+            const int64_t want = std::min<int64_t>(lim, std::max<int64_t>(2 * g->cap, g->n_slots + 1));
+            if (grow_cache(c, g, want) != FC_OK) g->max_cap = g->cap;  // no memory: evict from now on
+        }
+        if (g->n_slots < std::min<int64_t>(g->cap, lim)) {
+            *out = g->n_slots++;
+            return FC_OK;
+        }
+        if (lru.empty()) {
+            for (int32_t s = 0; s < g->n_slots; ++s)
+                if (g->slot_used[s] < ep && s != g->ident_slot) lru.push_back(s);
+            std::sort(lru.begin(), lru.end(),
+                      [&](int32_t a, int32_t b) { return g->slot_used[a] < g->slot_used[b]; });
+        }
+        while (lru_pos < lru.size() && g->slot_used[lru[lru_pos]] >= ep) ++lru_pos;
+        if (lru_pos >= lru.size())
+            return fail(FC_ERR_BUDGET, "covariance cache (" + std::to_string(g->cap) +
+                                           " slots) cannot hold the covariances of one scan");
+        const int32_t s = lru[lru_pos++];
+        const int32_t q_old = g->slot_q[s];
+        if (q_old >= 0) {
+            g->slot_host[q_old] = -1;
+            evicted_q.push_back(q_old);
+        }
+        g->q32_ready[s] = 0;
+        g->q64_ready[s] = 0;
+        *out = s;
+        return FC_OK;
+    };
+    if (cov_mode == FC_COV_IDENTITY) {
+        if (g->ident_slot < 0) {
+            int32_t s = -1;
+            FC_TRY(take_slot(&s));
+            g->ident_slot = s;
+            g->slot_q[s] = -2;
+            new_q.push_back(0);
+            new_s.push_back(s);
+        }
+        g->slot_used[g->ident_slot] = ep;
+        if (slots_out) slots_out->push_back(g->ident_slot);
+    } else {
+        for (int32_t q : qs) {
+            const int32_t s = g->slot_host[q];
+            if (s >= 0) g->slot_used[s] = ep;
+        }
+        for (int32_t q : qs) {
+            int32_t s = g->slot_host[q];
+            if (s < 0) {
+                FC_TRY(take_slot(&s));
+                g->slot_host[q] = s;
+                g->slot_q[s] = q;
+                g->slot_used[s] = ep;
+                new_q.push_back(q);
+                new_s.push_back(s);
+            }
+            if (slots_out) slots_out->push_back(s);
+        }
+    }
     auto want_q = [&](int32_t s) {
         if (need_q32 && !g->q32_ready[s]) { q32_list.push_back(s); g->q32_ready[s] = 1; }
         if (need_q64 && !g->q64_ready[s]) { q64_list.push_back(s); g->q64_ready[s] = 1; }
     };
     if (cov_mode == FC_COV_IDENTITY) {
-        if (g->ident_slot < 0) {
-            if (g->n_slots >= g->cap) return fail(FC_ERR_BUDGET, "covariance cache full");
-            g->ident_slot = g->n_slots++;
-            new_q.push_back(0);
-            new_s.push_back(g->ident_slot);
-        }
         want_q(g->ident_slot);
-        if (slots_out) slots_out->push_back(g->ident_slot);
     } else {
-        for (int32_t q : qs) {
-            int32_t s = g->slot_host[q];
-            if (s < 0) {
-                if (g->n_slots >= g->cap)
-                    return fail(FC_ERR_BUDGET, "covariance cache full (" + std::to_string(g->cap) + " slots)");
-                s = g->n_slots++;
-                g->slot_host[q] = s;
-                new_q.push_back(q);
-                new_s.push_back(s);
-            }
-            want_q(s);
-            if (slots_out) slots_out->push_back(s);
-        }
+        for (int32_t q : qs) want_q(g->slot_host[q]);
     }
     int32_t *dq = nullptr, *ds = nullptr;
-    const size_t nn = std::max(new_q.size(), std::max(q32_list.size(), q64_list.size()));
+    const size_t nn = std::max(std::max(new_q.size(), evicted_q.size()), std::max(q32_list.size(), q64_list.size()));
     FC_TRY(scratch(c, "slot_q", nn + 1, &dq));
     FC_TRY(scratch(c, "slot_s", nn + 1, &ds));
+    if (!evicted_q.empty()) {
+        // evicted grid indices lose their slot on the device too
+        std::vector<int32_t> minus(evicted_q.size(), -1);
+        FC_CUDA(cudaMemcpyAsync(dq, evicted_q.data(), evicted_q.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        FC_CUDA(cudaMemcpyAsync(ds, minus.data(), minus.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        launch_set_slots(dq, ds, (int)evicted_q.size(), g->slot_of, c->stream);
+        FC_TRY(sync(c));
+        c->acc->evicted += (int64_t)evicted_q.size();
+    }
     if (!new_q.empty()) {
         double* work = nullptr;
         FC_TRY(scratch(c, "cov_work", new_q.size() * g->nfit * g->nfit, &work));
@@ -408,9 +539,17 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
     if (!q32_list.empty()) {
         FC_TRY(ensure_q32_storage(c, g));
         FC_CUDA(cudaMemcpyAsync(ds, q32_list.data(), q32_list.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        launch_qvec32(g->Sc32, g->gnorm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(), g->Qc,
-                      g->Qb, g->Qb3, c->stream);
-        FC_TRY(sync(c));
+        if (use_qvec_tc(g)) {
+            if (!g->Wimg) FC_TRY(dalloc_t(c, &g->Wimg, (size_t)g->cap * 2 * g->K * g->K));
+            if (!g->wnorm) FC_TRY(dalloc_t(c, &g->wnorm, (size_t)g->cap));
+            launch_wimage(g->W64, ds, (int)q32_list.size(), g->nfit, g->K, g->Wimg, g->wnorm, c->stream);
+            launch_qvec_tc(g->Bt, g->Wimg, g->wnorm, g->gnorm, ds, (int)q32_list.size(), g->G, g->G_pad, g->nfit,
+                           g->K, g->Qc, g->Qb, g->Qb3, c->status_dev, c->n_sm, c->stream);
+        } else {
+            launch_qvec32(g->Sc32, g->gnorm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(),
+                          g->Qc, g->Qb, g->Qb3, c->stream);
+        }
+        FC_TRY(check_status(c));
     }
     if (!q64_list.empty()) {
         FC_TRY(ensure_q64_storage(c, g));
@@ -427,8 +566,8 @@ fc_status validate_opts(const fc_opts* o, const Grid* g) {
     if (o->top_k < 1 || o->top_k > kMaxTopK) return fail(FC_ERR_ARG, "top_k must be in [1, 16]");
     if (o->fluct != FC_FLUCT_POISSON_SYS && o->fluct != FC_FLUCT_GAUSS) return fail(FC_ERR_ARG, "bad fluct");
     if (o->cov < FC_COV_ITERATE || o->cov > FC_COV_IDENTITY) return fail(FC_ERR_ARG, "bad cov mode");
-    if (o->precision == FC_PREC_MIXED && g->K > 64)
-        return fail(FC_ERR_ARG, "the tensor-core screen supports N_fit <= 63 (use FC_PREC_FP64)");
+    if (o->precision == FC_PREC_MIXED && g->K > kMaxScreenK)
+        return fail(FC_ERR_ARG, "no tensor-core screen for this N_fit (use FC_PREC_FP64)");
     return FC_OK;
 }
 
@@ -470,6 +609,20 @@ __global__ void k_drop_jobs(const int32_t* __restrict__ active, int64_t n, const
     if (i >= n) return;
     const int32_t u = active[i];
     if (!dead[job_of[u]]) out[atomicAdd(n_out, 1)] = u;
+}
+
+__global__ void k_flag_list(const int32_t* __restrict__ q, int n, uint8_t* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[q[i]] = 1;
+}
+
+// The universes of `active` whose covariance index at the start of the scan
+// (cur0, by list position) is flagged, in any order.
+__global__ void k_select_cur(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ cur0,
+                             const uint8_t* __restrict__ flag, int32_t* __restrict__ out, int32_t* __restrict__ n_out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flag[cur0[i]]) out[atomicAdd(n_out, 1)] = active[i];
 }
 
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -718,144 +871,193 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
         }
         return FC_OK;
     };
-    // ---- covariances for this scan
-    {
-        std::vector<int32_t> qs, slots;
-        stage_begin(c);
-        if (o.cov == FC_COV_IDENTITY) {
-            FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, &slots));
-            launch_fill_i32(uslot, n_active, slots[0], c->stream);
+    // one scan of the universes in `list` (their covariance slots in lslot, by list position)
+    auto scan_list = [&](const int32_t* sl_list, int64_t sl_n, const int32_t* sl_slot) -> fc_status {
+        FC_CUDA(cudaMemsetAsync(cnts + 3, 0, 12, c->stream));  // n_fin, n_fb2, n_tiles
+        FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));   // n_fb
+        if (!mixed) {
+            FC_TRY(exact_scan(sl_list, sl_n));
         } else {
-            FC_TRY(distinct_cur(c, g, active, n_active, cur, qs));
-            FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, nullptr));
-            launch_lookup_slots(active, n_active, cur, g->slot_of, uslot, c->stream);
+            int32_t *fb = L->fb, *fb2 = L->fb2, *fslot = L->fbslot;
+            float* thr = L->thr;
+            // one certified screen round over `list` (grouped into tiles by covariance slot)
+            auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
+                                    int32_t* fb_out, int32_t* n_fb_out) -> fc_status {
+                const bool listing = (round == 2);
+                const int64_t n_slots = g->n_slots;
+                const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
+                const std::string sfx = round ? std::to_string(round + 1) : "";
+                int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
+                        *tj0 = nullptr, *cidx = nullptr;
+                uint16_t* Yt = nullptr;
+                float *cval = nullptr, *tau0 = nullptr;
+                float4* alpha = nullptr;
+                FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
+                FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
+                FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
+                FC_TRY(scratch(c, ("tslot" + sfx).c_str(), (size_t)max_tiles, &tslot));
+                FC_TRY(scratch(c, ("tuniv" + sfx).c_str(), (size_t)max_tiles * kBM, &tuniv));
+                FC_TRY(scratch(c, ("Yt" + sfx).c_str(), (size_t)max_tiles * kBM * 2 * g->K, &Yt));
+                FC_TRY(scratch(c, ("alpha" + sfx).c_str(), (size_t)max_tiles * kBM, &alpha));
+                FC_TRY(scratch(c, ("tau0" + sfx).c_str(), (size_t)max_tiles * kBM, &tau0));
+                FC_TRY(scratch(c, ("tile_j0" + sfx).c_str(), (size_t)max_tiles, &tj0));
+                const size_t per_row = listing ? 2 * kListCap : rtopk;
+                int32_t* ccount = nullptr;
+                FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cval));
+                FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cidx));
+                FC_TRY(scratch(c, "ccount", (size_t)max_tiles * kBM * 2, &ccount));
+                stage_begin(c);
+                launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
+                             c->stream);
+                int32_t n_tiles = 0;
+                FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
+                FC_TRY(sync(c));
+                launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
+                             g->gnorm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
+                if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
+                FC_TRY(stage_end(c, &S->ms_prep));
+                stage_begin(c);
+                // round 0: a min-only pass to tighten the seeds when most rows are on their first scan (the probe
+                // at the true point is loose there; later scans probe at the previous minimum), then the top-k
+                // pass.  Later rounds are seeded by the best binary64 value (round 1: top-k, round 2: list).
+                const bool min_pass = (round == 0 && first_heavy);
+                for (int pass = min_pass ? 0 : 1; pass < 2; ++pass) {
+                    const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
+                    if (!launch_screen(g->K, rtopk, mode, g->tune.screen_stages, g->tune.screen_ybuf, Yt, g->Bt, g->Qb3,
+                                       tslot, tau0, tj0, n_tiles, g->G, g->G_pad, cval, cidx, ccount, c->status_dev,
+                                       g->Qc, g->Qb, g->gnorm, alpha, g->Sc32, g->nfit, c->n_sm, c->stream))
+                        return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
+                    S->screen_launches += 1;
+                }
+                FC_TRY(stage_end(c, &S->ms_screen));
+                S->screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
+                ResolveArgs ra;
+                ra.tile_slot = tslot;
+                ra.tile_univ = tuniv;
+                ra.topk = rtopk;
+                ra.cval = cval;
+                ra.cidx = cidx;
+                ra.alpha = alpha;
+                ra.gnorm = g->gnorm;
+                ra.Qc = g->Qc;
+                ra.Qb = g->Qb;
+                ra.G_pad = g->G_pad;
+                ra.d = d;
+                ra.centre = g->centre;
+                ra.S_fit = g->S_fit;
+                ra.nfit = g->nfit;
+                ra.W64 = g->W64;
+                ra.cur = cur;
+                ra.pt = L->pt;
+                ra.maxit = L->maxit;
+                ra.job_of = L->job_of;
+                ra.job_left = L->job_left;
+                ra.best = L->best;
+                ra.nscan = L->nscan;
+                ra.dchi2 = L->dchi2;
+                ra.chi2min = L->chi2min;
+                ra.next = next;
+                ra.n_next = cnts + 2;
+                ra.fb = fb_out;
+                ra.n_fb = n_fb_out;
+                ra.counters = c->counters_dev + 3 * round;
+                ra.thr = thr;
+                stage_begin(c);
+                if (listing)
+                    launch_resolve_list(ra, ccount, n_tiles, c->stream);
+                else
+                    launch_resolve(ra, n_tiles, c->stream);
+                FC_TRY(stage_end(c, &S->ms_rescore));
+                return check_status(c);
+            };
+            FC_TRY(screen_round(0, sl_list, sl_n, sl_slot, topk, fb, cnts + 1));
+            int32_t n_fb = 0;
+            FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+            FC_TRY(sync(c));
+            if (n_fb > 0) {
+                // second certified round for the universes whose certificate failed
+                if (o.cov == FC_COV_IDENTITY)
+                    launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
+                else
+                    launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
+                FC_TRY(screen_round(1, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4));
+                int32_t n_fb2 = 0;
+                FC_CUDA(cudaMemcpyAsync(&n_fb2, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
+                FC_TRY(sync(c));
+                if (n_fb2 > 0) {
+                    // third round: list every point that can still be the minimum
+                    if (o.cov == FC_COV_IDENTITY)
+                        launch_fill_i32(fslot, n_fb2, g->ident_slot, c->stream);
+                    else
+                        launch_lookup_slots(fb2, n_fb2, cur, g->slot_of, fslot, c->stream);
+                    FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
+                    FC_TRY(screen_round(2, fb2, n_fb2, fslot, kMaxTopK, fb, cnts + 1));
+                    int32_t n_fb3 = 0;
+                    FC_CUDA(cudaMemcpyAsync(&n_fb3, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
+                    FC_TRY(sync(c));
+                    if (n_fb3 > 0) FC_TRY(exact_scan(fb, n_fb3));
+                }
+            }
         }
-        FC_TRY(stage_end(c, &S->ms_cov));
-    }
+        return FC_OK;
+    };
     S->chi2_evals += n_active * g->G;
     S->scans += n_active;
-    FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 20, c->stream));  // n_fb, n_next, n_fin, n_fb2, n_tiles2
-    if (!mixed) {
-        FC_TRY(exact_scan(active, n_active));
+    FC_CUDA(cudaMemsetAsync(cnts + 2, 0, 4, c->stream));  // n_next: continuing universes of the whole scan
+    // ---- covariances for this scan, then the scan itself; a scan that needs more
+    // distinct covariances than the cache holds runs in waves of cache-sized groups
+    if (o.cov == FC_COV_IDENTITY) {
+        std::vector<int32_t> qs, slots;
+        stage_begin(c);
+        FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, &slots));
+        launch_fill_i32(uslot, n_active, slots[0], c->stream);
+        FC_TRY(stage_end(c, &S->ms_cov));
+        FC_TRY(scan_list(active, n_active, uslot));
     } else {
-        int32_t *fb = L->fb, *fb2 = L->fb2, *fslot = L->fbslot;
-        float* thr = L->thr;
-        // one certified screen round over `list` (grouped into tiles by covariance slot)
-        auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
-                                int32_t* fb_out, int32_t* n_fb_out) -> fc_status {
-            const bool listing = (round == 2);
-            const int64_t n_slots = g->n_slots;
-            const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
-            const std::string sfx = round ? std::to_string(round + 1) : "";
-            int32_t *tcnt = nullptr, *tbase = nullptr, *tfill = nullptr, *tslot = nullptr, *tuniv = nullptr,
-                    *tj0 = nullptr, *cidx = nullptr;
-            uint16_t* Yt = nullptr;
-            float *cval = nullptr, *tau0 = nullptr;
-            float4* alpha = nullptr;
-            FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
-            FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
-            FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
-            FC_TRY(scratch(c, ("tslot" + sfx).c_str(), (size_t)max_tiles, &tslot));
-            FC_TRY(scratch(c, ("tuniv" + sfx).c_str(), (size_t)max_tiles * kBM, &tuniv));
-            FC_TRY(scratch(c, ("Yt" + sfx).c_str(), (size_t)max_tiles * kBM * 2 * g->K, &Yt));
-            FC_TRY(scratch(c, ("alpha" + sfx).c_str(), (size_t)max_tiles * kBM, &alpha));
-            FC_TRY(scratch(c, ("tau0" + sfx).c_str(), (size_t)max_tiles * kBM, &tau0));
-            FC_TRY(scratch(c, ("tile_j0" + sfx).c_str(), (size_t)max_tiles, &tj0));
-            const size_t per_row = listing ? 2 * kListCap : rtopk;
-            int32_t* ccount = nullptr;
-            FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cval));
-            FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cidx));
-            FC_TRY(scratch(c, "ccount", (size_t)max_tiles * kBM * 2, &ccount));
-            stage_begin(c);
-            launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
-                         c->stream);
-            int32_t n_tiles = 0;
-            FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
-            FC_TRY(sync(c));
-            launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
-                         g->gnorm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
-            if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
-            FC_TRY(stage_end(c, &S->ms_prep));
-            stage_begin(c);
-            // round 0: a min-only pass to tighten the seeds when most rows are on their first scan (the probe
-            // at the true point is loose there; later scans probe at the previous minimum), then the top-k
-            // pass.  Later rounds are seeded by the best binary64 value (round 1: top-k, round 2: list).
-            const bool min_pass = (round == 0 && first_heavy);
-            for (int pass = min_pass ? 0 : 1; pass < 2; ++pass) {
-                const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
-                if (!launch_screen(g->K, rtopk, mode, Yt, g->Bt, g->Qb3, tslot, tau0, tj0, n_tiles, g->G, g->G_pad,
-                                   cval, cidx, ccount, c->status_dev, g->Qc, g->Qb, g->gnorm, alpha, g->Sc32,
-                                   g->nfit, c->n_sm, c->stream))
-                    return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
-                S->screen_launches += 1;
-            }
-            FC_TRY(stage_end(c, &S->ms_screen));
-            S->screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
-            ResolveArgs ra;
-            ra.tile_slot = tslot;
-            ra.tile_univ = tuniv;
-            ra.topk = rtopk;
-            ra.cval = cval;
-            ra.cidx = cidx;
-            ra.alpha = alpha;
-            ra.gnorm = g->gnorm;
-            ra.Qc = g->Qc;
-            ra.Qb = g->Qb;
-            ra.G_pad = g->G_pad;
-            ra.d = d;
-            ra.centre = g->centre;
-            ra.S_fit = g->S_fit;
-            ra.nfit = g->nfit;
-            ra.W64 = g->W64;
-            ra.cur = cur;
-            ra.pt = L->pt;
-            ra.maxit = L->maxit;
-            ra.job_of = L->job_of;
-            ra.job_left = L->job_left;
-            ra.best = L->best;
-            ra.nscan = L->nscan;
-            ra.dchi2 = L->dchi2;
-            ra.chi2min = L->chi2min;
-            ra.next = next;
-            ra.n_next = cnts + 2;
-            ra.fb = fb_out;
-            ra.n_fb = n_fb_out;
-            ra.counters = c->counters_dev + 3 * round;
-            ra.thr = thr;
-            stage_begin(c);
-            if (listing)
-                launch_resolve_list(ra, ccount, n_tiles, c->stream);
-            else
-                launch_resolve(ra, n_tiles, c->stream);
-            FC_TRY(stage_end(c, &S->ms_rescore));
-            return check_status(c);
-        };
-        FC_TRY(screen_round(0, active, n_active, uslot, topk, fb, cnts + 1));
-        int32_t n_fb = 0;
-        FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
-        FC_TRY(sync(c));
-        if (n_fb > 0) {
-            // second certified round for the universes whose certificate failed
-            if (o.cov == FC_COV_IDENTITY)
-                launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
-            else
-                launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
-            FC_TRY(screen_round(1, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4));
-            int32_t n_fb2 = 0;
-            FC_CUDA(cudaMemcpyAsync(&n_fb2, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
-            FC_TRY(sync(c));
-            if (n_fb2 > 0) {
-                // third round: list every point that can still be the minimum
-                if (o.cov == FC_COV_IDENTITY)
-                    launch_fill_i32(fslot, n_fb2, g->ident_slot, c->stream);
-                else
-                    launch_lookup_slots(fb2, n_fb2, cur, g->slot_of, fslot, c->stream);
-                FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
-                FC_TRY(screen_round(2, fb2, n_fb2, fslot, kMaxTopK, fb, cnts + 1));
-                int32_t n_fb3 = 0;
-                FC_CUDA(cudaMemcpyAsync(&n_fb3, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
-                FC_TRY(sync(c));
-                if (n_fb3 > 0) FC_TRY(exact_scan(fb, n_fb3));
+        std::vector<int32_t> qs;
+        stage_begin(c);
+        FC_TRY(distinct_cur(c, g, active, n_active, cur, qs));
+        FC_TRY(ensure_cache(c, g));
+        const int64_t lim =
+            g->tune.cache_slots > 0 ? std::min<int64_t>(g->tune.cache_slots, g->max_cap) : g->max_cap;
+        const int64_t wave = std::max<int64_t>(1, lim - 1 - (g->ident_slot >= 0 ? 1 : 0));
+        S->max_distinct_cov = std::max<int64_t>(S->max_distinct_cov, (int64_t)qs.size());
+        if ((int64_t)qs.size() <= wave) {
+            FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, nullptr));
+            launch_lookup_slots(active, n_active, cur, g->slot_of, uslot, c->stream);
+            FC_TRY(stage_end(c, &S->ms_cov));
+            FC_TRY(scan_list(active, n_active, uslot));
+        } else {
+            FC_TRY(stage_end(c, &S->ms_cov));
+            uint8_t* flag = nullptr;
+            int32_t *wq = nullptr, *wl = nullptr, *wn = nullptr, *cur0 = nullptr;
+            FC_TRY(scratch(c, "wave_flag", (size_t)g->G, &flag));
+            FC_TRY(scratch(c, "wave_q", (size_t)wave, &wq));
+            FC_TRY(scratch(c, "wave_list", (size_t)n_active, &wl));
+            FC_TRY(scratch(c, "wave_n", 1, &wn));
+            FC_TRY(scratch(c, "wave_cur0", (size_t)n_active, &cur0));
+            // the waves partition the universes by their covariance index before any of them
+            // moves on (a universe advanced by one wave must not join a later one)
+            count_launch();
+            k_gather_cur<<<nb(n_active), 256, 0, c->stream>>>(active, (int)n_active, cur, cur0);
+            for (size_t q0 = 0; q0 < qs.size(); q0 += (size_t)wave) {
+                const std::vector<int32_t> part(qs.begin() + q0,
+                                                qs.begin() + std::min(qs.size(), q0 + (size_t)wave));
+                S->scan_waves += 1;
+                stage_begin(c);
+                // the universes whose covariance index is in this part
+                FC_CUDA(cudaMemsetAsync(flag, 0, (size_t)g->G, c->stream));
+                FC_CUDA(cudaMemsetAsync(wn, 0, 4, c->stream));
+                FC_CUDA(cudaMemcpyAsync(wq, part.data(), part.size() * 4, cudaMemcpyHostToDevice, c->stream));
+                count_launch(2);
+                k_flag_list<<<nb((int64_t)part.size()), 256, 0, c->stream>>>(wq, (int)part.size(), flag);
+                k_select_cur<<<nb(n_active), 256, 0, c->stream>>>(active, n_active, cur0, flag, wl, wn);
+                int32_t n_w = 0;
+                FC_CUDA(cudaMemcpyAsync(&n_w, wn, 4, cudaMemcpyDeviceToHost, c->stream));
+                FC_TRY(ensure_slots(c, g, part, o.cov, mixed, !mixed, nullptr));
+                launch_lookup_slots(wl, n_w, cur, g->slot_of, uslot, c->stream);
+                FC_TRY(stage_end(c, &S->ms_cov));
+                FC_TRY(scan_list(wl, n_w, uslot));
             }
         }
     }
@@ -1045,6 +1247,7 @@ fc_status run_points_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t
         c->stats.ms_total = t_all;
         c->stats.universes = n;
         c->stats.kernel_launches = g_launches.load() - launches0;
+        c->stats.cache_slots = g->cap;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1244,6 +1447,9 @@ fc_status fc_create(fc_ctx** out, int device, size_t hbm_budget_bytes, void* cud
     cudaDeviceProp prop;
     FC_CUDA(cudaGetDeviceProperties(&prop, device));
     c->n_sm = prop.multiProcessorCount;
+    c->dev_name = prop.name;
+    for (char& ch : c->dev_name)
+        if (ch == ' ' || ch == '\t') ch = '_';
     if (prop.major != 10) return fail(FC_ERR_ARG, "libfc is built for sm_103a (Blackwell Ultra); device is sm_" +
                                                       std::to_string(prop.major) + std::to_string(prop.minor));
     if (cuda_stream) {
@@ -1381,14 +1587,7 @@ fc_status fc_set_frac_cov(fc_ctx* c, int32_t grid_id, const double* F, int32_t n
                 return fail(FC_ERR_ARG, "F must be symmetric");
         }
     // a new F invalidates every cached covariance; keep the storage
-    if (g->cap) {
-        g->n_slots = 0;
-        g->ident_slot = -1;
-        std::fill(g->slot_host.begin(), g->slot_host.end(), -1);
-        std::fill(g->q32_ready.begin(), g->q32_ready.end(), 0);
-        std::fill(g->q64_ready.begin(), g->q64_ready.end(), 0);
-        launch_fill_i32(g->slot_of, g->G, -1, c->stream);
-    }
+    reset_cache(c, g);
     if (!g->F) FC_TRY(dalloc_t(c, &g->F, (size_t)nf * nf));
     FC_CUDA(cudaMemcpyAsync(g->F, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->stream));
     FC_TRY(sync(c));
@@ -1591,6 +1790,142 @@ fc_status fc_cancel(fc_ctx* c, uint64_t ticket) {
     if (it == c->jobs.end()) return fail(FC_ERR_NOT_FOUND, "unknown ticket");
     it->second->cancelled.store(true);
     return FC_OK;
+}
+
+fc_status fc_set_tuning(fc_ctx* c, int32_t grid_id, const fc_tuning* t) {
+    if (!c || !t) return fail(FC_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (t->qvec < FC_QVEC_AUTO || t->qvec > FC_QVEC_TC) return fail(FC_ERR_ARG, "bad qvec choice");
+    if (t->qvec == FC_QVEC_TC && !qvec_tc_supported(g->K))
+        return fail(FC_ERR_ARG, "tensor-core q-vectors need K <= 128");
+    if (!screen_config_ok(g->K, t->screen_stages, t->screen_ybuf))
+        return fail(FC_ERR_ARG, "screen depth / buffering does not fit this K");
+    if (t->cache_slots < 0 || t->cache_slots == 1) return fail(FC_ERR_ARG, "cache_slots must be 0 or >= 2");
+    // q-vectors from the other kernel have a different (still certified) bound: recompute them
+    if (t->qvec != g->tune.qvec) std::fill(g->q32_ready.begin(), g->q32_ready.end(), 0);
+    if (t->cache_slots > 0 && t->cache_slots < g->n_slots) reset_cache(c, g);
+    g->tune = *t;
+    return sync(c);
+}
+
+fc_status fc_get_tuning(fc_ctx* c, int32_t grid_id, fc_tuning* t) {
+    if (!c || !t) return fail(FC_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    *t = g->tune;
+    return FC_OK;
+}
+
+fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tuning* out) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
+    char key[512];
+    snprintf(key, sizeof key, "fc-tune-v1 dev=%s sms=%d G=%lld nf=%d nfit=%d", c->dev_name.c_str(), c->n_sm,
+             (long long)g->G, g->nf, g->nfit);
+    auto valid = [&](const fc_tuning& t) {
+        return t.qvec >= FC_QVEC_AUTO && t.qvec <= FC_QVEC_TC &&
+               (t.qvec != FC_QVEC_TC || qvec_tc_supported(g->K)) &&
+               screen_config_ok(g->K, t.screen_stages, t.screen_ybuf);
+    };
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[768];
+            const size_t kl = strlen(key);
+            bool hit = false;
+            fc_tuning t{};
+            while (fgets(line, sizeof line, f)) {
+                if (strncmp(line, key, kl) != 0 || line[kl] != ' ') continue;
+                fc_tuning r{};
+                r.cache_slots = g->tune.cache_slots;
+                if (sscanf(line + kl, " qvec=%d stages=%d ybuf=%d", &r.qvec, &r.screen_stages, &r.screen_ybuf) == 3 &&
+                    valid(r)) {
+                    t = r;
+                    hit = true;
+                }
+            }
+            fclose(f);
+            if (hit) {
+                if (t.qvec != g->tune.qvec) std::fill(g->q32_ready.begin(), g->q32_ready.end(), 0);
+                g->tune = t;
+                if (out) *out = t;
+                return FC_OK;
+            }
+        }
+    }
+    // the timing workload: one scan of 64 evenly spread true points x 256 universes
+    const int32_t P = (int32_t)std::min<int64_t>(64, g->G), U = 256;
+    std::vector<int64_t> ps(P);
+    for (int32_t i = 0; i < P; ++i) ps[i] = (int64_t)i * g->G / P;
+    std::vector<double> dchi2((size_t)P * U);
+    fc_opts o;
+    fc_default_opts(&o);
+    o.max_iter = 1;
+    const fc_tuning saved = g->tune;
+    auto run = [&](const fc_tuning& t, bool cold, fc_stats* st) -> fc_status {
+        if (t.qvec != g->tune.qvec || cold) reset_cache(c, g);
+        g->tune = t;
+        FC_TRY(run_points_impl(c, grid_id, ps.data(), P, 0x5eed, U, &o, dchi2.data(), nullptr, nullptr));
+        *st = c->stats;
+        return FC_OK;
+    };
+    fc_tuning best{};
+    best.cache_slots = saved.cache_slots;
+    fc_stats st{};
+    fc_status rc = FC_OK;
+    // q-vector kernel: covariance stage of a cold cache (P new covariances and q-vectors)
+    std::vector<int> qv{FC_QVEC_SIMT};
+    if (qvec_tc_supported(g->K)) qv.push_back(FC_QVEC_TC);
+    double best_ms = 1e300;
+    for (int q : qv) {
+        fc_tuning t = best;
+        t.qvec = q;
+        if ((rc = run(t, true, &st)) != FC_OK) break;  // warm-up: scratch, cache storage
+        if ((rc = run(t, true, &st)) != FC_OK) break;
+        if (st.ms_cov < best_ms) {
+            best_ms = st.ms_cov;
+            best.qvec = q;
+        }
+    }
+    // screen depth and A-image buffering, warm cache
+    if (rc == FC_OK) {
+        best_ms = 1e300;
+        const int ks[] = {2, 3, 4, 5, 6, 8};
+        for (int stg : ks)
+            for (int yb = 1; yb <= 2; ++yb) {
+                fc_tuning t = best;
+                t.screen_stages = stg;
+                t.screen_ybuf = yb;
+                if (!screen_config_ok(g->K, stg, yb)) continue;
+                if ((rc = run(t, false, &st)) != FC_OK) break;
+                if ((rc = run(t, false, &st)) != FC_OK) break;
+                if (st.ms_screen < best_ms) {
+                    best_ms = st.ms_screen;
+                    best.screen_stages = stg;
+                    best.screen_ybuf = yb;
+                }
+            }
+    }
+    reset_cache(c, g);
+    if (rc != FC_OK) {
+        g->tune = saved;
+        return rc;
+    }
+    g->tune = best;
+    if (out) *out = best;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s qvec=%d stages=%d ybuf=%d\n", key, best.qvec, best.screen_stages, best.screen_ybuf);
+            fclose(f);
+        }
+    }
+    return sync(c);
 }
 
 fc_status fc_get_stats(fc_ctx* c, fc_stats* out) {

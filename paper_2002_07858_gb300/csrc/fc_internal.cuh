@@ -1,5 +1,6 @@
 // fc_internal.cuh -- declarations shared by the library's translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -19,6 +20,7 @@ constexpr int kBM = 128;
 constexpr int kBN = 256;
 constexpr int kMaxTopK = 16;
 constexpr int kMaxBins = 200;
+constexpr int kMaxScreenK = 208;  // screen_k(kMaxBins): K of the largest tensor-core screen
 
 // Error flags written by kernels into the context's device status word.
 enum : int {
@@ -38,6 +40,39 @@ __host__ __device__ inline int screen_k(int nfit) { return ((nfit + 3 + 15) / 16
 // screen's products are within dot(alpha, gnorm) of -2 y.s~_g.
 __device__ __forceinline__ float bound_dot(const float4& a, const float4& n) {
     return 1.0001f * fmaf(a.x, n.x, fmaf(a.y, n.y, a.z * n.z));
+}
+
+// Relative slack on q_g: its own binary32 rounding plus its share of the
+// screen's binary32 accumulation.  The q-step enters the tensor-core
+// accumulator first and 3K products follow; bounding every add as a truncated
+// binary32 add of the running sum gives (3K + 3) 2^-23 |q| (K = padded N_fit).
+__device__ __forceinline__ float q_rel_slack(int nfit) {
+    const int K = screen_k(nfit);
+    return (float)(3 * K + 5) * 1.1920929e-07f;
+}
+
+// qb as a sum of three bf16 (hi + mid + lo <= qb, residual <= 2^-24 |qb|): the
+// B-operand row of the screen's q-step, [hi, mid, lo, 0, 0, 0, 0, 0].
+__device__ __forceinline__ void store_qb3(uint16_t* o, float qb) {
+    uint16_t h = 0, m = 0, l = 0;
+    if (qb < 1.0e38f) {
+        const __nv_bfloat16 bh = __float2bfloat16_rn(qb);
+        const float r1 = qb - __bfloat162float(bh);
+        const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(bm);
+        const __nv_bfloat16 bl = __float2bfloat16_rd(r2);
+        h = __bfloat16_as_ushort(bh);
+        m = __bfloat16_as_ushort(bm);
+        l = __bfloat16_as_ushort(bl);
+    } else {
+        h = __bfloat16_as_ushort(__float2bfloat16_rn(3.0e38f));  // padding rows: never a candidate
+    }
+    uint4 v;
+    v.x = (uint32_t)h | ((uint32_t)m << 16);
+    v.y = (uint32_t)l;
+    v.z = 0;
+    v.w = 0;
+    *reinterpret_cast<uint4*>(o) = v;
 }
 
 // ---- ingest (a1) ----
@@ -61,6 +96,15 @@ void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, con
 void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
                    cudaStream_t st);
+
+// q_g = ||W s~_g||^2 on the tensor cores (A = W^T W), for 16 <= K <= 128:
+// W image + norms per slot, then the certified Qc / Qb / Qb3 (see fc_qvec.cu).
+bool qvec_tc_supported(int K);
+void launch_wimage(const double* W64, const int32_t* slots, int n, int nfit, int K, uint16_t* Wimg, float4* wnorm,
+                   cudaStream_t st);
+bool launch_qvec_tc(const uint16_t* Bt, const uint16_t* Wimg, const float4* wnorm, const float4* gnorm,
+                    const int32_t* slots, int n, int64_t G, int64_t G_pad, int nfit, int K, float* Qc, float* Qb,
+                    uint16_t* Qb3, int* status, int n_sm, cudaStream_t st);
 
 // ---- fake data (a3) ----
 void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* collapse, int nfit,
@@ -100,7 +144,10 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
 // Returns false if the padded K has no compiled instance.
 constexpr int kScreenTopK = 0, kScreenMin = 1, kScreenList = 2;
 constexpr int kListCap = 64;
-bool launch_screen(int K, int topk, int mode, const uint16_t* Ytiles, const uint16_t* Btiles, const uint16_t* Qb3,
+// stages / ybuf: pipeline depth and A-image buffers, 0 = built-in choice.
+bool screen_config_ok(int K, int stages, int ybuf);
+bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Ytiles, const uint16_t* Btiles,
+                   const uint16_t* Qb3,
                    const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,

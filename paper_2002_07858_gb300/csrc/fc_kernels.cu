@@ -29,12 +29,6 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) {
     return (unsigned)b;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // (value, index) lexicographic minimum across a warp
 __device__ __forceinline__ void warp_argmin(double& v, int32_t& g) {
 #pragma unroll
@@ -60,6 +54,24 @@ __device__ double resid_chi2(const double* __restrict__ W, int n, const double* 
         for (int j = 0; j <= i; ++j) t = fma(Wi[j], r[j], t);
         acc = fma(t, t, acc);
     }
+    return acc;
+}
+
+// resid_chi2 spread over a warp with the same bits: lanes form the row dot
+// products t_i (each summed over j in order), lane 0 sums t_i^2 in row order.
+// r and t are this warp's shared-memory vectors; the result is lane 0's.
+__device__ double resid_chi2_warp(const double* __restrict__ W, int n, const double* r, double* t, int lane) {
+    for (int i = lane; i < n; i += 32) {
+        const double* Wi = W + i * n;
+        double x = 0.0;
+        for (int j = 0; j <= i; ++j) x = fma(Wi[j], r[j], x);
+        t[i] = x;
+    }
+    __syncwarp();
+    double acc = 0.0;
+    if (lane == 0)
+        for (int i = 0; i < n; ++i) acc = fma(t[i], t[i], acc);
+    __syncwarp();
     return acc;
 }
 
@@ -379,39 +391,6 @@ __global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, con
         }
         Q64[(size_t)slot * ldq + g] = q;
     }
-}
-
-// Relative slack on q_g: its own binary32 rounding plus its share of the
-// screen's binary32 accumulation.  The q-step enters the tensor-core
-// accumulator first and 3K products follow; bounding every add as a truncated
-// binary32 add of the running sum gives (3K + 3) 2^-23 |q| (K = padded N_fit).
-__device__ __forceinline__ float q_rel_slack(int nfit) {
-    const int K = screen_k(nfit);
-    return (float)(3 * K + 5) * 1.1920929e-07f;
-}
-
-// qb as a sum of three bf16 (hi + mid + lo <= qb, residual <= 2^-24 |qb|): the
-// B-operand row of the screen's q-step, [hi, mid, lo, 0, 0, 0, 0, 0].
-__device__ __forceinline__ void store_qb3(uint16_t* o, float qb) {
-    uint16_t h = 0, m = 0, l = 0;
-    if (qb < 1.0e38f) {
-        const __nv_bfloat16 bh = __float2bfloat16_rn(qb);
-        const float r1 = qb - __bfloat162float(bh);
-        const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-        const float r2 = r1 - __bfloat162float(bm);
-        const __nv_bfloat16 bl = __float2bfloat16_rd(r2);
-        h = __bfloat16_as_ushort(bh);
-        m = __bfloat16_as_ushort(bm);
-        l = __bfloat16_as_ushort(bl);
-    } else {
-        h = __bfloat16_as_ushort(__float2bfloat16_rn(3.0e38f));  // padding rows: never a candidate
-    }
-    uint4 v;
-    v.x = (uint32_t)h | ((uint32_t)m << 16);
-    v.y = (uint32_t)l;
-    v.z = 0;
-    v.w = 0;
-    *reinterpret_cast<uint4*>(o) = v;
 }
 
 // binary32 q_g with its rounding bound; s~_g held in registers (NMAX >= nfit,
@@ -754,17 +733,6 @@ __device__ __forceinline__ int64_t ytile_offset(int64_t t, int r, int c, int K) 
     return t * (int64_t)(2 * K * kBM) + (int64_t)(c >> 3) * (kBM * 8) + (r >> 3) * 64 + (r & 7) * 8 + (c & 7);
 }
 
-constexpr int kMaxScreenK = 64;
-
-// element i of a register array of packed bf16 pairs (i a loop index: the
-// compiler resolves the selection with predicated moves, no local memory)
-__device__ __forceinline__ void put_bf16(uint32_t (&w)[kMaxScreenK / 2], int i, uint16_t v) {
-#pragma unroll
-    for (int c = 0; c < kMaxScreenK / 2; ++c) {
-        if (c == (i >> 1)) w[c] = (i & 1) ? ((w[c] & 0x0000FFFFu) | ((uint32_t)v << 16)) : ((w[c] & 0xFFFF0000u) | v);
-    }
-}
-
 // One CTA per tile, one thread per row: y^ = A (d - v) in binary32, Y = -2 y^
 // split into bf16 hi + lo, and the error-bound coefficient alpha in the spare
 // column so that the screen directly yields a lower bound of chi2_g - c_u.
@@ -789,23 +757,9 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     const int u = tile_univ[t * kBM + r];
     // the screen walks this tile's grid tiles starting at the one holding row 0's q
     if (r == 0) tile_j0[t] = (u >= 0) ? cur[u] / kBN : 0;
-    // the row's A-image entries, written as 16-byte runs (8 bf16 of one core-matrix row)
-    uint32_t hw[kMaxScreenK / 2], lw[kMaxScreenK / 2];
-#pragma unroll
-    for (int c = 0; c < kMaxScreenK / 2; ++c) hw[c] = lw[c] = 0u;
-    auto store_row = [&]() {
-#pragma unroll
-        for (int c8 = 0; c8 < kMaxScreenK / 8; ++c8) {
-            if (c8 * 8 >= K) break;
-            uint4 vh, vl;
-            vh.x = hw[4 * c8]; vh.y = hw[4 * c8 + 1]; vh.z = hw[4 * c8 + 2]; vh.w = hw[4 * c8 + 3];
-            vl.x = lw[4 * c8]; vl.y = lw[4 * c8 + 1]; vl.z = lw[4 * c8 + 2]; vl.w = lw[4 * c8 + 3];
-            *reinterpret_cast<uint4*>(Yt + ytile_offset(t, r, c8 * 8, K)) = vh;
-            *reinterpret_cast<uint4*>(Yt + ytile_offset(t, r, K + c8 * 8, K)) = vl;
-        }
-    };
     if (u < 0) {
-        store_row();
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (int c8 = 0; c8 < 2 * K / 8; ++c8) *reinterpret_cast<uint4*>(Yt + ytile_offset(t, r, c8 * 8, K)) = z;
         alpha[t * kBM + r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         tau0[t * kBM + r] = -FLT_MAX;  // padding rows keep no candidate
         return;
@@ -820,23 +774,33 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
         dn2 = fmaf(dt[j], dt[j], dn2);
     }
     float yn2 = 0.0f, yl2 = 0.0f, yhl2 = 0.0f, ry2 = 0.0f, dot = 0.0f, adot = 0.0f;
-    for (int i = 0; i < nfit; ++i) {
-        float y = 0.0f;
-        for (int j = 0; j < nfit; ++j) y = fmaf(sA[i * nfit + j], dt[j], y);
-        const float Y = -2.0f * y;
-        yn2 = fmaf(Y, Y, yn2);
-        dot = fmaf(Y, sq[i], dot);
-        adot = fmaf(fabsf(Y), fabsf(sq[i]), adot);
-        const __nv_bfloat16 h = __float2bfloat16_rn(Y);
-        const float rem = Y - __bfloat162float(h);           // exact
-        const __nv_bfloat16 l = __float2bfloat16_rn(rem);
-        const float lo = __bfloat162float(l), hl = __bfloat162float(h) + lo;
-        const float ry = rem - lo;                            // exact: r_Y = Y - hi - lo
-        yl2 = fmaf(lo, lo, yl2);
-        yhl2 = fmaf(hl, hl, yhl2);
-        ry2 = fmaf(ry, ry, ry2);
-        put_bf16(hw, i, __bfloat16_as_ushort(h));
-        put_bf16(lw, i, __bfloat16_as_ushort(l));
+    // the row's A-image entries in runs of 8 columns (one 16-byte core-matrix row per half)
+    for (int c8 = 0; c8 < K / 8; ++c8) {
+        uint32_t vh[4] = {0u, 0u, 0u, 0u}, vl[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int ii = 0; ii < 8; ++ii) {
+            const int i = c8 * 8 + ii;
+            if (i < nfit) {
+                float y = 0.0f;
+                for (int j = 0; j < nfit; ++j) y = fmaf(sA[i * nfit + j], dt[j], y);
+                const float Y = -2.0f * y;
+                yn2 = fmaf(Y, Y, yn2);
+                dot = fmaf(Y, sq[i], dot);
+                adot = fmaf(fabsf(Y), fabsf(sq[i]), adot);
+                const __nv_bfloat16 h = __float2bfloat16_rn(Y);
+                const float rem = Y - __bfloat162float(h);           // exact
+                const __nv_bfloat16 l = __float2bfloat16_rn(rem);
+                const float lo = __bfloat162float(l), hl = __bfloat162float(h) + lo;
+                const float ry = rem - lo;                            // exact: r_Y = Y - hi - lo
+                yl2 = fmaf(lo, lo, yl2);
+                yhl2 = fmaf(hl, hl, yhl2);
+                ry2 = fmaf(ry, ry, ry2);
+                vh[ii >> 1] |= (uint32_t)__bfloat16_as_ushort(h) << (16 * (ii & 1));
+                vl[ii >> 1] |= (uint32_t)__bfloat16_as_ushort(l) << (16 * (ii & 1));
+            }
+        }
+        *reinterpret_cast<uint4*>(Yt + ytile_offset(t, r, c8 * 8, K)) = make_uint4(vh[0], vh[1], vh[2], vh[3]);
+        *reinterpret_cast<uint4*>(Yt + ytile_offset(t, r, K + c8 * 8, K)) = make_uint4(vl[0], vl[1], vl[2], vl[3]);
     }
     // -2 y.s~_g - (hi*hi + lo*hi + hi*lo products)  =  -2 (y - y^).s~ + Y_lo.S_lo + (Y_hi + Y_lo).r_S + r_Y.s~
     // and the binary32 accumulation of the 3K products (each add bounded as truncated, Sum|products| <= 1.02 |Y||s~|):
@@ -847,10 +811,10 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
                                  (float)(3 * K + 2) * 1.1920929e-07f * 1.02f * yn + sqrtf(ry2));
     const float4 al = make_float4(a_acc, 1.0001f * sqrtf(yl2), 1.0001f * sqrtf(yhl2), 0.0f);
     alpha[t * kBM + r] = al;
-    put_bf16(hw, nfit, __bfloat16_as_ushort(__float2bfloat16_rd(-al.x)));
-    put_bf16(hw, nfit + 1, __bfloat16_as_ushort(__float2bfloat16_rd(-al.y)));
-    put_bf16(hw, nfit + 2, __bfloat16_as_ushort(__float2bfloat16_rd(-al.z)));
-    store_row();
+    // the spare columns nfit .. nfit+2 of the hi half (written as zero above; same thread, program order)
+    Yt[ytile_offset(t, r, nfit, K)] = __bfloat16_as_ushort(__float2bfloat16_rd(-al.x));
+    Yt[ytile_offset(t, r, nfit + 1, K)] = __bfloat16_as_ushort(__float2bfloat16_rd(-al.y));
+    Yt[ytile_offset(t, r, nfit + 2, K)] = __bfloat16_as_ushort(__float2bfloat16_rd(-al.z));
     // probe at q: sigma^ = q^_q + Y.s~_q (binary32), |sigma^ - sigma| <= 2|y - y^||s~_q| + |q^ - q|
     //   + (nfit+1) 2^-24 (sum |Y_i s~_i| + |q^|) + 2^-24 |sigma^|   (all inside eps below)
     const int64_t qi = (int64_t)slot * G_pad + q;
@@ -1070,6 +1034,7 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
     __syncthreads();
     const double* W = staged ? sW : Wg;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double s_r[8][kMaxBins], s_t[8][kMaxBins];
     for (int r = warp; r < kBM; r += blockDim.x >> 5) {
         const int u = a.tile_univ[t * kBM + r];
         if (u < 0) continue;
@@ -1101,13 +1066,10 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
             const int p = a.pt[u];
             double cp = 0.0;
             if (p != bg) {
-                // chi2_p in residual form, rows of W split over the lanes
-                for (int i = lane; i < n; i += 32) {
-                    double tt = 0.0;
-                    for (int j = 0; j <= i; ++j) tt = fma(W[i * n + j], a.S_fit[(int64_t)p * n + j] - (double)du[j], tt);
-                    cp = fma(tt, tt, cp);
-                }
-                cp = warp_sum(cp);
+                // chi2_p in residual form (row dot products over the lanes, the bits of resid_chi2)
+                for (int j = lane; j < n; j += 32) s_r[warp][j] = a.S_fit[(int64_t)p * n + j] - (double)du[j];
+                __syncwarp();
+                cp = resid_chi2_warp(W, n, s_r[warp], s_t[warp], lane);
             }
             if (lane == 0) {
                 a.best[u] = bg;
@@ -1139,15 +1101,15 @@ __global__ void k_min_tau(const int32_t* __restrict__ tile_univ, int64_t n_rows,
 
 // One warp per finishing universe: chi2_p and chi2_min in residual form under
 // the last scan's covariance (A = W^T W), dchi2 = chi2_p - chi2_min.
-__global__ void __launch_bounds__(256) k_finish(const int32_t* __restrict__ list, int64_t n,
+__global__ void __launch_bounds__(128) k_finish(const int32_t* __restrict__ list, int64_t n,
                                                  const int32_t* __restrict__ uslot, const int32_t* __restrict__ best,
                                                  UniverseState us, const float* __restrict__ d,
                                                  const double* __restrict__ Sfit, int nfit,
                                                  const double* __restrict__ W64, double* __restrict__ dchi2,
                                                  double* __restrict__ chi2min) {
-    __shared__ double rp[8][kMaxBins], rm[8][kMaxBins];
+    __shared__ double rp[4][kMaxBins], rm[4][kMaxBins], tt[4][kMaxBins];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = blockIdx.x * 8LL + w;
+    const int64_t i = blockIdx.x * 4LL + w;
     if (i >= n) return;
     const int u = list[i];
     const int slot = uslot[i];
@@ -1160,19 +1122,9 @@ __global__ void __launch_bounds__(256) k_finish(const int32_t* __restrict__ list
     }
     __syncwarp();
     const double* W = W64 + (size_t)slot * nfit * nfit;
-    double cp = 0.0, cm = 0.0;
-    for (int r = lane; r < nfit; r += 32) {
-        double tp = 0.0, tm = 0.0;
-        for (int j = 0; j <= r; ++j) {
-            const double wv = W[r * nfit + j];
-            tp = fma(wv, rp[w][j], tp);
-            tm = fma(wv, rm[w][j], tm);
-        }
-        cp = fma(tp, tp, cp);
-        cm = fma(tm, tm, cm);
-    }
-    cp = warp_sum(cp);
-    cm = warp_sum(cm);
+    // both in the summation order of resid_chi2, so every path gives the same bits
+    const double cp = (p == g) ? 0.0 : resid_chi2_warp(W, nfit, rp[w], tt[w], lane);
+    const double cm = resid_chi2_warp(W, nfit, rm[w], tt[w], lane);
     if (lane == 0) {
         dchi2[u] = (p == g) ? 0.0 : cp - cm;
         if (chi2min) chi2min[u] = cm;
@@ -1448,7 +1400,7 @@ void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const i
                    cudaStream_t st) {
     if (n <= 0) return;
     count_launch();
-    k_finish<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, best, us, d, Sfit, nfit, W64, dchi2, chi2min);
+    k_finish<<<(unsigned)((n + 3) / 4), 128, 0, st>>>(list, n, uslot, best, us, d, Sfit, nfit, W64, dchi2, chi2min);
 }
 
 void launch_advance(const int32_t* active, int64_t n, const int32_t* best, const UniverseState& us,

@@ -33,122 +33,15 @@
 #include <cstdint>
 
 #include "fc_internal.cuh"
+#include "fc_tc.cuh"
 
 namespace fcdev {
 namespace {
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using namespace tc;
 
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-constexpr uint64_t kWaitNs = 2000000000ull;
-
-// Bounded wait on a phase parity; false on timeout or when another role aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
-    if (mbar_test(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if ((it & 63) == 0) {
-            if (abort_flag && *abort_flag) return false;
-            if (global_ns() - t0 > kWaitNs) return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// K-major operand without swizzle: 8x8 core matrices of 16-byte rows; LBO steps
-// along K between the two core matrices of a K=16 slice, SBO steps 8 rows.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, M = BM, N = BN
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// Asynchronous 32-column TMEM load (one lane = one row); the registers are only
-// valid after tmem_wait() on the same buffer.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-}
-
-// tcgen05.wait::ld; the buffer's registers are in-out operands so no use of
-// them can be scheduled before the wait.
-__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
-                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
-                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]),
-                   "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
-                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-}
-
-__device__ __forceinline__ void named_bar(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
+// kind::f16 instruction descriptor of the screen: D f32, A/B bf16, both K-major, M = BM, N = BN
+constexpr uint32_t kIdesc = idesc_bf16(kBM, kBN);
 
 // (value, index) insertion into a sorted list, lexicographic order
 template <int TOPK>
@@ -289,54 +182,77 @@ __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item
 constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
 constexpr int kEpiWarps = 8;
 constexpr int kHalfCols = kBN / 2;
+constexpr uint32_t kAChunk = kBM * 16u;  // one 8-column slab of the A image
+constexpr uint32_t kBChunk = kBN * 16u;  // one 8-column slab of the B image
+constexpr uint32_t kQBytes = kBN * 16u;  // one 8-column slab of q-step rows
+constexpr uint32_t kSmemMax = 232448u;   // dynamic shared memory per CTA
 
-template <int K, int STAGES, int YBUF>
-struct ScreenSmem {
-    static constexpr uint32_t kYBytes = 2u * K * kBM * 2u;   // hi + lo, bf16
-    static constexpr uint32_t kBBytes = 2u * K * kBN * 2u;
-    static constexpr uint32_t kQBytes = kBN * 16u;           // one 8-column slab of q-step rows
-    static constexpr uint32_t kAChunk = kBM * 16u;           // one 8-column slab of the A image
-    static constexpr uint32_t kBChunk = kBN * 16u;
-    static constexpr uint32_t kOffY = 0;
-    static constexpr uint32_t kOffB = YBUF * kYBytes;
-    static constexpr uint32_t kOffQ = kOffB + STAGES * kBBytes;
-    static constexpr uint32_t kOffOnes = kOffQ + STAGES * kQBytes;   // A slab of the q-step: [1,1,1,0..] per row
-    static constexpr uint32_t kOffZero = kOffOnes + kAChunk;         // second slab of the q-step, all zero
-    // per epilogue warp 4 KB: slow-path scratch inside a tile, top-k hand-over at the end of a row tile
-    static constexpr uint32_t kOffScratch = kOffZero + kBChunk;
-    static constexpr uint32_t kOffBar = kOffScratch + kEpiWarps * 4096;
-    static constexpr uint32_t kNumBars = 2 + 2 + STAGES + STAGES + 2 + 2 + 1;
-    static constexpr uint32_t kBytes = kOffBar + kNumBars * 8 + 16 + 1024;
+// Shared-memory plan of one screen launch.  A pipeline stage holds either a
+// whole B tile (2K columns x BN rows, for K <= 64) or, with kchunk, one
+// 16-column K slice of it (two hi slabs, two lo slabs) so that large K still
+// gets a deep pipeline; the stage's q-step slab follows its B part.
+struct ScreenLayout {
+    int K, stages, ybuf, kchunk;
+    uint32_t y_bytes;       // one A-image tile: 2K columns x BM rows, bf16
+    uint32_t bpart_bytes;   // B part of a stage
+    uint32_t stage_bytes;   // B part + q slab
+    uint32_t off_b, off_ones, off_zero, off_scratch, off_bar, bytes;
 };
 
-template <int K, int TOPK, int STAGES, int YBUF, int MODE>
+constexpr int kNumBars(int stages) { return 2 + 2 + stages + stages + 2 + 2 + 1; }
+
+inline ScreenLayout screen_layout(int K, int stages, int ybuf, int kchunk) {
+    ScreenLayout l{};
+    l.K = K;
+    l.stages = stages;
+    l.ybuf = ybuf;
+    l.kchunk = kchunk;
+    l.y_bytes = 2u * K * kBM * 2u;
+    l.bpart_bytes = kchunk ? 4u * kBChunk : 2u * K * kBN * 2u;
+    l.stage_bytes = l.bpart_bytes + kQBytes;
+    l.off_b = ybuf * l.y_bytes;
+    l.off_ones = l.off_b + stages * l.stage_bytes;  // A slab of the q-step: [1,1,1,0..] per row
+    l.off_zero = l.off_ones + kAChunk;               // second slab of the q-step, all zero
+    // per epilogue warp 4 KB: slow-path scratch inside a tile, top-k hand-over at the end of a row tile
+    l.off_scratch = l.off_zero + kBChunk;
+    l.off_bar = l.off_scratch + kEpiWarps * 4096;
+    l.bytes = l.off_bar + kNumBars(stages) * 8 + 16 + 1024;
+    return l;
+}
+
+template <int TOPK, int MODE, bool KCHUNK>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
              const int32_t* __restrict__ tile_slot, float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
              int64_t n_tiles, int64_t G, int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
-             int32_t* __restrict__ cand_count, int* __restrict__ status, ProbeArgs pa) {
-    using L = ScreenSmem<K, STAGES, YBUF>;
+             int32_t* __restrict__ cand_count, int* __restrict__ status, ProbeArgs pa, ScreenLayout lay) {
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_addr(smem);
-    uint64_t* bars = (uint64_t*)(smem + L::kOffBar);
-    uint32_t* tmem_holder = (uint32_t*)(smem + L::kOffBar + L::kNumBars * 8);
+    const int K = lay.K, STAGES = lay.stages, YBUF = lay.ybuf;
+    uint64_t* bars = (uint64_t*)(smem + lay.off_bar);
+    uint32_t* tmem_holder = (uint32_t*)(smem + lay.off_bar + kNumBars(STAGES) * 8);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
     auto bar = [&](int i) { return smem_addr(&bars[i]); };
     const int Y_FULL = 0, Y_EMPTY = 2, B_FULL = 4, B_EMPTY = 4 + STAGES, T_FULL = 4 + 2 * STAGES,
               T_EMPTY = 6 + 2 * STAGES, DONE = 8 + 2 * STAGES;
+    // pipeline steps per grid tile: one whole tile, or K/16 slices
+    const int NC = KCHUNK ? K / 16 : 1;
+    // min mode multiplies only the hi halves, so only they are copied
+    constexpr bool kLo = (MODE != kModeMin);
+    const uint32_t tile_elems = 2u * K * kBN;  // bf16 elements of one B tile
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // constant q-step operand slabs (generic-proxy writes, fenced for the tensor core below)
     {
-        uint32_t* ones = (uint32_t*)(smem + L::kOffOnes);
-        for (int i = threadIdx.x; i < (int)(L::kAChunk / 4); i += blockDim.x) {
+        uint32_t* ones = (uint32_t*)(smem + lay.off_ones);
+        for (int i = threadIdx.x; i < (int)(kAChunk / 4); i += blockDim.x) {
             const int w = i & 3;  // 4 words per 16-byte row: bf16 pairs (1,1), (1,0), (0,0), (0,0)
             ones[i] = (w == 0) ? 0x3F803F80u : (w == 1 ? 0x00003F80u : 0u);
         }
-        uint32_t* zero = (uint32_t*)(smem + L::kOffZero);
-        for (int i = threadIdx.x; i < (int)(L::kBChunk / 4); i += blockDim.x) zero[i] = 0u;
+        uint32_t* zero = (uint32_t*)(smem + lay.off_zero);
+        for (int i = threadIdx.x; i < (int)(kBChunk / 4); i += blockDim.x) zero[i] = 0u;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (threadIdx.x == 0) {
@@ -369,31 +285,45 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------- producer
-        int y_par[2] = {-1, -1}, b_par[STAGES];
+        int y_par[2] = {-1, -1};
+        int b_par[16];
         for (int s = 0; s < STAGES; ++s) b_par[s] = -1;
         bool ok = true;
-        int it = 0;
-        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
-            const int yb = it % YBUF;
-            const uint32_t yph = (it / YBUF) & 1;
+        // ring positions and phases advance by counting (no division in the issue loop)
+        int yb = 0, s = 0;
+        uint32_t yph = 0, ph = 0;
+        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x) {
             if (!mbar_wait(bar(Y_EMPTY + yb), yph ^ 1, abort_flag)) { ok = false; break; }
-            mbar_expect_tx(bar(Y_FULL + yb), L::kYBytes);
-            bulk_g2s(sbase + L::kOffY + yb * L::kYBytes, Yt + item * (int64_t)(L::kYBytes / 2), L::kYBytes,
+            mbar_expect_tx(bar(Y_FULL + yb), lay.y_bytes);
+            bulk_g2s(sbase + yb * lay.y_bytes, Yt + item * (int64_t)(lay.y_bytes / 2), lay.y_bytes,
                      bar(Y_FULL + yb));
             y_par[yb] = (int)yph;
+            if (++yb == YBUF) { yb = 0; yph ^= 1u; }
             const uint16_t* qrow = Qb3 + (int64_t)tile_slot[item] * G_pad * 8;
-            const int j0 = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
-            for (int jj = 0; jj < n_gt; ++jj) {
-                const int j = (j0 + jj) % n_gt;
-                const int64_t seq = (int64_t)it * n_gt + jj;
-                const int s = (int)(seq % STAGES);
-                const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
-                if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag)) { ok = false; break; }
-                mbar_expect_tx(bar(B_FULL + s), L::kBBytes + L::kQBytes);
-                bulk_g2s(sbase + L::kOffB + s * L::kBBytes, Bt + (int64_t)j * (L::kBBytes / 2), L::kBBytes,
-                         bar(B_FULL + s));
-                bulk_g2s(sbase + L::kOffQ + s * L::kQBytes, qrow + (int64_t)j * kBN * 8, L::kQBytes, bar(B_FULL + s));
-                b_par[s] = (int)ph;
+            int j = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
+            for (int jj = 0; ok && jj < n_gt; ++jj) {
+                const uint16_t* btile = Bt + (int64_t)j * tile_elems;
+                for (int c = 0; c < NC; ++c) {
+                    if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag)) { ok = false; break; }
+                    const uint32_t st0 = sbase + lay.off_b + s * lay.stage_bytes;
+                    const uint32_t hi_bytes = KCHUNK ? 2u * kBChunk : lay.bpart_bytes / 2u;
+                    const uint32_t bytes = (kLo ? 2u * hi_bytes : hi_bytes) + (c == 0 ? kQBytes : 0u);
+                    mbar_expect_tx(bar(B_FULL + s), bytes);
+                    if (KCHUNK) {
+                        // hi slabs 2c, 2c+1 and lo slabs K/8 + 2c, K/8 + 2c + 1 of the tile
+                        bulk_g2s(st0, btile + (int64_t)(2 * c) * (kBChunk / 2), hi_bytes, bar(B_FULL + s));
+                        if (kLo)
+                            bulk_g2s(st0 + hi_bytes, btile + (int64_t)(K / 8 + 2 * c) * (kBChunk / 2), hi_bytes,
+                                     bar(B_FULL + s));
+                    } else {
+                        bulk_g2s(st0, btile, kLo ? lay.bpart_bytes : hi_bytes, bar(B_FULL + s));
+                    }
+                    if (c == 0)
+                        bulk_g2s(st0 + lay.bpart_bytes, qrow + (int64_t)j * kBN * 8, kQBytes, bar(B_FULL + s));
+                    b_par[s] = (int)ph;
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                }
+                if (++j == n_gt) j = 0;
             }
         }
         if (!ok) {
@@ -408,43 +338,46 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     } else if (warp == 1 && lane == 0) {
         // --------------------------------------------------------------- MMA
         bool ok = true;
-        int it = 0;
-        const uint64_t a_q = smem_desc(sbase + L::kOffOnes, L::kOffZero - L::kOffOnes, 128);
-        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x, ++it) {
-            const int yb = it % YBUF;
-            if (!mbar_wait(bar(Y_FULL + yb), (it / YBUF) & 1, abort_flag)) { ok = false; break; }
+        const uint64_t a_q = smem_desc(sbase + lay.off_ones, lay.off_zero - lay.off_ones, 128);
+        int yb = 0, s = 0, ab = 0;
+        uint32_t yph = 0, ph = 0, aph = 0;
+        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x) {
+            if (!mbar_wait(bar(Y_FULL + yb), yph, abort_flag)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t a0 = sbase + L::kOffY + yb * L::kYBytes;
-            for (int jj = 0; jj < n_gt; ++jj) {
-                const int64_t seq = (int64_t)it * n_gt + jj;
-                const int s = (int)(seq % STAGES);
-                const uint32_t ph = (uint32_t)((seq / STAGES) & 1);
-                const int ab = (int)(seq & 1);
-                const uint32_t aph = (uint32_t)((seq >> 1) & 1);
+            const uint32_t a0 = sbase + yb * lay.y_bytes;
+            for (int jj = 0; ok && jj < n_gt; ++jj) {
                 if (!mbar_wait(bar(T_EMPTY + ab), aph ^ 1, abort_flag)) { ok = false; break; }
-                if (!mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t b0 = sbase + L::kOffB + s * L::kBBytes;
-                const uint32_t qs = L::kOffQ + s * L::kQBytes;
                 const uint32_t d = tmem_base + (uint32_t)(ab * kBN);
-                // q-step: accumulator <- qb_g
-                mma_bf16(d, a_q, smem_desc(sbase + qs, L::kOffZero - qs, 128), 0u);
-#pragma unroll
-                for (int kk = 0; kk < K / 16; ++kk) {
-                    const uint64_t a_hi = smem_desc(a0 + (2 * kk) * L::kAChunk, L::kAChunk, 128);
-                    const uint64_t a_lo = smem_desc(a0 + (K / 8 + 2 * kk) * L::kAChunk, L::kAChunk, 128);
-                    const uint64_t b_hi = smem_desc(b0 + (2 * kk) * L::kBChunk, L::kBChunk, 128);
-                    const uint64_t b_lo = smem_desc(b0 + (K / 8 + 2 * kk) * L::kBChunk, L::kBChunk, 128);
-                    mma_bf16(d, a_hi, b_hi, 1u);
-                    if (MODE != kModeMin) {
-                        mma_bf16(d, a_lo, b_hi, 1u);
-                        mma_bf16(d, a_hi, b_lo, 1u);
+                for (int c = 0; c < NC; ++c) {
+                    if (!mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t b0 = sbase + lay.off_b + s * lay.stage_bytes;
+                    if (c == 0) {
+                        // q-step: accumulator <- qb_g
+                        const uint32_t qs = lay.off_b + s * lay.stage_bytes + lay.bpart_bytes;
+                        mma_bf16(d, a_q, smem_desc(sbase + qs, lay.off_zero - qs, 128), kIdesc, 0u);
                     }
+                    const int k_lo = KCHUNK ? c : 0, k_hi = KCHUNK ? c + 1 : K / 16;
+                    for (int kk = k_lo; kk < k_hi; ++kk) {
+                        const uint64_t a_hi = smem_desc(a0 + (2 * kk) * kAChunk, kAChunk, 128);
+                        const uint64_t a_lo = smem_desc(a0 + (K / 8 + 2 * kk) * kAChunk, kAChunk, 128);
+                        const uint32_t bh = KCHUNK ? b0 : b0 + (2 * kk) * kBChunk;
+                        const uint32_t bl = KCHUNK ? b0 + 2 * kBChunk : b0 + (K / 8 + 2 * kk) * kBChunk;
+                        const uint64_t b_hi = smem_desc(bh, kBChunk, 128);
+                        mma_bf16(d, a_hi, b_hi, kIdesc, 1u);
+                        if (kLo) {
+                            mma_bf16(d, a_lo, b_hi, kIdesc, 1u);
+                            mma_bf16(d, a_hi, smem_desc(bl, kBChunk, 128), kIdesc, 1u);
+                        }
+                    }
+                    mma_commit(bar(B_EMPTY + s));
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
                 }
-                mma_commit(bar(B_EMPTY + s));
-                mma_commit(bar(T_FULL + ab));
+                if (ok) mma_commit(bar(T_FULL + ab));
+                if (++ab == 2) { ab = 0; aph ^= 1u; }
             }
             if (ok) mma_commit(bar(Y_EMPTY + yb));
+            if (++yb == YBUF) { yb = 0; yph ^= 1u; }
         }
         if (!ok) {
             *abort_flag = 1;
@@ -459,9 +392,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         const int half = (warp - 2) >> 2;    // which half of the BN columns
         const int row = quad * 32 + lane;
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        float* scratch = (float*)(smem + L::kOffScratch + (warp - 2) * 4096);
+        float* scratch = (float*)(smem + lay.off_scratch + (warp - 2) * 4096);
         // hand-over area of this row's half-1 warp (warp + 4 for a half-0 warp)
-        float* mval = (float*)(smem + L::kOffScratch + (half ? warp - 2 : warp + 2) * 4096);
+        float* mval = (float*)(smem + lay.off_scratch + (half ? warp - 2 : warp + 2) * 4096);
         int32_t* midx = (int32_t*)(mval + TOPK * 32);
         bool ok = true;
         int it = 0;
@@ -479,9 +412,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             int32_t bi = INT32_MAX;
             int32_t nlist = 0;        // kModeList: entries found by this half row
             const int64_t lbase = ((item * kBM + row) * 2 + half) * (int64_t)kListCap;
-            const int j0 = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
-            for (int jj = 0; ok && jj < n_gt; ++jj) {
-                const int j = (j0 + jj) % n_gt;
+            int j = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
+            for (int jj = 0; ok && jj < n_gt; ++jj, j = (j + 1 == n_gt) ? 0 : j + 1) {
                 const int64_t seq = (int64_t)it * n_gt + jj;
                 const int ab = (int)(seq & 1);
                 const uint32_t aph = (uint32_t)((seq >> 1) & 1);
@@ -587,52 +519,82 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     }
 }
 
-template <int K, int TOPK, int STAGES, int YBUF, int MODE>
-void run_screen(const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3, const int32_t* tile_slot, float* tau0,
-                const int32_t* tile_j0, int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci,
-                int32_t* cc, int* status, const ProbeArgs& pa, int n_sm, cudaStream_t st) {
-    using L = ScreenSmem<K, STAGES, YBUF>;
-    static_assert(L::kBytes <= 232448, "screen tile does not fit in shared memory");
-    auto kern = k_screen<K, TOPK, STAGES, YBUF, MODE>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes);
+template <int TOPK, int MODE, bool KCHUNK>
+void run_screen(const ScreenLayout& lay, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
+                const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
+                int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const ProbeArgs& pa, int n_sm,
+                cudaStream_t st) {
+    auto kern = k_screen<TOPK, MODE, KCHUNK>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
-    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, L::kBytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles,
-                                                                   G, G_pad, cv, ci, cc, status, pa);
+    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, lay.bytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G,
+                                                                   G_pad, cv, ci, cc, status, pa, lay);
+}
+
+// Shared-memory plan for K with the requested depth / buffering (0 = built-in:
+// whole-tile stages at the depths measured on the 100x100, N_fit 45 workload for
+// K <= 64; 16-column slices as deep as shared memory allows, up to 8, above).
+ScreenLayout choose_layout(int K, int stages, int ybuf) {
+    const int kchunk = K > 64 ? 1 : 0;
+    if (ybuf <= 0) ybuf = (K <= 32) ? 2 : 1;
+    if (stages <= 0) {
+        if (!kchunk) {
+            stages = K == 16 ? 4 : (K == 64 ? 2 : 3);
+        } else {
+            const ScreenLayout one = screen_layout(K, 1, ybuf, 1);
+            stages = one.bytes > kSmemMax ? 0 : 1 + (int)((kSmemMax - one.bytes) / (one.stage_bytes + 16u));
+            stages = stages > 8 ? 8 : stages;
+        }
+    }
+    return screen_layout(K, stages, ybuf, kchunk);
 }
 
 }  // namespace
 
-bool launch_screen(int K, int topk, int mode, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
-                   const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
-                   int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const float* Qc, const float* Qb,
-                   const float4* gnorm, const float4* alpha, const float* Sc32, int nfit, int n_sm, cudaStream_t st) {
+bool screen_config_ok(int K, int stages, int ybuf) {
+    if (K < 16 || K % 16 != 0 || K > kMaxScreenK) return false;
+    if (stages != 0 && (stages < 2 || stages > 8)) return false;
+    if (ybuf < 0 || ybuf > 2) return false;
+    const ScreenLayout lay = choose_layout(K, stages, ybuf);
+    return lay.stages >= 2 && lay.bytes <= kSmemMax;
+}
+
+bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Yt, const uint16_t* Bt,
+                   const uint16_t* Qb3, const int32_t* tile_slot, float* tau0, const int32_t* tile_j0,
+                   int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status,
+                   const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
+                   int nfit, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
+    if (!screen_config_ok(K, stages, ybuf) || (topk != 8 && topk != 16)) return false;
+    const ScreenLayout lay = choose_layout(K, stages, ybuf);
     const ProbeArgs pa{Qc, Qb, gnorm, alpha, Sc32, nfit};
-#define FC_SCREEN_RUN(KK, TT, SS, YY, MM) \
-    run_screen<KK, TT, SS, YY, MM>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, n_sm, st)
-#define FC_SCREEN_CASE(KK, TT, SS, YY)                                   \
-    if (K == KK && topk == TT) {                                         \
-        if (mode == kModeMin)                                            \
-            FC_SCREEN_RUN(KK, TT, SS, YY, kModeMin);                     \
-        else if (mode == kModeList)                                      \
-            FC_SCREEN_RUN(KK, TT, SS, YY, kModeList);                    \
-        else                                                             \
-            FC_SCREEN_RUN(KK, TT, SS, YY, kModeTopK);                    \
-        return true;                                                     \
+#define FC_SCREEN_RUN(TT, MM, CC) \
+    run_screen<TT, MM, CC>(lay, Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, n_sm, st)
+#define FC_SCREEN_MODES(TT, CC)                 \
+    do {                                        \
+        if (mode == kModeMin)                   \
+            FC_SCREEN_RUN(TT, kModeMin, CC);    \
+        else if (mode == kModeList)             \
+            FC_SCREEN_RUN(TT, kModeList, CC);   \
+        else                                    \
+            FC_SCREEN_RUN(TT, kModeTopK, CC);   \
+    } while (0)
+    if (topk == 8) {
+        if (lay.kchunk)
+            FC_SCREEN_MODES(8, true);
+        else
+            FC_SCREEN_MODES(8, false);
+    } else {
+        if (lay.kchunk)
+            FC_SCREEN_MODES(16, true);
+        else
+            FC_SCREEN_MODES(16, false);
     }
-    FC_SCREEN_CASE(16, 8, 4, 2)
-    FC_SCREEN_CASE(32, 8, 3, 2)
-    FC_SCREEN_CASE(48, 8, 3, 1)
-    FC_SCREEN_CASE(64, 8, 2, 1)
-    FC_SCREEN_CASE(16, 16, 4, 2)
-    FC_SCREEN_CASE(32, 16, 3, 2)
-    FC_SCREEN_CASE(48, 16, 3, 1)
-    FC_SCREEN_CASE(64, 16, 2, 1)
-#undef FC_SCREEN_CASE
+#undef FC_SCREEN_MODES
 #undef FC_SCREEN_RUN
-    return false;
+    return true;
 }
 
 }  // namespace fcdev

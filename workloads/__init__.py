@@ -26,6 +26,9 @@ __all__ = [
     "cfg1",
     "cfg2",
     "cfg3",
+    "cfg4_grid",
+    "cfg4_pool",
+    "cfg4_jobs",
     "cfg5",
     "linear_gauss",
     "tiny",
@@ -146,6 +149,87 @@ def cfg3(U: int = 500, n_points: int = 2048, n_axis: int = 64) -> Workload:
     S = np.ascontiguousarray(np.concatenate([app, dis], axis=-1).reshape(-1, 2 * h))
     pts = np.sort(rng.choice(S.shape[0], n_points, replace=False)).astype(np.int64)
     return Workload("cfg3_d3_64cubed_n120", S, F, None, 2 * h, pts, U, 5, 0, (dm2, ue, um))
+
+
+def cfg4_grid(D: int, G_target: int, n_full: int, seed: int) -> Workload:
+    """One grid of the serving pool: D = 2, 3 or 4 parameters, about G_target
+    points (n = round(G_target^(1/D)) per axis), N = n_full bins.
+
+    D=2: the osc_2d model.  D=3: the cfg3 model (appearance bins
+    b + 4 Ue Um sin^2(1.27 dm2 L/E) f, then disappearance bins
+    b'(1 - 4 Um (1 - Um) sin^2(.))), split N//2 + N - N//2, Um <= 0.45.  D=4: two
+    (amplitude, dm2) terms, s = b + sum_j A_j sin^2(1.27 dm2_j L/E) f_j with
+    A_j log-spaced over [1e-3, 0.1].  Draw order from default_rng(seed):
+    b, f (or f_j), b' (D=3 only), then the fractional covariance, then L.
+    """
+    n_ax = max(2, int(round(G_target ** (1.0 / D))))
+    rng = np.random.default_rng(seed)
+    n = n_full
+    if D == 2:
+        S, F, axes = osc_2d(n_ax, n_ax, n, seed=seed)
+    elif D == 3:
+        h1, h2 = n // 2, n - n // 2
+        b = rng.uniform(50.0, 500.0, h1)
+        f = rng.uniform(5.0, 50.0, h1)
+        bp = rng.uniform(50.0, 500.0, h2)
+        F, _ = _frac_cov(rng, n)
+        L = rng.choice(np.array([110.0, 470.0, 600.0]), n)
+        E = np.concatenate([np.linspace(0.2, 3.0, h1), np.linspace(0.2, 3.0, h2)])
+        dm2 = np.logspace(-2, 2, n_ax)
+        ue = np.logspace(-4, np.log10(0.5), n_ax)
+        # |Umu4|^2 stops at 0.45 so the disappearance factor 1 - 4 U (1 - U) >= 0.01 keeps M positive definite
+        um = np.logspace(-4, np.log10(0.45), n_ax)
+        osc = np.sin(1.27 * dm2[:, None] * L[None, :] / E[None, :]) ** 2      # [n_ax, n]
+        app = b + 4.0 * ue[None, :, None, None] * um[None, None, :, None] * osc[:, None, None, :h1] * f
+        dis = bp * (1.0 - 4.0 * um[None, None, :, None] * (1.0 - um[None, None, :, None]) * osc[:, None, None, h1:])
+        dis = np.broadcast_to(dis, (n_ax, n_ax, n_ax, h2))
+        S = np.ascontiguousarray(np.concatenate([app, dis], axis=-1).reshape(-1, n))
+        axes = (dm2, ue, um)
+    elif D == 4:
+        b = rng.uniform(50.0, 500.0, n)
+        fj = rng.uniform(5.0, 50.0, (2, n))
+        F, _ = _frac_cov(rng, n)
+        L = rng.choice(np.array([110.0, 470.0, 600.0]), n)
+        E = np.linspace(0.2, 3.0, n)
+        amp = np.logspace(-3, -1, n_ax)
+        dm2 = np.logspace(-2, 2, n_ax)
+        osc = np.sin(1.27 * dm2[:, None] * L[None, :] / E[None, :]) ** 2      # [n_ax, n]
+        t1 = (amp[:, None, None] * osc[None, :, :] * fj[0]).reshape(n_ax * n_ax, n)
+        t2 = (amp[:, None, None] * osc[None, :, :] * fj[1]).reshape(n_ax * n_ax, n)
+        S = np.ascontiguousarray((b + t1[:, None, :] + t2[None, :, :]).reshape(-1, n))
+        axes = (amp, dm2, amp, dm2)
+    else:
+        raise ValueError("D must be 2, 3 or 4")
+    return Workload(f"cfg4_d{D}_g{S.shape[0]}_n{n}", S, F, None, n, np.zeros(0, np.int64), 0, 5, seed, axes)
+
+
+def cfg4_pool(n_grids: int = 8, seed: int = 0, G_lo: float = 1e3, G_hi: float = 1e6, N_lo: int = 40,
+              N_hi: int = 200) -> list:
+    """Resident grids of the serving stream: D ~ U{2,3,4}, G log-uniform in
+    [G_lo, G_hi], N ~ U{N_lo..N_hi}; grid k is built from seed 1000 + k."""
+    rng = np.random.default_rng(seed)
+    D = rng.integers(2, 5, n_grids)
+    G = np.exp(rng.uniform(np.log(G_lo), np.log(G_hi), n_grids))
+    N = rng.integers(N_lo, N_hi + 1, n_grids)
+    return [cfg4_grid(int(D[k]), int(G[k]), int(N[k]), 1000 + k) for k in range(n_grids)]
+
+
+def cfg4_jobs(pool_sizes: list, rate: float, duration: float, seed: int = 0, U_lo: int = 100,
+              U_hi: int = 10000) -> list:
+    """Poisson arrivals at `rate` jobs/s over `duration` s.  Job = (arrival s,
+    grid k uniform over the pool, one true point uniform over that grid's G,
+    job seed, U log-uniform in [U_lo, U_hi])."""
+    rng = np.random.default_rng(seed)
+    jobs, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        k = int(rng.integers(0, len(pool_sizes)))
+        p = int(rng.integers(0, pool_sizes[k]))
+        U = int(round(np.exp(rng.uniform(np.log(U_lo), np.log(U_hi)))))
+        jobs.append((t, k, p, int(rng.integers(0, 2 ** 62)), U))
+    return jobs
 
 
 def cfg5(n_axis: int = 16, n_points: int = 256, U: int = 16) -> Workload:
