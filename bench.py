@@ -339,6 +339,7 @@ def _serve_stream(fc, ctx, gids, sizes, rate, duration, seed, drain_s):
 
     jobs = workloads.cfg4_jobs(sizes, rate, duration, seed)
     pending, lat, failed, evals, univ = {}, [], 0, 0, 0
+    errors = {}
     t0 = time.perf_counter()
     i = 0
     while i < len(jobs) or pending:
@@ -351,8 +352,9 @@ def _serve_stream(fc, ctx, gids, sizes, rate, duration, seed, drain_s):
         for tk in list(pending):
             try:
                 st, ms = fc.fc_poll(ctx, tk)
-            except fc.FCError:
+            except fc.FCError as e:
                 failed += 1
+                errors[str(e)] = errors.get(str(e), 0) + 1
                 pending.pop(tk)
                 continue
             if st == fc.FC_PENDING:
@@ -364,7 +366,8 @@ def _serve_stream(fc, ctx, gids, sizes, rate, duration, seed, drain_s):
         if now > duration + drain_s:
             for tk in list(pending):
                 fc.fc_cancel(ctx, tk)
-            while pending:
+            t_cancel = time.perf_counter()
+            while pending and time.perf_counter() - t_cancel < 120.0:
                 for tk in list(pending):
                     try:
                         st, _ = fc.fc_poll(ctx, tk)
@@ -382,7 +385,7 @@ def _serve_stream(fc, ctx, gids, sizes, rate, duration, seed, drain_s):
             "p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
             "mean_ms": float(a.mean()), "max_ms": float(a.max()),
             "throughput_jobs_per_s": len(lat) / wall, "chi2_evals_per_s": evals / wall,
-            "universes_per_s": univ / wall}
+            "universes_per_s": univ / wall, "errors": errors}
 
 
 def run_serve(args):

@@ -100,7 +100,7 @@ typedef struct {
     int64_t screened;         /* universe-scans decided by the tensor-core screen     */
     int64_t rescored;         /* universe-scans that needed binary64 rescoring        */
     int64_t rescreened;       /* universe-scans whose first certificate failed -> second screen round */
-    int64_t fallback;         /* universe-scans whose certificates failed twice -> exact fp64 scan */
+    int64_t fallback;         /* universe-scans no certified round decided -> exact fp64 scan */
     int64_t kernel_launches;  /* CUDA kernels launched by the call                    */
     int64_t screen_launches;  /* launches of the tensor-core screen kernel             */
     double  screen_flops;     /* algorithmic flops of those launches: 2 N_fit per eval */
@@ -109,6 +109,7 @@ typedef struct {
     int64_t cache_slots;      /* covariance-cache slots allocated for the grid        */
     int64_t max_distinct_cov; /* most distinct covariance indices one scan needed     */
     int64_t scan_waves;       /* cache-sized groups run by scans that needed more     */
+    int64_t big_listed;       /* universe-scans sent to the exact-size list round     */
 } fc_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -249,6 +250,9 @@ FC_API fc_status fc_autotune(fc_ctx* ctx, int32_t grid_id, const char* cache_pat
 
 /* Counters of the last synchronous run on this context. */
 FC_API fc_status fc_get_stats(fc_ctx* ctx, fc_stats* out);
+/* Counters summed over everything the serving worker has run (fc_submit jobs).
+ * Takes the context's device lock, so it returns between two scans. */
+FC_API fc_status fc_get_serve_stats(fc_ctx* ctx, fc_stats* out);
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 FC_API const char* fc_last_error(const fc_ctx* ctx);

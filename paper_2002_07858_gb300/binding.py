@@ -29,7 +29,7 @@ _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_
 EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set_frac_cov", "fc_unload_grid",
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
            "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
-           "fc_set_tuning", "fc_get_tuning", "fc_autotune"]
+           "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats"]
 
 
 class FCError(RuntimeError):
@@ -51,7 +51,7 @@ class fc_stats(ctypes.Structure):
         (n, ctypes.c_double) for n in ("ms_fake", "ms_cov", "ms_prep", "ms_screen", "ms_rescore", "ms_fallback",
                                        "ms_scan64", "ms_finish", "ms_total")] + [
         ("evicted", ctypes.c_int64), ("cache_slots", ctypes.c_int64), ("max_distinct_cov", ctypes.c_int64),
-        ("scan_waves", ctypes.c_int64)]
+        ("scan_waves", ctypes.c_int64), ("big_listed", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -108,6 +108,7 @@ def load(build: bool = False):
         "fc_poll": (st, [vp, u64, ctypes.POINTER(ctypes.c_double)]),
         "fc_cancel": (st, [vp, u64]),
         "fc_get_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
+        "fc_get_serve_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
         "fc_set_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
         "fc_get_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
         "fc_autotune": (st, [vp, i32, ctypes.c_char_p, ctypes.POINTER(fc_tuning)]),
@@ -308,6 +309,12 @@ def fc_autotune(ctx, grid_id: int, cache_path: str | None = None) -> dict:
     path = cache_path.encode() if cache_path else None
     _check(load().fc_autotune(ctx, grid_id, path, ctypes.byref(t)), ctx)
     return t.as_dict()
+
+
+def fc_get_serve_stats(ctx) -> dict:
+    s = fc_stats()
+    _check(load().fc_get_serve_stats(ctx, ctypes.byref(s)), ctx)
+    return s.as_dict()
 
 
 def fc_get_stats(ctx) -> dict:

@@ -128,6 +128,7 @@ struct JobRec {
     std::atomic<int> state{FC_PENDING};
     std::atomic<bool> cancelled{false};
     std::chrono::steady_clock::time_point t_submit, t_done;
+    std::string error;  // message of a failed job (set before state)
 };
 
 // A lane holds the per-universe state of every job that runs with the same
@@ -367,8 +368,31 @@ fc_status regrow(fc_ctx* c, T** p, size_t per_slot, int64_t old_cap, int64_t new
     return FC_OK;
 }
 
+// Device memory the covariance caches leave free for scratch, lanes and other
+// grids: a tenth of the budget (of the device when there is none), 2 GiB at least.
+size_t cache_reserve(fc_ctx* c) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t base = c->budget ? c->budget : total_b;
+    return std::max<size_t>(base / 10, size_t(2) << 30);
+}
+
+// Bytes a cache may still take: what the budget (or the device) has left
+// above the reserve.
+size_t cache_headroom(fc_ctx* c) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t room = free_b;
+    if (c->budget) room = std::min(room, c->budget > c->used ? c->budget - c->used : 0);
+    const size_t res = cache_reserve(c);
+    return room > res ? room - res : 0;
+}
+
 fc_status grow_cache(fc_ctx* c, Grid* g, int64_t new_cap) {
     const int64_t old = g->cap;
+    // the copy needs old and new arrays at once
+    if ((size_t)(new_cap - old) * slot_bytes(g) + (size_t)old * slot_bytes(g) > cache_headroom(c) && old > 0)
+        return fail(FC_ERR_BUDGET, "covariance cache at its memory limit");
     const size_t n2 = (size_t)g->nfit * g->nfit;
     FC_TRY(regrow(c, &g->A64, n2, old, new_cap));
     FC_TRY(regrow(c, &g->W64, n2, old, new_cap));
@@ -390,20 +414,25 @@ fc_status grow_cache(fc_ctx* c, Grid* g, int64_t new_cap) {
     return FC_OK;
 }
 
-// Covariance cache of a grid: the limit is half of the device memory free at
-// first use (and half of what the context budget has left).
+// Grow the cache towards `need` slots (doubling), as far as `lim` and memory allow.
+void grow_for(fc_ctx* c, Grid* g, int64_t need, int64_t lim) {
+    if (g->cap >= std::min(need, lim)) return;
+    int64_t target = std::min<int64_t>(lim, std::max<int64_t>(2 * g->cap, need));
+    target = std::min<int64_t>(target, (int64_t)(cache_headroom(c) / slot_bytes(g)));
+    if (target > g->cap && grow_cache(c, g, target) != FC_OK) cudaGetLastError();
+}
+
+// Covariance cache of a grid: at most one slot per grid index (plus A = I);
+// it grows while cache_headroom allows and evicts beyond that.
 fc_status ensure_cache(fc_ctx* c, Grid* g) {
     if (g->cap) return FC_OK;
-    size_t free_b = 0, total_b = 0;
-    FC_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    size_t limit = free_b / 2;
-    if (c->budget) limit = std::min(limit, (c->budget > c->used ? c->budget - c->used : 0) / 2);
-    g->max_cap = std::min<int64_t>(g->G + 1, (int64_t)(limit / slot_bytes(g)));
-    if (g->max_cap < 2) return fail(FC_ERR_BUDGET, "no room for the covariance cache");
+    // the slot count is bounded by the grid; memory decides at each growth step
+    g->max_cap = g->G + 1;
+    if ((int64_t)(cache_headroom(c) / slot_bytes(g)) < 2) return fail(FC_ERR_BUDGET, "no room for the covariance cache");
     g->slot_host.assign(g->G, -1);
     FC_TRY(dalloc_t(c, &g->slot_of, g->G));
     launch_fill_i32(g->slot_of, g->G, -1, c->stream);
-    return grow_cache(c, g, std::min<int64_t>(g->max_cap, 256));
+    return grow_cache(c, g, std::min<int64_t>(g->max_cap, 32));
 }
 
 fc_status ensure_q32_storage(fc_ctx* c, Grid* g) {
@@ -444,10 +473,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
     size_t lru_pos = 0;
     const int64_t lim = g->tune.cache_slots > 0 ? std::min<int64_t>(g->tune.cache_slots, g->max_cap) : g->max_cap;
     auto take_slot = [&](int32_t* out) -> fc_status {
-        if (g->n_slots >= g->cap && g->cap < lim) {
-            const int64_t want = std::min<int64_t>(lim, std::max<int64_t>(2 * g->cap, g->n_slots + 1));
-            if (grow_cache(c, g, want) != FC_OK) g->max_cap = g->cap;  // no memory: evict from now on
-        }
+        if (g->n_slots >= g->cap) grow_for(c, g, g->n_slots + 1, lim);
         if (g->n_slots < std::min<int64_t>(g->cap, lim)) {
             *out = g->n_slots++;
             return FC_OK;
@@ -625,6 +651,25 @@ __global__ void k_select_cur(const int32_t* __restrict__ active, int64_t n, cons
     if (flag[cur0[i]]) out[atomicAdd(n_out, 1)] = active[i];
 }
 
+__global__ void k_gather_int2(const int32_t* __restrict__ list, int n, const int2* __restrict__ src,
+                              int2* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = src[list[i]];
+}
+
+__global__ void k_scatter_lists(const int32_t* __restrict__ u, int n, const int64_t* __restrict__ off,
+                                const int2* __restrict__ cnt, int64_t* __restrict__ loff, int2* __restrict__ lnum) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        loff[u[i]] = off[i];
+        lnum[u[i]] = cnt[i];
+    }
+}
+
+// Longest candidate list (both half rows) rescored from a fourth screen round;
+// longer ones take the exact scan.
+constexpr int64_t kBigList = 1 << 16;
+
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 // Distinct grid indices currently used as fit covariances by the active set.
@@ -740,7 +785,8 @@ void lane_release(Lane* L, int64_t base, int64_t n) {
     }
 }
 
-bool lane_idle(const Lane* L) { return L->free_jobs.size() == (size_t)kLaneJobs; }
+// No job resident (an unallocated lane, cap 0, has none either).
+bool lane_idle(const Lane* L) { return L->cap == 0 || L->free_jobs.size() == (size_t)kLaneJobs; }
 
 // Admit a job into reserved range [base, base+n): data (fake, from the job's
 // seed, or the caller's), per-universe state, active-list entries.  On error
@@ -807,7 +853,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     us.maxit = L->maxit;
     us.job_of = L->job_of;
     us.job_left = L->job_left;
-    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 9 * sizeof(unsigned long long), c->stream));
+    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 12 * sizeof(unsigned long long), c->stream));
     // exact binary64 scan for `list`, then advance / finish them
     auto exact_scan = [&](const int32_t* list, int64_t cnt) -> fc_status {
         std::vector<int32_t> fq;
@@ -853,6 +899,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             FC_TRY(stage_end(c, &S->ms_scan64));
         }
         // finishing universes keep cur (the covariance of this scan); others move to their minimum
+        FC_CUDA(cudaMemsetAsync(cnts + 3, 0, 4, c->stream));
         launch_advance(list, cnt, L->best, us, next, cnts + 2, fin, cnts + 3, c->stream);
         int32_t n_fin = 0;
         FC_CUDA(cudaMemcpyAsync(&n_fin, cnts + 3, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -880,10 +927,15 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
         } else {
             int32_t *fb = L->fb, *fb2 = L->fb2, *fslot = L->fbslot;
             float* thr = L->thr;
+            int2* lcount = nullptr;
+            FC_TRY(scratch(c, "lcount", (size_t)L->cap, &lcount));
             // one certified screen round over `list` (grouped into tiles by covariance slot)
+            // rounds 2 and 3 list candidates; round 3 stores them in the exact-size regions
+            // loff / lnum (u-indexed, list_total entries) sized by round 2's overflow counts
             auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
-                                    int32_t* fb_out, int32_t* n_fb_out) -> fc_status {
-                const bool listing = (round == 2);
+                                    int32_t* fb_out, int32_t* n_fb_out, const int64_t* loff = nullptr,
+                                    const int2* lnum = nullptr, int64_t list_total = 0) -> fc_status {
+                const bool listing = (round >= 2);
                 const int64_t n_slots = g->n_slots;
                 const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
                 const std::string sfx = round ? std::to_string(round + 1) : "";
@@ -902,9 +954,10 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 FC_TRY(scratch(c, ("tau0" + sfx).c_str(), (size_t)max_tiles * kBM, &tau0));
                 FC_TRY(scratch(c, ("tile_j0" + sfx).c_str(), (size_t)max_tiles, &tj0));
                 const size_t per_row = listing ? 2 * kListCap : rtopk;
+                const size_t n_cand = loff ? (size_t)list_total : (size_t)max_tiles * kBM * per_row;
                 int32_t* ccount = nullptr;
-                FC_TRY(scratch(c, ("cval" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cval));
-                FC_TRY(scratch(c, ("cidx" + sfx).c_str(), (size_t)max_tiles * kBM * per_row, &cidx));
+                FC_TRY(scratch(c, ("cval" + sfx).c_str(), n_cand, &cval));
+                FC_TRY(scratch(c, ("cidx" + sfx).c_str(), n_cand, &cidx));
                 FC_TRY(scratch(c, "ccount", (size_t)max_tiles * kBM * 2, &ccount));
                 stage_begin(c);
                 launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
@@ -925,7 +978,8 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
                     if (!launch_screen(g->K, rtopk, mode, g->tune.screen_stages, g->tune.screen_ybuf, Yt, g->Bt, g->Qb3,
                                        tslot, tau0, tj0, n_tiles, g->G, g->G_pad, cval, cidx, ccount, c->status_dev,
-                                       g->Qc, g->Qb, g->gnorm, alpha, g->Sc32, g->nfit, c->n_sm, c->stream))
+                                       g->Qc, g->Qb, g->gnorm, alpha, g->Sc32, g->nfit, ListArgs{tuniv, loff, lnum},
+                                       c->n_sm, c->stream))
                         return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
                     S->screen_launches += 1;
                 }
@@ -962,6 +1016,9 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 ra.n_fb = n_fb_out;
                 ra.counters = c->counters_dev + 3 * round;
                 ra.thr = thr;
+                ra.lcount = (round == 2) ? lcount : nullptr;
+                ra.list_off = loff;
+                ra.list_n = lnum;
                 stage_begin(c);
                 if (listing)
                     launch_resolve_list(ra, ccount, n_tiles, c->stream);
@@ -969,6 +1026,72 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     launch_resolve(ra, n_tiles, c->stream);
                 FC_TRY(stage_end(c, &S->ms_rescore));
                 return check_status(c);
+            };
+            // fourth round for universes whose candidate lists overflowed: the same list screen
+            // again with exact-size storage, then binary64 rescoring of every listed point;
+            // lists above kBigList entries (or aborted ones) take the exact scan
+            auto big_lists = [&](const int32_t* ov, int32_t n_ov, const int2* cnt2) -> fc_status {
+                std::vector<int32_t> hu(n_ov);
+                std::vector<int2> hn(n_ov);
+                int2* dn = nullptr;
+                FC_TRY(scratch(c, "big_n", (size_t)n_ov, &dn));
+                count_launch();
+                k_gather_int2<<<nb(n_ov), 256, 0, c->stream>>>(ov, n_ov, cnt2, dn);
+                FC_CUDA(cudaMemcpyAsync(hu.data(), ov, (size_t)n_ov * 4, cudaMemcpyDeviceToHost, c->stream));
+                FC_CUDA(cudaMemcpyAsync(hn.data(), dn, (size_t)n_ov * 8, cudaMemcpyDeviceToHost, c->stream));
+                FC_TRY(sync(c));
+                std::vector<int32_t> big_u, exact_u;
+                std::vector<int64_t> big_off;
+                std::vector<int2> big_n;
+                int64_t total = 0;
+                for (int32_t i = 0; i < n_ov; ++i) {
+                    const int64_t m = (int64_t)hn[i].x + hn[i].y;
+                    if (hn[i].x < 0 || hn[i].y < 0 || m > kBigList) {
+                        exact_u.push_back(hu[i]);
+                    } else {
+                        big_u.push_back(hu[i]);
+                        big_off.push_back(total);
+                        big_n.push_back(hn[i]);
+                        total += m;
+                    }
+                }
+                S->fallback += (int64_t)exact_u.size();
+                int32_t *d_u = nullptr, *d_x = nullptr, *n_x = nullptr;
+                FC_TRY(scratch(c, "big_u", std::max<size_t>(big_u.size(), exact_u.size()) + 1, &d_u));
+                if (!big_u.empty()) {
+                    const int32_t nb4 = (int32_t)big_u.size();
+                    int64_t* loff = nullptr;
+                    int2* lnum = nullptr;
+                    int64_t* d_off = nullptr;
+                    FC_TRY(scratch(c, "big_loff", (size_t)L->cap, &loff));
+                    FC_TRY(scratch(c, "big_lnum", (size_t)L->cap, &lnum));
+                    FC_TRY(scratch(c, "big_off", (size_t)nb4, &d_off));
+                    FC_TRY(scratch(c, "big_x", (size_t)nb4, &d_x));
+                    FC_TRY(scratch(c, "big_nx", 1, &n_x));
+                    FC_CUDA(cudaMemcpyAsync(d_u, big_u.data(), (size_t)nb4 * 4, cudaMemcpyHostToDevice, c->stream));
+                    FC_CUDA(cudaMemcpyAsync(d_off, big_off.data(), (size_t)nb4 * 8, cudaMemcpyHostToDevice,
+                                            c->stream));
+                    FC_CUDA(cudaMemcpyAsync(dn, big_n.data(), (size_t)nb4 * 8, cudaMemcpyHostToDevice, c->stream));
+                    count_launch();
+                    k_scatter_lists<<<nb(nb4), 256, 0, c->stream>>>(d_u, nb4, d_off, dn, loff, lnum);
+                    if (o.cov == FC_COV_IDENTITY)
+                        launch_fill_i32(fslot, nb4, g->ident_slot, c->stream);
+                    else
+                        launch_lookup_slots(d_u, nb4, cur, g->slot_of, fslot, c->stream);
+                    FC_CUDA(cudaMemsetAsync(n_x, 0, 4, c->stream));
+                    FC_TRY(screen_round(3, d_u, nb4, fslot, kMaxTopK, d_x, n_x, loff, lnum, total));
+                    int32_t nx = 0;
+                    FC_CUDA(cudaMemcpyAsync(&nx, n_x, 4, cudaMemcpyDeviceToHost, c->stream));
+                    FC_TRY(sync(c));
+                    S->fallback += nx;
+                    if (nx > 0) FC_TRY(exact_scan(d_x, nx));
+                }
+                if (!exact_u.empty()) {
+                    FC_CUDA(cudaMemcpyAsync(d_u, exact_u.data(), exact_u.size() * 4, cudaMemcpyHostToDevice,
+                                            c->stream));
+                    FC_TRY(exact_scan(d_u, (int64_t)exact_u.size()));
+                }
+                return FC_OK;
             };
             FC_TRY(screen_round(0, sl_list, sl_n, sl_slot, topk, fb, cnts + 1));
             int32_t n_fb = 0;
@@ -995,7 +1118,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     int32_t n_fb3 = 0;
                     FC_CUDA(cudaMemcpyAsync(&n_fb3, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
                     FC_TRY(sync(c));
-                    if (n_fb3 > 0) FC_TRY(exact_scan(fb, n_fb3));
+                    if (n_fb3 > 0) FC_TRY(big_lists(fb, n_fb3, lcount));
                 }
             }
         }
@@ -1020,7 +1143,9 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
         FC_TRY(ensure_cache(c, g));
         const int64_t lim =
             g->tune.cache_slots > 0 ? std::min<int64_t>(g->tune.cache_slots, g->max_cap) : g->max_cap;
-        const int64_t wave = std::max<int64_t>(1, lim - 1 - (g->ident_slot >= 0 ? 1 : 0));
+        // room for this scan's covariances as far as memory allows; beyond that, waves
+        grow_for(c, g, (int64_t)qs.size() + 2, lim);
+        const int64_t wave = std::max<int64_t>(1, std::min(lim, g->cap) - 1 - (g->ident_slot >= 0 ? 1 : 0));
         S->max_distinct_cov = std::max<int64_t>(S->max_distinct_cov, (int64_t)qs.size());
         if ((int64_t)qs.size() <= wave) {
             FC_TRY(ensure_slots(c, g, qs, o.cov, mixed, !mixed, nullptr));
@@ -1063,16 +1188,17 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     }
     int32_t n_next = 0;
     FC_CUDA(cudaMemcpyAsync(&n_next, cnts + 2, 4, cudaMemcpyDeviceToHost, c->stream));
-    // [0..2] round 1: screened, rescored, handed on; [3..5] round 2 likewise; [6] listed, [7] list overflow
-    unsigned long long cn[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // [0..2] round 1: screened, rescored, handed on; [3..5] round 2 likewise; [6] listed, [7] list
+    // overflow; [9] resolved from exact-size lists, [10] their failures (counted with the fallback)
+    unsigned long long cn[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     FC_CUDA(cudaMemcpyAsync(cn, c->counters_dev, sizeof(cn), cudaMemcpyDeviceToHost, c->stream));
     FC_TRY(sync(c));
     std::swap(L->active, L->next);
     L->n_active = n_next;
     S->screened += (int64_t)(cn[0] + cn[3]);
-    S->rescored += (int64_t)(cn[1] + cn[4] + cn[6]);
+    S->rescored += (int64_t)(cn[1] + cn[4] + cn[6] + cn[9]);
     S->rescreened += (int64_t)(cn[2] + cn[5]);
-    S->fallback += (int64_t)cn[7];
+    S->big_listed += (int64_t)(cn[9] + cn[10]);
     return check_status(c);
 }
 
@@ -1299,13 +1425,14 @@ bool same_key(int32_t grid_a, const fc_opts& a, int32_t grid_b, const fc_opts& b
 
 bool same_lane(const Lane* L, const fc_job& j) { return L->g && same_key(L->g->id, L->o, j.grid_id, j.opts); }
 
-constexpr int64_t kServeLaneMin = int64_t(1) << 20;  // universes per serving lane at least
+constexpr int64_t kServeLaneMin = int64_t(1) << 18;  // universes per serving lane at least
 
 void complete(fc_ctx* c, const std::shared_ptr<JobRec>& jr, fc_status st) {
     std::lock_guard<std::mutex> lk(c->q_mu);
     auto it = c->grids.find(jr->job.grid_id);
     if (it != c->grids.end()) it->second->busy--;
     jr->t_done = std::chrono::steady_clock::now();
+    if (st != FC_OK) jr->error = st == FC_ERR_CANCELLED ? "job cancelled" : t_last_error;
     jr->state.store(st);
 }
 
@@ -1778,8 +1905,9 @@ fc_status fc_poll(fc_ctx* c, uint64_t ticket, double* latency_ms) {
     if (latency_ms)
         *latency_ms =
             std::chrono::duration<double, std::milli>(it->second->t_done - it->second->t_submit).count();
+    const std::string msg = it->second->error;
     c->jobs.erase(it);
-    if (st != FC_OK) return fail((fc_status)st, "job failed");
+    if (st != FC_OK) return fail((fc_status)st, msg.empty() ? "job failed" : msg);
     return FC_OK;
 }
 
@@ -1926,6 +2054,13 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
         }
     }
     return sync(c);
+}
+
+fc_status fc_get_serve_stats(fc_ctx* c, fc_stats* out) {
+    if (!c || !out) return fail(FC_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    *out = c->serve_stats;
+    return FC_OK;
 }
 
 fc_status fc_get_stats(fc_ctx* c, fc_stats* out) {

@@ -140,10 +140,19 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                   uint16_t* Ytiles, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st);
 // Tensor-core screen of BM-row tiles (see fc_screen.cu).  mode: kScreenTopK,
 // kScreenMin (first pass; tightens tau0 in place) or kScreenList (every point
-// with LB <= tau0, kListCap per half row; cand_count > kListCap = overflow).
+// with LB <= tau0; cand_count holds the full count per half row, so a count
+// above the storage means the list overflowed; -1 = aborted).
 // Returns false if the padded K has no compiled instance.
 constexpr int kScreenTopK = 0, kScreenMin = 1, kScreenList = 2;
 constexpr int kListCap = 64;
+// List mode with exact-size storage: universe u's half-row lists start at
+// off[u] (half 0, n[u].x entries) and off[u] + n[u].x (half 1, n[u].y).
+// off == nullptr: kListCap slots per half row, indexed by tile row.
+struct ListArgs {
+    const int32_t* tile_univ;
+    const int64_t* off;
+    const int2* n;
+};
 // stages / ybuf: pipeline depth and A-image buffers, 0 = built-in choice.
 bool screen_config_ok(int K, int stages, int ybuf);
 bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Ytiles, const uint16_t* Btiles,
@@ -151,7 +160,7 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
                    const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
-                   int nfit, int n_sm, cudaStream_t st);
+                   int nfit, const ListArgs& la, int n_sm, cudaStream_t st);
 // Resolution of one mixed-path scan per screen tile (see k_resolve).
 struct ResolveArgs {
     const int32_t* tile_slot;
@@ -184,6 +193,9 @@ struct ResolveArgs {
     int32_t* n_fb;
     unsigned long long* counters;  // screened, rescored, handed on
     float* thr;            // [n] nullable: for handed-on universes, an upper bound of min_g (chi2_g - c_u)
+    int2* lcount;          // [n] nullable, list rounds: half-row counts of an overflowing universe
+    const int64_t* list_off;  // [n] nullable: exact-size list storage (see ListArgs)
+    const int2* list_n;
 };
 // tau0[row] = min(tau0[row], thr[u]) for the rows of the tiles
 void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st);

@@ -1040,8 +1040,23 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
         if (u < 0) continue;
         const int64_t row = t * kBM + r;
         const int n0 = cand_count[row * 2], n1 = cand_count[row * 2 + 1];
-        if (n0 > kListCap || n1 > kListCap || n0 + n1 == 0) {
+        // where the two half-row lists live and whether they are complete
+        int64_t base0, base1;
+        bool complete;
+        if (a.list_off) {
+            const int2 want = a.list_n[u];
+            base0 = a.list_off[u];
+            base1 = base0 + want.x;
+            complete = (n0 == want.x && n1 == want.y);
+        } else {
+            base0 = row * 2 * (int64_t)kListCap;
+            base1 = base0 + kListCap;
+            complete = (n0 >= 0 && n1 >= 0 && n0 <= kListCap && n1 <= kListCap);
+        }
+        if (!complete || n0 + n1 == 0) {
             if (lane == 0) {
+                // counts of an overflowing list size the next, exact-size list round
+                if (a.lcount) a.lcount[u] = (n0 >= 0 && n1 >= 0) ? make_int2(n0, n1) : make_int2(-1, -1);
                 a.fb[atomicAdd(a.n_fb, 1)] = u;
                 atomicAdd(&a.counters[1], 1ull);
             }
@@ -1051,7 +1066,7 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
         double bv = DBL_MAX;
         int32_t bg = INT32_MAX;
         for (int k = lane; k < n0 + n1; k += 32) {
-            const int64_t e = (row * 2 + (k < n0 ? 0 : 1)) * (int64_t)kListCap + (k < n0 ? k : k - n0);
+            const int64_t e = (k < n0) ? base0 + k : base1 + (k - n0);
             const int32_t g = a.cidx[e];
             const double c = resid_chi2(W, n, a.S_fit + (int64_t)g * n, du);
             if (c < bv || (c == bv && g < bg)) {

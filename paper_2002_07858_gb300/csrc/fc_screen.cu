@@ -111,8 +111,8 @@ constexpr int kModeMin = 1;
 constexpr int kModeList = 2;
 
 // List mode: append every value at or below the seed (and its grid index).
-__device__ __forceinline__ void list_chunk(int32_t& n, float* __restrict__ lval, int32_t* __restrict__ lidx, float seed,
-                                           const uint32_t (&r)[32], int64_t g0, int64_t G) {
+__device__ __forceinline__ void list_chunk(int32_t& n, int32_t cap, float* __restrict__ lval, int32_t* __restrict__ lidx,
+                                           float seed, const uint32_t (&r)[32], int64_t g0, int64_t G) {
     float m = __uint_as_float(r[0]);
 #pragma unroll
     for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
@@ -125,7 +125,7 @@ __device__ __forceinline__ void list_chunk(int32_t& n, float* __restrict__ lval,
         while (mask) {
             const int i = __ffs(mask) - 1;
             mask &= mask - 1;
-            if (n < kListCap) {
+            if (n < cap) {
                 lidx[n] = (int32_t)(g0 + i);
                 lval[n] = m;  // a lower bound of the entry (the chunk minimum); only the index is used
             }
@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
              const int32_t* __restrict__ tile_slot, float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
              int64_t n_tiles, int64_t G, int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
-             int32_t* __restrict__ cand_count, int* __restrict__ status, ProbeArgs pa, ScreenLayout lay) {
+             int32_t* __restrict__ cand_count, int* __restrict__ status, ProbeArgs pa, ScreenLayout lay,
+             ListArgs la) {
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -411,7 +412,16 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             float bv = FLT_MAX;       // kModeMin: running minimum of the row and its index
             int32_t bi = INT32_MAX;
             int32_t nlist = 0;        // kModeList: entries found by this half row
-            const int64_t lbase = ((item * kBM + row) * 2 + half) * (int64_t)kListCap;
+            // list storage of this half row: fixed kListCap slots, or the exact-size compact
+            // region of its universe (la.off, counts known from an earlier list round)
+            int64_t lbase = ((item * kBM + row) * 2 + half) * (int64_t)kListCap;
+            int32_t lcap = kListCap;
+            if (MODE == kModeList && la.off) {
+                const int32_t u = la.tile_univ[item * kBM + row];
+                const int2 nn = (u >= 0) ? la.n[u] : make_int2(0, 0);
+                lbase = (u >= 0) ? la.off[u] + (half ? nn.x : 0) : 0;
+                lcap = half ? nn.y : nn.x;
+            }
             int j = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
             for (int jj = 0; ok && jj < n_gt; ++jj, j = (j + 1 == n_gt) ? 0 : j + 1) {
                 const int64_t seq = (int64_t)it * n_gt + jj;
@@ -431,7 +441,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                     if (MODE == kModeMin)
                         min_chunk(bv, bi, r, gc, G);
                     else if (MODE == kModeList)
-                        list_chunk(nlist, cand_val + lbase, cand_idx + lbase, seed, r, gc, G);
+                        list_chunk(nlist, lcap, cand_val + lbase, cand_idx + lbase, seed, r, gc, G);
                     else
                         topk_chunk<TOPK>(vals, idx, r, gc, G, scratch, lane);
                 };
@@ -458,7 +468,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 __syncwarp();
             }
             if (MODE == kModeList) {
-                cand_count[(item * kBM + row) * 2 + half] = ok ? nlist : kListCap + 1;
+                cand_count[(item * kBM + row) * 2 + half] = ok ? nlist : -1;
                 if (!ok) break;
                 continue;
             }
@@ -522,15 +532,15 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 template <int TOPK, int MODE, bool KCHUNK>
 void run_screen(const ScreenLayout& lay, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
                 const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
-                int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const ProbeArgs& pa, int n_sm,
-                cudaStream_t st) {
+                int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const ProbeArgs& pa,
+                const ListArgs& la, int n_sm, cudaStream_t st) {
     auto kern = k_screen<TOPK, MODE, KCHUNK>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
     kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, lay.bytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G,
-                                                                   G_pad, cv, ci, cc, status, pa, lay);
+                                                                   G_pad, cv, ci, cc, status, pa, lay, la);
 }
 
 // Shared-memory plan for K with the requested depth / buffering (0 = built-in:
@@ -565,13 +575,14 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
                    const uint16_t* Qb3, const int32_t* tile_slot, float* tau0, const int32_t* tile_j0,
                    int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
-                   int nfit, int n_sm, cudaStream_t st) {
+                   int nfit, const ListArgs& la, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
     if (!screen_config_ok(K, stages, ybuf) || (topk != 8 && topk != 16)) return false;
     const ScreenLayout lay = choose_layout(K, stages, ybuf);
     const ProbeArgs pa{Qc, Qb, gnorm, alpha, Sc32, nfit};
 #define FC_SCREEN_RUN(TT, MM, CC) \
-    run_screen<TT, MM, CC>(lay, Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, n_sm, st)
+    run_screen<TT, MM, CC>(lay, Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, la, \
+                           n_sm, st)
 #define FC_SCREEN_MODES(TT, CC)                 \
     do {                                        \
         if (mode == kModeMin)                   \
