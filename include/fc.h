@@ -81,12 +81,17 @@ enum { FC_QVEC_AUTO = 0,     /* tensor cores above N_fit ~ 61, binary32 SIMT bel
        FC_QVEC_SIMT = 1,     /* q_g = s~^T A s~ in binary32, A in shared memory    */
        FC_QVEC_TC = 2 };     /* q_g = |W s~|^2 on tcgen05 (bf16 hi/lo), K <= 128  */
 
+enum { FC_ROUND_AUTO = 0,    /* TOPK, or LIST once top-k certifies < 30 % of a grid's scans */
+       FC_ROUND_TOPK = 1,    /* rounds: top-k, top-16, list, exact-size lists               */
+       FC_ROUND_LIST = 2 };  /* rounds: top-k, list, exact-size lists (no top-16 round)     */
+
 typedef struct {
     int32_t qvec;           /* FC_QVEC_*                                            */
     int32_t screen_stages;  /* screen pipeline depth, 0 = built-in choice (2..8)    */
     int32_t screen_ybuf;    /* A-image buffers of the screen, 0 = built-in (1 or 2) */
     int32_t cache_slots;    /* covariance-cache slots at most, 0 = as memory allows;
                                one scan needs a slot per distinct covariance index */
+    int32_t first_round;    /* FC_ROUND_*                                           */
 } fc_tuning;
 
 /* Counters and stage timings of the last synchronous call on a context.
@@ -235,7 +240,7 @@ FC_API fc_status fc_fake_data_noalloc(const double* S, int64_t G, int32_t N_full
 /* Set / read the kernel choices of a loaded grid.  A choice the grid cannot
  * use (FC_QVEC_TC above K = 128, a screen depth that does not fit in shared
  * memory) gives FC_ERR_ARG.  Lowering cache_slots below the slots in use
- * clears the grid's covariance cache.  fc_autotune keeps cache_slots.
+ * clears the grid's covariance cache.  fc_autotune keeps cache_slots and first_round.
  * Errors: FC_ERR_ARG, FC_ERR_NOT_FOUND. */
 FC_API fc_status fc_set_tuning(fc_ctx* ctx, int32_t grid_id, const fc_tuning* t);
 FC_API fc_status fc_get_tuning(fc_ctx* ctx, int32_t grid_id, fc_tuning* t);

@@ -21,6 +21,7 @@ FC_PREC_FP64, FC_PREC_MIXED = 0, 1
 FC_FLUCT_POISSON_SYS, FC_FLUCT_GAUSS = 0, 1
 FC_COV_ITERATE, FC_COV_FIXED, FC_COV_IDENTITY = 0, 1, 2
 FC_QVEC_AUTO, FC_QVEC_SIMT, FC_QVEC_TC = 0, 1, 2
+FC_ROUND_AUTO, FC_ROUND_TOPK, FC_ROUND_LIST = 0, 1, 2
 
 _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_SPD", -3: "FC_ERR_BUDGET",
                  -4: "FC_ERR_CUDA", -5: "FC_ERR_TIMEOUT", -6: "FC_ERR_CANCELLED", -7: "FC_ERR_NOT_FOUND",
@@ -59,7 +60,7 @@ class fc_stats(ctypes.Structure):
 
 class fc_tuning(ctypes.Structure):
     _fields_ = [("qvec", ctypes.c_int32), ("screen_stages", ctypes.c_int32), ("screen_ybuf", ctypes.c_int32),
-                ("cache_slots", ctypes.c_int32)]
+                ("cache_slots", ctypes.c_int32), ("first_round", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -293,8 +294,8 @@ def fc_cancel(ctx, ticket: int):
 
 
 def fc_set_tuning(ctx, grid_id: int, qvec: int = 0, screen_stages: int = 0, screen_ybuf: int = 0,
-                  cache_slots: int = 0):
-    t = fc_tuning(qvec, screen_stages, screen_ybuf, cache_slots)
+                  cache_slots: int = 0, first_round: int = 0):
+    t = fc_tuning(qvec, screen_stages, screen_ybuf, cache_slots, first_round)
     _check(load().fc_set_tuning(ctx, grid_id, ctypes.byref(t)), ctx)
 
 

@@ -113,6 +113,7 @@ struct Grid {
     double* Q64 = nullptr;           // [cap][G]   (plain)
     std::vector<uint8_t> q32_ready, q64_ready;
     fc_tuning tune{};                // kernel choices (all zero: built-in)
+    int64_t r1_in = 0, r1_ok = 0;    // universe-scans through a top-k first round, and certified there
     int busy = 0;                    // queued jobs referencing the grid
 };
 
@@ -842,6 +843,12 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     // are on their first scan a min-only pass tightens the seeds first.
     const bool first_heavy = 2 * L->n_first >= n_active;
     L->n_first = 0;
+    // the top-16 round is skipped (round 1's failures go straight to the list round) when asked, or
+    // when round 1 has certified under 30 % of this grid's universe-scans (after enough to judge)
+    const bool skip16 =
+        mixed && (g->tune.first_round == FC_ROUND_LIST ||
+                  (g->tune.first_round == FC_ROUND_AUTO && g->r1_in >= 4096 && 10 * g->r1_ok < 3 * g->r1_in));
+    int64_t r1_in = 0;
     int32_t *active = L->active, *next = L->next, *fin = L->fin, *uslot = L->uslot, *cur = L->cur;
     const float* d = L->d;
     int32_t* cnts = nullptr;
@@ -932,9 +939,12 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             // one certified screen round over `list` (grouped into tiles by covariance slot)
             // rounds 2 and 3 list candidates; round 3 stores them in the exact-size regions
             // loff / lnum (u-indexed, list_total entries) sized by round 2's overflow counts
+            // seeded: the rows carry an upper bound of their minimum from an earlier round (thr); else
+            // the probe seeds them, tightened by a min-only pass when most rows are on their first scan
             auto screen_round = [&](int round, const int32_t* list, int64_t cnt, const int32_t* lslot, int rtopk,
-                                    int32_t* fb_out, int32_t* n_fb_out, const int64_t* loff = nullptr,
-                                    const int2* lnum = nullptr, int64_t list_total = 0) -> fc_status {
+                                    int32_t* fb_out, int32_t* n_fb_out, bool seeded,
+                                    const int64_t* loff = nullptr, const int2* lnum = nullptr,
+                                    int64_t list_total = 0) -> fc_status {
                 const bool listing = (round >= 2);
                 const int64_t n_slots = g->n_slots;
                 const int64_t max_tiles = cnt / kBM + std::min<int64_t>(n_slots, cnt) + 1;
@@ -967,13 +977,13 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 FC_TRY(sync(c));
                 launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
                              g->gnorm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
-                if (round) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
+                if (seeded) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
                 FC_TRY(stage_end(c, &S->ms_prep));
                 stage_begin(c);
                 // round 0: a min-only pass to tighten the seeds when most rows are on their first scan (the probe
                 // at the true point is loose there; later scans probe at the previous minimum), then the top-k
                 // pass.  Later rounds are seeded by the best binary64 value (round 1: top-k, round 2: list).
-                const bool min_pass = (round == 0 && first_heavy);
+                const bool min_pass = (!seeded && first_heavy);
                 for (int pass = min_pass ? 0 : 1; pass < 2; ++pass) {
                     const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
                     if (!launch_screen(g->K, rtopk, mode, g->tune.screen_stages, g->tune.screen_ybuf, Yt, g->Bt, g->Qb3,
@@ -1079,7 +1089,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     else
                         launch_lookup_slots(d_u, nb4, cur, g->slot_of, fslot, c->stream);
                     FC_CUDA(cudaMemsetAsync(n_x, 0, 4, c->stream));
-                    FC_TRY(screen_round(3, d_u, nb4, fslot, kMaxTopK, d_x, n_x, loff, lnum, total));
+                    FC_TRY(screen_round(3, d_u, nb4, fslot, kMaxTopK, d_x, n_x, true, loff, lnum, total));
                     int32_t nx = 0;
                     FC_CUDA(cudaMemcpyAsync(&nx, n_x, 4, cudaMemcpyDeviceToHost, c->stream));
                     FC_TRY(sync(c));
@@ -1093,17 +1103,29 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 }
                 return FC_OK;
             };
-            FC_TRY(screen_round(0, sl_list, sl_n, sl_slot, topk, fb, cnts + 1));
+            r1_in += sl_n;
+            FC_TRY(screen_round(0, sl_list, sl_n, sl_slot, topk, fb, cnts + 1, false));
             int32_t n_fb = 0;
             FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
             FC_TRY(sync(c));
-            if (n_fb > 0) {
+            if (n_fb > 0 && skip16) {
+                // straight to the list round, seeded by the binary64 value round 1 found
+                if (o.cov == FC_COV_IDENTITY)
+                    launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
+                else
+                    launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
+                FC_TRY(screen_round(2, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4, true));
+                int32_t n_ov = 0;
+                FC_CUDA(cudaMemcpyAsync(&n_ov, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
+                FC_TRY(sync(c));
+                if (n_ov > 0) FC_TRY(big_lists(fb2, n_ov, lcount));
+            } else if (n_fb > 0) {
                 // second certified round for the universes whose certificate failed
                 if (o.cov == FC_COV_IDENTITY)
                     launch_fill_i32(fslot, n_fb, g->ident_slot, c->stream);
                 else
                     launch_lookup_slots(fb, n_fb, cur, g->slot_of, fslot, c->stream);
-                FC_TRY(screen_round(1, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4));
+                FC_TRY(screen_round(1, fb, n_fb, fslot, kMaxTopK, fb2, cnts + 4, true));
                 int32_t n_fb2 = 0;
                 FC_CUDA(cudaMemcpyAsync(&n_fb2, cnts + 4, 4, cudaMemcpyDeviceToHost, c->stream));
                 FC_TRY(sync(c));
@@ -1114,7 +1136,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     else
                         launch_lookup_slots(fb2, n_fb2, cur, g->slot_of, fslot, c->stream);
                     FC_CUDA(cudaMemsetAsync(cnts + 1, 0, 4, c->stream));
-                    FC_TRY(screen_round(2, fb2, n_fb2, fslot, kMaxTopK, fb, cnts + 1));
+                    FC_TRY(screen_round(2, fb2, n_fb2, fslot, kMaxTopK, fb, cnts + 1, true));
                     int32_t n_fb3 = 0;
                     FC_CUDA(cudaMemcpyAsync(&n_fb3, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
                     FC_TRY(sync(c));
@@ -1196,6 +1218,8 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     std::swap(L->active, L->next);
     L->n_active = n_next;
     S->screened += (int64_t)(cn[0] + cn[3]);
+    g->r1_in += r1_in;
+    g->r1_ok += (int64_t)cn[0];
     S->rescored += (int64_t)(cn[1] + cn[4] + cn[6] + cn[9]);
     S->rescreened += (int64_t)(cn[2] + cn[5]);
     S->big_listed += (int64_t)(cn[9] + cn[10]);
@@ -1931,6 +1955,7 @@ fc_status fc_set_tuning(fc_ctx* c, int32_t grid_id, const fc_tuning* t) {
     if (!screen_config_ok(g->K, t->screen_stages, t->screen_ybuf))
         return fail(FC_ERR_ARG, "screen depth / buffering does not fit this K");
     if (t->cache_slots < 0 || t->cache_slots == 1) return fail(FC_ERR_ARG, "cache_slots must be 0 or >= 2");
+    if (t->first_round < FC_ROUND_AUTO || t->first_round > FC_ROUND_LIST) return fail(FC_ERR_ARG, "bad first_round");
     // q-vectors from the other kernel have a different (still certified) bound: recompute them
     if (t->qvec != g->tune.qvec) std::fill(g->q32_ready.begin(), g->q32_ready.end(), 0);
     if (t->cache_slots > 0 && t->cache_slots < g->n_slots) reset_cache(c, g);
@@ -1972,6 +1997,7 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
                 if (strncmp(line, key, kl) != 0 || line[kl] != ' ') continue;
                 fc_tuning r{};
                 r.cache_slots = g->tune.cache_slots;
+                r.first_round = g->tune.first_round;
                 if (sscanf(line + kl, " qvec=%d stages=%d ybuf=%d", &r.qvec, &r.screen_stages, &r.screen_ybuf) == 3 &&
                     valid(r)) {
                     t = r;
@@ -2005,6 +2031,7 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
     };
     fc_tuning best{};
     best.cache_slots = saved.cache_slots;
+    best.first_round = saved.first_round;
     fc_stats st{};
     fc_status rc = FC_OK;
     // q-vector kernel: covariance stage of a cold cache (P new covariances and q-vectors)

@@ -4,8 +4,9 @@
   16-column K-slice stages and the tensor-core q-vectors (whole S~ tiles, or
   K slices beside a resident W), against the oracle (same bars as the other
   mixed-path tests).
-* Kernel choices (q-vector kernel, screen depth, A-image buffering) change
-  speed only: the outputs are identical bit for bit.
+* Kernel choices (q-vector kernel, screen depth, A-image buffering, top-k
+  or list first round) change speed only: the outputs are identical bit for
+  bit.
 * A covariance cache smaller than the run's distinct covariances reuses
   slots (least recently used first) without changing any output.
 * fc_autotune picks a valid choice and reuses its cache file.
@@ -98,7 +99,8 @@ def test_kernel_choices_do_not_change_results(fc, ctx, which, request):
     pts = w.points if len(w.points) > 1 else np.array([w.points[0], 17, 600], np.int64)
     U = 300 if which == "cfg1" else 64
     ref = _run_all(fc, ctx, gid, pts, 3, U)
-    choices = [dict(qvec=fc.FC_QVEC_SIMT), dict(qvec=fc.FC_QVEC_TC), dict(qvec=fc.FC_QVEC_TC, screen_stages=2)]
+    choices = [dict(qvec=fc.FC_QVEC_SIMT), dict(qvec=fc.FC_QVEC_TC), dict(qvec=fc.FC_QVEC_TC, screen_stages=2),
+               dict(first_round=fc.FC_ROUND_LIST), dict(first_round=fc.FC_ROUND_TOPK, qvec=fc.FC_QVEC_TC)]
     if which == "cfg1":
         choices.append(dict(screen_stages=2, screen_ybuf=2))       # whole-tile stages, double A image
     else:
@@ -115,7 +117,7 @@ def test_bad_tuning_rejected(fc, ctx):
     w = workloads.cfg1()
     gid = _load(fc, ctx, w)
     for bad in (dict(qvec=7), dict(screen_stages=1), dict(screen_stages=9), dict(screen_ybuf=3), dict(cache_slots=1),
-                dict(cache_slots=-4)):
+                dict(cache_slots=-4), dict(first_round=3)):
         with pytest.raises(fc.FCError) as e:
             fc.fc_set_tuning(ctx, gid, **bad)
         assert e.value.status == fc.FC_ERR_ARG
