@@ -84,6 +84,8 @@ struct Grid {
     double* S_fit = nullptr;    // [G][nfit]
     double* centre = nullptr;   // [nfit]
     double* Sc = nullptr;       // [G][nfit] centred
+    float2* Sdf = nullptr;      // [G][nfit] S_fit as double-float (mixed-path residuals)
+    float2* centre_df = nullptr;  // [nfit]
     float* Sc32 = nullptr;      // [G][nfit]
     float4* gnorm = nullptr;    // [G] |s~|, |S_lo|, |r_S|
     uint16_t* Bt = nullptr;     // screen B image [G_pad/BN][2K/8][BN/8][8][8]
@@ -103,6 +105,7 @@ struct Grid {
     int32_t* slot_of = nullptr;      // device [G]
     double* A64 = nullptr;           // [cap][nfit][nfit]
     double* W64 = nullptr;           // [cap][nfit][nfit]  A = W^T W, W lower triangular
+    float2* Wdf = nullptr;           // [cap][nfit][nfit]  W as double-float
     float* A32 = nullptr;
     float* rho = nullptr;
     uint16_t* Wimg = nullptr;        // [cap][2K][K] bf16 hi/lo image of W (tensor-core q-vectors)
@@ -316,6 +319,7 @@ void free_cache(fc_ctx* c, Grid* g) {
     dfree(c, g->slot_of); g->slot_of = nullptr;
     dfree(c, g->A64); g->A64 = nullptr;
     dfree(c, g->W64); g->W64 = nullptr;
+    dfree(c, g->Wdf); g->Wdf = nullptr;
     dfree(c, g->A32); g->A32 = nullptr;
     dfree(c, g->rho); g->rho = nullptr;
     dfree(c, g->Wimg); g->Wimg = nullptr;
@@ -351,7 +355,7 @@ void reset_cache(fc_ctx* c, Grid* g) {
 // Device bytes one cache slot costs (covariance, W image, binary32 q-vectors,
 // binary64 q-vectors).
 size_t slot_bytes(const Grid* g) {
-    return (size_t)g->nfit * g->nfit * (8 + 8 + 4) + 4 + (size_t)4 * g->K * g->K + 16 + (size_t)g->G_pad * 24 +
+    return (size_t)g->nfit * g->nfit * (8 + 8 + 8 + 4) + 4 + (size_t)4 * g->K * g->K + 16 + (size_t)g->G_pad * 24 +
            (size_t)g->G * 8;
 }
 
@@ -397,6 +401,7 @@ fc_status grow_cache(fc_ctx* c, Grid* g, int64_t new_cap) {
     const size_t n2 = (size_t)g->nfit * g->nfit;
     FC_TRY(regrow(c, &g->A64, n2, old, new_cap));
     FC_TRY(regrow(c, &g->W64, n2, old, new_cap));
+    FC_TRY(regrow(c, &g->Wdf, n2, old, new_cap));
     FC_TRY(regrow(c, &g->A32, n2, old, new_cap));
     FC_TRY(regrow(c, &g->rho, 1, old, new_cap));
     if (g->Wimg) FC_TRY(regrow(c, &g->Wimg, (size_t)2 * g->K * g->K, old, new_cap));
@@ -559,6 +564,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
         launch_build_cov(g->S_full, g->nf, g->nfit, g->identity_collapse ? nullptr : g->collapse, g->F, dq, ds,
                          (int)new_q.size(), cov_mode == FC_COV_IDENTITY ? 2 : 0, g->A64, g->W64, g->A32, g->rho,
                          work, c->status_dev, c->stream);
+        launch_wdf(g->W64, ds, (int)new_q.size(), g->nfit, g->Wdf, c->stream);
         if (cov_mode != FC_COV_IDENTITY) launch_set_slots(dq, ds, (int)new_q.size(), g->slot_of, c->stream);
         c->acc->distinct_cov += (int64_t)new_q.size();
         FC_TRY(check_status(c));
@@ -880,7 +886,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             FC_TRY(scratch(c, "fb_pv", (size_t)cnt * nsp, &pv));
             FC_TRY(scratch(c, "fb_pg", (size_t)cnt * nsp, &pg));
             stage_begin(c);
-            launch_scan_resid(list, cnt, fslot, d, g->S_fit, g->G, g->nfit, g->W64, pv, pg, nsp, L->best,
+            launch_scan_resid(list, cnt, fslot, d, g->Sdf, g->G, g->nfit, g->Wdf, pv, pg, nsp, L->best,
                               c->stream);
             FC_TRY(stage_end(c, &S->ms_fallback));
         } else if (o.cov == FC_COV_IDENTITY) {
@@ -919,8 +925,8 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             else
                 launch_lookup_slots(fin, n_fin, cur, g->slot_of, finslot, c->stream);
             stage_begin(c);
-            launch_finish(fin, n_fin, finslot, L->best, us, d, g->S_fit, g->nfit, g->W64, L->dchi2, L->chi2min,
-                          c->stream);
+            launch_finish(fin, n_fin, finslot, L->best, us, d, g->S_fit, g->nfit, g->W64, mixed ? g->Sdf : nullptr,
+                          mixed ? g->Wdf : nullptr, L->dchi2, L->chi2min, c->stream);
             FC_TRY(stage_end(c, &S->ms_finish));
         }
         return FC_OK;
@@ -1011,6 +1017,9 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 ra.S_fit = g->S_fit;
                 ra.nfit = g->nfit;
                 ra.W64 = g->W64;
+                ra.Wdf = g->Wdf;
+                ra.Sdf = g->Sdf;
+                ra.centre_df = g->centre_df;
                 ra.cur = cur;
                 ra.pt = L->pt;
                 ra.maxit = L->maxit;
@@ -1674,13 +1683,15 @@ fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const 
     fc_status st = FC_OK;
     auto cleanup = [&](fc_status s) {
         dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
-        dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse);
+        dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->Sdf); dfree(c, g->centre_df);
         return s;
     };
     if ((st = dalloc_t(c, &g->S_full, (size_t)G * nf)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->S_fit, (size_t)G * nfit)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->centre, (size_t)nfit)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->Sc, (size_t)G * nfit)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->Sdf, (size_t)G * nfit)) != FC_OK) return cleanup(st);
+    if ((st = dalloc_t(c, &g->centre_df, (size_t)nfit)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->Sc32, (size_t)G * nfit)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->gnorm, (size_t)G)) != FC_OK) return cleanup(st);
     if ((st = dalloc_t(c, &g->Bt, (size_t)g->G_pad * 2 * g->K)) != FC_OK) return cleanup(st);
@@ -1708,6 +1719,8 @@ fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const 
     launch_collapse(g->S_full, G, nf, ident ? nullptr : g->collapse, nfit, g->S_fit, c->stream);
     launch_centre(g->S_fit, G, nfit, g->centre, nullptr, c->stream);
     launch_centred(g->S_fit, g->centre, G, g->G_pad, nfit, g->K, g->Sc, g->Sc32, g->gnorm, g->Bt, c->stream);
+    launch_to_df(g->S_fit, G * nfit, g->Sdf, c->stream);
+    launch_to_df(g->centre, nfit, g->centre_df, c->stream);
     if ((st = sync(c)) != FC_OK) return cleanup(st);
     {
         std::lock_guard<std::mutex> lq(c->q_mu);
@@ -1771,7 +1784,8 @@ fc_status fc_unload_grid(fc_ctx* c, int32_t grid_id) {
     }
     free_cache(c, g);
     dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
-    dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->F);
+    dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->F); dfree(c, g->Sdf);
+    dfree(c, g->centre_df);
     return FC_OK;
 }
 

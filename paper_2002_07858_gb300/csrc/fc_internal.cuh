@@ -124,10 +124,13 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot_of_list,
                    const double* centre, const double* Sc, int64_t G, int nfit, const double* A64,
                    const double* Q64, int64_t ldq, int32_t* best, cudaStream_t st);
 
-// exact residual-form scan (one CTA per listed universe), no q-vectors needed
-void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* Sfit,
-                       int64_t G, int nfit, const double* W64, double* part_v, int32_t* part_g, int nsp,
+// exact residual-form scan of the mixed path (double-float, split over nsp CTAs per universe)
+void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const float2* Sdf,
+                       int64_t G, int nfit, const float2* Wdf, double* part_v, int32_t* part_g, int nsp,
                        int32_t* best, cudaStream_t st);
+// double-float copies: W of a list of slots; any binary64 array
+void launch_wdf(const double* W64, const int32_t* slots, int n, int nfit, float2* Wdf, cudaStream_t st);
+void launch_to_df(const double* x, int64_t n, float2* y, cudaStream_t st);
 
 // ---- mixed path: grouping, y prep, screen, decision ----
 // counting sort of active universes by slot into BM-row tiles
@@ -178,6 +181,9 @@ struct ResolveArgs {
     const double* S_fit;
     int nfit;
     const double* W64;
+    const float2* Wdf;     // [slots][nfit][nfit] double-float W
+    const float2* Sdf;     // [G][nfit] double-float S_fit
+    const float2* centre_df;  // [nfit] double-float centre
     int32_t* cur;          // [n] covariance grid index, advanced for continuing universes
     const int32_t* pt;     // [n] true point of the universe
     const int8_t* maxit;   // [n] scan limit of the universe
@@ -215,9 +221,10 @@ struct UniverseState {
     const int32_t* job_of;
     int32_t* job_left;
 };
+// Sdf / Wdf given: the mixed path's double-float residuals; null: binary64 (plain path)
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot_of_list, const int32_t* best,
                    const UniverseState& us, const float* d, const double* S_fit, int nfit, const double* W64,
-                   double* dchi2, double* chi2min, cudaStream_t st);
+                   const float2* Sdf, const float2* Wdf, double* dchi2, double* chi2min, cudaStream_t st);
 // advance: converged / exhausted universes -> finish list, others stay active
 void launch_advance(const int32_t* active, int64_t n_active, const int32_t* best, const UniverseState& us,
                     int32_t* next_active, int32_t* n_next, int32_t* finish_list, int32_t* n_finish, cudaStream_t st);

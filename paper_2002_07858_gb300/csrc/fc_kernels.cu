@@ -12,6 +12,7 @@
 
 #include <cstdint>
 
+#include "fc_df.cuh"
 #include "fc_internal.cuh"
 #include "fc_sampler.cuh"
 
@@ -73,6 +74,60 @@ __device__ double resid_chi2_warp(const double* __restrict__ W, int n, const dou
         for (int i = 0; i < n; ++i) acc = fma(t[i], t[i], acc);
     __syncwarp();
     return acc;
+}
+
+// The mixed path's residual chi2 = |W (s - d)|^2 in double-float (fc_df.cuh):
+// r_j = s_j - d_j, t_i = sum_{j<=i} W_ij r_j in increasing j (renormalised per
+// row), chi2 = sum_i t_i^2 in increasing i.  Every mixed-path kernel evaluates
+// it in this order, so a universe's result has the same bits whichever
+// certified round decided it.  W and s are double-float copies of the
+// binary64 arrays; the value is returned as binary64.
+__device__ double resid_df(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+                           const float* __restrict__ du) {
+    float2 r[kMaxBins];
+    for (int j = 0; j < n; ++j) r[j] = df_sub_f(s[j], du[j]);
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int i = 0; i < n; ++i) {
+        const float2* Wi = W + i * n;
+        float2 t = make_float2(0.0f, 0.0f);
+        for (int j = 0; j <= i; ++j) t = df_fma(t, Wi[j], r[j]);
+        t = df_norm(t.x, t.y);
+        acc = df_fma(acc, t, t);
+    }
+    return df_to(df_norm(acc.x, acc.y));
+}
+
+// resid_df spread over a warp with the same bits: r_j = s_j - d_j is formed in
+// this warp's shared vector r, lanes form the rows t_i into t, lane 0 sums
+// t_i^2 in row order.  The result is lane 0's.
+__device__ double resid_df_warp(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+                                const float* __restrict__ du, float2* r, float2* t, int lane) {
+    for (int j = lane; j < n; j += 32) r[j] = df_sub_f(s[j], du[j]);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const float2* Wi = W + i * n;
+        float2 x = make_float2(0.0f, 0.0f);
+        for (int j = 0; j <= i; ++j) x = df_fma(x, Wi[j], r[j]);
+        t[i] = df_norm(x.x, x.y);
+    }
+    __syncwarp();
+    float2 acc = make_float2(0.0f, 0.0f);
+    if (lane == 0)
+        for (int i = 0; i < n; ++i) acc = df_fma(acc, t[i], t[i]);
+    __syncwarp();
+    return df_to(df_norm(acc.x, acc.y));
+}
+
+// double-float copies of W for a list of slots
+__global__ void k_wdf(const double* __restrict__ W64, const int32_t* __restrict__ slots, int nfit,
+                      float2* __restrict__ Wdf) {
+    const size_t base = (size_t)slots[blockIdx.x] * nfit * nfit;
+    for (int e = threadIdx.x; e < nfit * nfit; e += blockDim.x) Wdf[base + e] = df_from(W64[base + e]);
+}
+
+__global__ void k_to_df(const double* __restrict__ x, int64_t n, float2* __restrict__ y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = df_from(x[i]);
 }
 
 // ---------------------------------------------------------------- ingest ---
@@ -604,25 +659,25 @@ __global__ void __launch_bounds__(256) k_scan64(const int32_t* __restrict__ list
 // universe's covariance in shared memory and scans every split-th grid point;
 // k_scan_resid_reduce takes the first minimum over the splits.
 __global__ void __launch_bounds__(256) k_scan_resid(const int32_t* __restrict__ list, const int32_t* __restrict__ uslot,
-                                                     const float* __restrict__ d, const double* __restrict__ Sfit,
-                                                     int64_t G, int nfit, const double* __restrict__ W64,
+                                                     const float* __restrict__ d, const float2* __restrict__ Sdf,
+                                                     int64_t G, int nfit, const float2* __restrict__ Wdf,
                                                      double* __restrict__ part_v, int32_t* __restrict__ part_g) {
-    extern __shared__ double sW[];
+    extern __shared__ float2 sWd[];
     __shared__ double rv[8];
     __shared__ int32_t rg[8];
     const int i = blockIdx.x, sp = blockIdx.y, nsp = gridDim.y;
     const int u = list[i];
-    const double* Wg = W64 + (size_t)uslot[i] * nfit * nfit;
+    const float2* Wg = Wdf + (size_t)uslot[i] * nfit * nfit;
     const bool staged = (nfit <= kResolveMaxN);
     if (staged)
-        for (int e = threadIdx.x; e < nfit * nfit; e += blockDim.x) sW[e] = Wg[e];
+        for (int e = threadIdx.x; e < nfit * nfit; e += blockDim.x) sWd[e] = Wg[e];
     __syncthreads();
-    const double* W = staged ? sW : Wg;
+    const float2* W = staged ? sWd : Wg;
     const float* du = d + (size_t)u * nfit;
     double bv = DBL_MAX;
     int32_t bg = INT32_MAX;
     for (int64_t g = (int64_t)sp * blockDim.x + threadIdx.x; g < G; g += (int64_t)nsp * blockDim.x) {
-        const double c = resid_chi2(W, nfit, Sfit + g * nfit, du);
+        const double c = resid_df(W, nfit, Sdf + g * nfit, du);
         if (c < bv) {
             bv = c;
             bg = (int32_t)g;
@@ -846,7 +901,7 @@ constexpr int kItemCodes = kMaxTopK + 3;
 //     their last scan) get chi2_p and chi2_min in residual form and finish
 //     with dchi2; the others move their covariance index to the minimum.
 __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
-    extern __shared__ double sW[];
+    extern __shared__ float2 sWd[];
     __shared__ int s_nitem, s_nnext, s_nfb, s_cnt[3];
     __shared__ int s_base_next, s_base_fb;
     __shared__ uint16_t s_item[kBM * kItemCodes];
@@ -857,11 +912,11 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
     const int r = threadIdx.x;
     const int n = a.nfit;
     const int slot = a.tile_slot[t];
-    const double* Wg = a.W64 + (size_t)slot * n * n;
+    const float2* Wg = a.Wdf + (size_t)slot * n * n;
     const bool staged = (n <= kResolveMaxN);
     if (staged)
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sW[e] = Wg[e];
-    const double* W = staged ? sW : Wg;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sWd[e] = Wg[e];
+    const float2* W = staged ? sWd : Wg;
     if (r == 0) {
         s_nitem = 0;
         s_nnext = 0;
@@ -923,8 +978,8 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         const int code = s_item[it];
         const int rr = code / kItemCodes, j = code % kItemCodes;
         const float* du = a.d + (size_t)s_u[rr] * n;
-        const double* sv = (j == kItemCu) ? a.centre : a.S_fit + (int64_t)s_g[rr][j] * n;
-        s_res[rr][j] = resid_chi2(W, n, sv, du);
+        const float2* sv = (j == kItemCu) ? a.centre_df : a.Sdf + (int64_t)s_g[rr][j] * n;
+        s_res[rr][j] = resid_df(W, n, sv, du);
     }
     __syncthreads();
     if (state == 2) {
@@ -1001,7 +1056,7 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         const int code = s_item[it];
         const int rr = code / kItemCodes, j = code % kItemCodes;
         const float* du = a.d + (size_t)s_u[rr] * n;
-        s_res[rr][j] = resid_chi2(W, n, a.S_fit + (int64_t)s_g[rr][j] * n, du);
+        s_res[rr][j] = resid_df(W, n, a.Sdf + (int64_t)s_g[rr][j] * n, du);
     }
     __syncthreads();
     if (to_next) a.next[s_base_next + my_next] = u;
@@ -1023,18 +1078,18 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
 // then finishes (dchi2) or advances exactly as in k_resolve; rows whose list
 // overflowed go to the exact scan.
 __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32_t* __restrict__ cand_count) {
-    extern __shared__ double sW[];
+    extern __shared__ float2 sWd[];
     const int64_t t = blockIdx.x;
     const int n = a.nfit;
     const int slot = a.tile_slot[t];
-    const double* Wg = a.W64 + (size_t)slot * n * n;
+    const float2* Wg = a.Wdf + (size_t)slot * n * n;
     const bool staged = (n <= kResolveMaxN);
     if (staged)
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sW[e] = Wg[e];
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sWd[e] = Wg[e];
     __syncthreads();
-    const double* W = staged ? sW : Wg;
+    const float2* W = staged ? sWd : Wg;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ double s_r[8][kMaxBins], s_t[8][kMaxBins];
+    __shared__ float2 s_r[8][kMaxBins], s_t[8][kMaxBins];
     for (int r = warp; r < kBM; r += blockDim.x >> 5) {
         const int u = a.tile_univ[t * kBM + r];
         if (u < 0) continue;
@@ -1068,7 +1123,7 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
         for (int k = lane; k < n0 + n1; k += 32) {
             const int64_t e = (k < n0) ? base0 + k : base1 + (k - n0);
             const int32_t g = a.cidx[e];
-            const double c = resid_chi2(W, n, a.S_fit + (int64_t)g * n, du);
+            const double c = resid_df(W, n, a.Sdf + (int64_t)g * n, du);
             if (c < bv || (c == bv && g < bg)) {
                 bv = c;
                 bg = g;
@@ -1081,10 +1136,8 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
             const int p = a.pt[u];
             double cp = 0.0;
             if (p != bg) {
-                // chi2_p in residual form (row dot products over the lanes, the bits of resid_chi2)
-                for (int j = lane; j < n; j += 32) s_r[warp][j] = a.S_fit[(int64_t)p * n + j] - (double)du[j];
-                __syncwarp();
-                cp = resid_chi2_warp(W, n, s_r[warp], s_t[warp], lane);
+                // chi2_p in residual form (row dot products over the lanes, the bits of resid_df)
+                cp = resid_df_warp(W, n, a.Sdf + (int64_t)p * n, du, s_r[warp], s_t[warp], lane);
             }
             if (lane == 0) {
                 a.best[u] = bg;
@@ -1120,9 +1173,11 @@ __global__ void __launch_bounds__(128) k_finish(const int32_t* __restrict__ list
                                                  const int32_t* __restrict__ uslot, const int32_t* __restrict__ best,
                                                  UniverseState us, const float* __restrict__ d,
                                                  const double* __restrict__ Sfit, int nfit,
-                                                 const double* __restrict__ W64, double* __restrict__ dchi2,
+                                                 const double* __restrict__ W64, const float2* __restrict__ Sdf,
+                                                 const float2* __restrict__ Wdf, double* __restrict__ dchi2,
                                                  double* __restrict__ chi2min) {
     __shared__ double rp[4][kMaxBins], rm[4][kMaxBins], tt[4][kMaxBins];
+    __shared__ float2 fr[4][kMaxBins], ft[4][kMaxBins];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = blockIdx.x * 4LL + w;
     if (i >= n) return;
@@ -1131,15 +1186,23 @@ __global__ void __launch_bounds__(128) k_finish(const int32_t* __restrict__ list
     const int p = us.pt[u];
     const int g = best[u];
     const float* du = d + (size_t)u * nfit;
-    for (int j = lane; j < nfit; j += 32) {
-        rp[w][j] = Sfit[(int64_t)p * nfit + j] - (double)du[j];
-        rm[w][j] = Sfit[(int64_t)g * nfit + j] - (double)du[j];
+    double cp = 0.0, cm = 0.0;
+    if (Wdf) {
+        // mixed path: the double-float residual of every other mixed-path kernel
+        const float2* W = Wdf + (size_t)slot * nfit * nfit;
+        cp = (p == g) ? 0.0 : resid_df_warp(W, nfit, Sdf + (int64_t)p * nfit, du, fr[w], ft[w], lane);
+        cm = resid_df_warp(W, nfit, Sdf + (int64_t)g * nfit, du, fr[w], ft[w], lane);
+    } else {
+        // plain path: binary64, in the summation order of resid_chi2
+        for (int j = lane; j < nfit; j += 32) {
+            rp[w][j] = Sfit[(int64_t)p * nfit + j] - (double)du[j];
+            rm[w][j] = Sfit[(int64_t)g * nfit + j] - (double)du[j];
+        }
+        __syncwarp();
+        const double* W = W64 + (size_t)slot * nfit * nfit;
+        cp = (p == g) ? 0.0 : resid_chi2_warp(W, nfit, rp[w], tt[w], lane);
+        cm = resid_chi2_warp(W, nfit, rm[w], tt[w], lane);
     }
-    __syncwarp();
-    const double* W = W64 + (size_t)slot * nfit * nfit;
-    // both in the summation order of resid_chi2, so every path gives the same bits
-    const double cp = (p == g) ? 0.0 : resid_chi2_warp(W, nfit, rp[w], tt[w], lane);
-    const double cm = resid_chi2_warp(W, nfit, rm[w], tt[w], lane);
     if (lane == 0) {
         dchi2[u] = (p == g) ? 0.0 : cp - cm;
         if (chi2min) chi2min[u] = cm;
@@ -1339,13 +1402,13 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const f
     k_scan64<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, d, centre, Sc, G, nfit, A64, Q64, ldq, best);
 }
 
-void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* Sfit,
-                       int64_t G, int nfit, const double* W64, double* part_v, int32_t* part_g, int nsp,
+void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const float2* Sdf,
+                       int64_t G, int nfit, const float2* Wdf, double* part_v, int32_t* part_g, int nsp,
                        int32_t* best, cudaStream_t st) {
     if (n <= 0) return;
-    const size_t smem = nfit <= kResolveMaxN ? (size_t)nfit * nfit * sizeof(double) : 0;
+    const size_t smem = nfit <= kResolveMaxN ? (size_t)nfit * nfit * sizeof(float2) : 0;
     count_launch(2);
-    k_scan_resid<<<dim3((unsigned)n, (unsigned)nsp), 256, smem, st>>>(list, uslot, d, Sfit, G, nfit, W64, part_v,
+    k_scan_resid<<<dim3((unsigned)n, (unsigned)nsp), 256, smem, st>>>(list, uslot, d, Sdf, G, nfit, Wdf, part_v,
                                                                       part_g);
     k_scan_resid_reduce<<<blocks_for(n), kThreads, 0, st>>>(list, n, nsp, part_v, part_g, best);
 }
@@ -1411,11 +1474,24 @@ void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
 }
 
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const int32_t* best, const UniverseState& us,
-                   const float* d, const double* Sfit, int nfit, const double* W64, double* dchi2, double* chi2min,
-                   cudaStream_t st) {
+                   const float* d, const double* Sfit, int nfit, const double* W64, const float2* Sdf,
+                   const float2* Wdf, double* dchi2, double* chi2min, cudaStream_t st) {
     if (n <= 0) return;
     count_launch();
-    k_finish<<<(unsigned)((n + 3) / 4), 128, 0, st>>>(list, n, uslot, best, us, d, Sfit, nfit, W64, dchi2, chi2min);
+    k_finish<<<(unsigned)((n + 3) / 4), 128, 0, st>>>(list, n, uslot, best, us, d, Sfit, nfit, W64, Sdf, Wdf, dchi2,
+                                                       chi2min);
+}
+
+void launch_wdf(const double* W64, const int32_t* slots, int n, int nfit, float2* Wdf, cudaStream_t st) {
+    if (n <= 0) return;
+    count_launch();
+    k_wdf<<<n, 256, 0, st>>>(W64, slots, nfit, Wdf);
+}
+
+void launch_to_df(const double* x, int64_t n, float2* y, cudaStream_t st) {
+    if (n <= 0) return;
+    count_launch();
+    k_to_df<<<blocks_for(n), kThreads, 0, st>>>(x, n, y);
 }
 
 void launch_advance(const int32_t* active, int64_t n, const int32_t* best, const UniverseState& us,
