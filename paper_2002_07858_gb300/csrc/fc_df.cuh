@@ -49,6 +49,13 @@ __device__ __forceinline__ float2 df_fma(float2 acc, float2 a, float2 b) {
     return make_float2(s, __fadd_rn(acc.y, __fadd_rn(err, e)));
 }
 
+// a + b, both double-float
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+
 // a - b for a double-float a and a binary32 b (exact up to the lo rounding)
 __device__ __forceinline__ float2 df_sub_f(float2 a, float b) {
     float s, e;

@@ -77,21 +77,38 @@ __device__ double resid_chi2_warp(const double* __restrict__ W, int n, const dou
 }
 
 // The mixed path's residual chi2 = |W (s - d)|^2 in double-float (fc_df.cuh):
-// r_j = s_j - d_j, t_i = sum_{j<=i} W_ij r_j in increasing j (renormalised per
-// row), chi2 = sum_i t_i^2 in increasing i.  Every mixed-path kernel evaluates
+// r_j = s_j - d_j, t_i = sum_{j<=i} W_ij r_j (df_row), chi2 = sum_i t_i^2 in
+// increasing i.  Every mixed-path kernel evaluates
 // it in this order, so a universe's result has the same bits whichever
 // certified round decided it.  W and s are double-float copies of the
 // binary64 arrays; the value is returned as binary64.
+// Row i of W r: four interleaved partial sums (j = 0, 1, 2, 3 mod 4, each in
+// increasing j) so that four double-float chains run side by side, combined
+// as (p0 + p1) + (p2 + p3) and renormalised.
+__device__ __forceinline__ float2 df_row(const float2* __restrict__ Wi, const float2* __restrict__ r, int len) {
+    float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0, p3 = p0;
+    int j = 0;
+    for (; j + 3 < len; j += 4) {
+        p0 = df_fma(p0, Wi[j], r[j]);
+        p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
+        p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
+        p3 = df_fma(p3, Wi[j + 3], r[j + 3]);
+    }
+    if (j < len) p0 = df_fma(p0, Wi[j], r[j]);
+    if (j + 1 < len) p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
+    if (j + 2 < len) p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
+    const float2 a = df_add(df_norm(p0.x, p0.y), df_norm(p1.x, p1.y));
+    const float2 b = df_add(df_norm(p2.x, p2.y), df_norm(p3.x, p3.y));
+    return df_add(a, b);
+}
+
 __device__ double resid_df(const float2* __restrict__ W, int n, const float2* __restrict__ s,
                            const float* __restrict__ du) {
     float2 r[kMaxBins];
     for (int j = 0; j < n; ++j) r[j] = df_sub_f(s[j], du[j]);
     float2 acc = make_float2(0.0f, 0.0f);
     for (int i = 0; i < n; ++i) {
-        const float2* Wi = W + i * n;
-        float2 t = make_float2(0.0f, 0.0f);
-        for (int j = 0; j <= i; ++j) t = df_fma(t, Wi[j], r[j]);
-        t = df_norm(t.x, t.y);
+        const float2 t = df_row(W + i * n, r, i + 1);
         acc = df_fma(acc, t, t);
     }
     return df_to(df_norm(acc.x, acc.y));
@@ -104,12 +121,7 @@ __device__ double resid_df_warp(const float2* __restrict__ W, int n, const float
                                 const float* __restrict__ du, float2* r, float2* t, int lane) {
     for (int j = lane; j < n; j += 32) r[j] = df_sub_f(s[j], du[j]);
     __syncwarp();
-    for (int i = lane; i < n; i += 32) {
-        const float2* Wi = W + i * n;
-        float2 x = make_float2(0.0f, 0.0f);
-        for (int j = 0; j <= i; ++j) x = df_fma(x, Wi[j], r[j]);
-        t[i] = df_norm(x.x, x.y);
-    }
+    for (int i = lane; i < n; i += 32) t[i] = df_row(W + i * n, r, i + 1);
     __syncwarp();
     float2 acc = make_float2(0.0f, 0.0f);
     if (lane == 0)
