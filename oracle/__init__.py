@@ -81,6 +81,9 @@ def _load():
                                                  c_i64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_i64p, c_i8p,
                                                  c_fp]),
+            "oracle_run_samples": (ctypes.c_int, [c_dp, ctypes.c_int64, ctypes.c_int, c_i32p, ctypes.c_int, c_dp,
+                                                  c_i64p, c_i32p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_i64p, c_i8p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -262,6 +265,35 @@ def run_points(S, F, points, seed: int, U: int, collapse=None, n_fit=None, max_i
         raise np.linalg.LinAlgError("covariance not SPD")
     if want_fake:
         return dchi2, best, ns, fk
+    return dchi2, best, ns
+
+
+def run_samples(S, F, points, universes, seed: int, collapse=None, n_fit=None, max_iter: int = 5,
+                fluct: int = FLUCT_POISSON_SYS, cov: int = COV_ITERATE, nthreads: int | None = None):
+    """dchi2, bestfit, nscans of sampled universes: entry i is universe universes[i] of true point points[i]."""
+    S = _c(S, np.float64)
+    F = _c(F, np.float64)
+    G, nf = S.shape
+    nfit = nf if n_fit is None else int(n_fit)
+    pts = _c(points, np.int64)
+    us = _c(universes, np.int32)
+    n = len(pts)
+    if len(us) != n:
+        raise ValueError("points and universes differ in length")
+    coll = None if collapse is None else _c(collapse, np.int32)
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    dchi2 = np.zeros(n)
+    best = np.zeros(n, np.int64)
+    ns = np.zeros(n, np.int8)
+    rc = _load().oracle_run_samples(_ptr(S, ctypes.c_double), G, nf, _ptr(coll, ctypes.c_int32), nfit,
+                                    _ptr(F, ctypes.c_double), _ptr(pts, ctypes.c_int64), _ptr(us, ctypes.c_int32), n,
+                                    seed, max_iter, fluct, cov, nthreads, _ptr(dchi2, ctypes.c_double),
+                                    _ptr(best, ctypes.c_int64), _ptr(ns, ctypes.c_int8))
+    if rc == -1:
+        raise ValueError("bad argument")
+    if rc != 0:
+        raise np.linalg.LinAlgError("covariance not SPD")
     return dchi2, best, ns
 
 

@@ -521,6 +521,7 @@ typedef struct {
     int64_t G;
     int nf, nfit;
     const int64_t* ps;
+    const int32_t* us;     /* sample mode: universe of sample i (ps[i] its point), else NULL */
     int P, U;
     uint64_t seed;
     int max_iter, fluct, cov;
@@ -591,10 +592,11 @@ static void* orc_worker(void* arg) {
     double* d = (double*)malloc(sizeof(double) * (size_t)nfit);
     float* z = (float*)malloc(sizeof(float) * (size_t)(nf + 4));
     float* dfitf = (float*)malloc(sizeof(float) * (size_t)nfit);
-    const int64_t total = (int64_t)jb->P * jb->U;
+    const int64_t total = jb->us ? (int64_t)jb->P : (int64_t)jb->P * jb->U;
     for (int64_t w = jb->tid; w < total && jb->status == 0; w += jb->nthreads) {
-        const int ip = (int)(w / jb->U), u = (int)(w % jb->U);
-        const size_t o = (size_t)ip * jb->U + u;
+        const int ip = jb->us ? (int)w : (int)(w / jb->U);
+        const int u = jb->us ? jb->us[w] : (int)(w % jb->U);
+        const size_t o = jb->us ? (size_t)w : (size_t)ip * jb->U + u;
         double dr = NAN;
         int64_t br = -1;
         int8_t nr = 0;
@@ -638,12 +640,36 @@ int oracle_fake_data(const double* S, int64_t G, int nf, const int32_t* collapse
     return rc;
 }
 
+static int orc_run(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
+                   const int64_t* ps, const int32_t* us, int P, uint64_t seed, int U, int max_iter, int fluct, int cov,
+                   int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans, float* dfit_out);
+
 /* Full FC pass: for every true point ps[ip] and universe u, the dchi2 of
  * Algorithm 1 with the covariance refit of §2.  Threaded over universes.
  * Returns 0, -1 (bad argument) or -2 (covariance not SPD). */
 int oracle_run_points(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
                       const int64_t* ps, int P, uint64_t seed, int U, int max_iter, int fluct, int cov,
                       int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans, float* dfit_out) {
+    return orc_run(S, G, nf, collapse, nfit, F, ps, NULL, P, seed, U, max_iter, fluct, cov, nthreads, dchi2, bestfit,
+                   nscans, dfit_out);
+}
+
+/* The same procedure for n sampled universes: sample i is universe us[i] of
+ * true point ps[i] (each universe's random numbers depend only on (seed,
+ * point, universe), so a sample equals that entry of a full pass). */
+int oracle_run_samples(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
+                       const int64_t* ps, const int32_t* us, int n, uint64_t seed, int max_iter, int fluct, int cov,
+                       int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans) {
+    if (!us) return -1;
+    for (int i = 0; i < n; ++i)
+        if (us[i] < 0) return -1;
+    return orc_run(S, G, nf, collapse, nfit, F, ps, us, n, seed, 1, max_iter, fluct, cov, nthreads, dchi2, bestfit,
+                   nscans, NULL);
+}
+
+static int orc_run(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
+                   const int64_t* ps, const int32_t* us, int P, uint64_t seed, int U, int max_iter, int fluct, int cov,
+                   int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans, float* dfit_out) {
     if (G <= 0 || nf <= 0 || nfit <= 0 || P < 0 || U < 0 || max_iter < 1) return -1;
     for (int ip = 0; ip < P; ++ip)
         if (ps[ip] < 0 || ps[ip] >= G) return -1;
@@ -659,7 +685,7 @@ int oracle_run_points(const double* S, int64_t G, int nf, const int32_t* collaps
         for (int t = 0; t < nthreads; ++t) {
             orc_job* jb = &jobs[t];
             jb->S = S; jb->Sfit = Sfit; jb->F = F; jb->collapse = collapse; jb->G = G;
-            jb->nf = nf; jb->nfit = nfit; jb->ps = ps; jb->P = P; jb->U = U; jb->seed = seed;
+            jb->nf = nf; jb->nfit = nfit; jb->ps = ps; jb->us = us; jb->P = P; jb->U = U; jb->seed = seed;
             jb->max_iter = max_iter; jb->fluct = fluct; jb->cov = cov; jb->Lf = Lf; jb->sf = sf;
             jb->dchi2 = dchi2; jb->bestfit = bestfit; jb->nscans = nscans; jb->dfit_out = dfit_out;
             jb->nthreads = nthreads; jb->tid = t; jb->status = 0;

@@ -197,3 +197,17 @@ def test_wilks_linear_gaussian():
     gap = chi2_grid - chi2_cont
     assert np.all(gap[inside] >= -1e-9)
     assert np.all(gap[inside] <= bound + 1e-9)
+
+
+def test_samples_equal_full_pass_entries():
+    """A sampled universe is the same computation as that entry of a full pass."""
+    w = workloads.tiny(n_a=4, n_b=4, n_full=6, U=12, collapse=True)
+    pts = np.array([0, 5, 9, 15], np.int64)
+    d, b, n = oracle.run_points(w.S, w.F, pts, 3, 12, collapse=w.collapse, n_fit=w.n_fit)
+    rng = np.random.default_rng(1)
+    ip = rng.integers(0, len(pts), 20)
+    u = rng.integers(0, 12, 20).astype(np.int32)
+    ds, bs, ns = oracle.run_samples(w.S, w.F, pts[ip], u, 3, collapse=w.collapse, n_fit=w.n_fit)
+    np.testing.assert_array_equal(ds, d[ip, u])
+    np.testing.assert_array_equal(bs, b[ip, u])
+    np.testing.assert_array_equal(ns, n[ip, u])
