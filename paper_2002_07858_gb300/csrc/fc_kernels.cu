@@ -1467,7 +1467,14 @@ void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr,
 
 void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, cudaStream_t st) {
     if (n_tiles <= 0) return;
-    const size_t smem = a.nfit <= kResolveMaxN ? (size_t)a.nfit * a.nfit * sizeof(double) : 0;
+    const size_t smem = a.nfit <= kResolveMaxN ? (size_t)a.nfit * a.nfit * sizeof(float2) : 0;
+    // static per-warp vectors plus a staged W exceed the 48 KB default
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_resolve_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kResolveMaxN * kResolveMaxN * (int)sizeof(float2));
+        attr = true;
+    }
     count_launch();
     k_resolve_list<<<(unsigned)n_tiles, 256, smem, st>>>(a, cand_count);
 }

@@ -59,6 +59,13 @@ def w70():
 
 
 @pytest.fixture(scope="module")
+def w64():
+    # N=64: the largest N_fit whose W is staged in shared memory by the binary64-accuracy kernels (K=80)
+    S, F, axes = workloads.osc_2d(24, 24, 64, seed=8)
+    return workloads.Workload("osc24x24_n64", S, F, None, 64, np.array([50, 300, 571], np.int64), 150, 5, 6, axes)
+
+
+@pytest.fixture(scope="module")
 def w150():
     # D=2 grid with N=150 (K=160: q-vectors stream S~ in K slices beside a resident W)
     S, F, axes = workloads.osc_2d(20, 20, 150, seed=6)
@@ -75,7 +82,7 @@ def _compare_mixed(d, b, od, ob, tol=TOL_MIXED, max_mism=0.02):
     assert np.all(np.abs(qg - qo) <= 1e-3 * np.maximum(np.abs(qo), 1e-3))
 
 
-@pytest.mark.parametrize("which", ["w3s", "w70", "w150"])
+@pytest.mark.parametrize("which", ["w3s", "w64", "w70", "w150"])
 def test_large_n_mixed_vs_oracle(fc, ctx, which, request):
     w = request.getfixturevalue(which)
     gid = _load(fc, ctx, w)
