@@ -43,6 +43,20 @@ using namespace tc;
 // kind::f16 instruction descriptor of the screen: D f32, A/B bf16, both K-major, M = BM, N = BN
 constexpr uint32_t kIdesc = idesc_bf16(kBM, kBN);
 
+// Minimum of 32 accumulator values as a depth-5 tree (fminf is exact, so the
+// result does not depend on the order; the tree keeps the dependency chain
+// short for the epilogue warps).
+__device__ __forceinline__ float min32(const uint32_t (&r)[32]) {
+    float m[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) m[i] = fminf(__uint_as_float(r[i]), __uint_as_float(r[i + 16]));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m[i] = fminf(m[i], m[i + 8]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) m[i] = fminf(m[i], m[i + 4]);
+    return fminf(fminf(m[0], m[2]), fminf(m[1], m[3]));
+}
+
 // (value, index) insertion into a sorted list, lexicographic order
 template <int TOPK>
 __device__ __forceinline__ void topk_insert(float (&vals)[TOPK], int32_t (&idx)[TOPK], float x, int32_t g) {
@@ -67,10 +81,7 @@ __device__ __forceinline__ void topk_insert(float (&vals)[TOPK], int32_t (&idx)[
 // inserted in a rolled loop (small code for the instruction cache).
 template <int TOPK>
 __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[TOPK], const uint32_t (&r)[32],
-                                           int64_t g0, int64_t G, float* scratch, int lane) {
-    float m = __uint_as_float(r[0]);
-#pragma unroll
-    for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
+                                           float m, int64_t g0, int64_t G, float* scratch, int lane) {
     if (m <= vals[TOPK - 1]) {
         const float tau = vals[TOPK - 1];
         uint32_t mask = 0;
@@ -112,10 +123,7 @@ constexpr int kModeList = 2;
 
 // List mode: append every value at or below the seed (and its grid index).
 __device__ __forceinline__ void list_chunk(int32_t& n, int32_t cap, float* __restrict__ lval, int32_t* __restrict__ lidx,
-                                           float seed, const uint32_t (&r)[32], int64_t g0, int64_t G) {
-    float m = __uint_as_float(r[0]);
-#pragma unroll
-    for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
+                                           float seed, const uint32_t (&r)[32], float m, int64_t g0, int64_t G) {
     if (m <= seed) {
         uint32_t mask = 0;
 #pragma unroll
@@ -136,10 +144,8 @@ __device__ __forceinline__ void list_chunk(int32_t& n, int32_t cap, float* __res
 
 // First pass: running minimum of a row.  The index is recovered only when the
 // chunk improves the minimum (rare after the first tiles).
-__device__ __forceinline__ void min_chunk(float& bv, int32_t& bi, const uint32_t (&r)[32], int64_t g0, int64_t G) {
-    float m = __uint_as_float(r[0]);
-#pragma unroll
-    for (int i = 1; i < 32; ++i) m = fminf(m, __uint_as_float(r[i]));
+__device__ __forceinline__ void min_chunk(float& bv, int32_t& bi, const uint32_t (&r)[32], float m, int64_t g0,
+                                          int64_t G) {
     if (m < bv) {
         int ii = 31;
 #pragma unroll
@@ -358,18 +364,26 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                         const uint32_t qs = lay.off_b + s * lay.stage_bytes + lay.bpart_bytes;
                         mma_bf16(d, a_q, smem_desc(sbase + qs, lay.off_zero - qs, 128), kIdesc, 0u);
                     }
+                    // descriptors of the first K step; a step of 16 columns moves the start address by
+                    // two slabs, i.e. adds (2 slab bytes) >> 4 to the descriptor's address field
                     const int k_lo = KCHUNK ? c : 0, k_hi = KCHUNK ? c + 1 : K / 16;
+                    uint64_t a_hi = smem_desc(a0 + (2 * k_lo) * kAChunk, kAChunk, 128);
+                    uint64_t a_lo = smem_desc(a0 + (K / 8 + 2 * k_lo) * kAChunk, kAChunk, 128);
+                    uint64_t b_hi = smem_desc(KCHUNK ? b0 : b0 + (2 * k_lo) * kBChunk, kBChunk, 128);
+                    uint64_t b_lo = smem_desc(KCHUNK ? b0 + 2 * kBChunk : b0 + (K / 8 + 2 * k_lo) * kBChunk,
+                                              kBChunk, 128);
+                    constexpr uint64_t kAStep = (2 * kAChunk) >> 4, kBStep = (2 * kBChunk) >> 4;
+#pragma unroll 4
                     for (int kk = k_lo; kk < k_hi; ++kk) {
-                        const uint64_t a_hi = smem_desc(a0 + (2 * kk) * kAChunk, kAChunk, 128);
-                        const uint64_t a_lo = smem_desc(a0 + (K / 8 + 2 * kk) * kAChunk, kAChunk, 128);
-                        const uint32_t bh = KCHUNK ? b0 : b0 + (2 * kk) * kBChunk;
-                        const uint32_t bl = KCHUNK ? b0 + 2 * kBChunk : b0 + (K / 8 + 2 * kk) * kBChunk;
-                        const uint64_t b_hi = smem_desc(bh, kBChunk, 128);
                         mma_bf16(d, a_hi, b_hi, kIdesc, 1u);
                         if (kLo) {
                             mma_bf16(d, a_lo, b_hi, kIdesc, 1u);
-                            mma_bf16(d, a_hi, smem_desc(bl, kBChunk, 128), kIdesc, 1u);
+                            mma_bf16(d, a_hi, b_lo, kIdesc, 1u);
                         }
+                        a_hi += kAStep;
+                        a_lo += kAStep;
+                        b_hi += kBStep;
+                        b_lo += kBStep;
                     }
                     mma_commit(bar(B_EMPTY + s));
                     if (++s == STAGES) { s = 0; ph ^= 1u; }
@@ -437,13 +451,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 const uint32_t tb = tmem_base + lane_base + (uint32_t)(ab * kBN + half * kHalfCols);
                 const int64_t g0 = (int64_t)j * kBN + half * kHalfCols;
                 uint32_t r0[32], r1[32], r2[32], r3[32];
-                auto chunk = [&](const uint32_t(&r)[32], int64_t gc) {
+                auto chunk = [&](const uint32_t(&r)[32], float m, int64_t gc) {
                     if (MODE == kModeMin)
-                        min_chunk(bv, bi, r, gc, G);
+                        min_chunk(bv, bi, r, m, gc, G);
                     else if (MODE == kModeList)
-                        list_chunk(nlist, lcap, cand_val + lbase, cand_idx + lbase, seed, r, gc, G);
+                        list_chunk(nlist, lcap, cand_val + lbase, cand_idx + lbase, seed, r, m, gc, G);
                     else
-                        topk_chunk<TOPK>(vals, idx, r, gc, G, scratch, lane);
+                        topk_chunk<TOPK>(vals, idx, r, m, gc, G, scratch, lane);
                 };
                 // the warp's 128 columns go to registers at once, so the accumulator is
                 // handed back to the MMA after one load latency, before any filtering
@@ -458,13 +472,15 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar(T_EMPTY + ab));
-                chunk(r0, g0 + 0);
+                // the four chunk minima first (independent trees), then the rare slow paths
+                const float m0 = min32(r0), m1 = min32(r1), m2 = min32(r2), m3 = min32(r3);
+                chunk(r0, m0, g0 + 0);
                 __syncwarp();
-                chunk(r1, g0 + 32);
+                chunk(r1, m1, g0 + 32);
                 __syncwarp();
-                chunk(r2, g0 + 64);
+                chunk(r2, m2, g0 + 64);
                 __syncwarp();
-                chunk(r3, g0 + 96);
+                chunk(r3, m3, g0 + 96);
                 __syncwarp();
             }
             if (MODE == kModeList) {
