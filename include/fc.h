@@ -191,6 +191,25 @@ FC_API fc_status fc_scan(fc_ctx* ctx, int32_t grid_id, const float* d, const int
 FC_API fc_status fc_quantiles(fc_ctx* ctx, const double* x, int32_t rows, int32_t n, const double* probs,
                        int32_t nq, double* out);
 
+/* The observed data's dchi2 at grid points ps (the statistic the critical
+ * values are for, §1 and Fig. 1): the per-universe procedure of §2 run on the
+ * given fit-space data vector d [N_fit] (float32, host or device) in place of
+ * fake data -- first covariance at ps[i], refit at the best fit until it
+ * repeats, dchi2 = chi2_p - chi2_min under the last scan's A -- so that
+ * dchi2[i] is comparable with the distribution of ps[i]'s universes.
+ * Outputs [P]: dchi2 (required), bestfit, nscans (nullable).  opts.fluct is
+ * not used.  Errors as fc_run_points. */
+FC_API fc_status fc_data_dchi2(fc_ctx* ctx, int32_t grid_id, const float* d, const int64_t* ps, int32_t P,
+                               const fc_opts* opts, double* dchi2, int64_t* bestfit, int8_t* nscans);
+
+/* Feldman-Cousins acceptance (the use of the distributions, §1 / Fig. 1):
+ * crit[i] = the cl-quantile (numpy "linear" rule) of dchi2_univ[i][0..U-1]
+ * (point i's universes, float64 [P][U]) and accepted[i] = 1 when
+ * dchi2_data[i] <= crit[i], else 0.  All arrays host or device; crit may be
+ * NULL.  Errors: FC_ERR_ARG (cl outside [0, 1], U < 1, U > 16384), FC_ERR_CUDA. */
+FC_API fc_status fc_fc_region(fc_ctx* ctx, const double* dchi2_univ, int32_t P, int32_t U, const double* dchi2_data,
+                              double cl, double* crit, uint8_t* accepted);
+
 /* Asynchronous serving (continuous batching).  A job = fc_run_points'
  * arguments; output pointers must stay valid until fc_poll returns a final
  * status.  fc_submit admits the job when the context's memory budget allows

@@ -84,6 +84,9 @@ def _load():
             "oracle_run_samples": (ctypes.c_int, [c_dp, ctypes.c_int64, ctypes.c_int, c_i32p, ctypes.c_int, c_dp,
                                                   c_i64p, c_i32p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, c_dp, c_i64p, c_i8p]),
+            "oracle_run_data": (ctypes.c_int, [c_dp, ctypes.c_int64, ctypes.c_int, c_i32p, ctypes.c_int, c_dp,
+                                               c_i64p, ctypes.c_int, c_fp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               c_dp, c_i64p, c_i8p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -290,6 +293,35 @@ def run_samples(S, F, points, universes, seed: int, collapse=None, n_fit=None, m
                                     _ptr(F, ctypes.c_double), _ptr(pts, ctypes.c_int64), _ptr(us, ctypes.c_int32), n,
                                     seed, max_iter, fluct, cov, nthreads, _ptr(dchi2, ctypes.c_double),
                                     _ptr(best, ctypes.c_int64), _ptr(ns, ctypes.c_int8))
+    if rc == -1:
+        raise ValueError("bad argument")
+    if rc != 0:
+        raise np.linalg.LinAlgError("covariance not SPD")
+    return dchi2, best, ns
+
+
+def run_data(S, F, points, data, collapse=None, n_fit=None, max_iter: int = 5, cov: int = COV_ITERATE,
+             nthreads: int | None = None):
+    """The observed data's dchi2, bestfit, nscans at each grid point (the universe procedure on given data)."""
+    S = _c(S, np.float64)
+    F = _c(F, np.float64)
+    G, nf = S.shape
+    nfit = nf if n_fit is None else int(n_fit)
+    pts = _c(points, np.int64)
+    dv = _c(data, np.float32)
+    if dv.shape != (nfit,):
+        raise ValueError("data must have N_fit entries")
+    coll = None if collapse is None else _c(collapse, np.int32)
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    n = len(pts)
+    dchi2 = np.zeros(n)
+    best = np.zeros(n, np.int64)
+    ns = np.zeros(n, np.int8)
+    rc = _load().oracle_run_data(_ptr(S, ctypes.c_double), G, nf, _ptr(coll, ctypes.c_int32), nfit,
+                                 _ptr(F, ctypes.c_double), _ptr(pts, ctypes.c_int64), n, _ptr(dv, ctypes.c_float),
+                                 max_iter, cov, nthreads, _ptr(dchi2, ctypes.c_double), _ptr(best, ctypes.c_int64),
+                                 _ptr(ns, ctypes.c_int8))
     if rc == -1:
         raise ValueError("bad argument")
     if rc != 0:

@@ -522,6 +522,7 @@ typedef struct {
     int nf, nfit;
     const int64_t* ps;
     const int32_t* us;     /* sample mode: universe of sample i (ps[i] its point), else NULL */
+    const float* data;     /* given-data mode: every fit uses this [nfit] vector instead of fake data */
     int P, U;
     uint64_t seed;
     int max_iter, fluct, cov;
@@ -539,8 +540,11 @@ static void orc_fit_universe(orc_job* jb, int ip, int u, double* A, double* M, d
                              double* r, double* d, float* z, float* dfitf, double* dres, int64_t* bres, int8_t* nres) {
     const int nf = jb->nf, nfit = jb->nfit;
     const int64_t p = jb->ps[ip];
-    orc_fake_one(nf, nfit, jb->collapse, jb->sf + (size_t)ip * nf, jb->Lf + (size_t)ip * nf * nf, jb->seed,
-                 (uint32_t)p, (uint32_t)u, jb->fluct, z, dfitf);
+    if (jb->data)
+        memcpy(dfitf, jb->data, sizeof(float) * nfit);
+    else
+        orc_fake_one(nf, nfit, jb->collapse, jb->sf + (size_t)ip * nf, jb->Lf + (size_t)ip * nf * nf, jb->seed,
+                     (uint32_t)p, (uint32_t)u, jb->fluct, z, dfitf);
     if (jb->dfit_out) memcpy(jb->dfit_out + ((size_t)ip * jb->U + u) * nfit, dfitf, sizeof(float) * nfit);
     for (int j = 0; j < nfit; ++j) d[j] = (double)dfitf[j];
     int64_t q = p;
@@ -641,8 +645,9 @@ int oracle_fake_data(const double* S, int64_t G, int nf, const int32_t* collapse
 }
 
 static int orc_run(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
-                   const int64_t* ps, const int32_t* us, int P, uint64_t seed, int U, int max_iter, int fluct, int cov,
-                   int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans, float* dfit_out);
+                   const int64_t* ps, const int32_t* us, const float* data, int P, uint64_t seed, int U, int max_iter,
+                   int fluct, int cov, int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans,
+                   float* dfit_out);
 
 /* Full FC pass: for every true point ps[ip] and universe u, the dchi2 of
  * Algorithm 1 with the covariance refit of §2.  Threaded over universes.
@@ -650,8 +655,8 @@ static int orc_run(const double* S, int64_t G, int nf, const int32_t* collapse, 
 int oracle_run_points(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
                       const int64_t* ps, int P, uint64_t seed, int U, int max_iter, int fluct, int cov,
                       int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans, float* dfit_out) {
-    return orc_run(S, G, nf, collapse, nfit, F, ps, NULL, P, seed, U, max_iter, fluct, cov, nthreads, dchi2, bestfit,
-                   nscans, dfit_out);
+    return orc_run(S, G, nf, collapse, nfit, F, ps, NULL, NULL, P, seed, U, max_iter, fluct, cov, nthreads, dchi2,
+                   bestfit, nscans, dfit_out);
 }
 
 /* The same procedure for n sampled universes: sample i is universe us[i] of
@@ -663,13 +668,27 @@ int oracle_run_samples(const double* S, int64_t G, int nf, const int32_t* collap
     if (!us) return -1;
     for (int i = 0; i < n; ++i)
         if (us[i] < 0) return -1;
-    return orc_run(S, G, nf, collapse, nfit, F, ps, us, n, seed, 1, max_iter, fluct, cov, nthreads, dchi2, bestfit,
-                   nscans, NULL);
+    return orc_run(S, G, nf, collapse, nfit, F, ps, us, NULL, n, seed, 1, max_iter, fluct, cov, nthreads, dchi2,
+                   bestfit, nscans, NULL);
+}
+
+/* The observed data's dchi2 at each grid point ps[i]: the per-universe
+ * procedure of §2 with the given fit-space data vector in place of fake data
+ * (first covariance at ps[i], refit, dchi2 under the last scan's A), so it is
+ * comparable with the distribution of ps[i]'s universes (Fig. 1 critical
+ * values). */
+int oracle_run_data(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
+                    const int64_t* ps, int n, const float* data, int max_iter, int cov, int nthreads, double* dchi2,
+                    int64_t* bestfit, int8_t* nscans) {
+    if (!data) return -1;
+    return orc_run(S, G, nf, collapse, nfit, F, ps, NULL, data, n, 0, 1, max_iter, ORC_FLUCT_POISSON_SYS, cov,
+                   nthreads, dchi2, bestfit, nscans, NULL);
 }
 
 static int orc_run(const double* S, int64_t G, int nf, const int32_t* collapse, int nfit, const double* F,
-                   const int64_t* ps, const int32_t* us, int P, uint64_t seed, int U, int max_iter, int fluct, int cov,
-                   int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans, float* dfit_out) {
+                   const int64_t* ps, const int32_t* us, const float* data, int P, uint64_t seed, int U, int max_iter,
+                   int fluct, int cov, int nthreads, double* dchi2, int64_t* bestfit, int8_t* nscans,
+                   float* dfit_out) {
     if (G <= 0 || nf <= 0 || nfit <= 0 || P < 0 || U < 0 || max_iter < 1) return -1;
     for (int ip = 0; ip < P; ++ip)
         if (ps[ip] < 0 || ps[ip] >= G) return -1;
@@ -685,7 +704,8 @@ static int orc_run(const double* S, int64_t G, int nf, const int32_t* collapse, 
         for (int t = 0; t < nthreads; ++t) {
             orc_job* jb = &jobs[t];
             jb->S = S; jb->Sfit = Sfit; jb->F = F; jb->collapse = collapse; jb->G = G;
-            jb->nf = nf; jb->nfit = nfit; jb->ps = ps; jb->us = us; jb->P = P; jb->U = U; jb->seed = seed;
+            jb->nf = nf; jb->nfit = nfit; jb->ps = ps; jb->us = us; jb->data = data; jb->P = P; jb->U = U;
+            jb->seed = seed;
             jb->max_iter = max_iter; jb->fluct = fluct; jb->cov = cov; jb->Lf = Lf; jb->sf = sf;
             jb->dchi2 = dchi2; jb->bestfit = bestfit; jb->nscans = nscans; jb->dfit_out = dfit_out;
             jb->nthreads = nthreads; jb->tid = t; jb->status = 0;

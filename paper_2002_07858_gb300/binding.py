@@ -30,7 +30,7 @@ _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_
 EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set_frac_cov", "fc_unload_grid",
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
            "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
-           "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats"]
+           "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats", "fc_data_dchi2", "fc_fc_region"]
 
 
 class FCError(RuntimeError):
@@ -110,6 +110,8 @@ def load(build: bool = False):
         "fc_cancel": (st, [vp, u64]),
         "fc_get_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
         "fc_get_serve_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
+        "fc_data_dchi2": (st, [vp, i32, vp, vp, i32, ctypes.POINTER(fc_opts), vp, vp, vp]),
+        "fc_fc_region": (st, [vp, vp, i32, i32, vp, ctypes.c_double, vp, vp]),
         "fc_set_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
         "fc_get_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
         "fc_autotune": (st, [vp, i32, ctypes.c_char_p, ctypes.POINTER(fc_tuning)]),
@@ -251,6 +253,31 @@ def fc_scan(ctx, grid_id: int, d, q_cov, precision: int = FC_PREC_MIXED, top_k: 
     chi2 = np.empty(U, np.float64)
     _check(load().fc_scan(ctx, grid_id, _ptr(d), _ptr(q), U, precision, top_k, _ptr(best), _ptr(chi2)), ctx)
     return best, chi2
+
+
+def fc_data_dchi2(ctx, grid_id: int, d, ps, opts=None):
+    """Observed data's (dchi2, bestfit, nscans) at each grid point of ps."""
+    d = _host(d, np.float32)
+    ps = _host(ps, np.int64)
+    P = int(ps.shape[0])
+    o = _opts(opts)
+    dchi2 = np.empty(P, np.float64)
+    best = np.empty(P, np.int64)
+    ns = np.empty(P, np.int8)
+    _check(load().fc_data_dchi2(ctx, grid_id, _ptr(d), _ptr(ps), P, ctypes.byref(o), _ptr(dchi2), _ptr(best),
+                                _ptr(ns)), ctx)
+    return dchi2, best, ns
+
+
+def fc_fc_region(ctx, dchi2_univ, dchi2_data, cl: float):
+    """(crit [P], accepted [P] uint8): cl-quantile of each point's universes and dchi2_data <= crit."""
+    x = _host(dchi2_univ, np.float64)
+    dd = _host(dchi2_data, np.float64)
+    P, U = int(x.shape[0]), int(x.shape[1])
+    crit = np.empty(P, np.float64)
+    acc = np.empty(P, np.uint8)
+    _check(load().fc_fc_region(ctx, _ptr(x), P, U, _ptr(dd), float(cl), _ptr(crit), _ptr(acc)), ctx)
+    return crit, acc
 
 
 def fc_quantiles(ctx, x, probs):

@@ -279,6 +279,17 @@ fc_status copy_out(fc_ctx* c, void* dst, const void* src, size_t bytes) {
     return FC_OK;
 }
 
+// host data to a caller buffer that may be host or device memory
+fc_status put_out(fc_ctx* c, void* dst, const void* host_src, size_t bytes) {
+    if (is_device_ptr(dst)) {
+        FC_CUDA(cudaMemcpyAsync(dst, host_src, bytes, cudaMemcpyHostToDevice, c->stream));
+        FC_CUDA(cudaStreamSynchronize(c->stream));
+    } else {
+        memcpy(dst, host_src, bytes);
+    }
+    return FC_OK;
+}
+
 fc_status sync(fc_ctx* c) {
     FC_CUDA(cudaStreamSynchronize(c->stream));
     FC_CUDA(cudaGetLastError());
@@ -1863,6 +1874,69 @@ fc_status fc_scan(fc_ctx* c, int32_t grid_id, const float* d, const int64_t* q_c
     // every universe is its own point: its true point and first covariance are q_cov[u]
     FC_TRY(run_sync(c, g, o, hq, 1, 0, d, nullptr, best, nullptr, chi2_min, nullptr));
     return sync(c);
+}
+
+fc_status fc_data_dchi2(fc_ctx* c, int32_t grid_id, const float* d, const int64_t* ps, int32_t P,
+                        const fc_opts* opts, double* dchi2, int64_t* bestfit, int8_t* nscans) {
+    if (!c || !d || (P > 0 && (!ps || !dchi2))) return fail(FC_ERR_ARG, "NULL argument");
+    if (P < 0) return fail(FC_ERR_ARG, "P < 0");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
+    fc_opts o;
+    fc_default_opts(&o);
+    if (opts) o = *opts;
+    FC_TRY(validate_opts(&o, g));
+    if (P == 0) return FC_OK;
+    std::vector<int64_t> hps;
+    FC_TRY(check_points(g, ps, P, &hps));
+    std::vector<float> hd(g->nfit);
+    if (is_device_ptr(d)) {
+        FC_CUDA(cudaMemcpy(hd.data(), d, (size_t)g->nfit * 4, cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(hd.data(), d, (size_t)g->nfit * 4);
+    }
+    for (float v : hd)
+        if (!std::isfinite(v)) return fail(FC_ERR_ARG, "data must be finite");
+    // every point is one universe whose data is the observed vector
+    std::vector<float> rep((size_t)P * g->nfit);
+    for (int32_t i = 0; i < P; ++i) memcpy(rep.data() + (size_t)i * g->nfit, hd.data(), (size_t)g->nfit * 4);
+    c->stats = fc_stats{};
+    c->acc = &c->stats;
+    FC_TRY(run_sync(c, g, o, hps, 1, 0, rep.data(), dchi2, bestfit, nscans, nullptr, nullptr));
+    return sync(c);
+}
+
+fc_status fc_fc_region(fc_ctx* c, const double* dchi2_univ, int32_t P, int32_t U, const double* dchi2_data,
+                       double cl, double* crit, uint8_t* accepted) {
+    if (!c || (P > 0 && (!dchi2_univ || !dchi2_data || !accepted))) return fail(FC_ERR_ARG, "NULL argument");
+    if (P < 0 || U < 1 || U > 16384) return fail(FC_ERR_ARG, "bad sizes (1 <= U <= 16384)");
+    if (!(cl >= 0.0 && cl <= 1.0)) return fail(FC_ERR_ARG, "cl must be in [0, 1]");
+    if (P == 0) return FC_OK;
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    double *dx = nullptr, *dp = nullptr, *dout = nullptr;
+    FC_TRY(scratch(c, "qx", (size_t)P * U, &dx));
+    FC_TRY(scratch(c, "qp", 1, &dp));
+    FC_TRY(scratch(c, "qout", (size_t)P, &dout));
+    FC_TRY(copy_in(c, dx, dchi2_univ, (size_t)P * U * 8));
+    FC_CUDA(cudaMemcpyAsync(dp, &cl, 8, cudaMemcpyHostToDevice, c->stream));
+    launch_quantiles(dx, P, U, dp, 1, dout, c->stream);
+    std::vector<double> hc(P), hd(P);
+    FC_CUDA(cudaMemcpyAsync(hc.data(), dout, (size_t)P * 8, cudaMemcpyDeviceToHost, c->stream));
+    FC_TRY(sync(c));
+    if (is_device_ptr(dchi2_data)) {
+        FC_CUDA(cudaMemcpy(hd.data(), dchi2_data, (size_t)P * 8, cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(hd.data(), dchi2_data, (size_t)P * 8);
+    }
+    std::vector<uint8_t> acc(P);
+    for (int32_t i = 0; i < P; ++i) acc[i] = (hd[i] <= hc[i]) ? 1 : 0;
+    if (crit) FC_TRY(put_out(c, crit, hc.data(), (size_t)P * 8));
+    FC_TRY(put_out(c, accepted, acc.data(), (size_t)P));
+    return FC_OK;
 }
 
 fc_status fc_quantiles(fc_ctx* c, const double* x, int32_t rows, int32_t n, const double* probs, int32_t nq,

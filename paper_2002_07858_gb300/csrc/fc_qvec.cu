@@ -248,16 +248,21 @@ __global__ void __launch_bounds__(64 + 128, 1)
                 tc_fence_after();
                 const uint32_t a0 = sbase + lay.off_s + s * lay.s_bytes;
                 const int k_lo = lay.sliced ? c : 0, k_hi = lay.sliced ? c + 1 : K / 16;
+                // first K step's descriptors, advanced by adding the slab offset to the address field
+                uint64_t a_hi = smem_desc(lay.sliced ? a0 : a0 + (2 * k_lo) * kQSlab, kQSlab, 128);
+                uint64_t a_lo = smem_desc(lay.sliced ? a0 + 2 * kQSlab : a0 + (K / 8 + 2 * k_lo) * kQSlab, kQSlab, 128);
+                uint64_t b_hi = smem_desc(sbase + (2 * k_lo) * (K * 16), K * 16, 128);
+                uint64_t b_lo = smem_desc(sbase + (K / 8 + 2 * k_lo) * (K * 16), K * 16, 128);
+                const uint64_t a_step = lay.sliced ? 0 : (2 * kQSlab) >> 4, b_step = (uint64_t)(2 * K * 16) >> 4;
+#pragma unroll 4
                 for (int kk = k_lo; kk < k_hi; ++kk) {
-                    const uint32_t ah = lay.sliced ? a0 : a0 + (2 * kk) * kQSlab;
-                    const uint32_t al = lay.sliced ? a0 + 2 * kQSlab : a0 + (K / 8 + 2 * kk) * kQSlab;
-                    const uint64_t a_hi = smem_desc(ah, kQSlab, 128);
-                    const uint64_t a_lo = smem_desc(al, kQSlab, 128);
-                    const uint64_t b_hi = smem_desc(sbase + (2 * kk) * (K * 16), K * 16, 128);
-                    const uint64_t b_lo = smem_desc(sbase + (K / 8 + 2 * kk) * (K * 16), K * 16, 128);
                     mma_bf16(d, a_hi, b_hi, idesc, kk > 0 ? 1u : 0u);
                     mma_bf16(d, a_lo, b_hi, idesc, 1u);
                     mma_bf16(d, a_hi, b_lo, idesc, 1u);
+                    a_hi += a_step;
+                    a_lo += a_step;
+                    b_hi += b_step;
+                    b_lo += b_step;
                 }
                 mma_commit(bar(S_EMPTY + s));
                 if (++s == STAGES) { s = 0; ph ^= 1u; }

@@ -271,3 +271,32 @@ def test_serving_matches_synchronous(fc, ctx, w1, w2):
         pending = keep
         time.sleep(0.01)
     assert not pending
+
+
+# ------------------------------------------------ FC region (critical values) --
+
+def test_data_dchi2_and_region(fc, ctx, w1, w2):
+    """The observed data's dchi2 at every grid point against the oracle, and the
+    accepted region at 68/90 % CL from the points' own universes."""
+    g2 = grid(fc, ctx, w2)
+    # an "observed" spectrum: one fluctuation of a true point (its fake data)
+    obs = oracle.fake_data(w2.S, w2.F, [5555], 3, 1, collapse=w2.collapse, n_fit=w2.n_fit)[0, 0]
+    pts = _cfg2_points(w2, 40)
+    for prec, tol in ((fc.FC_PREC_FP64, 1e-9), (fc.FC_PREC_MIXED, TOL_MIXED)):
+        d, b, n = fc.fc_data_dchi2(ctx, g2, obs, pts, opts=dict(precision=prec))
+        od, ob, on = oracle.run_data(w2.S, w2.F, pts, obs, collapse=w2.collapse, n_fit=w2.n_fit)
+        err = np.abs(d - od) / np.maximum(np.abs(od), 1.0)
+        assert err.max() <= tol, (prec, err.max())
+        assert (b == ob).mean() >= 0.95
+    # region: universes of each point, then the acceptance at two confidence levels
+    U = 400
+    du = fc.fc_run_points(ctx, g2, pts, 17, U)[0]
+    ddat = fc.fc_data_dchi2(ctx, g2, obs, pts)[0]
+    for cl in (0.68, 0.90):
+        crit, acc = fc.fc_fc_region(ctx, du, ddat, cl)
+        ref = np.quantile(du, cl, axis=1)
+        np.testing.assert_allclose(crit, ref, rtol=1e-12, atol=0)
+        np.testing.assert_array_equal(acc, (ddat <= ref).astype(np.uint8))
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_fc_region(ctx, du, ddat, 1.5)
+    assert e.value.status == fc.FC_ERR_ARG

@@ -211,3 +211,20 @@ def test_samples_equal_full_pass_entries():
     np.testing.assert_array_equal(ds, d[ip, u])
     np.testing.assert_array_equal(bs, b[ip, u])
     np.testing.assert_array_equal(ns, n[ip, u])
+
+
+def test_data_mode_is_the_universe_procedure():
+    """The observed-data statistic is the universe procedure on given data: with a
+    universe's own fake data it reproduces that universe, and data equal to a
+    grid spectrum gives dchi2 = 0 at that point."""
+    w = workloads.tiny(n_a=4, n_b=4, n_full=6, U=6, collapse=True)
+    pts = np.array([2, 7, 13], np.int64)
+    d, b, n, fk = oracle.run_points(w.S, w.F, pts, 9, 6, collapse=w.collapse, n_fit=w.n_fit, want_fake=True)
+    for ip in range(len(pts)):
+        for u in (0, 5):
+            dd, bb, nn = oracle.run_data(w.S, w.F, pts[ip:ip + 1], fk[ip, u], collapse=w.collapse, n_fit=w.n_fit)
+            assert dd[0] == d[ip, u] and bb[0] == b[ip, u] and nn[0] == n[ip, u]
+    sfit = oracle.collapse_spectra(w.S, w.collapse, w.n_fit)
+    dd, bb, _ = oracle.run_data(w.S, w.F, np.array([7]), sfit[7].astype(np.float32), collapse=w.collapse,
+                                n_fit=w.n_fit)
+    assert bb[0] == 7 and dd[0] == 0.0
