@@ -77,7 +77,7 @@ typedef struct {
 /* Kernel choices of one grid.  They change speed only: every choice gives
  * the same dchi2, best fits and scan counts (the screen's decisions are
  * certified and resolved in binary64).  fc_autotune picks them by timing. */
-enum { FC_QVEC_AUTO = 0,     /* tensor cores above N_fit ~ 61, binary32 SIMT below */
+enum { FC_QVEC_AUTO = 0,     /* tensor cores (the faster kernel at every N_fit)      */
        FC_QVEC_SIMT = 1,     /* q_g = s~^T A s~ in binary32, A in shared memory    */
        FC_QVEC_TC = 2 };     /* q_g = |W s~|^2 on tcgen05 (bf16 hi/lo), K <= 128  */
 
@@ -115,6 +115,8 @@ typedef struct {
     int64_t max_distinct_cov; /* most distinct covariance indices one scan needed     */
     int64_t scan_waves;       /* cache-sized groups run by scans that needed more     */
     int64_t big_listed;       /* universe-scans sent to the exact-size list round     */
+    int64_t screen_tiles;     /* 128-row universe tiles screened (all launches)       */
+    int64_t screen_rows;      /* universe rows in them (fill = rows / (128 tiles))    */
 } fc_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -52,7 +52,8 @@ class fc_stats(ctypes.Structure):
         (n, ctypes.c_double) for n in ("ms_fake", "ms_cov", "ms_prep", "ms_screen", "ms_rescore", "ms_fallback",
                                        "ms_scan64", "ms_finish", "ms_total")] + [
         ("evicted", ctypes.c_int64), ("cache_slots", ctypes.c_int64), ("max_distinct_cov", ctypes.c_int64),
-        ("scan_waves", ctypes.c_int64), ("big_listed", ctypes.c_int64)]
+        ("scan_waves", ctypes.c_int64), ("big_listed", ctypes.c_int64), ("screen_tiles", ctypes.c_int64),
+        ("screen_rows", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

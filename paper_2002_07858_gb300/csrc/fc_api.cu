@@ -466,13 +466,11 @@ fc_status ensure_q64_storage(fc_ctx* c, Grid* g) {
     return FC_OK;
 }
 
-// q-vector kernel of a grid: the tensor-core form above K = 64 (where the
-// register-resident binary32 kernel stops) unless the grid's tuning says otherwise.
+// q-vector kernel of a grid: the tensor-core form unless the grid's tuning asks
+// for the binary32 one (measured faster at every K, including N_fit = 45).
 bool use_qvec_tc(const Grid* g) {
     if (!qvec_tc_supported(g->K)) return false;
-    if (g->tune.qvec == FC_QVEC_TC) return true;
-    if (g->tune.qvec == FC_QVEC_SIMT) return false;
-    return g->K > 64;
+    return g->tune.qvec != FC_QVEC_SIMT;
 }
 
 // Make sure every grid index in `qs` has a covariance slot (build + invert the
@@ -1009,6 +1007,8 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                                        c->n_sm, c->stream))
                         return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
                     S->screen_launches += 1;
+                    S->screen_tiles += n_tiles;
+                    S->screen_rows += cnt;
                 }
                 FC_TRY(stage_end(c, &S->ms_screen));
                 S->screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
