@@ -15,6 +15,8 @@ end-to-end figure through the C ABI with host buffers, the roofline of the
 dominant kernel, the CPU oracle on a bounded sample, and the SM clocks seen.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+  python bench.py --serve      (cfg4 stream: p50/p99 job latency)
+  python bench.py --sweep      (job time vs universes and vs grid points)
 """
 from __future__ import annotations
 
@@ -431,6 +433,70 @@ def run_serve(args):
     fc.fc_destroy(ctx)
 
 
+def run_sweep(args):
+    """Scaling laws of the FC job (§4, Figs. 2, 3 and 7 re-measured on one GPU).
+
+    Series 1: the 100x100 grid (N 90->45), every point a true point, U swept
+    (the paper: run time linear in N_univ).  Series 2: U = 1000 at every point
+    of an n x n grid of the same generator, n swept (the paper: run time
+    quadratic in the number of grid points, since every point is scanned over
+    the whole grid).  Each configuration: one untimed job, then one job timed
+    with CUDA events on the library's stream (cold covariance cache both
+    times).  Prints one JSON line with ms per job, chi2 evals/s ("velocity",
+    Fig. 7), universes/s and the log-log slope of each series."""
+    import numpy as np
+    import torch
+
+    import paper_2002_07858_gb300 as fc
+    import workloads
+
+    fc.load()
+    stream = torch.cuda.Stream()
+    ctx = fc.fc_create(0, 0, stream.cuda_stream)
+    opts = dict(precision=fc.FC_PREC_MIXED, top_k=8, max_iter=5)
+
+    def job(n_axis, U):
+        S, F, _ = workloads.osc_2d(n_axis, n_axis, 90, seed=0)
+        gid = fc.fc_load_grid(ctx, S, workloads.pair_collapse(90), 45)
+        G = S.shape[0]
+        dev = torch.device("cuda", 0)
+        ps = torch.arange(G, dtype=torch.int64, device=dev)
+        outs = (torch.empty(G * U, dtype=torch.float64, device=dev), torch.empty(G * U, dtype=torch.int64, device=dev),
+                torch.empty(G * U, dtype=torch.int8, device=dev))
+        fc.fc_set_frac_cov(ctx, gid, F)
+        fc.fc_run_points(ctx, gid, ps, 5, U, opts, *outs)
+        torch.cuda.synchronize()
+        fc.fc_set_frac_cov(ctx, gid, F)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fc.fc_run_points(ctx, gid, ps, 6, U, opts, *outs)
+        b.record(stream)
+        torch.cuda.synchronize()
+        st = fc.fc_get_stats(ctx)
+        fc.fc_unload_grid(ctx, gid)
+        ms = a.elapsed_time(b)
+        return {"grid": f"{n_axis}x{n_axis}", "G": G, "U": U, "ms": ms, "chi2_evals_per_s": st["chi2_evals"] / ms * 1e3,
+                "universes_per_s": G * U / ms * 1e3, "scans_per_universe": st["scans"] / (G * U)}
+
+    def slope(xs, ys):
+        return float(np.polyfit(np.log(xs), np.log(ys), 1)[0])
+
+    with ClockSampler(0) as clk:
+        by_u = [job(100, U) for U in (125, 250, 500, 1000, 2000)]
+        by_g = [job(n, 1000) for n in (25, 50, 71, 100, 141, 200)]
+    big_u = [r for r in by_u if r["U"] >= 500]
+    big_g = [r for r in by_g if r["G"] >= 5000]
+    line = {"metric": "FC job time scaling", "unit": "ms", "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "D=2 n x n grids of the 100x100 generator, N 90->45, every grid point a true "
+                                   "point, <= 5 scans, top-8, mixed precision"},
+            "vs_universes": by_u, "vs_grid_points": by_g,
+            "slope_time_vs_U": slope([r["U"] for r in big_u], [r["ms"] for r in big_u]),
+            "slope_time_vs_G": slope([r["G"] for r in big_g], [r["ms"] for r in big_g]),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    fc.fc_destroy(ctx)
+
+
 def run_once(args):
     """One untimed FC job (for profilers): the configured points x universes, stats printed as JSON."""
     import numpy as np
@@ -475,9 +541,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the overload stream")
     ap.add_argument("--serve-seconds-low", type=float, default=20.0, help="arrival window below saturation")
     ap.add_argument("--serve-drain", type=float, default=240.0, help="seconds after a window before cancelling")
+    ap.add_argument("--sweep", action="store_true", help="job time vs universes and vs grid size (own JSON line)")
     args = ap.parse_args()
     if args.once:
         run_once(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.serve:
         run_serve(args)
     elif args.impl == "reference":
