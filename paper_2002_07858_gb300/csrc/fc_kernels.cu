@@ -348,13 +348,20 @@ __global__ void k_chol_sys(const double* __restrict__ S, int nf, const double* _
 }
 
 // One CTA per (slot, q): M(q) = C [diag(s) F diag(s) + diag(s)] C^T, L = chol(M),
-// W = L^-1, A = W^T W.
+// W = L^-1, A = W^T W.  The binary64 pipe of this GPU is narrow, so every
+// phase spreads its elements over all threads of the CTA (a phase with a few
+// busy lanes would hold the pipe for whole warps) and a column's divisions
+// become one reciprocal and multiplies.  These factors feed the fit, not the
+// fake data, so they need not repeat the oracle's rounding bit for bit.
 __global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, const int32_t* __restrict__ coll,
                             const double* __restrict__ F, const int32_t* __restrict__ q_list,
                             const int32_t* __restrict__ slot_list, int cov_mode, double* __restrict__ A64,
                             double* __restrict__ W64, float* __restrict__ A32, float* __restrict__ rho,
                             double* __restrict__ work, int* __restrict__ status) {
     extern __shared__ double sLW[];
+    __shared__ int s_moff[kMaxBins + 1], s_mem[kMaxBins], s_cur[kMaxBins];
+    __shared__ double s_inv[kMaxBins];
+    __shared__ int s_bad;
     const int e0 = blockIdx.x;
     const int q = q_list[e0];
     const int slot = slot_list[e0];
@@ -375,48 +382,86 @@ __global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, cons
         if (threadIdx.x == 0) rho[slot] = 1.0f;
         return;
     }
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = 0.0;
-    __syncthreads();
-    if (coll == nullptr) {
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const int i = e / n, m = e % n;
-            if (m > i) continue;
-            double v = (s[i] * F[i * nf + m]) * s[m];
-            if (i == m) v += s[i];
-            L[e] = v;
+    // full bins of each fit bin, in increasing order (counting sort by one thread)
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        if (coll) {
+            for (int j = 0; j <= n; ++j) s_moff[j] = 0;
+            for (int i = 0; i < nf; ++i) ++s_moff[coll[i] + 1];
+            for (int j = 0; j < n; ++j) s_moff[j + 1] += s_moff[j];
+            for (int j = 0; j < n; ++j) s_cur[j] = s_moff[j];
+            for (int i = 0; i < nf; ++i) s_mem[s_cur[coll[i]]++] = i;
         }
-    } else {
-        // row j of the fit-space matrix is owned by one thread: no races
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            for (int i = 0; i < nf; ++i) {
-                if (coll[i] != j) continue;
-                for (int m = 0; m < nf; ++m) {
-                    const int l = coll[m];
-                    if (l > j) continue;
-                    double v = (s[i] * F[i * nf + m]) * s[m];
-                    if (i == m) v += s[i];
-                    L[j * n + l] += v;
+    }
+    __syncthreads();
+    // 1. M in fit space (lower triangle; upper zero): element (j, l) sums (s_a F_ab) s_b (+ s_a when a == b)
+    //    over full bins a -> j, b -> l in increasing (a, b)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int j = e / n, l = e % n;
+        double v = 0.0;
+        if (l <= j) {
+            if (coll == nullptr) {
+                v = (s[j] * F[j * nf + l]) * s[l];
+                if (j == l) v += s[j];
+            } else {
+                for (int ia = s_moff[j]; ia < s_moff[j + 1]; ++ia) {
+                    const int a = s_mem[ia];
+                    for (int ib = s_moff[l]; ib < s_moff[l + 1]; ++ib) {
+                        const int b = s_mem[ib];
+                        double t = (s[a] * F[a * nf + b]) * s[b];
+                        if (a == b) t += s[a];
+                        v += t;
+                    }
                 }
             }
         }
+        L[e] = v;
     }
     __syncthreads();
-    const bool ok = chol_inplace(L, n);
-    if (!ok) {
+    // 2. Cholesky, right-looking; column k is scaled by the reciprocal of its pivot
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            double d = L[k * n + k];
+            if (!(d > 0.0)) {
+                s_bad = 1;
+                d = 1.0;
+            }
+            const double sd = __dsqrt_rn(d);
+            L[k * n + k] = sd;
+            s_inv[k] = 1.0 / sd;
+        }
+        __syncthreads();
+        const double ik = s_inv[k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) L[i * n + k] *= ik;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int a = e / m, b = e % m;
+            if (b > a) continue;
+            const int i = k + 1 + a, jj = k + 1 + b;
+            L[i * n + jj] -= L[i * n + k] * L[jj * n + k];
+        }
+        __syncthreads();
+    }
+    if (s_bad) {
         if (threadIdx.x == 0) atomicOr(status, kDevNotSpd);
         return;
     }
-    // W = L^-1 (lower): column c by one thread, forward substitution
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        for (int i = 0; i < c; ++i) W[i * n + c] = 0.0;
-        W[c * n + c] = 1.0 / L[c * n + c];
-        for (int i = c + 1; i < n; ++i) {
-            double acc = 0.0;
-            for (int k = c; k < i; ++k) acc = fma(L[i * n + k], W[k * n + c], acc);
-            W[i * n + c] = -acc / L[i * n + i];
-        }
-    }
+    // 3. W = L^-1 by elimination on [L | I]: at step k row k of W is scaled by 1/L_kk and
+    //    final; every row i > k then subtracts L_ik times it (columns c <= k)
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) W[e] = (e / n == e % n) ? 1.0 : 0.0;
     __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const double ik = s_inv[k];
+        for (int c = threadIdx.x; c <= k; c += blockDim.x) W[k * n + c] *= ik;
+        __syncthreads();
+        const int m = n - k - 1, w = k + 1;
+        for (int e = threadIdx.x; e < m * w; e += blockDim.x) {
+            const int i = k + 1 + e / w, c = e % w;
+            W[i * n + c] -= L[i * n + k] * W[k * n + c];
+        }
+        __syncthreads();
+    }
     // A = W^T W: A_ij = sum_{k >= max(i,j)} W_ki W_kj
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e % n;
@@ -806,6 +851,11 @@ __device__ __forceinline__ int64_t ytile_offset(int64_t t, int r, int c, int K) 
 // It also evaluates the row's screen value at its own covariance point q
 // (= cur[u]) with an upper bound UB_q: no grid point with LB >= UB_q can be the
 // minimum, so tau0 = UB_q seeds the screen's top-k threshold.
+// NR > 0: N_fit <= NR and the row's d - v lives in registers (every index a
+// compile-time constant, the loops unrolled to NR with the columns past N_fit
+// skipped); NR = 0: any N_fit, with d - v in a per-thread array.  Same
+// operations in the same order either way.
+template <int NR>
 __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_slot,
                                                 const int32_t* __restrict__ tile_univ, const float* __restrict__ d,
                                                 const double* __restrict__ centre, int nfit, int K,
@@ -834,11 +884,22 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
     const int q = cur[u];
     const float* sq = Sc32 + (int64_t)q * nfit;
 
-    float dt[kMaxBins];
+    float dt[NR > 0 ? NR : kMaxBins];
     float dn2 = 0.0f;
-    for (int j = 0; j < nfit; ++j) {
-        dt[j] = (float)((double)d[(size_t)u * nfit + j] - centre[j]);
-        dn2 = fmaf(dt[j], dt[j], dn2);
+    if (NR > 0) {
+#pragma unroll
+        for (int j = 0; j < (NR > 0 ? NR : 1); ++j) {
+            dt[j] = 0.0f;
+            if (j < nfit) {
+                dt[j] = (float)((double)d[(size_t)u * nfit + j] - centre[j]);
+                dn2 = fmaf(dt[j], dt[j], dn2);
+            }
+        }
+    } else {
+        for (int j = 0; j < nfit; ++j) {
+            dt[j] = (float)((double)d[(size_t)u * nfit + j] - centre[j]);
+            dn2 = fmaf(dt[j], dt[j], dn2);
+        }
     }
     float yn2 = 0.0f, yl2 = 0.0f, yhl2 = 0.0f, ry2 = 0.0f, dot = 0.0f, adot = 0.0f;
     // the row's A-image entries in runs of 8 columns (one 16-byte core-matrix row per half)
@@ -849,7 +910,14 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
             const int i = c8 * 8 + ii;
             if (i < nfit) {
                 float y = 0.0f;
-                for (int j = 0; j < nfit; ++j) y = fmaf(sA[i * nfit + j], dt[j], y);
+                const float* Ai = sA + i * nfit;
+                if (NR > 0) {
+#pragma unroll
+                    for (int j = 0; j < (NR > 0 ? NR : 1); ++j)
+                        if (j < nfit) y = fmaf(Ai[j], dt[j], y);
+                } else {
+                    for (int j = 0; j < nfit; ++j) y = fmaf(Ai[j], dt[j], y);
+                }
                 const float Y = -2.0f * y;
                 yn2 = fmaf(Y, Y, yn2);
                 dot = fmaf(Y, sq[i], dot);
@@ -1451,12 +1519,11 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                   uint16_t* Yt, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st) {
     if (n_tiles <= 0) return;
     const size_t smem = (size_t)nfit * nfit * sizeof(float);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_yprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = nfit <= 48 ? k_yprep<48> : k_yprep<0>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    k_yprep<<<(unsigned)n_tiles, kBM, (size_t)nfit * nfit * sizeof(float), st>>>(tile_slot, tile_univ, d, centre,
-                                                                                  nfit, K, A32, rho, cur, Sc32, gnorm,
-                                                                                  Qc, Qb, G_pad, Yt, alpha, tau0,
-                                                                                  tile_j0);
+    kern<<<(unsigned)n_tiles, kBM, smem, st>>>(tile_slot, tile_univ, d, centre, nfit, K, A32, rho, cur, Sc32, gnorm, Qc,
+                                               Qb, G_pad, Yt, alpha, tau0, tile_j0);
 }
 
 void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st) {
