@@ -35,6 +35,13 @@ sys.path.insert(0, ROOT)
 METRIC = "chi2 evals/s"
 UNIT = "chi2 evals/s"
 
+# DRAM bytes (read + write) per screened universe row of the tensor-core screen on the
+# 100x100 grid with N 90->45 (K = 48): an ncu capture of one top-8 launch over 10^6
+# universes read 368.0 MB and wrote 56.4 MB.  The traffic is the rows' A images, the
+# q-step rows of their covariance slots and the candidate lists, so a launch's traffic
+# is taken as proportional to the rows it screens.
+SCREEN_DRAM_BYTES_PER_ROW_CFG2 = 424.3
+
 
 def _peaks():
     try:
@@ -260,10 +267,17 @@ def run_native(args):
     scr_flops = sum(s["screen_flops"] for s in stats)
     scr_launch = sum(s["screen_launches"] for s in stats)
     achieved = scr_flops / (scr_ms / 1e3) / 1e12 if scr_ms > 0 else 0.0
+    scr_rows = sum(s["screen_rows"] for s in stats)
+    traffic = None
+    if args.config == "cfg2" and scr_launch > 0:
+        # bytes per launch, scaled from the captured launch by the rows screened
+        traffic = SCREEN_DRAM_BYTES_PER_ROW_CFG2 * scr_rows / scr_launch
     peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     roofline = {"kernel": "k_screen (tcgen05 BF16 hi/lo screen + fused top-k)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"bf16_tflops_sustained ({peak_src})", "traffic": None,
+                "peak_source": f"bf16_tflops_sustained ({peak_src})", "traffic": traffic,
+                "traffic_source": ("DRAM bytes per launch: an ncu capture of one top-8 launch (424.3 B per "
+                                   "screened row) scaled by the rows each launch screens") if traffic else None,
                 "flops_per_eval": 2 * w.n_fit, "launches": scr_launch,
                 "avg_launch_ms": scr_ms / max(scr_launch, 1)}
 
