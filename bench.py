@@ -204,6 +204,12 @@ def run_native(args):
         desc = (f"cfg3: D=3 64^3 grid (262144 points), N=120 (K=128), {len(pts)} seeded true points x {w.U} "
                 f"universes, <= {w.max_iter} scans, top-{args.top_k}")
         l2 = "working set per step > L2 (screen B image 134 MB, q-vectors 6.3 MB per covariance)"
+    elif args.config == "cfg5":
+        w = workloads.cfg5(U=args.universes or 16)
+        pts = w.points if args.points is None else w.points[np.linspace(0, len(w.points) - 1, args.points).astype(int)]
+        desc = (f"cfg5: D=6 16^6 grid (16777216 points), N=64, {len(pts)} seeded true points x {w.U} universes "
+                f"(one batch of {len(pts) * w.U}), <= {w.max_iter} scans, top-{args.top_k}")
+        l2 = "working set per step > L2 (screen B image 4.3 GB, q-vectors 0.4 GB per covariance)"
     else:
         w = workloads.cfg2(U=args.universes or 1000)
         P_all = w.G if args.points is None else args.points
@@ -302,7 +308,7 @@ def run_native(args):
         # ---- plain binary64 GPU fit on a sample (same metric)
         plain = None
         if not args.no_plain:
-            n_pp = args.plain_points if args.plain_points is not None else (1 if args.config == "cfg3" else 20)
+            n_pp = args.plain_points if args.plain_points is not None else (20 if args.config == "cfg2" else 1)
             pp = torch.from_numpy(np.linspace(0, w.G - 1, n_pp).round().astype(np.int64)).to(dev)
             m = n_pp * U
             outs = (torch.empty(m, dtype=torch.float64, device=dev), torch.empty(m, dtype=torch.int64, device=dev),
@@ -519,8 +525,8 @@ def run_once(args):
     import workloads
 
     fc.load()
-    if args.config == "cfg3":
-        w = workloads.cfg3(U=args.universes or 500)
+    if args.config in ("cfg3", "cfg5"):
+        w = workloads.cfg3(U=args.universes or 500) if args.config == "cfg3" else workloads.cfg5(U=args.universes or 16)
         pts = w.points if args.points is None else w.points[np.linspace(0, len(w.points) - 1, args.points).astype(int)]
     else:
         w = workloads.cfg2(U=args.universes or 1000)
@@ -539,12 +545,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--config", default="cfg2", choices=["cfg2", "cfg3"],
-                    help="cfg2 (the metric's workload, default) or cfg3 (D=3, N=120, 2048 points x 500)")
+    ap.add_argument("--config", default="cfg2", choices=["cfg2", "cfg3", "cfg5"],
+                    help="cfg2 (the metric's workload, default), cfg3 (D=3, N=120, 2048 points x 500) or "
+                         "cfg5 (D=6, 16^6 points, N=64, 256 points x 16)")
     ap.add_argument("--universes", type=int, default=None, help="universes per true point (default: the config's)")
     ap.add_argument("--points", type=int, default=None, help="true points (default: all 10^4)")
-    ap.add_argument("--top-k", type=int, default=8)
-    ap.add_argument("--plain-points", type=int, default=None, help="plain binary64 sample (default 20; cfg3: 1)")
+    ap.add_argument("--top-k", type=int, default=None, help="candidates per universe (default 8; cfg5: 16)")
+    ap.add_argument("--plain-points", type=int, default=None, help="plain binary64 sample (default 20; cfg3, cfg5: 1)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -557,6 +564,8 @@ def main():
     ap.add_argument("--serve-drain", type=float, default=240.0, help="seconds after a window before cancelling")
     ap.add_argument("--sweep", action="store_true", help="job time vs universes and vs grid size (own JSON line)")
     args = ap.parse_args()
+    if args.top_k is None:
+        args.top_k = 16 if args.config == "cfg5" else 8
     if args.once:
         run_once(args)
     elif args.sweep:

@@ -212,6 +212,27 @@ FC_API fc_status fc_data_dchi2(fc_ctx* ctx, int32_t grid_id, const float* d, con
 FC_API fc_status fc_fc_region(fc_ctx* ctx, const double* dchi2_univ, int32_t P, int32_t U, const double* dchi2_data,
                               double cl, double* crit, uint8_t* accepted);
 
+/* Feldman-Cousins acceptance with an adaptive number of universes per point
+ * (the future-work outlook of §5.1: spend universes where the decision is close).
+ * For point ps[i] with data statistic dchi2_data[i] (e.g. from fc_data_dchi2):
+ * F_i = #{universes u of ps[i] : dchi2_u < dchi2_data[i]} / U_i, the
+ * empirical distribution of the point's dchi2 at the data's value, and
+ * accepted[i] = 1 when F_i <= cl (dchi2_data[i] at or below the cl-quantile).
+ * Round 0 runs U0 universes at every point (fc_run_points' procedure, key
+ * seed); a point stays open while |F_i - cl| <= z sqrt(cl (1 - cl) / U_i) and
+ * U_i < U_max, and round r runs as many new universes as an open point already
+ * has (key seed + r, so the total doubles; the last round is capped at U_max).
+ * Counting runs on the device; only P counts per round return to the host.
+ * Inputs ps [P] int64, dchi2_data [P] float64 (host or device); outputs
+ * accepted [P] uint8 (required), U_used [P] int32 and frac [P] float64 (F_i),
+ * nullable, host or device.  Errors: FC_ERR_ARG (NULL, P < 0,
+ * not 1 <= U0 <= U_max <= 2^20, cl outside [0, 1], z < 0, NaN data),
+ * FC_ERR_NOT_FOUND, FC_ERR_STATE (F not set), and those of fc_run_points. */
+FC_API fc_status fc_fc_region_adaptive(fc_ctx* ctx, int32_t grid_id, const int64_t* ps, int32_t P,
+                                       const double* dchi2_data, double cl, int32_t U0, int32_t U_max, double z,
+                                       uint64_t seed, const fc_opts* opts, uint8_t* accepted, int32_t* U_used,
+                                       double* frac);
+
 /* Asynchronous serving (continuous batching).  A job = fc_run_points'
  * arguments; output pointers must stay valid until fc_poll returns a final
  * status.  fc_submit admits the job when the context's memory budget allows

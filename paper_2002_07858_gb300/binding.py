@@ -30,7 +30,8 @@ _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_
 EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set_frac_cov", "fc_unload_grid",
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
            "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
-           "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats", "fc_data_dchi2", "fc_fc_region"]
+           "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats", "fc_data_dchi2", "fc_fc_region",
+           "fc_fc_region_adaptive"]
 
 
 class FCError(RuntimeError):
@@ -113,6 +114,8 @@ def load(build: bool = False):
         "fc_get_serve_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
         "fc_data_dchi2": (st, [vp, i32, vp, vp, i32, ctypes.POINTER(fc_opts), vp, vp, vp]),
         "fc_fc_region": (st, [vp, vp, i32, i32, vp, ctypes.c_double, vp, vp]),
+        "fc_fc_region_adaptive": (st, [vp, i32, vp, i32, vp, ctypes.c_double, i32, i32, ctypes.c_double, u64,
+                                       ctypes.POINTER(fc_opts), vp, vp, vp]),
         "fc_set_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
         "fc_get_tuning": (st, [vp, i32, ctypes.POINTER(fc_tuning)]),
         "fc_autotune": (st, [vp, i32, ctypes.c_char_p, ctypes.POINTER(fc_tuning)]),
@@ -279,6 +282,23 @@ def fc_fc_region(ctx, dchi2_univ, dchi2_data, cl: float):
     acc = np.empty(P, np.uint8)
     _check(load().fc_fc_region(ctx, _ptr(x), P, U, _ptr(dd), float(cl), _ptr(crit), _ptr(acc)), ctx)
     return crit, acc
+
+
+def fc_fc_region_adaptive(ctx, grid_id: int, ps, dchi2_data, cl: float, U0: int, U_max: int, z: float = 3.0,
+                          seed: int = 0, opts=None):
+    """(accepted [P] uint8, U_used [P] int32, frac [P] float64): FC acceptance with universes added per point
+    until the empirical distribution at the data's value is z standard errors from cl (or U_max)."""
+    ps = _host(ps, np.int64)
+    dd = _host(dchi2_data, np.float64)
+    P = int(ps.shape[0])
+    o = _opts(opts)
+    acc = np.empty(P, np.uint8)
+    used = np.empty(P, np.int32)
+    frac = np.empty(P, np.float64)
+    _check(load().fc_fc_region_adaptive(ctx, grid_id, _ptr(ps), P, _ptr(dd), float(cl), int(U0), int(U_max),
+                                        float(z), int(seed), ctypes.byref(o), _ptr(acc), _ptr(used), _ptr(frac)),
+           ctx)
+    return acc, used, frac
 
 
 def fc_quantiles(ctx, x, probs):

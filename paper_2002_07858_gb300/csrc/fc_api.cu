@@ -1939,6 +1939,91 @@ fc_status fc_fc_region(fc_ctx* c, const double* dchi2_univ, int32_t P, int32_t U
     return FC_OK;
 }
 
+fc_status fc_fc_region_adaptive(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t P, const double* dchi2_data,
+                                double cl, int32_t U0, int32_t U_max, double z, uint64_t seed, const fc_opts* opts,
+                                uint8_t* accepted, int32_t* U_used, double* frac) {
+    if (!c || (P > 0 && (!ps || !dchi2_data || !accepted))) return fail(FC_ERR_ARG, "NULL argument");
+    if (P < 0 || U0 < 1 || U_max < U0 || U_max > (1 << 20))
+        return fail(FC_ERR_ARG, "bad sizes (1 <= U0 <= U_max <= 2^20)");
+    if (!(cl >= 0.0 && cl <= 1.0)) return fail(FC_ERR_ARG, "cl must be in [0, 1]");
+    if (!(z >= 0.0) || !std::isfinite(z)) return fail(FC_ERR_ARG, "z must be finite and >= 0");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    Grid* g = find_grid(c, grid_id);
+    if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
+    if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
+    fc_opts o;
+    fc_default_opts(&o);
+    if (opts) o = *opts;
+    FC_TRY(validate_opts(&o, g));
+    if (P == 0) return FC_OK;
+    std::vector<int64_t> hps;
+    FC_TRY(check_points(g, ps, P, &hps));
+    std::vector<double> hd(P);
+    if (is_device_ptr(dchi2_data))
+        FC_CUDA(cudaMemcpy(hd.data(), dchi2_data, (size_t)P * 8, cudaMemcpyDeviceToHost));
+    else
+        memcpy(hd.data(), dchi2_data, (size_t)P * 8);
+    for (double v : hd)
+        if (std::isnan(v)) return fail(FC_ERR_ARG, "dchi2_data must not be NaN");
+    c->stats = fc_stats{};
+    c->acc = &c->stats;
+    std::vector<int64_t> cnt(P, 0), used(P, 0);
+    std::vector<uint8_t> acc(P, 0);
+    std::vector<int32_t> open(P);
+    for (int32_t i = 0; i < P; ++i) open[i] = i;
+    // round r draws U_r new universes per open point with key seed + r: U0, then as many as the point
+    // already has (the total doubles), the last round capped at U_max
+    for (int round = 0; !open.empty(); ++round) {
+        const int64_t have = used[open[0]];  // every open point has had the same rounds
+        const int64_t U_r = std::min<int64_t>(round == 0 ? U0 : have, (int64_t)U_max - have);
+        const int64_t Pr = (int64_t)open.size();
+        if (Pr * U_r > (int64_t)INT32_MAX / 2) return fail(FC_ERR_ARG, "points x universes of a round too large");
+        std::vector<int64_t> rps(Pr), rcnt(Pr, 0);
+        std::vector<double> rthr(Pr);
+        for (int64_t k = 0; k < Pr; ++k) {
+            rps[k] = hps[open[k]];
+            rthr[k] = hd[open[k]];
+        }
+        double *dx = nullptr, *dthr = nullptr;
+        int64_t* dcnt = nullptr;
+        FC_TRY(scratch(c, "ad_x", (size_t)(Pr * U_r), &dx));
+        FC_TRY(scratch(c, "ad_thr", (size_t)Pr, &dthr));
+        FC_TRY(scratch(c, "ad_cnt", (size_t)Pr, &dcnt));
+        FC_TRY(run_sync(c, g, o, rps, (int32_t)U_r, seed + (uint64_t)round, nullptr, dx, nullptr, nullptr, nullptr,
+                        nullptr));
+        FC_CUDA(cudaMemcpyAsync(dthr, rthr.data(), (size_t)Pr * 8, cudaMemcpyHostToDevice, c->stream));
+        FC_CUDA(cudaMemsetAsync(dcnt, 0, (size_t)Pr * 8, c->stream));
+        launch_count_below(dx, (int)Pr, (int)U_r, dthr, dcnt, c->stream);
+        FC_CUDA(cudaMemcpyAsync(rcnt.data(), dcnt, (size_t)Pr * 8, cudaMemcpyDeviceToHost, c->stream));
+        FC_TRY(sync(c));
+        c->stats.universes += Pr * U_r;
+        std::vector<int32_t> still;
+        for (int64_t k = 0; k < Pr; ++k) {
+            const int32_t i = open[k];
+            cnt[i] += rcnt[k];
+            used[i] += U_r;
+            const double F = (double)cnt[i] / (double)used[i];
+            const double half = z * std::sqrt(cl * (1.0 - cl) / (double)used[i]);
+            acc[i] = (F <= cl) ? 1 : 0;
+            if (used[i] < U_max && std::fabs(F - cl) <= half) still.push_back(i);
+        }
+        open.swap(still);
+    }
+    FC_TRY(put_out(c, accepted, acc.data(), (size_t)P));
+    if (U_used) {
+        std::vector<int32_t> uu(P);
+        for (int32_t i = 0; i < P; ++i) uu[i] = (int32_t)used[i];
+        FC_TRY(put_out(c, U_used, uu.data(), (size_t)P * 4));
+    }
+    if (frac) {
+        std::vector<double> f(P);
+        for (int32_t i = 0; i < P; ++i) f[i] = (double)cnt[i] / (double)used[i];
+        FC_TRY(put_out(c, frac, f.data(), (size_t)P * 8));
+    }
+    return sync(c);
+}
+
 fc_status fc_quantiles(fc_ctx* c, const double* x, int32_t rows, int32_t n, const double* probs, int32_t nq,
                        double* out) {
     if (!c || !x || !probs || !out) return fail(FC_ERR_ARG, "NULL argument");

@@ -1310,6 +1310,24 @@ __global__ void k_advance(const int32_t* __restrict__ active, int64_t n, const i
 
 // ---------------------------------------------------------- quantiles -------
 
+// One CTA per row: counts[row] += #{u < n : x[row][u] < thr[row]} (the empirical
+// distribution of the row's dchi2 at the data's value).
+__global__ void k_count_below(const double* __restrict__ x, int n, const double* __restrict__ thr,
+                              int64_t* __restrict__ counts) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const double t = thr[blockIdx.x];
+    const double* xr = x + (size_t)blockIdx.x * n;
+    int c = 0;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) c += (xr[u] < t) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] += s_cnt;
+}
+
+
 // One CTA per row: bitonic sort in shared memory, then numpy's "linear" rule.
 __global__ void k_quantiles(const double* __restrict__ x, int n, int npow2, const double* __restrict__ probs,
                             int nq, double* __restrict__ out) {
@@ -1585,6 +1603,12 @@ void launch_advance(const int32_t* active, int64_t n, const int32_t* best, const
     if (n <= 0) return;
     count_launch();
     k_advance<<<blocks_for(n), kThreads, 0, st>>>(active, n, best, us, next_active, n_next, fin, n_fin);
+}
+
+void launch_count_below(const double* x, int rows, int n, const double* thr, int64_t* counts, cudaStream_t st) {
+    if (rows <= 0 || n <= 0) return;
+    count_launch();
+    k_count_below<<<rows, 256, 0, st>>>(x, n, thr, counts);
 }
 
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st) {

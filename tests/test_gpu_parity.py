@@ -300,3 +300,59 @@ def test_data_dchi2_and_region(fc, ctx, w1, w2):
     with pytest.raises(fc.FCError) as e:
         fc.fc_fc_region(ctx, du, ddat, 1.5)
     assert e.value.status == fc.FC_ERR_ARG
+
+
+def _adaptive_reference(w, pts, data_dchi2, cl, U0, U_max, z, seed):
+    """The adaptive acceptance rule restated on the oracle's universes: round r draws
+    U0, then as many universes as a still-open point has (key seed + r), counts those
+    below the data's dchi2, and closes a point once |F - cl| > z sqrt(cl (1 - cl) / U)
+    or U reaches U_max; accepted when F <= cl."""
+    P = len(pts)
+    cnt = np.zeros(P, np.int64)
+    used = np.zeros(P, np.int64)
+    open_ = list(range(P))
+    r = 0
+    while open_:
+        have = int(used[open_[0]])
+        Ur = U0 if r == 0 else min(have, U_max - have)
+        du, _, _ = oracle.run_points(w.S, w.F, pts[open_], seed + r, Ur, collapse=w.collapse, n_fit=w.n_fit)
+        still = []
+        for k, i in enumerate(open_):
+            cnt[i] += int((du[k] < data_dchi2[i]).sum())
+            used[i] += Ur
+            F = cnt[i] / used[i]
+            if used[i] < U_max and abs(F - cl) <= z * np.sqrt(cl * (1 - cl) / used[i]):
+                still.append(i)
+        open_ = still
+        r += 1
+    F = cnt / used
+    return (F <= cl).astype(np.uint8), used.astype(np.int32), F
+
+
+def test_fc_region_adaptive(fc, ctx, w1):
+    """Adaptive universes per point: the plain binary64 path's decisions, universe
+    counts and empirical fractions equal the rule run on the oracle's universes."""
+    g1 = grid(fc, ctx, w1)
+    obs = oracle.fake_data(w1.S, w1.F, [312], 5, 1)[0, 0]
+    # the dm2 row and the sin^2 2theta column through the true point: the contour crosses both
+    pts = np.unique(np.concatenate([np.arange(300, 325), np.arange(12, 625, 25)])).astype(np.int64)
+    od, _, _ = oracle.run_data(w1.S, w1.F, pts, obs)
+    cl, U0, U_max, z, seed = 0.9, 32, 256, 2.0, 23
+    acc, used, frac = fc.fc_fc_region_adaptive(ctx, g1, pts, od, cl, U0, U_max, z, seed,
+                                               opts=dict(precision=fc.FC_PREC_FP64))
+    racc, rused, rfrac = _adaptive_reference(w1, pts, od, cl, U0, U_max, z, seed)
+    np.testing.assert_array_equal(used, rused)
+    np.testing.assert_array_equal(acc, racc)
+    np.testing.assert_array_equal(frac, rfrac)
+    assert len(np.unique(used)) >= 2          # some points stop at U0, some take more universes
+    assert used.min() >= U0 and used.max() <= U_max
+    # a point that stopped early is z standard errors from cl
+    early = used < U_max
+    se = np.sqrt(cl * (1 - cl) / used[early])
+    assert np.all(np.abs(frac[early] - cl) > z * se)
+    # the tensor-core path decides the same points (its dchi2 agree with the binary64 fit to 1e-4)
+    acc_m, used_m, _ = fc.fc_fc_region_adaptive(ctx, g1, pts, od, cl, U0, U_max, z, seed)
+    assert (acc_m == acc).mean() >= 0.95
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_fc_region_adaptive(ctx, g1, pts, od, cl, 64, 32, z, seed)
+    assert e.value.status == fc.FC_ERR_ARG
