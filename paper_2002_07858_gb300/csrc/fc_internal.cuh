@@ -160,7 +160,7 @@ struct ListArgs {
 bool screen_config_ok(int K, int stages, int ybuf);
 bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Ytiles, const uint16_t* Btiles,
                    const uint16_t* Qb3,
-                   const int32_t* tile_slot, float* tau0, int32_t* tile_j0, int64_t n_tiles, int64_t G,
+                   const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
                    int nfit, const ListArgs& la, int n_sm, cudaStream_t st);
