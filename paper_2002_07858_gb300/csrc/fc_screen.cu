@@ -109,9 +109,9 @@ __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[T
     }
 }
 
-// Screen modes: kModeMin (first pass) uses only the hi*hi products, keeps each
-// row's minimum and turns it into a certified upper bound that tightens the
-// row's seed tau0 in place; kModeTopK keeps the full top-k; kModeList lists
+// Screen modes: kModeMin (first pass) uses only the hi*hi products and keeps
+// each row's minimum index, which k_min_seed then turns into a certified upper
+// bound that tightens the row's seed tau0 in place; kModeTopK keeps the full top-k; kModeList lists
 // every grid point whose lower bound is at or below the seed (kListCap per
 // half row, the count says whether the list overflowed).
 struct ProbeArgs {
@@ -189,6 +189,21 @@ __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item
     const float eps = bound_dot(pa.alpha[item * kBM + row], pa.gnorm[g]) + (qc - pa.Qb[qi]) +
                       (float)(n + 2) * 5.9604645e-08f * (adot + fabsf(qc)) + 1.1920929e-07f * (fabsf(sig) + 1.0f);
     return (sig + 2.0f * eps) * 1.0000005f + 1.0e-6f + 4.7683716e-07f * fabsf(sig);
+}
+
+// After a min-only pass: tau0 <- min(tau0, certified upper bound at the row's
+// minimum index bidx), one thread per row (bidx = INT32_MAX: no minimum).
+__global__ void k_min_seed(const uint16_t* __restrict__ Yt, const int32_t* __restrict__ tile_slot,
+                           const int32_t* __restrict__ bidx, float* __restrict__ tau0, int64_t n_rows, int64_t G_pad,
+                           ProbeArgs pa) {
+    const int64_t orow = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (orow >= n_rows) return;
+    const int32_t bi = bidx[orow];
+    const float seed = tau0[orow];
+    if (bi == INT32_MAX || !(seed > -FLT_MAX)) return;
+    const int64_t item = orow / kBM;
+    const int row = (int)(orow % kBM);
+    tau0[orow] = fminf(seed, probe_upper_bound(Yt, item, row, tile_slot[item], bi, G_pad, pa));
 }
 
 constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
@@ -517,8 +532,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                         bv = x;
                         bi = xi;
                     }
-                    if (ok && bi != INT32_MAX && seed > -FLT_MAX)
-                        tau0[orow] = fminf(seed, probe_upper_bound(Yt, item, row, tile_slot[item], bi, G_pad, pa));
+                    // the row's minimum index; k_min_seed turns it into the certified seed after the
+                    // launch, so the epilogue never stalls the MMAs on the probe's scattered loads
+                    cand_idx[orow] = (ok && seed > -FLT_MAX) ? bi : INT32_MAX;
                 } else {
 #pragma unroll 1
                     for (int t = 0; t < TOPK; ++t) {
@@ -563,6 +579,11 @@ void run_screen(const ScreenLayout& lay, const uint16_t* Yt, const uint16_t* Bt,
     count_launch();
     kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, lay.bytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G,
                                                                    G_pad, cv, ci, cc, status, pa, lay, la);
+    if (MODE == kModeMin) {
+        const int64_t rows = n_tiles * kBM;
+        count_launch();
+        k_min_seed<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Yt, tile_slot, ci, tau0, rows, G_pad, pa);
+    }
 }
 
 // Shared-memory plan for K with the requested depth / buffering (0 = built-in:
