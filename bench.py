@@ -147,6 +147,23 @@ def _dist_init():
     return dist.get_rank(), int(os.environ.get("LOCAL_RANK", "0")), ws, dist
 
 
+def _combine_ranks(dist, ms: float, evals: float, univ: float):
+    """Whole-job figures of N replicas: the slowest rank's time, the sum of every rank's work."""
+    import torch
+
+    t = torch.tensor([ms, evals, univ], dtype=torch.float64)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
+def replica_seed(rank: int) -> int:
+    """Seed offset of a replica: ranks draw disjoint Philox keys, so their universes are independent."""
+    return 1000003 * rank
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle, timed on the host cores (rank 0 only)."""
     rank, _, ws, dist = _dist_init()
@@ -230,7 +247,7 @@ def run_native(args):
     best = torch.empty(n, dtype=torch.int64, device=dev)
     nsc = torch.empty(n, dtype=torch.int8, device=dev)
     opts = dict(precision=fc.FC_PREC_MIXED, top_k=args.top_k, max_iter=w.max_iter)
-    seed_base = 1000003 * rank
+    seed_base = replica_seed(rank)
 
     def step(i, ps=ps_dev, outs=(dchi2, best, nsc)):
         fc.fc_set_frac_cov(ctx, gid, w.F)          # cold covariance cache: every step builds its own
@@ -257,12 +274,7 @@ def run_native(args):
     evals = float(sum(s["chi2_evals"] for s in stats))
     univ = float(sum(s["universes"] for s in stats))
     if dist:
-        t = torch.tensor([ms, evals, univ], dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms, evals, univ = float(mx[0]), float(sm[1]), float(sm[2])
+        ms, evals, univ = _combine_ranks(dist, ms, evals, univ)
     value = evals / (ms / 1e3)
 
     # ---- stage breakdown and roofline of the dominant kernel (event-timed inside the library)
