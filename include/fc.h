@@ -81,7 +81,7 @@ enum { FC_QVEC_AUTO = 0,     /* tensor cores (the faster kernel at every N_fit) 
        FC_QVEC_SIMT = 1,     /* q_g = s~^T A s~ in binary32, A in shared memory    */
        FC_QVEC_TC = 2 };     /* q_g = |W s~|^2 on tcgen05 (bf16 hi/lo), K <= 128  */
 
-enum { FC_ROUND_AUTO = 0,    /* TOPK, or LIST once top-k certifies < 30 % of a grid's scans */
+enum { FC_ROUND_AUTO = 0,    /* LIST (the faster policy on every grid measured)             */
        FC_ROUND_TOPK = 1,    /* rounds: top-k, top-16, list, exact-size lists               */
        FC_ROUND_LIST = 2 };  /* rounds: top-k, list, exact-size lists (no top-16 round)     */
 

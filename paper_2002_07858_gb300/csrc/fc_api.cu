@@ -116,7 +116,6 @@ struct Grid {
     double* Q64 = nullptr;           // [cap][G]   (plain)
     std::vector<uint8_t> q32_ready, q64_ready;
     fc_tuning tune{};                // kernel choices (all zero: built-in)
-    int64_t r1_in = 0, r1_ok = 0;    // universe-scans through a top-k first round, and certified there
     int busy = 0;                    // queued jobs referencing the grid
 };
 
@@ -858,12 +857,10 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     // are on their first scan a min-only pass tightens the seeds first.
     const bool first_heavy = 2 * L->n_first >= n_active;
     L->n_first = 0;
-    // the top-16 round is skipped (round 1's failures go straight to the list round) when asked, or
-    // when round 1 has certified under 30 % of this grid's universe-scans (after enough to judge)
-    const bool skip16 =
-        mixed && (g->tune.first_round == FC_ROUND_LIST ||
-                  (g->tune.first_round == FC_ROUND_AUTO && g->r1_in >= 4096 && 10 * g->r1_ok < 3 * g->r1_in));
-    int64_t r1_in = 0;
+    // round 1's failures go straight to the list round unless the top-16 round is asked for: the
+    // failures are few per covariance, so each round costs its sparse tiles, and one round fewer was
+    // faster on the 100x100 (N 90->45) and 64^3 (N 120) grids
+    const bool skip16 = mixed && g->tune.first_round != FC_ROUND_TOPK;
     int32_t *active = L->active, *next = L->next, *fin = L->fin, *uslot = L->uslot, *cur = L->cur;
     const float* d = L->d;
     int32_t* cnts = nullptr;
@@ -1123,7 +1120,6 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 }
                 return FC_OK;
             };
-            r1_in += sl_n;
             FC_TRY(screen_round(0, sl_list, sl_n, sl_slot, topk, fb, cnts + 1, false));
             int32_t n_fb = 0;
             FC_CUDA(cudaMemcpyAsync(&n_fb, cnts + 1, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1238,8 +1234,6 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     std::swap(L->active, L->next);
     L->n_active = n_next;
     S->screened += (int64_t)(cn[0] + cn[3]);
-    g->r1_in += r1_in;
-    g->r1_ok += (int64_t)cn[0];
     S->rescored += (int64_t)(cn[1] + cn[4] + cn[6] + cn[9]);
     S->rescreened += (int64_t)(cn[2] + cn[5]);
     S->big_listed += (int64_t)(cn[9] + cn[10]);
