@@ -777,9 +777,15 @@ __global__ void k_scan_resid_reduce(const int32_t* __restrict__ list, int64_t n,
 
 // ------------------------------------------------------ mixed: grouping -----
 
+// Universes of one job sit next to each other and mostly share a slot, so the
+// lanes of a warp that hold the same slot add their count with one atomic.
 __global__ void k_count_slots(const int32_t* __restrict__ uslot, int64_t n, int32_t* __restrict__ cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[uslot[i]], 1);
+    const unsigned act = __ballot_sync(0xffffffffu, i < n);
+    if (i >= n) return;
+    const int s = uslot[i];
+    const unsigned peers = __match_any_sync(act, s);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[s], __popc(peers));
 }
 
 // exclusive scan of ceil(cnt/BM) over slots (single CTA), writes the tile count
@@ -832,9 +838,16 @@ __global__ void k_scatter_tiles(const int32_t* __restrict__ active, int64_t n, c
                                 const int32_t* __restrict__ base, int32_t* __restrict__ fill,
                                 int32_t* __restrict__ tile_univ) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const unsigned act = __ballot_sync(0xffffffffu, i < n);
     if (i >= n) return;
     const int s = uslot[i];
-    const int pos = atomicAdd(&fill[s], 1);
+    // one atomic per slot per warp; the lanes of a slot take consecutive positions
+    const unsigned peers = __match_any_sync(act, s);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int first = 0;
+    if (lane == leader) first = atomicAdd(&fill[s], __popc(peers));
+    first = __shfl_sync(peers, first, leader);
+    const int pos = first + __popc(peers & ((1u << lane) - 1u));
     tile_univ[(int64_t)(base[s] + pos / kBM) * kBM + pos % kBM] = active[i];
 }
 
