@@ -268,11 +268,29 @@ __global__ void k_centred(const double* __restrict__ Sfit, const double* __restr
 
 // ------------------------------------------------------------ covariances ---
 
-constexpr int kCholSmemN = 110;  // n*n doubles <= 96.8 KB of shared memory
+// The systematic factor is staged in shared memory as a packed lower triangle
+// (element (i, j), j <= i, at i(i+1)/2 + j) up to this N_full: 98 KB at 155,
+// 33 KB at N_full = 90, so six true points share an SM.
+constexpr int kCholPackN = 155;
 
-// Cholesky in place on the lower triangle of a row-major n x n matrix (shared
-// or global memory); every element's sum runs k = 0..j-1 with separately rounded
-// multiply and subtract, so the factor is reproducible bit for bit.
+// e -> (a, b) with 0 <= b <= a and e = a(a+1)/2 + b
+__device__ __forceinline__ void tri_decode(int e, int& a, int& b) {
+    a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= e) ++a;
+    while (a * (a + 1) / 2 > e) --a;
+    b = e - a * (a + 1) / 2;
+}
+
+template <bool PACKED>
+__device__ __forceinline__ int lidx(int i, int j, int n) {
+    return PACKED ? i * (i + 1) / 2 + j : i * n + j;
+}
+
+// Cholesky in place on the lower triangle (packed, or row-major n x n with the
+// upper triangle zeroed at the end; shared or global memory); every element's
+// sum runs k = 0..j-1 with separately rounded multiply and subtract, so the
+// factor is reproducible bit for bit.
+template <bool PACKED>
 __device__ bool chol_inplace(double* L, int n) {
     // Right-looking form: after column k is final, every trailing element
     // (i >= j > k) subtracts L_ik L_jk.  Each element therefore still sees its
@@ -285,37 +303,38 @@ __device__ bool chol_inplace(double* L, int n) {
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         if (threadIdx.x == 0) {
-            double acc = L[k * n + k];
+            double acc = L[lidx<PACKED>(k, k, n)];
             if (!(acc > 0.0)) {
                 s_bad = 1;
                 acc = 1.0;
             }
             s_d = __dsqrt_rn(acc);
-            L[k * n + k] = s_d;
+            L[lidx<PACKED>(k, k, n)] = s_d;
         }
         __syncthreads();
         const double dk = s_d;
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) L[i * n + k] = __ddiv_rn(L[i * n + k], dk);
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+            L[lidx<PACKED>(i, k, n)] = __ddiv_rn(L[lidx<PACKED>(i, k, n)], dk);
         __syncthreads();
         // trailing update of the lower triangle, rows i > k, columns k < j <= i
         const int m = n - k - 1;
         const int cnt = m * (m + 1) / 2;
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            // e -> (a, b) with 0 <= b <= a < m
-            int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-            while ((a + 1) * (a + 2) / 2 <= e) ++a;
-            while (a * (a + 1) / 2 > e) --a;
-            const int b = e - a * (a + 1) / 2;
+            int a, b;
+            tri_decode(e, a, b);
             const int i = k + 1 + a, jj = k + 1 + b;
-            L[i * n + jj] = __dsub_rn(L[i * n + jj], __dmul_rn(L[i * n + k], L[jj * n + k]));
+            L[lidx<PACKED>(i, jj, n)] =
+                __dsub_rn(L[lidx<PACKED>(i, jj, n)], __dmul_rn(L[lidx<PACKED>(i, k, n)], L[lidx<PACKED>(jj, k, n)]));
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, c = e % n;
-        if (c > i) L[e] = 0.0;
+    if (!PACKED) {
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = e / n, c = e % n;
+            if (c > i) L[e] = 0.0;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     return s_bad == 0;
 }
 
@@ -326,24 +345,40 @@ __global__ void k_chol_sys(const double* __restrict__ S, int nf, const double* _
     const int ip = blockIdx.x;
     const double* s = S + ps[ip] * nf;
     double* Lg = L64 + (size_t)ip * nf * nf;
-    // factor in shared memory when it fits (the dependent sums then run at shared-memory latency)
-    const bool staged = (nf <= kCholSmemN);
-    double* L = staged ? sL : Lg;
-    for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) {
-        const int i = e / nf, j = e % nf;
-        if (j <= i) {
-            double v = __dmul_rn(__dmul_rn(s[i], F[i * nf + j]), s[j]);
-            if (gauss && i == j) v = __dadd_rn(v, s[i]);
-            L[e] = v;
+    float* Lf = L32 + (size_t)ip * nf * nf;
+    // element (i, j), j <= i, of diag(s) F diag(s) (+ diag(s) in the Gaussian mode)
+    auto msys = [&](int i, int j) {
+        double v = __dmul_rn(__dmul_rn(s[i], F[i * nf + j]), s[j]);
+        if (gauss && i == j) v = __dadd_rn(v, s[i]);
+        return v;
+    };
+    bool ok;
+    if (nf <= kCholPackN) {
+        // packed in shared memory (the dependent sums run at shared-memory latency)
+        const int np = nf * (nf + 1) / 2;
+        for (int e = threadIdx.x; e < np; e += blockDim.x) {
+            int i, j;
+            tri_decode(e, i, j);
+            sL[e] = msys(i, j);
         }
+        __syncthreads();
+        ok = chol_inplace<true>(sL, nf);
+        for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) {
+            const int i = e / nf, j = e % nf;
+            const double v = (j <= i) ? sL[i * (i + 1) / 2 + j] : 0.0;
+            Lg[e] = v;
+            Lf[e] = __double2float_rn(v);
+        }
+    } else {
+        for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) {
+            const int i = e / nf, j = e % nf;
+            if (j <= i) Lg[e] = msys(i, j);
+        }
+        __syncthreads();
+        ok = chol_inplace<false>(Lg, nf);
+        for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) Lf[e] = __double2float_rn(Lg[e]);
     }
-    __syncthreads();
-    const bool ok = chol_inplace(L, nf);
     if (!ok && threadIdx.x == 0) atomicOr(status, kDevNotSpd);
-    for (int e = threadIdx.x; e < nf * nf; e += blockDim.x) {
-        if (staged) Lg[e] = L[e];
-        L32[(size_t)ip * nf * nf + e] = __double2float_rn(L[e]);
-    }
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s32[(size_t)ip * nf + i] = __double2float_rn(s[i]);
 }
 
@@ -1401,11 +1436,11 @@ void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps
                      float* L32, float* s32, double*, int* status, cudaStream_t st) {
     if (P <= 0) return;
     count_launch();
-    const size_t smem = nf <= kCholSmemN ? (size_t)nf * nf * sizeof(double) : 0;
+    const size_t smem = nf <= kCholPackN ? (size_t)nf * (nf + 1) / 2 * sizeof(double) : 0;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_chol_sys, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kCholSmemN * kCholSmemN * (int)sizeof(double));
+                             kCholPackN * (kCholPackN + 1) / 2 * (int)sizeof(double));
         attr = true;
     }
     k_chol_sys<<<P, 256, smem, st>>>(S, nf, F, ps, gauss, L64, L32, s32, status);
