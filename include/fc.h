@@ -141,6 +141,35 @@ FC_API fc_status fc_destroy(fc_ctx* ctx);
 FC_API fc_status fc_load_grid(fc_ctx* ctx, const double* S, int64_t G, int32_t N_full,
                        const int32_t* collapse, int32_t N_fit, int32_t* grid_id);
 
+/* Grid spectra generated on the device from an oscillation shape model, so a
+ * large grid never exists on the host (the paper recomputes S(q) from its
+ * model, §3 and Table 2; here the model is evaluated once and the spectra stay
+ * resident).  The grid has D axes; grid point p is the row-major index over
+ * them (axis 0 slowest) and the model's spectrum is
+ *     s_i(p) = b_i + sum_t amp_t(p) sin^2(1.27 dm2_t(p) L_i / E_i) f_ti,
+ * the terms added to b_i in order t = 0, 1, ..., where term t reads its
+ * amplitude from axis amp_axis[t] and its dm2 from axis dm2_axis[t] (e.g. a
+ * two-flavour model: D = 2, axes dm2 and sin^2 2theta, one term).
+ * Everything after the spectra is fc_load_grid's (collapse, N_fit, the
+ * resident arrays).  All model arrays are host memory. */
+typedef struct {
+    int32_t D;                  /* axes, 1..8 */
+    const int32_t* axis_len;    /* [D] points per axis; G = their product */
+    const double* axis_values;  /* the axes' values, axis 0 first: sum(axis_len) entries */
+    int32_t n_terms;            /* oscillation terms, 1..4 */
+    const int32_t* amp_axis;    /* [n_terms] axis of each term's amplitude */
+    const int32_t* dm2_axis;    /* [n_terms] axis of each term's dm2 (eV^2) */
+    const double* b;            /* [N_full] background */
+    const double* f;            /* [n_terms][N_full] each term's signal shape */
+    const double* L;            /* [N_full] baseline of each bin (m) */
+    const double* E;            /* [N_full] energy of each bin (GeV), > 0 */
+} fc_osc_model;
+
+/* Errors: FC_ERR_ARG (sizes, axes, E <= 0, a spectrum not finite or < 0, and
+ * fc_load_grid's), FC_ERR_BUDGET, FC_ERR_CUDA. */
+FC_API fc_status fc_load_grid_osc(fc_ctx* ctx, const fc_osc_model* model, int32_t N_full, const int32_t* collapse,
+                                  int32_t N_fit, int32_t* grid_id);
+
 /* Set the fractional systematic covariance F (N_full x N_full float64,
  * symmetric) of a loaded grid.  The systematic covariance of spectrum s is
  * diag(s) F diag(s); the statistical part is diag(s).  Invalidates the grid's

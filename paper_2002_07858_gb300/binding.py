@@ -31,7 +31,7 @@ EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
            "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
            "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats", "fc_data_dchi2", "fc_fc_region",
-           "fc_fc_region_adaptive"]
+           "fc_fc_region_adaptive", "fc_load_grid_osc"]
 
 
 class FCError(RuntimeError):
@@ -43,6 +43,12 @@ class FCError(RuntimeError):
 class fc_opts(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32), ("top_k", ctypes.c_int32),
                 ("fluct", ctypes.c_int32), ("cov", ctypes.c_int32)]
+
+
+class fc_osc_model(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int32), ("axis_len", ctypes.c_void_p), ("axis_values", ctypes.c_void_p),
+                ("n_terms", ctypes.c_int32), ("amp_axis", ctypes.c_void_p), ("dm2_axis", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("f", ctypes.c_void_p), ("L", ctypes.c_void_p), ("E", ctypes.c_void_p)]
 
 
 class fc_stats(ctypes.Structure):
@@ -99,6 +105,7 @@ def load(build: bool = False):
         "fc_create": (st, [ctypes.POINTER(vp), ctypes.c_int, sz, vp]),
         "fc_destroy": (st, [vp]),
         "fc_load_grid": (st, [vp, vp, i64, i32, vp, i32, ctypes.POINTER(i32)]),
+        "fc_load_grid_osc": (st, [vp, ctypes.POINTER(fc_osc_model), i32, vp, i32, ctypes.POINTER(i32)]),
         "fc_set_frac_cov": (st, [vp, i32, vp, i32]),
         "fc_unload_grid": (st, [vp, i32]),
         "fc_run_points": (st, [vp, i32, vp, i32, u64, i32, ctypes.POINTER(fc_opts), vp, vp, vp]),
@@ -195,6 +202,27 @@ def fc_load_grid(ctx, S, collapse=None, n_fit: int | None = None) -> int:
     nfit = nf if n_fit is None else int(n_fit)
     gid = ctypes.c_int32()
     _check(load().fc_load_grid(ctx, _ptr(S), G, nf, _ptr(coll), nfit, ctypes.byref(gid)), ctx)
+    return gid.value
+
+
+def fc_load_grid_osc(ctx, axes, terms, b, f, L, E, collapse=None, n_fit: int | None = None) -> int:
+    """Grid spectra generated on the device: axes = list of 1-D value arrays (axis 0 slowest),
+    terms = list of (amplitude axis, dm2 axis), b/L/E [N_full], f [n_terms][N_full]."""
+    axes = [_host(a, np.float64) for a in axes]
+    lens = np.array([len(a) for a in axes], np.int32)
+    vals = np.ascontiguousarray(np.concatenate(axes), np.float64)
+    amp = np.array([t[0] for t in terms], np.int32)
+    dm2 = np.array([t[1] for t in terms], np.int32)
+    b, L, E = (_host(x, np.float64) for x in (b, L, E))
+    f = np.ascontiguousarray(_host(f, np.float64).reshape(len(terms), -1))
+    nf = int(b.shape[0])
+    coll = _host(collapse, np.int32)
+    nfit = nf if n_fit is None else int(n_fit)
+    m = fc_osc_model(len(axes), _ptr(lens), _ptr(vals), len(terms), _ptr(amp), _ptr(dm2), _ptr(b), _ptr(f), _ptr(L),
+                     _ptr(E))
+    gid = ctypes.c_int32()
+    _check(load().fc_load_grid_osc(ctx, ctypes.byref(m), nf, _ptr(coll) if coll is not None else None, nfit,
+                                   ctypes.byref(gid)), ctx)
     return gid.value
 
 

@@ -1652,88 +1652,179 @@ fc_status fc_destroy(fc_ctx* c) {
     return FC_OK;
 }
 
-fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const int32_t* collapse, int32_t nfit,
-                       int32_t* grid_id) {
-    if (!c || !S || !grid_id) return fail(FC_ERR_ARG, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Validate the grid's sizes and collapse map (copied to the host in hcoll).
+fc_status check_grid_args(int64_t G, int32_t nf, const int32_t* collapse, int32_t nfit, std::vector<int32_t>* hcoll) {
     if (G < 1 || G > (int64_t)INT32_MAX - 1) return fail(FC_ERR_ARG, "G out of range");
     if (nf < 1 || nf > kMaxBins || nfit < 1 || nfit > kMaxBins) return fail(FC_ERR_ARG, "bins out of range [1, 200]");
     if (!collapse && nfit != nf) return fail(FC_ERR_ARG, "N_fit must equal N_full without a collapse map");
-    std::lock_guard<std::mutex> lk(c->api_mu);
-    cudaSetDevice(c->device);
-    std::vector<int32_t> hcoll;
     if (collapse) {
-        hcoll.resize(nf);
+        hcoll->resize(nf);
         if (is_device_ptr(collapse))
-            FC_CUDA(cudaMemcpy(hcoll.data(), collapse, (size_t)nf * 4, cudaMemcpyDeviceToHost));
+            FC_CUDA(cudaMemcpy(hcoll->data(), collapse, (size_t)nf * 4, cudaMemcpyDeviceToHost));
         else
-            memcpy(hcoll.data(), collapse, (size_t)nf * 4);
+            memcpy(hcoll->data(), collapse, (size_t)nf * 4);
         std::vector<int> seen(nfit, 0);
-        for (int32_t v : hcoll) {
+        for (int32_t v : *hcoll) {
             if (v < 0 || v >= nfit) return fail(FC_ERR_ARG, "collapse map entry out of [0, N_fit)");
             seen[v] = 1;
         }
         for (int v : seen)
             if (!v) return fail(FC_ERR_ARG, "collapse map leaves a fit bin empty");
     }
-    auto g = std::make_unique<Grid>();
+    return FC_OK;
+}
+
+void free_grid_arrays(fc_ctx* c, Grid* g) {
+    dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
+    dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->Sdf); dfree(c, g->centre_df);
+}
+
+// A new grid's sizes and its resident arrays (S_full still to be filled).
+fc_status alloc_grid(fc_ctx* c, Grid* g, int64_t G, int32_t nf, int32_t nfit, const std::vector<int32_t>& hcoll) {
     g->G = G;
     g->G_pad = ((G + kBN - 1) / kBN) * kBN;
     g->nf = nf;
     g->nfit = nfit;
     g->K = screen_k(nfit);
     bool ident = true;
-    if (collapse)
+    if (!hcoll.empty())
         for (int i = 0; i < nf; ++i) ident = ident && (hcoll[i] == i) && (nf == nfit);
     g->identity_collapse = ident;
-    fc_status st = FC_OK;
-    auto cleanup = [&](fc_status s) {
-        dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
-        dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->Sdf); dfree(c, g->centre_df);
-        return s;
-    };
-    if ((st = dalloc_t(c, &g->S_full, (size_t)G * nf)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->S_fit, (size_t)G * nfit)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->centre, (size_t)nfit)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->Sc, (size_t)G * nfit)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->Sdf, (size_t)G * nfit)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->centre_df, (size_t)nfit)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->Sc32, (size_t)G * nfit)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->gnorm, (size_t)G)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->Bt, (size_t)g->G_pad * 2 * g->K)) != FC_OK) return cleanup(st);
-    if ((st = dalloc_t(c, &g->collapse, (size_t)nf)) != FC_OK) return cleanup(st);
-    if ((st = copy_in(c, g->S_full, S, (size_t)G * nf * 8)) != FC_OK) return cleanup(st);
-    if (collapse)
+    FC_TRY(dalloc_t(c, &g->S_full, (size_t)G * nf));
+    FC_TRY(dalloc_t(c, &g->S_fit, (size_t)G * nfit));
+    FC_TRY(dalloc_t(c, &g->centre, (size_t)nfit));
+    FC_TRY(dalloc_t(c, &g->Sc, (size_t)G * nfit));
+    FC_TRY(dalloc_t(c, &g->Sdf, (size_t)G * nfit));
+    FC_TRY(dalloc_t(c, &g->centre_df, (size_t)nfit));
+    FC_TRY(dalloc_t(c, &g->Sc32, (size_t)G * nfit));
+    FC_TRY(dalloc_t(c, &g->gnorm, (size_t)G));
+    FC_TRY(dalloc_t(c, &g->Bt, (size_t)g->G_pad * 2 * g->K));
+    FC_TRY(dalloc_t(c, &g->collapse, (size_t)nf));
+    if (!hcoll.empty())
         FC_CUDA(cudaMemcpyAsync(g->collapse, hcoll.data(), (size_t)nf * 4, cudaMemcpyHostToDevice, c->stream));
-    // spectra must be finite and non-negative
-    {
-        double* mm = nullptr;
-        if ((st = scratch(c, "minmax", 2, &mm)) != FC_OK) return cleanup(st);
-        std::vector<double> hs;
-        // reduce on the host view of a device copy only when S came from the device
-        const bool dev = is_device_ptr(S);
-        if (!dev) {
-            for (int64_t e = 0; e < G * nf; ++e)
-                if (!(S[e] >= 0.0) || !std::isfinite(S[e])) return cleanup(fail(FC_ERR_ARG, "spectra must be finite and >= 0"));
-        } else {
-            hs.resize((size_t)G * nf);
-            FC_CUDA(cudaMemcpy(hs.data(), S, hs.size() * 8, cudaMemcpyDeviceToHost));
-            for (double v : hs)
-                if (!(v >= 0.0) || !std::isfinite(v)) return cleanup(fail(FC_ERR_ARG, "spectra must be finite and >= 0"));
-        }
-    }
-    launch_collapse(g->S_full, G, nf, ident ? nullptr : g->collapse, nfit, g->S_fit, c->stream);
+    return FC_OK;
+}
+
+// Derived arrays of a grid whose S_full is in place (fit-space spectra, centre, the screen's
+// B image and norms, double-float copies), then the grid is registered under a new id.
+fc_status finish_grid(fc_ctx* c, std::unique_ptr<Grid>& g, int32_t* grid_id) {
+    const int64_t G = g->G;
+    const int nf = g->nf, nfit = g->nfit;
+    launch_collapse(g->S_full, G, nf, g->identity_collapse ? nullptr : g->collapse, nfit, g->S_fit, c->stream);
     launch_centre(g->S_fit, G, nfit, g->centre, nullptr, c->stream);
     launch_centred(g->S_fit, g->centre, G, g->G_pad, nfit, g->K, g->Sc, g->Sc32, g->gnorm, g->Bt, c->stream);
     launch_to_df(g->S_fit, G * nfit, g->Sdf, c->stream);
     launch_to_df(g->centre, nfit, g->centre_df, c->stream);
-    if ((st = sync(c)) != FC_OK) return cleanup(st);
-    {
-        std::lock_guard<std::mutex> lq(c->q_mu);
-        g->id = c->next_grid++;
-        *grid_id = g->id;
-        c->grids[g->id] = std::move(g);
-    }
+    FC_TRY(sync(c));
+    std::lock_guard<std::mutex> lq(c->q_mu);
+    g->id = c->next_grid++;
+    *grid_id = g->id;
+    c->grids[g->id] = std::move(g);
     return FC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const int32_t* collapse, int32_t nfit,
+                       int32_t* grid_id) {
+    if (!c || !S || !grid_id) return fail(FC_ERR_ARG, "NULL argument");
+    std::vector<int32_t> hcoll;
+    FC_TRY(check_grid_args(G, nf, collapse, nfit, &hcoll));
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    auto g = std::make_unique<Grid>();
+    fc_status st = alloc_grid(c, g.get(), G, nf, nfit, hcoll);
+    if (st == FC_OK) st = copy_in(c, g->S_full, S, (size_t)G * nf * 8);
+    // spectra must be finite and non-negative (checked on the host copy; a device S is read back)
+    if (st == FC_OK) {
+        std::vector<double> hs;
+        const double* hv = S;
+        if (is_device_ptr(S)) {
+            hs.resize((size_t)G * nf);
+            if (cudaMemcpy(hs.data(), S, hs.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                st = fail(FC_ERR_CUDA, "reading the spectra back failed");
+            hv = hs.data();
+        }
+        for (int64_t e = 0; st == FC_OK && e < G * nf; ++e)
+            if (!(hv[e] >= 0.0) || !std::isfinite(hv[e])) st = fail(FC_ERR_ARG, "spectra must be finite and >= 0");
+    }
+    if (st == FC_OK) st = finish_grid(c, g, grid_id);
+    if (st != FC_OK && g) free_grid_arrays(c, g.get());
+    return st;
+}
+
+fc_status fc_load_grid_osc(fc_ctx* c, const fc_osc_model* m, int32_t nf, const int32_t* collapse, int32_t nfit,
+                           int32_t* grid_id) {
+    if (!c || !m || !grid_id || !m->axis_len || !m->axis_values || !m->amp_axis || !m->dm2_axis || !m->b || !m->f ||
+        !m->L || !m->E)
+        return fail(FC_ERR_ARG, "NULL argument");
+    if (m->D < 1 || m->D > kMaxOscAxes) return fail(FC_ERR_ARG, "D out of range [1, 8]");
+    if (m->n_terms < 1 || m->n_terms > kMaxOscTerms) return fail(FC_ERR_ARG, "n_terms out of range [1, 4]");
+    int64_t G = 1;
+    std::vector<int32_t> off(m->D);
+    int32_t n_vals = 0;
+    for (int a = 0; a < m->D; ++a) {
+        if (m->axis_len[a] < 1) return fail(FC_ERR_ARG, "axis length < 1");
+        off[a] = n_vals;
+        n_vals += m->axis_len[a];
+        G *= m->axis_len[a];
+        if (G > (int64_t)INT32_MAX - 1) return fail(FC_ERR_ARG, "G out of range");
+    }
+    for (int t = 0; t < m->n_terms; ++t)
+        if (m->amp_axis[t] < 0 || m->amp_axis[t] >= m->D || m->dm2_axis[t] < 0 || m->dm2_axis[t] >= m->D)
+            return fail(FC_ERR_ARG, "term axis out of [0, D)");
+    for (int i = 0; i < nf && i < kMaxBins; ++i)
+        if (!(m->E[i] > 0.0) || !std::isfinite(m->L[i]) || !std::isfinite(m->E[i]))
+            return fail(FC_ERR_ARG, "energies must be > 0 and baselines finite");
+    std::vector<int32_t> hcoll;
+    FC_TRY(check_grid_args(G, nf, collapse, nfit, &hcoll));
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    // the model's small arrays, packed: lengths, offsets, term axes | axis values, b, f, L, E
+    std::vector<int32_t> hi;
+    hi.insert(hi.end(), m->axis_len, m->axis_len + m->D);
+    hi.insert(hi.end(), off.begin(), off.end());
+    hi.insert(hi.end(), m->amp_axis, m->amp_axis + m->n_terms);
+    hi.insert(hi.end(), m->dm2_axis, m->dm2_axis + m->n_terms);
+    hi.push_back(0);  // the count of invalid entries
+    std::vector<double> hd;
+    hd.insert(hd.end(), m->axis_values, m->axis_values + n_vals);
+    const size_t o_b = hd.size();
+    hd.insert(hd.end(), m->b, m->b + nf);
+    const size_t o_f = hd.size();
+    hd.insert(hd.end(), m->f, m->f + (size_t)m->n_terms * nf);
+    const size_t o_L = hd.size();
+    hd.insert(hd.end(), m->L, m->L + nf);
+    const size_t o_E = hd.size();
+    hd.insert(hd.end(), m->E, m->E + nf);
+    int32_t* di = nullptr;
+    double* dd = nullptr;
+    FC_TRY(scratch(c, "osc_i", hi.size(), &di));
+    FC_TRY(scratch(c, "osc_d", hd.size(), &dd));
+    FC_CUDA(cudaMemcpyAsync(di, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    FC_CUDA(cudaMemcpyAsync(dd, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    auto g = std::make_unique<Grid>();
+    fc_status st = alloc_grid(c, g.get(), G, nf, nfit, hcoll);
+    int bad = 0;
+    if (st == FC_OK) {
+        const int D = m->D, T = m->n_terms;
+        int* dbad = di + 2 * D + 2 * T;
+        launch_osc_spectra(G, nf, D, di, di + D, dd, T, di + 2 * D, di + 2 * D + T, dd + o_b, dd + o_f, dd + o_L,
+                           dd + o_E, g->S_full, dbad, c->stream);
+        if (cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            st = fail(FC_ERR_CUDA, "reading the generator's check back failed");
+        if (st == FC_OK) st = sync(c);
+        if (st == FC_OK && bad) st = fail(FC_ERR_ARG, "the model gives spectra that are not finite and >= 0");
+    }
+    if (st == FC_OK) st = finish_grid(c, g, grid_id);
+    if (st != FC_OK && g) free_grid_arrays(c, g.get());
+    return st;
 }
 
 fc_status fc_set_frac_cov(fc_ctx* c, int32_t grid_id, const double* F, int32_t nf) {

@@ -231,6 +231,13 @@ void launch_advance(const int32_t* active, int64_t n_active, const int32_t* best
 
 // ---- quantiles ----
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st);
+// grid spectra of an oscillation shape model (see fc_load_grid_osc); *bad += entries not finite and >= 0
+constexpr int kMaxOscAxes = 8;
+constexpr int kMaxOscTerms = 4;
+void launch_osc_spectra(int64_t G, int nf, int D, const int32_t* axis_len, const int32_t* axis_off,
+                        const double* axis_val, int n_terms, const int32_t* amp_ax, const int32_t* dm2_ax,
+                        const double* b, const double* f, const double* L, const double* E, double* S, int* bad,
+                        cudaStream_t st);
 // counts[r] += #{u : x[r][u] < thr[r]} for rows r < rows of x [rows][n]
 void launch_count_below(const double* x, int rows, int n, const double* thr, int64_t* counts, cudaStream_t st);
 

@@ -157,6 +157,39 @@ __global__ void k_collapse(const double* __restrict__ S, int64_t G, int nf, cons
     for (int j = 0; j < nfit; ++j) out[g * nfit + j] = acc[j];
 }
 
+// Grid spectra from an oscillation shape model, one thread per (grid point,
+// full bin): s_i(p) = b_i + sum_t amp_t(p) sin^2(1.27 dm2_t(p) L_i / E_i) f_ti,
+// the terms added in order t = 0, 1, ... to b_i.  Grid point p is the
+// row-major index over the axes (axis 0 slowest); term t reads its amplitude
+// from axis amp_ax[t] and its dm2 from axis dm2_ax[t].  bad counts entries
+// that are not finite and >= 0.
+__global__ void k_osc_spectra(int64_t G, int nf, int D, const int32_t* __restrict__ axis_len,
+                              const int32_t* __restrict__ axis_off, const double* __restrict__ axis_val, int n_terms,
+                              const int32_t* __restrict__ amp_ax, const int32_t* __restrict__ dm2_ax,
+                              const double* __restrict__ b, const double* __restrict__ f,
+                              const double* __restrict__ L, const double* __restrict__ E, double* __restrict__ S,
+                              int* __restrict__ bad) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= G * nf) return;
+    const int64_t g = e / nf;
+    const int i = (int)(e % nf);
+    int idx[kMaxOscAxes];
+    int64_t rem = g;
+    for (int a = D - 1; a >= 0; --a) {
+        idx[a] = (int)(rem % axis_len[a]);
+        rem /= axis_len[a];
+    }
+    double v = b[i];
+    for (int t = 0; t < n_terms; ++t) {
+        const double amp = axis_val[axis_off[amp_ax[t]] + idx[amp_ax[t]]];
+        const double dm2 = axis_val[axis_off[dm2_ax[t]] + idx[dm2_ax[t]]];
+        const double sn = sin(1.27 * dm2 * L[i] / E[i]);
+        v += amp * (sn * sn) * f[t * nf + i];
+    }
+    S[e] = v;
+    if (!(v >= 0.0) || !isfinite(v)) atomicAdd(bad, 1);
+}
+
 // Approximate per-bin median of the grid spectra by two rounds of a 4096-bucket
 // histogram; it only chooses the centring vector of the screen, any value works.
 __global__ void k_centre(const double* __restrict__ S, int64_t G, int nfit, double* __restrict__ centre) {
@@ -1657,6 +1690,17 @@ void launch_count_below(const double* x, int rows, int n, const double* thr, int
     if (rows <= 0 || n <= 0) return;
     count_launch();
     k_count_below<<<rows, 256, 0, st>>>(x, n, thr, counts);
+}
+
+void launch_osc_spectra(int64_t G, int nf, int D, const int32_t* axis_len, const int32_t* axis_off,
+                        const double* axis_val, int n_terms, const int32_t* amp_ax, const int32_t* dm2_ax,
+                        const double* b, const double* f, const double* L, const double* E, double* S, int* bad,
+                        cudaStream_t st) {
+    const int64_t n = G * nf;
+    if (n <= 0) return;
+    count_launch();
+    k_osc_spectra<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, nf, D, axis_len, axis_off, axis_val, n_terms, amp_ax,
+                                                                dm2_ax, b, f, L, E, S, bad);
 }
 
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st) {

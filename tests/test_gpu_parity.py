@@ -302,6 +302,35 @@ def test_data_dchi2_and_region(fc, ctx, w1, w2):
     assert e.value.status == fc.FC_ERR_ARG
 
 
+def test_device_generated_grid(fc, ctx, w2):
+    """Spectra generated on the device from the shape model behind the 100x100 grid give the
+    same fit as the host-generated spectra (plain path to 1e-9, mixed path to 1e-4)."""
+    m = workloads.osc_2d_model(100, 100, 90, seed=0)
+    gd = fc.fc_load_grid_osc(ctx, [m["dm2"], m["s2t"]], [(1, 0)], m["b"], m["f"][None, :], m["L"], m["E"],
+                             w2.collapse, w2.n_fit)
+    fc.fc_set_frac_cov(ctx, gd, w2.F)
+    gh = grid(fc, ctx, w2)
+    pts = _cfg2_points(w2, 24)
+    for prec, tol in ((fc.FC_PREC_FP64, TOL_PLAIN), (fc.FC_PREC_MIXED, TOL_MIXED)):
+        dd, bd, nd = fc.fc_run_points(ctx, gd, pts, 9, 64, dict(precision=prec))
+        dh, bh, nh = fc.fc_run_points(ctx, gh, pts, 9, 64, dict(precision=prec))
+        err = np.abs(dd - dh) / np.maximum(np.abs(dh), 1.0)
+        assert err.max() <= tol, (prec, err.max())
+        assert (bd == bh).mean() >= 0.99
+    # both grids' fake data are the oracle's bit for bit
+    fd = fc.fc_fake_data(ctx, gd, pts[:4], 3, 16, w2.n_fit)
+    np.testing.assert_array_equal(fd, oracle.fake_data(w2.S, w2.F, pts[:4], 3, 16, collapse=w2.collapse,
+                                                       n_fit=w2.n_fit))
+    fc.fc_unload_grid(ctx, gd)
+    for bad in (dict(E=-m["E"]), dict(terms=[(2, 0)])):
+        kw = dict(axes=[m["dm2"], m["s2t"]], terms=[(1, 0)], b=m["b"], f=m["f"][None, :], L=m["L"], E=m["E"],
+                  collapse=w2.collapse, n_fit=w2.n_fit)
+        kw.update(bad)
+        with pytest.raises(fc.FCError) as e:
+            fc.fc_load_grid_osc(ctx, **kw)
+        assert e.value.status == fc.FC_ERR_ARG
+
+
 def _adaptive_reference(w, pts, data_dchi2, cl, U0, U_max, z, seed):
     """The adaptive acceptance rule restated on the oracle's universes: round r draws
     U0, then as many universes as a still-open point has (key seed + r), counts those

@@ -80,15 +80,11 @@ def _frac_cov(rng, n, rank=5, diag=0.2, sig_lo=0.05, sig_hi=0.2):
     return F, sig
 
 
-def osc_2d(n_dm2: int, n_th: int, n_full: int, seed: int = 0):
-    """Two-parameter grid (dm2 slow axis, sin^2 2theta fast axis).
-
-    s_i(p) = b_i + sin^2(2theta) * sin^2(1.27 dm2 L_i / E_i) * f_i with
-    dm2 log-spaced over [1e-2, 1e2] eV^2, sin^2 2theta log-spaced over [1e-4, 1],
-    E_i linear over [0.2, 3] GeV.  Draw order from default_rng(seed):
-    b ~ U(50,500), f ~ U(5,50), sig ~ U(0.05,0.2), W ~ N(0,1)[N x 5],
-    L ~ choice{110,470,600}.
-    """
+def osc_2d_model(n_dm2: int, n_th: int, n_full: int, seed: int = 0) -> dict:
+    """The shape model behind osc_2d: axes dm2 (log-spaced over [1e-2, 1e2] eV^2)
+    and sin^2 2theta (log-spaced over [1e-4, 1]), E_i linear over [0.2, 3] GeV.
+    Draw order from default_rng(seed): b ~ U(50,500), f ~ U(5,50),
+    sig ~ U(0.05,0.2), W ~ N(0,1)[N x 5], L ~ choice{110,470,600}; F from sig, W."""
     rng = np.random.default_rng(seed)
     n = n_full
     b = rng.uniform(50.0, 500.0, n)
@@ -101,12 +97,20 @@ def osc_2d(n_dm2: int, n_th: int, n_full: int, seed: int = 0):
     C = W @ W.T + 0.2 * np.eye(n)
     F = sig[:, None] * C * sig[None, :]
     F = 0.5 * (F + F.T)
-    dm2 = np.logspace(-2, 2, n_dm2)
-    s2t = np.logspace(-4, 0, n_th)
+    return {"b": b, "f": f, "L": L, "E": E, "F": F, "dm2": np.logspace(-2, 2, n_dm2),
+            "s2t": np.logspace(-4, 0, n_th)}
+
+
+def osc_2d(n_dm2: int, n_th: int, n_full: int, seed: int = 0):
+    """Two-parameter grid (dm2 slow axis, sin^2 2theta fast axis) of osc_2d_model:
+    s_i(p) = b_i + sin^2(2theta) * sin^2(1.27 dm2 L_i / E_i) * f_i."""
+    m = osc_2d_model(n_dm2, n_th, n_full, seed)
+    b, f, L, E, dm2, s2t = m["b"], m["f"], m["L"], m["E"], m["dm2"], m["s2t"]
+    n = n_full
     osc = np.sin(1.27 * dm2[:, None] * L[None, :] / E[None, :]) ** 2   # [n_dm2, n]
     S = b[None, None, :] + s2t[None, :, None] * osc[:, None, :] * f[None, None, :]
     S = np.ascontiguousarray(S.reshape(n_dm2 * n_th, n))
-    return S, F, (dm2, s2t)
+    return S, m["F"], (dm2, s2t)
 
 
 def cfg1(U: int = 1000) -> Workload:
