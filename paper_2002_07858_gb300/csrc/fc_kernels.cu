@@ -43,23 +43,10 @@ __device__ __forceinline__ void warp_argmin(double& v, int32_t& g) {
     }
 }
 
-// Residual form ||W r||^2, r = s - d, A = W^T W (W lower triangular), binary64.
-__device__ double resid_chi2(const double* __restrict__ W, int n, const double* __restrict__ s,
-                             const float* __restrict__ du) {
-    double r[kMaxBins];
-    for (int j = 0; j < n; ++j) r[j] = s[j] - (double)du[j];
-    double acc = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double* Wi = W + i * n;
-        double t = 0.0;
-        for (int j = 0; j <= i; ++j) t = fma(Wi[j], r[j], t);
-        acc = fma(t, t, acc);
-    }
-    return acc;
-}
-
-// resid_chi2 spread over a warp with the same bits: lanes form the row dot
-// products t_i (each summed over j in order), lane 0 sums t_i^2 in row order.
+// The plain path's residual form ||W r||^2 (r = s - d, A = W^T W, W lower
+// triangular) in binary64, spread over a warp: lanes form the row dot products
+// t_i = sum_{j<=i} W_ij r_j (each summed over j in increasing order with fma),
+// lane 0 sums t_i^2 in row order with fma.
 // r and t are this warp's shared-memory vectors; the result is lane 0's.
 __device__ double resid_chi2_warp(const double* __restrict__ W, int n, const double* r, double* t, int lane) {
     for (int i = lane; i < n; i += 32) {
@@ -1354,7 +1341,7 @@ __global__ void __launch_bounds__(128) k_finish(const int32_t* __restrict__ list
         cp = (p == g) ? 0.0 : resid_df_warp(W, nfit, Sdf + (int64_t)p * nfit, du, fr[w], ft[w], lane);
         cm = resid_df_warp(W, nfit, Sdf + (int64_t)g * nfit, du, fr[w], ft[w], lane);
     } else {
-        // plain path: binary64, in the summation order of resid_chi2
+        // plain path: binary64, in the summation order of resid_chi2_warp
         for (int j = lane; j < nfit; j += 32) {
             rp[w][j] = Sfit[(int64_t)p * nfit + j] - (double)du[j];
             rm[w][j] = Sfit[(int64_t)g * nfit + j] - (double)du[j];
