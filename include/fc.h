@@ -288,9 +288,10 @@ FC_API fc_status fc_poll(fc_ctx* ctx, uint64_t ticket, double* latency_ms);
 FC_API fc_status fc_cancel(fc_ctx* ctx, uint64_t ticket);
 
 /* Fake data exactly as fc_fake_data produces it, for callers that cannot
- * allocate device memory when they need it: work recorded into a CUDA graph by
- * stream capture, code running inside another framework's allocator callback,
- * or request paths that must not allocate after start-up.  The paper has no
+ * allocate device memory when they need it: code running inside another
+ * framework's allocator callback (which may not re-enter the allocator), or
+ * services whose request paths must not allocate after start-up (an
+ * allocation can stall on the device or fail under memory pressure).  The paper has no
  * counterpart; it is a deployment variant of §2 step 2.
  * All pointers are device memory: S [G][N_full] float64, collapse [N_full]
  * int32 (NULL = identity, then N_fit == N_full), F [N_full][N_full] float64,

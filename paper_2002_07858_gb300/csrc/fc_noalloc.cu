@@ -1,10 +1,10 @@
 // fc_noalloc.cu -- fake-data generation that allocates no device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need fake data:
-// code recorded into a CUDA graph by stream capture (an allocation there
-// either breaks the capture or is not replayed), callers that run inside
-// another framework's allocator hook or callback, and services that forbid
-// device allocation on their request path after start-up.  For them
+// callers that run inside another framework's allocator hook or callback
+// (which may not re-enter the allocator), and services that forbid device
+// allocation on their request path after start-up (an allocation can stall
+// on the device or fail under memory pressure).  For them
 // fc_fake_data_noalloc produces exactly the output of fc_fake_data while its
 // only scratch memory (the per-point systematic Cholesky factors and a status
 // word) lives in the file-scope array below.

@@ -1,8 +1,8 @@
 """The allocation-free fake-data entry point (fc_fake_data_noalloc).
 
 It exists for callers that cannot allocate device memory where they need fake
-data (stream capture into a CUDA graph, allocator callbacks, request paths
-that must not allocate).  Its output must equal fc_fake_data's -- bit for bit,
+data (code inside another framework's allocator callback, request paths that
+must not allocate after start-up).  Its output must equal fc_fake_data's -- bit for bit,
 the fake-data tolerance used everywhere else -- on consecutive calls that
 share its static scratch.  This file is collected last on purpose.
 """
