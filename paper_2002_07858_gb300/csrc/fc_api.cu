@@ -1048,7 +1048,11 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 ra.list_n = lnum;
                 stage_begin(c);
                 if (listing)
-                    launch_resolve_list(ra, ccount, n_tiles, c->stream);
+                {
+                    int32_t* lrows = nullptr;
+                    FC_TRY(scratch(c, "lrows", (size_t)n_tiles * kBM, &lrows));
+                    launch_resolve_list(ra, ccount, n_tiles, cnt, lrows, cnts + 6, c->stream);
+                }
                 else
                     launch_resolve(ra, n_tiles, c->stream);
                 FC_TRY(stage_end(c, &S->ms_rescore));

@@ -207,7 +207,9 @@ struct ResolveArgs {
 void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st);
 // Third round: binary64 residual chi2 of every listed candidate of each row
 // (complete lists certify the minimum); overflowing rows go to `fb`.
-void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, cudaStream_t st);
+// list rounds: n_rows = universes in the round's tiles; rows [n_tiles * BM] and n_rows_dev are scratch
+void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, int64_t n_rows,
+                         int32_t* rows, int32_t* n_rows_dev, cudaStream_t st);
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st);
 
 // ---- final residual-form chi2 and dchi2 ----

@@ -1221,27 +1221,25 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
 // Third round: every grid point whose screen lower bound is at or below the
 // row's seed (an upper bound of the minimum) is listed, so the binary64
 // residual-form minimum over a complete list is the minimum of the scan.
-// One warp per row, W in shared memory; lanes split the list, then the first
-// minimum (lowest index among equal values) is taken across the warp.  The row
-// then finishes (dchi2) or advances exactly as in k_resolve; rows whose list
-// overflowed go to the exact scan.
-__global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32_t* __restrict__ cand_count) {
-    extern __shared__ float2 sWd[];
-    const int64_t t = blockIdx.x;
+// One warp per listed row (rows[] holds the round's occupied tile rows, so no
+// warp idles on the padding of a sparsely filled tile); lanes split the list,
+// then the first minimum (lowest index among equal values) is taken across the
+// warp.  The row then finishes (dchi2) or advances exactly as in k_resolve;
+// rows whose list overflowed go to the exact scan.
+__global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32_t* __restrict__ cand_count,
+                                                      const int32_t* __restrict__ rows, int64_t n_rows,
+                                                      const int32_t* __restrict__ n_rows_dev) {
     const int n = a.nfit;
-    const int slot = a.tile_slot[t];
-    const float2* Wg = a.Wdf + (size_t)slot * n * n;
-    const bool staged = (n <= kResolveMaxN);
-    if (staged)
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sWd[e] = Wg[e];
-    __syncthreads();
-    const float2* W = staged ? sWd : Wg;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ float2 s_r[8][kMaxBins], s_t[8][kMaxBins];
-    for (int r = warp; r < kBM; r += blockDim.x >> 5) {
-        const int u = a.tile_univ[t * kBM + r];
-        if (u < 0) continue;
-        const int64_t row = t * kBM + r;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (w >= n_rows || w >= *n_rows_dev) return;
+    {
+        const int64_t row = rows[w];
+        const int64_t t = row / kBM;
+        const int u = a.tile_univ[row];
+        // W of the row's tile (double-float, read through L1: the warp's lanes read the same element)
+        const float2* W = a.Wdf + (size_t)a.tile_slot[t] * n * n;
         const int n0 = cand_count[row * 2], n1 = cand_count[row * 2 + 1];
         // where the two half-row lists live and whether they are complete
         int64_t base0, base1;
@@ -1263,7 +1261,7 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
                 a.fb[atomicAdd(a.n_fb, 1)] = u;
                 atomicAdd(&a.counters[1], 1ull);
             }
-            continue;
+            return;
         }
         const float* du = a.d + (size_t)u * n;
         double bv = DBL_MAX;
@@ -1618,18 +1616,28 @@ void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr,
     k_min_tau<<<blocks_for(n_tiles * kBM), kThreads, 0, st>>>(tile_univ, n_tiles * kBM, thr, tau0);
 }
 
-void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, cudaStream_t st) {
-    if (n_tiles <= 0) return;
-    const size_t smem = a.nfit <= kResolveMaxN ? (size_t)a.nfit * a.nfit * sizeof(float2) : 0;
-    // static per-warp vectors plus a staged W exceed the 48 KB default
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_resolve_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kResolveMaxN * kResolveMaxN * (int)sizeof(float2));
-        attr = true;
-    }
+// rows[] <- the indices t * BM + r of the tile rows that hold a universe (any order)
+__global__ void k_list_rows(const int32_t* __restrict__ tile_univ, int64_t n, int32_t* __restrict__ rows,
+                            int32_t* __restrict__ n_rows) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool have = e < n && tile_univ[e] >= 0;
+    const unsigned m = __ballot_sync(0xffffffffu, have);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int first = 0;
+    if (lane == leader) first = atomicAdd(n_rows, __popc(m));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (have) rows[first + __popc(m & ((1u << lane) - 1u))] = (int32_t)e;
+}
+
+void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, int64_t n_rows,
+                         int32_t* rows, int32_t* n_rows_dev, cudaStream_t st) {
+    if (n_tiles <= 0 || n_rows <= 0) return;
+    cudaMemsetAsync(n_rows_dev, 0, 4, st);
     count_launch();
-    k_resolve_list<<<(unsigned)n_tiles, 256, smem, st>>>(a, cand_count);
+    k_list_rows<<<blocks_for(n_tiles * kBM), kThreads, 0, st>>>(a.tile_univ, n_tiles * kBM, rows, n_rows_dev);
+    count_launch();
+    k_resolve_list<<<(unsigned)((n_rows + 7) / 8), 256, 0, st>>>(a, cand_count, rows, n_rows, n_rows_dev);
 }
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
