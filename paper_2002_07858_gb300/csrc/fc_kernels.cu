@@ -1082,6 +1082,7 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
     int32_t g_best = -1;
     double chi2_min = 0.0;
     bool have_min = false;
+    bool early = false;  // decided here and finishing: chi2_p, chi2_min join the rescoring pass
     float lb[kMaxTopK], ub[kMaxTopK];
     bool full = false;
     float tau = FLT_MAX, min_ub = FLT_MAX;
@@ -1113,6 +1114,16 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         } else if (nR == 1 && ub[0] < tau) {
             state = 1;
             g_best = s_g[r][0];
+            // a universe that finishes on this certificate needs chi2_p and chi2_min in residual
+            // form; they join the rescoring items below instead of a pass of their own
+            if (g_best == a.cur[u] || a.nscan[u] + 1 >= a.maxit[u]) {
+                early = true;
+                const int32_t pp = a.pt[u];
+                s_g[r][kItemP] = pp;
+                s_g[r][kItemMin] = g_best;
+                if (pp != g_best) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemP);
+                s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemMin);
+            }
         } else {
             state = 2;
             for (int j = 0; j < topk; ++j)
@@ -1180,10 +1191,12 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         finishing = (g_best == a.cur[u]) || (a.nscan[u] + 1 >= a.maxit[u]);
         if (finishing) {
             p = a.pt[u];
-            s_g[r][kItemP] = p;
-            s_g[r][kItemMin] = g_best;
-            if (p != g_best) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemP);
-            if (!have_min) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemMin);
+            if (!early) {
+                s_g[r][kItemP] = p;
+                s_g[r][kItemMin] = g_best;
+                if (p != g_best) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemP);
+                if (!have_min) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemMin);
+            }
         } else {
             a.cur[u] = g_best;
             a.nscan[u] = (int8_t)(a.nscan[u] + 1);
