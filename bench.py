@@ -4,7 +4,7 @@
 Workload (one step = one full FC job): the D=2 100x100 grid, N_full = 90 bins
 collapsed pairwise to 45, every one of the 10^4 grid points a true point with
 U = 1000 universes (10^7 fits), covariance refit until the best fit repeats
-(<= 5 scans), tensor-core screen + certified binary64 rescoring.  Each step
+(<= 5 scans), tensor-core screen + certified double-float rescoring.  Each step
 starts from a cold covariance cache (fc_set_frac_cov), so covariance builds,
 inversions and q-vectors are inside the timed region.
 
@@ -344,7 +344,8 @@ def run_native(args):
         clocks = clk.summary()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32acc screen, f64 rescoring/cov",
+                "scaling": "weak", "vs_baseline": None, "dtype": ("bf16 hi/lo x3 screen with f32 accumulation; rescoring in double-float "
+                                                      "(2 x f32, ~48 bits); f64 covariances"),
                 "data": "synthetic",
                 "config": {"workload": desc,
                            "global_batch": n * ws, "true_points": P, "universes_per_point": U,
@@ -459,7 +460,7 @@ def run_serve(args):
             "config": {"workload": "cfg4 serving stream: 8 resident grids (D 2-4, G log-U[1e3,1e6], N U{40..200}), "
                                    "one true point per job, U log-U[100,1e4], Poisson arrivals",
                        "grids": [w.name for w in pool], "hbm_budget_bytes": 80 << 30,
-                       "precision": "mixed (tensor-core screen + binary64 rescoring)", "max_iter": 5},
+                       "precision": "mixed (tensor-core screen + double-float rescoring)", "max_iter": 5},
             "overload": over, "below_saturation": low, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     fc.fc_destroy(ctx)

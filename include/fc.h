@@ -59,7 +59,11 @@ typedef enum {
 } fc_status;
 
 enum { FC_PREC_FP64 = 0,     /* plain path: every step in binary64 on CUDA cores        */
-       FC_PREC_MIXED = 1 };  /* BF16 tensor-core screen (tcgen05) + binary64 rescoring  */
+       FC_PREC_MIXED = 1 };  /* BF16 tensor-core screen (tcgen05) with a certified
+                                bound; candidates rescored in residual form in
+                                double-float (a value = two binary32, about 48
+                                significant bits, on the FP32 pipe -- not binary64);
+                                covariances, Cholesky and inverse in binary64 */
 enum { FC_FLUCT_POISSON_SYS = 0,  /* d = Poisson(max(0, s + L z)), L = chol(diag(s)F diag(s)) */
        FC_FLUCT_GAUSS = 1 };      /* test mode: d = s + L z, L = chol(diag(s)F diag(s)+diag(s)) */
 enum { FC_COV_ITERATE = 0,   /* §2 step 5: refit the covariance at q_min until stable   */
@@ -76,7 +80,7 @@ typedef struct {
 
 /* Kernel choices of one grid.  They change speed only: every choice gives
  * the same dchi2, best fits and scan counts (the screen's decisions are
- * certified and resolved in binary64).  fc_autotune picks them by timing. */
+ * certified and resolved in double-float residual form).  fc_autotune picks them by timing. */
 enum { FC_QVEC_AUTO = 0,     /* tensor cores (the faster kernel at every N_fit)      */
        FC_QVEC_SIMT = 1,     /* q_g = s~^T A s~ in binary32, A in shared memory    */
        FC_QVEC_TC = 2 };     /* q_g = |W s~|^2 on tcgen05 (bf16 hi/lo), K <= 128  */
@@ -103,9 +107,11 @@ typedef struct {
     int64_t chi2_evals;       /* universe-scans x G: chi2 values the scans decided on */
     int64_t distinct_cov;     /* covariances built and inverted                       */
     int64_t screened;         /* universe-scans decided by the tensor-core screen     */
-    int64_t rescored;         /* universe-scans that needed binary64 rescoring        */
+    int64_t rescored;         /* universe-scans whose candidates needed double-float
+                                 residual rescoring                                  */
     int64_t rescreened;       /* universe-scans whose first certificate failed -> second screen round */
-    int64_t fallback;         /* universe-scans no certified round decided -> exact fp64 scan */
+    int64_t fallback;         /* universe-scans no certified round decided -> exact
+                                 residual scan over every g (double-float)           */
     int64_t kernel_launches;  /* CUDA kernels launched by the call                    */
     int64_t screen_launches;  /* launches of the tensor-core screen kernel             */
     double  screen_flops;     /* algorithmic flops of those launches: 2 N_fit per eval */
@@ -117,6 +123,10 @@ typedef struct {
     int64_t big_listed;       /* universe-scans sent to the exact-size list round     */
     int64_t screen_tiles;     /* 128-row universe tiles screened (all launches)       */
     int64_t screen_rows;      /* universe rows in them (fill = rows / (128 tiles))    */
+    int64_t deferred;         /* serving: admission turns a queued job waited for memory
+                                 (the budget held by running jobs)                   */
+    int64_t device_bytes;     /* device memory the context holds now (all grids,
+                                 caches, lanes and scratch)                          */
 } fc_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -211,7 +221,7 @@ FC_API fc_status fc_covariance(fc_ctx* ctx, int32_t grid_id, int64_t q, double* 
 /* One scan (§2 steps 3-4) of caller data against the grid under A(q_cov[u]):
  * d [U][N_fit] float32, q_cov [U] int64.  Outputs [U]: best (int64 first
  * index of the minimum), chi2_min (float64, residual form).  precision selects
- * the plain binary64 scan or the tensor-core screen with certified binary64
+ * the plain binary64 scan or the tensor-core screen with certified double-float
  * rescoring.  Errors as above. */
 FC_API fc_status fc_scan(fc_ctx* ctx, int32_t grid_id, const float* d, const int64_t* q_cov, int32_t U,
                   int32_t precision, int32_t top_k, int64_t* best, double* chi2_min);
@@ -304,7 +314,12 @@ FC_API fc_status fc_cancel(fc_ctx* ctx, uint64_t ticket);
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the array: calls whose work overlaps on the GPU
- * race.  Errors: FC_ERR_ARG, FC_ERR_NOT_SPD, FC_ERR_CUDA (fc_last_error(NULL)). */
+ * race.  The point indices and the collapse map (entries in [0, N_fit), no
+ * fit bin left empty) are checked on the device before use.  Any P the
+ * scratch limit admits is accepted (launches are split as needed).
+ * Errors: FC_ERR_ARG (sizes, a point index or collapse entry out of range),
+ * FC_ERR_NOT_SPD, FC_ERR_CUDA (a failed copy or launch) -- message in
+ * fc_last_error(NULL). */
 FC_API fc_status fc_fake_data_noalloc(const double* S, int64_t G, int32_t N_full, const int32_t* collapse,
                                       int32_t N_fit, const double* F, const int64_t* ps, int32_t P, uint64_t seed,
                                       int32_t U, int32_t fluct, float* d, void* cuda_stream);
@@ -324,6 +339,33 @@ FC_API fc_status fc_get_tuning(fc_ctx* ctx, int32_t grid_id, fc_tuning* t);
  * skips the timing, a miss appends the new result.  The covariance cache is
  * cleared afterwards.  Errors: as fc_run_points. */
 FC_API fc_status fc_autotune(fc_ctx* ctx, int32_t grid_id, const char* cache_path, fc_tuning* out);
+
+/* Test hook for failure detection without a GPU fault.  Every wait of the
+ * tensor-core screen on a pipeline barrier is bounded; when one runs out the
+ * kernel records a timeout, lets the copies it issued land, frees its tensor
+ * memory and returns, and the call gives FC_ERR_TIMEOUT with the context still
+ * usable.  wait_ns: limit of those waits on this context (0 = the built-in
+ * 2 s; at most 2 s).  screen_stop_after: >= 0 makes the copy producer of every
+ * screen CTA stop issuing after that many pipeline stages, so that the
+ * consumers' waits run out; -1 (default) = off.  Errors: FC_ERR_ARG. */
+FC_API fc_status fc_set_wait_test(fc_ctx* ctx, uint64_t wait_ns, int64_t screen_stop_after);
+
+/* Which certified rounds decided the scans of each universe in the last
+ * synchronous fit on this context (fc_run_points, fc_run_point, fc_scan,
+ * fc_data_dchi2): out [n] uint8 (host or device), [P][U] order, n = that
+ * call's universe count; each entry ORs the FC_DECIDED_* bit of every round
+ * that decided one of the universe's scans.  A diagnostic for tests: which
+ * round decides never changes a result bit, because every round evaluates the
+ * residual form in the same order (§2 steps 3-4, Algorithm 2).
+ * Errors: FC_ERR_ARG (n is not the last fit's count), FC_ERR_STATE (no fit). */
+enum { FC_DECIDED_CERT = 1,        /* top-k screen bounds alone certified the minimum    */
+       FC_DECIDED_RESCORED = 2,    /* top-k candidates rescored, then certified          */
+       FC_DECIDED_TOP16 = 4,       /* top-16 round (FC_ROUND_TOPK policy)                */
+       FC_DECIDED_LIST = 8,        /* list round: every g whose bound is below the best  */
+       FC_DECIDED_EXACT_LIST = 16, /* the same with exact-size lists (long lists)        */
+       FC_DECIDED_SCAN = 32,       /* residual form over every g (mixed path's last step)*/
+       FC_DECIDED_PLAIN = 64 };    /* plain binary64 scan (FC_PREC_FP64)                 */
+FC_API fc_status fc_get_decided_by(fc_ctx* ctx, uint8_t* out, int64_t n);
 
 /* Counters of the last synchronous run on this context. */
 FC_API fc_status fc_get_stats(fc_ctx* ctx, fc_stats* out);

@@ -22,6 +22,8 @@ FC_FLUCT_POISSON_SYS, FC_FLUCT_GAUSS = 0, 1
 FC_COV_ITERATE, FC_COV_FIXED, FC_COV_IDENTITY = 0, 1, 2
 FC_QVEC_AUTO, FC_QVEC_SIMT, FC_QVEC_TC = 0, 1, 2
 FC_ROUND_AUTO, FC_ROUND_TOPK, FC_ROUND_LIST = 0, 1, 2
+FC_DECIDED_CERT, FC_DECIDED_RESCORED, FC_DECIDED_TOP16, FC_DECIDED_LIST = 1, 2, 4, 8
+FC_DECIDED_EXACT_LIST, FC_DECIDED_SCAN, FC_DECIDED_PLAIN = 16, 32, 64
 
 _STATUS_NAMES = {0: "FC_OK", 1: "FC_PENDING", -1: "FC_ERR_ARG", -2: "FC_ERR_NOT_SPD", -3: "FC_ERR_BUDGET",
                  -4: "FC_ERR_CUDA", -5: "FC_ERR_TIMEOUT", -6: "FC_ERR_CANCELLED", -7: "FC_ERR_NOT_FOUND",
@@ -31,7 +33,7 @@ EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
            "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
            "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats", "fc_data_dchi2", "fc_fc_region",
-           "fc_fc_region_adaptive", "fc_load_grid_osc"]
+           "fc_fc_region_adaptive", "fc_load_grid_osc", "fc_get_decided_by", "fc_set_wait_test"]
 
 
 class FCError(RuntimeError):
@@ -60,7 +62,7 @@ class fc_stats(ctypes.Structure):
                                        "ms_scan64", "ms_finish", "ms_total")] + [
         ("evicted", ctypes.c_int64), ("cache_slots", ctypes.c_int64), ("max_distinct_cov", ctypes.c_int64),
         ("scan_waves", ctypes.c_int64), ("big_listed", ctypes.c_int64), ("screen_tiles", ctypes.c_int64),
-        ("screen_rows", ctypes.c_int64)]
+        ("screen_rows", ctypes.c_int64), ("deferred", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,6 +121,8 @@ def load(build: bool = False):
         "fc_cancel": (st, [vp, u64]),
         "fc_get_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
         "fc_get_serve_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
+        "fc_get_decided_by": (st, [vp, vp, i64]),
+        "fc_set_wait_test": (st, [vp, u64, i64]),
         "fc_data_dchi2": (st, [vp, i32, vp, vp, i32, ctypes.POINTER(fc_opts), vp, vp, vp]),
         "fc_fc_region": (st, [vp, vp, i32, i32, vp, ctypes.c_double, vp, vp]),
         "fc_fc_region_adaptive": (st, [vp, i32, vp, i32, vp, ctypes.c_double, i32, i32, ctypes.c_double, u64,
@@ -392,6 +396,18 @@ def fc_get_serve_stats(ctx) -> dict:
     s = fc_stats()
     _check(load().fc_get_serve_stats(ctx, ctypes.byref(s)), ctx)
     return s.as_dict()
+
+
+def fc_set_wait_test(ctx, wait_ns: int = 0, screen_stop_after: int = -1):
+    """Test hook: limit of the screen's pipeline waits (0 = built-in) and a producer stop after n stages (-1 = off)."""
+    _check(load().fc_set_wait_test(ctx, int(wait_ns), int(screen_stop_after)), ctx)
+
+
+def fc_get_decided_by(ctx, n: int) -> np.ndarray:
+    """Per universe of the last synchronous fit: OR of the FC_DECIDED_* bits of the rounds that decided it."""
+    out = np.empty(int(n), np.uint8)
+    _check(load().fc_get_decided_by(ctx, _ptr(out), int(n)), ctx)
+    return out
 
 
 def fc_get_stats(ctx) -> dict:

@@ -127,6 +127,7 @@ struct Scratch {
 // Served job: a copy of the caller's arguments and its completion state.
 struct JobRec {
     fc_job job;
+    size_t need = 0;  // device bytes the job may take while it runs (admission estimate)
     std::vector<int64_t> ps;
     std::atomic<int> state{FC_PENDING};
     std::atomic<bool> cancelled{false};
@@ -164,6 +165,7 @@ struct Lane {
     float* d = nullptr;    // [cap][nfit] data
     int32_t *cur = nullptr, *pt = nullptr, *best = nullptr, *job_of = nullptr;
     int8_t *nscan = nullptr, *maxit = nullptr;
+    uint8_t* rmask = nullptr;     // [cap] rounds that decided the universe's scans (FC_DECIDED_*)
     double *dchi2 = nullptr, *chi2min = nullptr;
     float* thr = nullptr;
     int32_t *active = nullptr, *next = nullptr, *fin = nullptr, *uslot = nullptr;
@@ -196,6 +198,9 @@ struct fc_ctx {
     fc_stats serve_stats{};        // everything the serving worker ran
     fc_stats* acc = &stats;        // where the running work counts
     Lane sync_lane;                // synchronous calls
+    int64_t last_base = 0, last_n = -1;  // universes of the last synchronous fit in sync_lane
+    WaitTest wait_test{0, -1};     // test hook of the screen's bounded waits (fc_set_wait_test)
+    size_t reserved = 0;           // serving: admission estimates of the running jobs (worker only)
     std::vector<std::unique_ptr<Lane>> lanes;  // serving (worker thread only)
     std::mutex api_mu;  // serialises device work of this context
     // serving
@@ -384,12 +389,13 @@ fc_status regrow(fc_ctx* c, T** p, size_t per_slot, int64_t old_cap, int64_t new
 }
 
 // Device memory the covariance caches leave free for scratch, lanes and other
-// grids: a tenth of the budget (of the device when there is none), 2 GiB at least.
+// grids: a tenth of the budget (of the device when there is none), at least
+// 2 GiB or a quarter of a budget below 8 GiB.
 size_t cache_reserve(fc_ctx* c) {
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     const size_t base = c->budget ? c->budget : total_b;
-    return std::max<size_t>(base / 10, size_t(2) << 30);
+    return std::max<size_t>(base / 10, std::min<size_t>(size_t(2) << 30, base / 4));
 }
 
 // Bytes a cache may still take: what the budget (or the device) has left
@@ -629,8 +635,8 @@ __global__ void k_gather_cur(const int32_t* __restrict__ list, int n, const int3
 // the lane's active list at `tail`.
 __global__ void k_lane_admit(const int64_t* __restrict__ ps, int64_t n, int U, int64_t base, int8_t max_iter,
                              int32_t job, int32_t* __restrict__ cur, int32_t* __restrict__ pt,
-                             int8_t* __restrict__ nscan, int8_t* __restrict__ maxit, int32_t* __restrict__ job_of,
-                             int32_t* __restrict__ tail) {
+                             int8_t* __restrict__ nscan, int8_t* __restrict__ maxit, uint8_t* __restrict__ rmask,
+                             int32_t* __restrict__ job_of, int32_t* __restrict__ tail) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t u = base + i;
@@ -639,6 +645,7 @@ __global__ void k_lane_admit(const int64_t* __restrict__ ps, int64_t n, int U, i
     pt[u] = p;
     nscan[u] = 0;
     maxit[u] = max_iter;
+    rmask[u] = 0;
     job_of[u] = job;
     tail[i] = (int32_t)u;
 }
@@ -715,7 +722,7 @@ fc_status distinct_cur(fc_ctx* c, Grid* g, const int32_t* active, int64_t n_acti
 
 void lane_free(fc_ctx* c, Lane* L) {
     for (void* p : {(void*)L->d, (void*)L->cur, (void*)L->pt, (void*)L->best, (void*)L->job_of, (void*)L->nscan,
-                    (void*)L->maxit, (void*)L->dchi2, (void*)L->chi2min, (void*)L->thr, (void*)L->active,
+                    (void*)L->maxit, (void*)L->rmask, (void*)L->dchi2, (void*)L->chi2min, (void*)L->thr, (void*)L->active,
                     (void*)L->next, (void*)L->fin, (void*)L->uslot, (void*)L->fb, (void*)L->fb2, (void*)L->fbslot,
                     (void*)L->job_left, (void*)L->job_dead})
         dfree(c, p);
@@ -749,6 +756,7 @@ fc_status lane_alloc(fc_ctx* c, Lane* L, Grid* g, const fc_opts& o, int64_t cap)
     A(&L->job_of, cap);
     A(&L->nscan, cap);
     A(&L->maxit, cap);
+    A(&L->rmask, cap);
     A(&L->dchi2, cap);
     A(&L->chi2min, cap);
     A(&L->thr, cap);
@@ -831,7 +839,8 @@ fc_status lane_admit(fc_ctx* c, Lane* L, const std::shared_ptr<LaneJob>& J, cons
     }
     count_launch();
     k_lane_admit<<<nb(n), 256, 0, c->stream>>>(ps_dev, n, U, J->base, (int8_t)max_iter, J->slot, L->cur, L->pt,
-                                               L->nscan, L->maxit, L->job_of, L->active + L->n_active);
+                                               L->nscan, L->maxit, L->rmask, L->job_of,
+                                               L->active + L->n_active);
     launch_fill_i32(L->job_left + J->slot, 1, (int32_t)n, c->stream);
     FC_CUDA(cudaGetLastError());
     L->jobs[J->slot] = J;
@@ -917,6 +926,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                           c->stream);
             FC_TRY(stage_end(c, &S->ms_scan64));
         }
+        launch_or_mask(list, cnt, mixed ? kDecidedScan : kDecidedPlain, L->rmask, c->stream);
         // finishing universes keep cur (the covariance of this scan); others move to their minimum
         FC_CUDA(cudaMemsetAsync(cnts + 3, 0, 4, c->stream));
         launch_advance(list, cnt, L->best, us, next, cnts + 2, fin, cnts + 3, c->stream);
@@ -1001,13 +1011,16 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     if (!launch_screen(g->K, rtopk, mode, g->tune.screen_stages, g->tune.screen_ybuf, Yt, g->Bt, g->Qb3,
                                        tslot, tau0, tj0, n_tiles, g->G, g->G_pad, cval, cidx, ccount, c->status_dev,
                                        g->Qc, g->Qb, g->gnorm, alpha, g->Sc32, g->nfit, ListArgs{tuniv, loff, lnum},
-                                       c->n_sm, c->stream))
+                                       c->wait_test, c->n_sm, c->stream))
                         return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
                     S->screen_launches += 1;
                     S->screen_tiles += n_tiles;
                     S->screen_rows += cnt;
                 }
                 FC_TRY(stage_end(c, &S->ms_screen));
+                // a screen that gave up (a bounded wait ran out) leaves its candidates incomplete:
+                // report it before anything reads them
+                FC_TRY(check_status(c));
                 S->screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
                 ResolveArgs ra;
                 ra.tile_slot = tslot;
@@ -1046,6 +1059,9 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 ra.lcount = (round == 2) ? lcount : nullptr;
                 ra.list_off = loff;
                 ra.list_n = lnum;
+                ra.rmask = L->rmask;
+                ra.round_bit = round == 0 ? 0 : (round == 1 ? kDecidedTop16 : (round == 2 ? kDecidedList
+                                                                                          : kDecidedExactList));
                 stage_begin(c);
                 if (listing)
                 {
@@ -1356,6 +1372,7 @@ fc_status run_sync(fc_ctx* c, Grid* g, const fc_opts& o, const std::vector<int64
                    const float* d_in, double* dchi2, int64_t* best, int8_t* nscans, double* chi2min,
                    cudaEvent_t ev_data) {
     const int64_t n = (int64_t)ps.size() * U;
+    c->last_n = -1;
     Lane* L = nullptr;
     FC_TRY(sync_lane(c, g, o, n, &L));
     auto J = std::make_shared<LaneJob>();
@@ -1375,6 +1392,8 @@ fc_status run_sync(fc_ctx* c, Grid* g, const fc_opts& o, const std::vector<int64
     if (st == FC_OK && (done.size() != 1 || !lane_idle(L)))
         st = fail(FC_ERR_STATE, "internal: synchronous job did not complete");
     if (st != FC_OK) lane_reset(L);
+    c->last_base = J->base;
+    c->last_n = st == FC_OK ? n : -1;
     return st;
 }
 
@@ -1492,6 +1511,14 @@ bool serve_admit(fc_ctx* c, const std::shared_ptr<JobRec>& jr) {
         complete(c, jr, jr->cancelled.load() ? FC_ERR_CANCELLED : FC_OK);
         return true;
     }
+    // admission by the memory budget: the running jobs' estimates plus this one's must fit;
+    // otherwise the job waits for running jobs to finish (it fits alone: fc_submit checked)
+    bool others_running = false;
+    for (auto& l : c->lanes) others_running = others_running || !lane_idle(l.get());
+    if (c->budget && others_running && c->reserved + jr->need > c->budget) {
+        c->acc->deferred += 1;
+        return false;
+    }
     Lane* L = nullptr;
     for (auto& l : c->lanes)
         if (same_lane(l.get(), jb)) L = l.get();
@@ -1504,8 +1531,20 @@ bool serve_admit(fc_ctx* c, const std::shared_ptr<JobRec>& jr) {
         if (L->cap && !lane_idle(L)) return false;  // wait for running jobs of the lane to finish
         // empty lane: (re)size it for this job, with headroom for later ones
         fc_status st = lane_alloc(c, L, g, jb.opts, std::max(n, kServeLaneMin));
-        if (st != FC_OK) st = lane_alloc(c, L, g, jb.opts, n);
         if (st != FC_OK) {
+            cudaGetLastError();
+            // give back the memory of idle lanes, then try the job's own size
+            for (auto& l : c->lanes)
+                if (l.get() != L && lane_idle(l.get())) lane_free(c, l.get());
+            st = lane_alloc(c, L, g, jb.opts, n);
+        }
+        if (st != FC_OK) {
+            cudaGetLastError();
+            if (others_running) {
+                // memory held by running jobs: retry when they finish
+                c->acc->deferred += 1;
+                return false;
+            }
             complete(c, jr, st);
             return true;
         }
@@ -1526,6 +1565,8 @@ bool serve_admit(fc_ctx* c, const std::shared_ptr<JobRec>& jr) {
         lane_release(L, base, n);
         L->free_jobs.push_back(J->slot);
         complete(c, jr, st);
+    } else {
+        c->reserved += jr->need;
     }
     return true;
 }
@@ -1575,6 +1616,7 @@ void worker_main(fc_ctx* c) {
             if (st == FC_OK) st = lane_harvest(c, L, &done);
             if (st != FC_OK) lane_fail_all(L, st, &done);
             for (auto& J : done) {
+                c->reserved -= std::min(c->reserved, J->jr->need);
                 complete(c, J->jr, J->status);
                 running--;
             }
@@ -2164,10 +2206,13 @@ fc_status fc_submit(fc_ctx* c, const fc_job* job, uint64_t* ticket) {
     for (int64_t p : jr->ps)
         if (p < 0 || p >= g->G) return fail(FC_ERR_ARG, "true point index out of range");
     if ((int64_t)job->P * job->U > (int64_t)INT32_MAX / 2) return fail(FC_ERR_ARG, "P * U too large");
-    // device memory this job needs at most (fake data, state, candidates); it must fit the budget
+    // device memory the job may hold while it runs: per universe its lane state (data, indices,
+    // results, work lists) and its share of the scan scratch (A-image row, bounds, candidates,
+    // list counts), with the scratch buffers' growth headroom; it must fit the budget
     const size_t n = (size_t)job->P * job->U;
-    const size_t need = n * ((size_t)g->nfit * 4 + 64 + 16 * 8 + (size_t)g->K * 4);
+    const size_t need = n * (((size_t)g->nfit * 4 + 64 + (size_t)g->K * 4 + 320) * 5 / 4);
     if (c->budget && need > c->budget) return fail(FC_ERR_BUDGET, "job can never fit the device-memory budget");
+    jr->need = need;
     it->second->busy++;
     const uint64_t t = c->next_ticket++;
     c->jobs[t] = jr;
@@ -2349,12 +2394,35 @@ fc_status fc_get_serve_stats(fc_ctx* c, fc_stats* out) {
     if (!c || !out) return fail(FC_ERR_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(c->api_mu);
     *out = c->serve_stats;
+    out->device_bytes = (int64_t)c->used;
     return FC_OK;
+}
+
+fc_status fc_set_wait_test(fc_ctx* c, uint64_t wait_ns, int64_t screen_stop_after) {
+    if (!c) return fail(FC_ERR_ARG, "ctx is NULL");
+    if (screen_stop_after < -1) return fail(FC_ERR_ARG, "screen_stop_after must be >= -1");
+    if (wait_ns > 2000000000ull) return fail(FC_ERR_ARG, "wait_ns above the built-in limit (2 s)");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    c->wait_test = WaitTest{wait_ns, screen_stop_after};
+    return FC_OK;
+}
+
+fc_status fc_get_decided_by(fc_ctx* c, uint8_t* out, int64_t n) {
+    if (!c || (n > 0 && !out)) return fail(FC_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    if (c->last_n < 0 || !c->sync_lane.rmask) return fail(FC_ERR_STATE, "no synchronous fit on this context yet");
+    if (n != c->last_n)
+        return fail(FC_ERR_ARG, "n must be the last fit's universe count (" + std::to_string(c->last_n) + ")");
+    if (n == 0) return FC_OK;
+    FC_TRY(copy_out(c, out, c->sync_lane.rmask + c->last_base, (size_t)n));
+    return sync(c);
 }
 
 fc_status fc_get_stats(fc_ctx* c, fc_stats* out) {
     if (!c || !out) return fail(FC_ERR_ARG, "NULL argument");
     *out = c->stats;
+    out->device_bytes = (int64_t)c->used;
     return FC_OK;
 }
 

@@ -156,6 +156,13 @@ struct ListArgs {
     const int64_t* off;
     const int2* n;
 };
+// Test hook of the screen's bounded waits: wait_ns = limit of the pipeline waits
+// (0 = the built-in 2 s); stop_after >= 0 = the copy producer of every CTA stops
+// issuing after that many pipeline stages, so that its consumers' waits run out.
+struct WaitTest {
+    uint64_t wait_ns;
+    int64_t stop_after;
+};
 // stages / ybuf: pipeline depth and A-image buffers, 0 = built-in choice.
 bool screen_config_ok(int K, int stages, int ybuf);
 bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Ytiles, const uint16_t* Btiles,
@@ -163,7 +170,7 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
                    const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
-                   int nfit, const ListArgs& la, int n_sm, cudaStream_t st);
+                   int nfit, const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st);
 // Resolution of one mixed-path scan per screen tile (see k_resolve).
 struct ResolveArgs {
     const int32_t* tile_slot;
@@ -202,7 +209,14 @@ struct ResolveArgs {
     int2* lcount;          // [n] nullable, list rounds: half-row counts of an overflowing universe
     const int64_t* list_off;  // [n] nullable: exact-size list storage (see ListArgs)
     const int2* list_n;
+    uint8_t* rmask;        // [n] nullable: bit of the round that decided each universe's scan, OR-ed in
+    uint8_t round_bit;     // that bit; 0 = the top-k round (certificate alone or after rescoring)
 };
+// Bits of a universe's round record (the FC_DECIDED_* values of fc.h).
+constexpr uint8_t kDecidedCert = 1, kDecidedRescored = 2, kDecidedTop16 = 4, kDecidedList = 8,
+                  kDecidedExactList = 16, kDecidedScan = 32, kDecidedPlain = 64;
+// rmask[list[i]] |= bit for the universes of a list
+void launch_or_mask(const int32_t* list, int64_t n, uint8_t bit, uint8_t* rmask, cudaStream_t st);
 // tau0[row] = min(tau0[row], thr[u]) for the rows of the tiles
 void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st);
 // Third round: binary64 residual chi2 of every listed candidate of each row

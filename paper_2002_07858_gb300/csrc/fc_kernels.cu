@@ -1180,6 +1180,8 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
         atomicAdd(&s_cnt[2], 1);
         if (a.thr) a.thr[u] = FLT_MAX;
     }
+    if (state == 1 && a.rmask)
+        a.rmask[u] |= a.round_bit ? a.round_bit : (have_min ? kDecidedRescored : kDecidedCert);
     __syncthreads();
     if (r == 0) s_nitem = 0;
     __syncthreads();
@@ -1289,6 +1291,7 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
             }
         }
         warp_argmin(bv, bg);
+        if (lane == 0 && a.rmask) a.rmask[u] |= a.round_bit;
         const int32_t cur_u = a.cur[u];
         const bool finishing = (bg == cur_u) || (a.nscan[u] + 1 >= a.maxit[u]);
         if (finishing) {
@@ -1314,6 +1317,11 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
             atomicAdd(&a.counters[0], 1ull);
         }
     }
+}
+
+__global__ void k_or_mask(const int32_t* __restrict__ list, int64_t n, uint8_t bit, uint8_t* __restrict__ rmask) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) rmask[list[i]] |= bit;
 }
 
 __global__ void k_min_tau(const int32_t* __restrict__ tile_univ, int64_t n_rows, const float* __restrict__ thr,
@@ -1468,12 +1476,9 @@ void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps
     if (P <= 0) return;
     count_launch();
     const size_t smem = nf <= kCholPackN ? (size_t)nf * (nf + 1) / 2 * sizeof(double) : 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_chol_sys, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kCholPackN * (kCholPackN + 1) / 2 * (int)sizeof(double));
-        attr = true;
-    }
+    // the attribute belongs to the current device, so it is set at every launch (a cheap host call)
+    cudaFuncSetAttribute(k_chol_sys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kCholPackN * (kCholPackN + 1) / 2 * (int)sizeof(double));
     k_chol_sys<<<P, 256, smem, st>>>(S, nf, F, ps, gauss, L64, L32, s32, status);
 }
 
@@ -1483,28 +1488,34 @@ void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, co
     if (n <= 0) return;
     count_launch();
     const size_t smem = nfit <= kResolveMaxN ? 2 * (size_t)nfit * nfit * sizeof(double) : 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_build_cov, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             2 * kResolveMaxN * kResolveMaxN * (int)sizeof(double));
-        attr = true;
-    }
+    cudaFuncSetAttribute(k_build_cov, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         2 * kResolveMaxN * kResolveMaxN * (int)sizeof(double));
     k_build_cov<<<n, 256, smem, st>>>(S, nf, nfit, coll, F, q_list, slot_list, cov_mode, A64, W64, A32, rho, work,
                                       status);
 }
 
 void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
                    int64_t ldq, double* Q64, cudaStream_t st) {
-    if (n <= 0) return;
-    dim3 grid(blocks_for(G, 128) < 64 ? blocks_for(G, 128) : 64, n);
-    count_launch();
-    k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, A64, slots, ldq, Q64);
+    // blockIdx.y is the slot within a launch: chunks of at most gridDim.y's limit
+    for (int s0 = 0; s0 < n; s0 += 65535) {
+        const int ns = n - s0 < 65535 ? n - s0 : 65535;
+        dim3 grid(blocks_for(G, 128) < 64 ? blocks_for(G, 128) : 64, ns);
+        count_launch();
+        k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, A64, slots + s0, ldq, Q64);
+    }
 }
 
 void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
                    cudaStream_t st) {
     if (n <= 0) return;
+    if (n > 65535) {
+        // blockIdx.y is the slot within a launch: chunks of at most gridDim.y's limit
+        for (int s0 = 0; s0 < n; s0 += 65535)
+            launch_qvec32(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots + s0, n - s0 < 65535 ? n - s0 : 65535, Qc, Qb,
+                          Qb3, st);
+        return;
+    }
     // ~16 grid points per thread so each block's staging of A is amortised
     unsigned gx = blocks_for(G_pad, 128 * 16);
     if (gx > 128) gx = 128;
@@ -1525,10 +1536,16 @@ void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_
 void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* coll, int nfit, const int64_t* ps,
                       int P, int U, uint64_t seed, int gauss, float* d, cudaStream_t st) {
     if (P <= 0 || U <= 0) return;
-    dim3 grid((U + 127) / 128, P);
-    count_launch();
-    k_fake_data<<<grid, 128, 0, st>>>(L32, s32, nf, coll, nfit, ps, U, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                       gauss, d);
+    // blockIdx.y is the point within a launch; more points than gridDim.y allows take several launches
+    constexpr int kMaxGridY = 65535;
+    for (int p0 = 0; p0 < P; p0 += kMaxGridY) {
+        const int np = P - p0 < kMaxGridY ? P - p0 : kMaxGridY;
+        dim3 grid((U + 127) / 128, np);
+        count_launch();
+        k_fake_data<<<grid, 128, 0, st>>>(L32 + (size_t)p0 * nf * nf, s32 + (size_t)p0 * nf, nf, coll, nfit, ps + p0,
+                                           U, (uint32_t)seed, (uint32_t)(seed >> 32), gauss,
+                                           d + (size_t)p0 * U * nfit);
+    }
 }
 
 void launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t st) {
@@ -1623,6 +1640,12 @@ void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_
                                                Qb, G_pad, Yt, alpha, tau0, tile_j0);
 }
 
+void launch_or_mask(const int32_t* list, int64_t n, uint8_t bit, uint8_t* rmask, cudaStream_t st) {
+    if (n <= 0 || !rmask) return;
+    count_launch();
+    k_or_mask<<<blocks_for(n), kThreads, 0, st>>>(list, n, bit, rmask);
+}
+
 void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr, float* tau0, cudaStream_t st) {
     if (n_tiles <= 0) return;
     count_launch();
@@ -1656,12 +1679,8 @@ void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
     if (n_tiles <= 0) return;
     const size_t smem = a.nfit <= kResolveMaxN ? (size_t)a.nfit * a.nfit * sizeof(double) : 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kResolveMaxN * kResolveMaxN * (int)sizeof(double));
-        attr = true;
-    }
+    cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kResolveMaxN * kResolveMaxN * (int)sizeof(double));
     count_launch();
     k_resolve<<<(unsigned)n_tiles, kBM, smem, st>>>(a);
 }

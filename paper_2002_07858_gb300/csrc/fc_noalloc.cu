@@ -27,6 +27,7 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
 constexpr int kMaxDevices = 64;
+constexpr int kDevBadCollapse = 8;  // status bit of k_check_collapse
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -43,6 +44,25 @@ fc_status noalloc_fail(fc_status st, const char* msg) {
 __global__ void k_check_points(const int64_t* __restrict__ ps, int P, int64_t G, int* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P && (ps[i] < 0 || ps[i] >= G)) atomicOr(status, fcdev::kDevBadIndex);
+}
+
+// The caller's collapse map (device memory, so it is checked on the device): every
+// entry in [0, N_fit) and every fit bin reached by at least one full bin, the
+// rules fc_load_grid applies on the host.  One CTA.
+__global__ void k_check_collapse(const int32_t* __restrict__ coll, int nf, int nfit, int* __restrict__ status) {
+    __shared__ int seen[fcdev::kMaxBins];
+    for (int j = threadIdx.x; j < nfit; j += blockDim.x) seen[j] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const int32_t v = coll[i];
+        if (v < 0 || v >= nfit)
+            atomicOr(status, kDevBadCollapse);
+        else
+            seen[v] = 1;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nfit; j += blockDim.x)
+        if (!seen[j]) atomicOr(status, kDevBadCollapse);
 }
 
 }  // namespace
@@ -89,14 +109,31 @@ fc_status fc_fake_data_noalloc(const double* S, int64_t G, int32_t N_full, const
     };
     // the status word is the only state that must start at zero
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return noalloc_fail(FC_ERR_CUDA, "memset failed");
-    // validate the point indices before any kernel dereferences them
+    // a launch error (bad configuration, no kernel image) is read before the call reports success
+    auto launched = [&]() -> bool {
+        const cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) return true;
+        noalloc_fail(FC_ERR_CUDA, cudaGetErrorString(e));
+        return false;
+    };
+    // validate the point indices and the collapse map before any kernel dereferences them
     fcdev::count_launch();
     k_check_points<<<(P + 255) / 256, 256, 0, st>>>(ps, P, G, status);
+    if (!launched()) return FC_ERR_CUDA;
+    if (collapse) {
+        fcdev::count_launch();
+        k_check_collapse<<<1, 256, 0, st>>>(collapse, N_full, N_fit, status);
+        if (!launched()) return FC_ERR_CUDA;
+    }
     int h = 0;
     if (!read_status(&h)) return noalloc_fail(FC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
     if (h & fcdev::kDevBadIndex) return noalloc_fail(FC_ERR_ARG, "true point index out of range");
+    if (h & kDevBadCollapse)
+        return noalloc_fail(FC_ERR_ARG, "collapse map entry out of [0, N_fit) or a fit bin left empty");
     fcdev::launch_chol_sys(S, N_full, F, ps, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr, status, st);
+    if (!launched()) return FC_ERR_CUDA;
     fcdev::launch_fake_data(L32, s32, N_full, collapse, N_fit, ps, P, U, seed, fluct == FC_FLUCT_GAUSS, d, st);
+    if (!launched()) return FC_ERR_CUDA;
     if (!read_status(&h)) return noalloc_fail(FC_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
     if (h & fcdev::kDevNotSpd) return noalloc_fail(FC_ERR_NOT_SPD, "systematic covariance not positive definite");
     return FC_OK;

@@ -194,13 +194,15 @@ __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item
 // After a min-only pass: tau0 <- min(tau0, certified upper bound at the row's
 // minimum index bidx), one thread per row (bidx = INT32_MAX: no minimum).
 __global__ void k_min_seed(const uint16_t* __restrict__ Yt, const int32_t* __restrict__ tile_slot,
-                           const int32_t* __restrict__ bidx, float* __restrict__ tau0, int64_t n_rows, int64_t G_pad,
-                           ProbeArgs pa) {
+                           const int32_t* __restrict__ bidx, float* __restrict__ tau0, int64_t n_rows, int64_t G,
+                           int64_t G_pad, ProbeArgs pa, const int* __restrict__ status) {
     const int64_t orow = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (orow >= n_rows) return;
+    // an aborted min pass leaves rows it never reached unwritten: use nothing of it
+    if (*status & kDevTimeout) return;
     const int32_t bi = bidx[orow];
     const float seed = tau0[orow];
-    if (bi == INT32_MAX || !(seed > -FLT_MAX)) return;
+    if (bi < 0 || bi >= G || !(seed > -FLT_MAX)) return;
     const int64_t item = orow / kBM;
     const int row = (int)(orow % kBM);
     tau0[orow] = fminf(seed, probe_upper_bound(Yt, item, row, tile_slot[item], bi, G_pad, pa));
@@ -243,7 +245,8 @@ inline ScreenLayout screen_layout(int K, int stages, int ybuf, int kchunk) {
     // per epilogue warp 4 KB: slow-path scratch inside a tile, top-k hand-over at the end of a row tile
     l.off_scratch = l.off_zero + kBChunk;
     l.off_bar = l.off_scratch + kEpiWarps * 4096;
-    l.bytes = l.off_bar + kNumBars(stages) * 8 + 16 + 1024;
+    // after the barriers: TMEM address, abort flag, pair flags [4][2]; then the alignment slack
+    l.bytes = l.off_bar + kNumBars(stages) * 8 + 48 + 1024;
     return l;
 }
 
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
              const int32_t* __restrict__ tile_slot, float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
              int64_t n_tiles, int64_t G, int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
              int32_t* __restrict__ cand_count, int* __restrict__ status, ProbeArgs pa, ScreenLayout lay,
-             ListArgs la) {
+             ListArgs la, WaitTest wt) {
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -262,6 +265,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     uint64_t* bars = (uint64_t*)(smem + lay.off_bar);
     uint32_t* tmem_holder = (uint32_t*)(smem + lay.off_bar + kNumBars(STAGES) * 8);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+    // per TMEM lane quadrant, whether each epilogue half finished the current item
+    volatile int* pair_ok = (volatile int*)(tmem_holder + 2);
     auto bar = [&](int i) { return smem_addr(&bars[i]); };
     const int Y_FULL = 0, Y_EMPTY = 2, B_FULL = 4, B_EMPTY = 4 + STAGES, T_FULL = 4 + 2 * STAGES,
               T_EMPTY = 6 + 2 * STAGES, DONE = 8 + 2 * STAGES;
@@ -310,18 +315,21 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_holder;
     const int n_gt = (int)(G_pad / kBN);
+    // limit of the pipeline waits (the drain and completion waits keep the built-in limit)
+    const uint64_t wlim = wt.wait_ns ? wt.wait_ns : kWaitNs;
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------- producer
         int y_par[2] = {-1, -1};
         int b_par[16];
         for (int s = 0; s < STAGES; ++s) b_par[s] = -1;
-        bool ok = true;
+        bool ok = true, stopped = false;
+        int64_t issued = 0;  // pipeline stages issued (for the test hook wt.stop_after)
         // ring positions and phases advance by counting (no division in the issue loop)
         int yb = 0, s = 0;
         uint32_t yph = 0, ph = 0;
-        for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x) {
-            if (!mbar_wait(bar(Y_EMPTY + yb), yph ^ 1, abort_flag)) { ok = false; break; }
+        for (int64_t item = blockIdx.x; ok && !stopped && item < n_tiles; item += gridDim.x) {
+            if (!mbar_wait(bar(Y_EMPTY + yb), yph ^ 1, abort_flag, wlim)) { ok = false; break; }
             mbar_expect_tx(bar(Y_FULL + yb), lay.y_bytes);
             bulk_g2s(sbase + yb * lay.y_bytes, Yt + item * (int64_t)(lay.y_bytes / 2), lay.y_bytes,
                      bar(Y_FULL + yb));
@@ -329,10 +337,12 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             if (++yb == YBUF) { yb = 0; yph ^= 1u; }
             const uint16_t* qrow = Qb3 + (int64_t)tile_slot[item] * G_pad * 8;
             int j = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
-            for (int jj = 0; ok && jj < n_gt; ++jj) {
+            for (int jj = 0; ok && !stopped && jj < n_gt; ++jj) {
                 const uint16_t* btile = Bt + (int64_t)j * tile_elems;
                 for (int c = 0; c < NC; ++c) {
-                    if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag)) { ok = false; break; }
+                    if (wt.stop_after >= 0 && issued >= wt.stop_after) { stopped = true; break; }
+                    ++issued;
+                    if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag, wlim)) { ok = false; break; }
                     const uint32_t st0 = sbase + lay.off_b + s * lay.stage_bytes;
                     const uint32_t hi_bytes = KCHUNK ? 2u * kBChunk : lay.bpart_bytes / 2u;
                     const uint32_t bytes = (kLo ? 2u * hi_bytes : hi_bytes) + (c == 0 ? kQBytes : 0u);
@@ -357,7 +367,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         if (!ok) {
             *abort_flag = 1;
             atomicOr(status, kDevTimeout);
-            // let every copy this thread issued land before the CTA can exit
+        }
+        if (!ok || stopped) {
+            // let every copy this thread issued land before the CTA can exit (the consumers of a
+            // stopped producer time out on the stages that never come)
             for (int i = 0; i < YBUF; ++i)
                 if (y_par[i] >= 0) mbar_wait(bar(Y_FULL + i), (uint32_t)y_par[i], nullptr);
             for (int s = 0; s < STAGES; ++s)
@@ -370,14 +383,14 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         int yb = 0, s = 0, ab = 0;
         uint32_t yph = 0, ph = 0, aph = 0;
         for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x) {
-            if (!mbar_wait(bar(Y_FULL + yb), yph, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(bar(Y_FULL + yb), yph, abort_flag, wlim)) { ok = false; break; }
             tc_fence_after();
             const uint32_t a0 = sbase + yb * lay.y_bytes;
             for (int jj = 0; ok && jj < n_gt; ++jj) {
-                if (!mbar_wait(bar(T_EMPTY + ab), aph ^ 1, abort_flag)) { ok = false; break; }
+                if (!mbar_wait(bar(T_EMPTY + ab), aph ^ 1, abort_flag, wlim)) { ok = false; break; }
                 const uint32_t d = tmem_base + (uint32_t)(ab * kBN);
                 for (int c = 0; c < NC; ++c) {
-                    if (!mbar_wait(bar(B_FULL + s), ph, abort_flag)) { ok = false; break; }
+                    if (!mbar_wait(bar(B_FULL + s), ph, abort_flag, wlim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t b0 = sbase + lay.off_b + s * lay.stage_bytes;
                     if (c == 0) {
@@ -462,7 +475,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 const int64_t seq = (int64_t)it * n_gt + jj;
                 const int ab = (int)(seq & 1);
                 const uint32_t aph = (uint32_t)((seq >> 1) & 1);
-                bool w_ok = mbar_wait(bar(T_FULL + ab), aph, abort_flag);
+                bool w_ok = mbar_wait(bar(T_FULL + ab), aph, abort_flag, wlim);
                 if (!__all_sync(0xffffffffu, w_ok)) {
                     ok = false;
                     if (lane == 0) *abort_flag = 1;
@@ -509,7 +522,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 if (!ok) break;
                 continue;
             }
-            // both halves of a row reach here even after a timeout, so the pair barrier cannot hang
+            // both halves of a row reach here once per item even after a timeout, and they leave the
+            // item loop together: each posts its ok before the pair barrier and both decide on the
+            // two posted values, so neither can wait at that barrier for a partner that has left
+            if (lane == 0) pair_ok[quad * 2 + half] = ok ? 1 : 0;
             if (half == 1) {
                 if (MODE == kModeMin) {
                     mval[lane] = bv;
@@ -523,6 +539,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 }
             }
             named_bar(1 + quad, 64);
+            const bool pair_done = pair_ok[quad * 2] && pair_ok[quad * 2 + 1];
             if (half == 0) {
                 const int64_t orow = item * kBM + row;
                 if (MODE == kModeMin) {
@@ -534,7 +551,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                     }
                     // the row's minimum index; k_min_seed turns it into the certified seed after the
                     // launch, so the epilogue never stalls the MMAs on the probe's scattered loads
-                    cand_idx[orow] = (ok && seed > -FLT_MAX) ? bi : INT32_MAX;
+                    cand_idx[orow] = (pair_done && seed > -FLT_MAX) ? bi : INT32_MAX;
                 } else {
 #pragma unroll 1
                     for (int t = 0; t < TOPK; ++t) {
@@ -551,7 +568,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 }
             }
             named_bar(1 + quad, 64);
-            if (!ok) break;
+            if (!pair_done) break;
         }
         if (!ok && lane == 0) {
             *abort_flag = 1;
@@ -571,18 +588,19 @@ template <int TOPK, int MODE, bool KCHUNK>
 void run_screen(const ScreenLayout& lay, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
                 const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                 int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const ProbeArgs& pa,
-                const ListArgs& la, int n_sm, cudaStream_t st) {
+                const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st) {
     auto kern = k_screen<TOPK, MODE, KCHUNK>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
     kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, lay.bytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G,
-                                                                   G_pad, cv, ci, cc, status, pa, lay, la);
+                                                                   G_pad, cv, ci, cc, status, pa, lay, la, wt);
     if (MODE == kModeMin) {
         const int64_t rows = n_tiles * kBM;
         count_launch();
-        k_min_seed<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Yt, tile_slot, ci, tau0, rows, G_pad, pa);
+        k_min_seed<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Yt, tile_slot, ci, tau0, rows, G, G_pad, pa,
+                                                                   status);
     }
 }
 
@@ -618,14 +636,14 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
                    const uint16_t* Qb3, const int32_t* tile_slot, float* tau0, const int32_t* tile_j0,
                    int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
-                   int nfit, const ListArgs& la, int n_sm, cudaStream_t st) {
+                   int nfit, const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
     if (!screen_config_ok(K, stages, ybuf) || (topk != 8 && topk != 16)) return false;
     const ScreenLayout lay = choose_layout(K, stages, ybuf);
     const ProbeArgs pa{Qc, Qb, gnorm, alpha, Sc32, nfit};
 #define FC_SCREEN_RUN(TT, MM, CC) \
     run_screen<TT, MM, CC>(lay, Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, la, \
-                           n_sm, st)
+                           wt, n_sm, st)
 #define FC_SCREEN_MODES(TT, CC)                 \
     do {                                        \
         if (mode == kModeMin)                   \

@@ -45,25 +45,28 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Default limit of a bounded wait (a context can shorten the screen's for tests).
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 // Bounded wait on a phase parity; false on timeout or when another role aborted.
-static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, const volatile int* abort_flag,
+                                                   uint64_t limit_ns) {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_test(bar, parity)) return true;
         if ((it & 63) == 0) {
             if (abort_flag && *abort_flag) return false;
-            if (global_ns() - t0 > kWaitNs) return false;
+            if (global_ns() - t0 > limit_ns) return false;
         }
     }
 }
 
 // Phase already complete: one try_wait, no call; otherwise the bounded loop.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag,
+                                          uint64_t limit_ns = kWaitNs) {
     if (mbar_test(bar, parity)) return true;
-    return mbar_wait_slow(bar, parity, abort_flag);
+    return mbar_wait_slow(bar, parity, abort_flag, limit_ns);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {

@@ -3,13 +3,18 @@
 A served job's results depend only on its own arguments: a job run alone,
 run through the synchronous entry point, or admitted between the scans of
 other jobs (same lane, different iteration counts, other lanes) gives the
-same dchi2, best fits and scan counts bit for bit.
+same dchi2, best fits and scan counts bit for bit -- and jobs served in a mix
+meet the oracle's bars (tests/_parity.py).  Under a device-memory budget a
+job that can never fit is refused at submit, and a job that does not fit
+beside the running ones waits for them.
 """
 import time
 
 import numpy as np
 import pytest
 
+import _parity
+import oracle
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -171,3 +176,83 @@ def test_submit_rejects_bad_jobs(fc, ctx, g2, w2):
     # an empty job completes at once
     t, _ = fc.fc_submit(ctx, g2, np.array([0], np.int64), 1, 0)
     assert _wait(fc, ctx, [t])[t][0] == fc.FC_OK
+
+
+def test_served_mix_matches_the_oracle(fc, ctx, g2, w2):
+    """Jobs submitted together (two mixed lanes with different iteration limits and top-k,
+    one binary64 lane) against complete oracle runs of the same points and seeds."""
+    specs = [(_points(w2, 2, 31), 41, 96, dict(max_iter=5)),
+             (_points(w2, 2, 32), 42, 80, dict(max_iter=3)),
+             (_points(w2, 1, 33), 43, 64, dict(max_iter=5, top_k=16)),
+             (_points(w2, 1, 34), 44, 48, dict(max_iter=5, precision=0))]
+    tickets, outs = [], []
+    for ps, seed, U, opts in specs:
+        t, o = fc.fc_submit(ctx, g2, ps, seed, U, opts=opts, want_bestfit=True, want_nscans=True)
+        tickets.append(t)
+        outs.append(o)
+    res = _wait(fc, ctx, tickets)
+    for t, o, (ps, seed, U, opts) in zip(tickets, outs, specs):
+        assert res[t][0] == fc.FC_OK
+        od, ob, on = oracle.run_points(w2.S, w2.F, ps, seed, U, collapse=w2.collapse, n_fit=w2.n_fit,
+                                       max_iter=opts["max_iter"])
+        if opts.get("precision", 1) == 0:
+            _parity.check_plain(o[0], o[1], o[2], od, ob, on)
+        else:
+            _parity.check_grid(fc, ctx, g2, w2, ps, seed, o[0], o[1], o[2], od, ob, on, opts=opts,
+                               max_iter=opts["max_iter"], label=f"served {opts}")
+
+
+def test_budget_refuses_a_job_that_can_never_fit(fc, w2):
+    c = fc.fc_create(0, 4 << 30)
+    try:
+        w1 = workloads.cfg1()
+        g = fc.fc_load_grid(c, w1.S)
+        fc.fc_set_frac_cov(c, g, w1.F)
+        with pytest.raises(fc.FCError) as e:
+            fc.fc_submit(c, g, np.array([312], np.int64), 1, 10_000_000)
+        assert e.value.status == fc.FC_ERR_BUDGET
+        # the context keeps serving jobs that fit
+        t, o = fc.fc_submit(c, g, np.array([312], np.int64), 1, 64, want_bestfit=True, want_nscans=True)
+        assert _wait(fc, c, [t])[t][0] == fc.FC_OK
+    finally:
+        fc.fc_destroy(c)
+
+
+def test_budget_defers_admission_until_memory_frees(fc):
+    """Two jobs whose admission estimates together exceed the budget, each fitting alone:
+    the second waits until the first has finished, then runs; both give the results of
+    their synchronous runs."""
+    w1 = workloads.cfg1()
+    budget = 8 << 30
+    P, U = 24, 262144            # 6.3 M universes: about 0.6 of the budget each
+    rng = np.random.default_rng(17)
+    jobs = [(np.sort(rng.choice(w1.G, P, replace=False)).astype(np.int64), 51, dict(top_k=8)),
+            (np.sort(rng.choice(w1.G, P, replace=False)).astype(np.int64), 52, dict(top_k=16))]
+    ref_ctx = fc.fc_create(0)
+    try:
+        gr = fc.fc_load_grid(ref_ctx, w1.S)
+        fc.fc_set_frac_cov(ref_ctx, gr, w1.F)
+        refs = [fc.fc_run_points(ref_ctx, gr, ps, seed, U, opts=o) for ps, seed, o in jobs]
+    finally:
+        fc.fc_destroy(ref_ctx)
+    c = fc.fc_create(0, budget)
+    try:
+        g = fc.fc_load_grid(c, w1.S)
+        fc.fc_set_frac_cov(c, g, w1.F)
+        tickets, outs = [], []
+        for ps, seed, o in jobs:
+            t, out = fc.fc_submit(c, g, ps, seed, U, opts=o, want_bestfit=True, want_nscans=True)
+            tickets.append(t)
+            outs.append(out)
+        res = _wait(fc, c, tickets)
+        st = fc.fc_get_serve_stats(c)
+        assert st["deferred"] > 0
+        assert 0 < st["device_bytes"] <= budget
+        for t, out, ref in zip(tickets, outs, refs):
+            assert res[t][0] == fc.FC_OK
+            for a, b in zip(out, ref):
+                np.testing.assert_array_equal(a, b)
+        # the second job waited for the first: it finished later although it was submitted at once
+        assert res[tickets[1]][1] > res[tickets[0]][1]
+    finally:
+        fc.fc_destroy(c)

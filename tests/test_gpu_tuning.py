@@ -1,9 +1,9 @@
 """Large-N paths, kernel choices and the covariance cache.
 
-* N_fit > 61 (K > 64, up to K = 160 here): the tensor-core screen with
-  16-column K-slice stages and the tensor-core q-vectors (whole S~ tiles, or
-  K slices beside a resident W), against the oracle (same bars as the other
-  mixed-path tests).
+* N_fit > 61 (K > 64, up to K = 208 at the N_fit = 200 limit): the
+  tensor-core screen with 16-column K-slice stages and the tensor-core
+  q-vectors (whole S~ tiles, or K slices beside a resident W; binary32
+  q-vectors above K = 128), against the oracle (tests/_parity.py's bars).
 * Kernel choices (q-vector kernel, screen depth, A-image buffering, top-k
   or list first round) change speed only: the outputs are identical bit for
   bit.
@@ -16,12 +16,12 @@ import os
 import numpy as np
 import pytest
 
+import _parity
 import oracle
 import workloads
 
 pytestmark = pytest.mark.gpu
 
-TOL_MIXED = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -66,23 +66,21 @@ def w64():
 
 
 @pytest.fixture(scope="module")
+def w200():
+    # the bin limit: N_fit = 200 (K = 208, a 13-step K loop in the screen; binary32 q-vectors; the
+    # largest covariance, Cholesky and inverse)
+    S, F, axes = workloads.osc_2d(12, 12, 200, seed=9)
+    return workloads.Workload("osc12x12_n200", S, F, None, 200, np.array([5, 77, 143], np.int64), 64, 5, 13, axes)
+
+
+@pytest.fixture(scope="module")
 def w150():
     # D=2 grid with N=150 (K=160: q-vectors stream S~ in K slices beside a resident W)
     S, F, axes = workloads.osc_2d(20, 20, 150, seed=6)
     return workloads.Workload("osc20x20_n150", S, F, None, 150, np.array([37, 210, 399], np.int64), 100, 5, 4, axes)
 
 
-def _compare_mixed(d, b, od, ob, tol=TOL_MIXED, max_mism=0.02):
-    err = np.abs(d - od) / np.maximum(np.abs(od), 1.0)
-    assert np.all(np.isfinite(d))
-    assert err.max() <= tol, f"max rel err {err.max():.3e}"
-    assert (b != ob).mean() <= max_mism
-    q = np.array([0.68, 0.90, 0.95])
-    qg, qo = np.quantile(d, q, axis=1), np.quantile(od, q, axis=1)
-    assert np.all(np.abs(qg - qo) <= 1e-3 * np.maximum(np.abs(qo), 1e-3))
-
-
-@pytest.mark.parametrize("which", ["w3s", "w64", "w70", "w150"])
+@pytest.mark.parametrize("which", ["w3s", "w64", "w70", "w150", "w200"])
 def test_large_n_mixed_vs_oracle(fc, ctx, which, request):
     w = request.getfixturevalue(which)
     gid = _load(fc, ctx, w)
@@ -91,7 +89,21 @@ def test_large_n_mixed_vs_oracle(fc, ctx, which, request):
     st = fc.fc_get_stats(ctx)
     assert st["screen_launches"] > 0
     od, ob, on = oracle.run_points(w.S, w.F, w.points, w.seed, w.U, collapse=w.collapse, n_fit=w.n_fit)
-    _compare_mixed(d, b, od, ob)
+    _parity.check_grid(fc, ctx, gid, w, w.points, w.seed, d, b, n, od, ob, on, label=w.name)
+    fc.fc_unload_grid(ctx, gid)
+
+
+def test_n_fit_200_plain_and_fake_data(fc, ctx, w200):
+    """At the bin limit the plain binary64 path keeps the oracle's indices and scan counts
+    and the fake data its bits (systematic factor of 200 bins in global memory)."""
+    gid = _load(fc, ctx, w200)
+    d, b, n = fc.fc_run_points(ctx, gid, w200.points, w200.seed, w200.U, opts=dict(precision=fc.FC_PREC_FP64))
+    od, ob, on = oracle.run_points(w200.S, w200.F, w200.points, w200.seed, w200.U)
+    _parity.check_plain(d, b, n, od, ob, on)
+    np.testing.assert_array_equal(fc.fc_fake_data(ctx, gid, w200.points, w200.seed, w200.U, 200),
+                                  oracle.fake_data(w200.S, w200.F, w200.points, w200.seed, w200.U))
+    _, L = fc.fc_covariance(ctx, gid, 77, 200, 200, want_A=False)
+    np.testing.assert_array_equal(L, oracle.chol_sys(w200.S[77], w200.F))
     fc.fc_unload_grid(ctx, gid)
 
 
