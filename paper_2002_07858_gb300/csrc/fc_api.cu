@@ -1022,7 +1022,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 // report it before anything reads them
                 FC_TRY(check_status(c));
                 S->screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
-                ResolveArgs ra;
+                ResolveArgs ra{};
                 ra.tile_slot = tslot;
                 ra.tile_univ = tuniv;
                 ra.topk = rtopk;
@@ -1069,8 +1069,22 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     FC_TRY(scratch(c, "lrows", (size_t)n_tiles * kBM, &lrows));
                     launch_resolve_list(ra, ccount, n_tiles, cnt, lrows, cnts + 6, c->stream);
                 }
-                else
+                else {
+                    // work lists of the flat resolution: up to topk + 1 residuals per row, and
+                    // chi2_p of at most every row
+                    const size_t rows = (size_t)n_tiles * kBM;
+                    FC_TRY(scratch(c, "rs_items", rows * (rtopk + 1), &ra.items));
+                    FC_TRY(scratch(c, "rs_res", rows * (rtopk + 1), &ra.res));
+                    FC_TRY(scratch(c, "rs_base", rows, &ra.item_base));
+                    FC_TRY(scratch(c, "rs_items2", rows, &ra.items2));
+                    FC_TRY(scratch(c, "rs_res2", rows, &ra.res2));
+                    FC_TRY(scratch(c, "rs_cmin2", rows, &ra.cmin2));
+                    FC_TRY(scratch(c, "rs_counts", 2, &ra.counts));
+                    FC_TRY(scratch(c, "rs_tiles", (size_t)n_tiles, &ra.tile_items));
+                    FC_TRY(scratch(c, "rs_tiles2", (size_t)n_tiles, &ra.tile_items2));
+                    ra.n_sm = c->n_sm;
                     launch_resolve(ra, n_tiles, c->stream);
+                }
                 FC_TRY(stage_end(c, &S->ms_rescore));
                 return check_status(c);
             };
@@ -2210,7 +2224,7 @@ fc_status fc_submit(fc_ctx* c, const fc_job* job, uint64_t* ticket) {
     // results, work lists) and its share of the scan scratch (A-image row, bounds, candidates,
     // list counts), with the scratch buffers' growth headroom; it must fit the budget
     const size_t n = (size_t)job->P * job->U;
-    const size_t need = n * (((size_t)g->nfit * 4 + 64 + (size_t)g->K * 4 + 320) * 5 / 4);
+    const size_t need = n * (((size_t)g->nfit * 4 + 64 + (size_t)g->K * 4 + 320 + 17 * 16 + 24) * 5 / 4);
     if (c->budget && need > c->budget) return fail(FC_ERR_BUDGET, "job can never fit the device-memory budget");
     jr->need = need;
     it->second->busy++;

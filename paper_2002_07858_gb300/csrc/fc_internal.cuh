@@ -211,6 +211,19 @@ struct ResolveArgs {
     const int2* list_n;
     uint8_t* rmask;        // [n] nullable: bit of the round that decided each universe's scan, OR-ed in
     uint8_t round_bit;     // that bit; 0 = the top-k round (certificate alone or after rescoring)
+    // top-k rounds: residual work lists of the flat resolution (launch_resolve), sized by the caller:
+    // items/res [n_tiles * BM * (topk + 1)], item_base [n_tiles * BM], items2/res2/cmin2
+    // [n_tiles * BM], counts [2] (zeroed by launch_resolve)
+    int2* items;           // (tile row, grid index; -1 = the centre, for c_u)
+    double* res;           // residual chi2 of each item
+    int32_t* item_base;    // first item of each tile row
+    int2* items2;          // chi2_p of the rescored rows that finish: (tile row, true point)
+    double* res2;
+    double* cmin2;         // their chi2_min
+    int32_t* counts;       // [0] items, [1] items2
+    int2* tile_items;      // [n_tiles] (first item, item count) of each tile's items
+    int2* tile_items2;     // [n_tiles] the same for items2
+    int n_sm;
 };
 // Bits of a universe's round record (the FC_DECIDED_* values of fc.h).
 constexpr uint8_t kDecidedCert = 1, kDecidedRescored = 2, kDecidedTop16 = 4, kDecidedList = 8,

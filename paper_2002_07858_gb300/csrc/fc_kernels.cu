@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <float.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "fc_df.cuh"
@@ -99,6 +100,56 @@ __device__ double resid_df(const float2* __restrict__ W, int n, const float2* __
         acc = df_fma(acc, t, t);
     }
     return df_to(df_norm(acc.x, acc.y));
+}
+
+// resid_df with the residual vector in registers, for N_fit <= NR: every index
+// of r is a compile-time constant (the column loop is unrolled in blocks of
+// four and a block runs only when the row reaches it, a branch that is uniform
+// across the warp because all its lanes walk the same rows).  The operations
+// and their order are resid_df's, term for term, so the bits are the same;
+// what changes is that no per-thread array lives in local memory.
+template <int NR>
+__device__ __forceinline__ double resid_df_reg(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+                                               const float* __restrict__ du) {
+    static_assert(NR % 4 == 0, "NR is a multiple of 4");
+    float2 r[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) r[j] = (j < n) ? df_sub_f(s[j], du[j]) : make_float2(0.0f, 0.0f);
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int i = 0; i < n; ++i) {
+        const float2* Wi = W + i * n;
+        const int len = i + 1;
+        float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0, p3 = p0;
+#pragma unroll
+        for (int j = 0; j < NR; j += 4) {
+            if (j + 3 < len) {
+                p0 = df_fma(p0, Wi[j], r[j]);
+                p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
+                p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
+                p3 = df_fma(p3, Wi[j + 3], r[j + 3]);
+            } else if (j < len) {
+                p0 = df_fma(p0, Wi[j], r[j]);
+                if (j + 1 < len) p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
+                if (j + 2 < len) p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
+            }
+        }
+        const float2 a = df_add(df_norm(p0.x, p0.y), df_norm(p1.x, p1.y));
+        const float2 b = df_add(df_norm(p2.x, p2.y), df_norm(p3.x, p3.y));
+        const float2 t = df_add(a, b);
+        acc = df_fma(acc, t, t);
+    }
+    return df_to(df_norm(acc.x, acc.y));
+}
+
+// The mixed path's residual chi2 for a compile-time bound NR on N_fit (0 = any N_fit).
+template <int NR>
+__device__ __forceinline__ double resid_mixed(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+                                              const float* __restrict__ du) {
+    if constexpr (NR > 0)
+        return resid_df_reg<NR>(W, n, s, du);
+    else
+        return resid_df(W, n, s, du);
 }
 
 // resid_df spread over a warp with the same bits: r_j = s_j - d_j is formed in
@@ -1035,128 +1086,217 @@ constexpr int kItemP = kMaxTopK + 1;
 constexpr int kItemMin = kMaxTopK + 2;
 constexpr int kItemCodes = kMaxTopK + 3;
 
-// One CTA per screen tile (the 128 universes share one covariance), one thread
-// per universe:
+// Resolution of a top-k round, as five flat launches (launch_resolve): the
+// residuals are the work, and a tile's rows need very different numbers of
+// them, so they are evaluated from flat lists that keep every lane busy
+// instead of inside the tile's CTA (where the lanes of rows with few residuals
+// waited at barriers for the rows with many).
+//  k_resolve_emit     per row: the screen certificate (decide_row); the
+//                     residual items the row needs, appended in tile order;
+//  k_resid_items      every item's double-float residual chi2 (W of the row's
+//                     covariance slot; the residual vector in registers);
+//  k_resolve_conclude per row: the same decision again, then the rescored
+//                     minimum and its certificate; finish (dchi2) / advance /
+//                     hand on, exactly as one kernel did before; rescored rows
+//                     that finish with p != best list their chi2_p;
+//  k_resid_items      those chi2_p;
+//  k_resolve_tail     their dchi2.
+// Decision per row (§2 steps 3-4 with the screen's certificate):
 //  1. from the screen's lower bounds LB and upper bounds UB = LB + 2 eps of
 //     its candidates, accept the first candidate when it is the only one that
 //     can still be the minimum and its UB is below every outside bound tau;
-//  2. otherwise evaluate the binary64 residual-form chi2 of every candidate
-//     that can still be the minimum (and c_u = |W (d - v)|^2 when the
-//     certificate needs it), all lanes of the CTA sharing W in shared memory;
-//     take the first minimum and certify it against tau, else hand the
-//     universe to the exact fallback scan;
+//  2. otherwise the residual-form chi2 of every candidate that can still be
+//     the minimum (and c_u = |W (d - v)|^2 when the certificate needs it):
+//     the first minimum, certified against tau, else the universe is handed
+//     to the next round;
 //  3. universes whose minimum repeats their covariance index (or that used
-//     their last scan) get chi2_p and chi2_min in residual form and finish
-//     with dchi2; the others move their covariance index to the minimum.
-__global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
+//     their last scan) finish with dchi2 = chi2_p - chi2_min; the others
+//     move their covariance index to the minimum.
+struct RowDecision {
+    int state;  // 0 padding, 1 certified by the bounds, 2 rescoring, 3 nothing below the seed
+    bool full;
+    float tau, min_ub;
+    int ncodes;                      // residual items of the row, in emission order
+    uint8_t code[kMaxTopK + 1];      // candidate j < topk, kItemCu, kItemP, kItemMin
+    int32_t g[kMaxTopK];
+    float lb[kMaxTopK];
+};
+
+__device__ __forceinline__ void decide_row(const ResolveArgs& a, int64_t row, int slot, int u, RowDecision& D) {
+    const int topk = a.topk;
+    D.state = 0;
+    D.ncodes = 0;
+    D.full = false;
+    D.tau = FLT_MAX;
+    D.min_ub = FLT_MAX;
+    if (u < 0) return;
+    const float4 al = a.alpha[row];
+    float ub[kMaxTopK];
+    int nvalid = 0;
+    for (int j = 0; j < topk; ++j) {
+        const int32_t gj = a.cidx[row * topk + j];
+        D.g[j] = gj;
+        D.lb[j] = a.cval[row * topk + j];
+        ub[j] = FLT_MAX;
+        if (gj < 0) continue;
+        ++nvalid;
+        const int64_t q = (int64_t)slot * a.G_pad + gj;
+        const float eps = bound_dot(al, a.gnorm[gj]) + (a.Qc[q] - a.Qb[q]);
+        ub[j] = D.lb[j] + 2.0f * eps + 4.7683716e-07f * (fabsf(D.lb[j]) + fabsf(a.Qc[q]) + 1.0f);
+        D.min_ub = fminf(D.min_ub, ub[j]);
+    }
+    // every grid point outside the list has LB >= the k-th kept value; an empty slot holds the
+    // seed tau0 = UB of the row's probe, so a list that is not full holds every point that can
+    // be the minimum
+    D.full = (nvalid == topk);
+    D.tau = D.lb[topk - 1] - 4.7683716e-07f * (fabsf(D.lb[topk - 1]) + 1.0f);
+    int nR = 0;
+    for (int j = 0; j < topk; ++j)
+        if (D.g[j] >= 0 && D.lb[j] <= D.min_ub) ++nR;
+    if (nvalid == 0) {
+        D.state = 3;  // nothing below the seed: only possible with non-finite data
+    } else if (nR == 1 && ub[0] < D.tau) {
+        D.state = 1;
+        // a universe that finishes on this certificate needs chi2_p and chi2_min in residual form
+        if (D.g[0] == a.cur[u] || a.nscan[u] + 1 >= a.maxit[u]) {
+            if (a.pt[u] != D.g[0]) D.code[D.ncodes++] = (uint8_t)kItemP;
+            D.code[D.ncodes++] = (uint8_t)kItemMin;
+        }
+    } else {
+        D.state = 2;
+        for (int j = 0; j < topk; ++j)
+            if (D.g[j] >= 0 && D.lb[j] <= D.min_ub) D.code[D.ncodes++] = (uint8_t)j;
+        if (D.full && !(D.min_ub < D.tau)) D.code[D.ncodes++] = (uint8_t)kItemCu;
+    }
+}
+
+// exclusive prefix sum of v over a CTA of kBM threads; *total receives the sum
+__device__ __forceinline__ int block_excl_scan(int v, int* s_warp, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    int before = 0, sum = 0;
+    for (int w = 0; w < kBM / 32; ++w) {
+        before += (w < warp) ? s_warp[w] : 0;
+        sum += s_warp[w];
+    }
+    *total = sum;
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kBM) k_resolve_emit(ResolveArgs a) {
+    __shared__ int s_warp[kBM / 32];
+    __shared__ int s_base;
+    const int64_t t = blockIdx.x;
+    const int64_t row = t * kBM + threadIdx.x;
+    const int slot = a.tile_slot[t];
+    const int u = a.tile_univ[row];
+    RowDecision D;
+    decide_row(a, row, slot, u, D);
+    int total = 0;
+    const int off = block_excl_scan(D.ncodes, s_warp, &total);
+    if (threadIdx.x == 0) {
+        s_base = total ? atomicAdd(&a.counts[0], total) : 0;
+        a.tile_items[t] = make_int2(s_base, total);
+    }
+    __syncthreads();
+    const int base = s_base + off;
+    a.item_base[row] = base;
+    for (int k = 0; k < D.ncodes; ++k) {
+        const int c = D.code[k];
+        const int32_t g = (c < kMaxTopK) ? D.g[c] : (c == kItemCu ? -1 : (c == kItemP ? a.pt[u] : D.g[0]));
+        a.items[base + k] = make_int2((int32_t)row, g);
+    }
+}
+
+// Residual chi2 of one tile's items (a contiguous range, tile_items[t]): the
+// tile's universes share one covariance, so its W is staged once in shared
+// memory and every lane reads the same element at once; the lanes then stride
+// over the items with no further barrier.  Small CTAs (two warps) keep the
+// last, partly filled round of a tile cheap.
+constexpr int kResidThreads = 64;
+
+template <int NR>
+__global__ void __launch_bounds__(kResidThreads, 6) k_resid_tiles(const ResolveArgs a, const int2* __restrict__ items,
+                                                                 const int2* __restrict__ tile_items,
+                                                                 double* __restrict__ res) {
     extern __shared__ float2 sWd[];
-    __shared__ int s_nitem, s_nnext, s_nfb, s_cnt[3];
-    __shared__ int s_base_next, s_base_fb;
-    __shared__ uint16_t s_item[kBM * kItemCodes];
-    __shared__ double s_res[kBM][kItemCodes];
-    __shared__ int32_t s_g[kBM][kItemCodes];
-    __shared__ int32_t s_u[kBM];
+    const int n = a.nfit;
+    const int64_t t = blockIdx.x;
+    const int2 range = tile_items[t];
+    if (range.y == 0) return;  // uniform over the CTA
+    const float2* Wg = a.Wdf + (size_t)a.tile_slot[t] * n * n;
+    const float2* W = Wg;
+    if constexpr (NR > 0) {  // staged where it fits (N_fit <= 64)
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sWd[e] = Wg[e];
+        __syncthreads();
+        W = sWd;
+    }
+    for (int k = threadIdx.x; k < range.y; k += blockDim.x) {
+        const int64_t i = (int64_t)range.x + k;
+        const int2 it = items[i];
+        const int u = a.tile_univ[it.x];
+        const float2* sv = (it.y < 0) ? a.centre_df : a.Sdf + (int64_t)it.y * n;
+        res[i] = resid_mixed<NR>(W, n, sv, a.d + (size_t)u * n);
+    }
+}
+
+__global__ void __launch_bounds__(kBM) k_resolve_conclude(ResolveArgs a) {
+    __shared__ int s_nnext, s_nfb, s_n2, s_cnt[3];
+    __shared__ int s_base_next, s_base_fb, s_base2;
     const int64_t t = blockIdx.x;
     const int r = threadIdx.x;
-    const int n = a.nfit;
+    const int64_t row = t * kBM + r;
     const int slot = a.tile_slot[t];
-    const float2* Wg = a.Wdf + (size_t)slot * n * n;
-    const bool staged = (n <= kResolveMaxN);
-    if (staged)
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sWd[e] = Wg[e];
-    const float2* W = staged ? sWd : Wg;
+    const int u = a.tile_univ[row];
     if (r == 0) {
-        s_nitem = 0;
         s_nnext = 0;
         s_nfb = 0;
+        s_n2 = 0;
         s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
     }
-    const int u = a.tile_univ[t * kBM + r];
-    s_u[r] = u;
-    const int64_t row = t * kBM + r;
+    __syncthreads();
+    RowDecision D;
+    decide_row(a, row, slot, u, D);
+    const int base = a.item_base[row];
     const int topk = a.topk;
-    __syncthreads();
-
-    // ---- 1. screen decision
-    int state = 0;  // 0 padding, 1 decided, 2 rescoring, 3 fallback
+    int state = D.state;
     int32_t g_best = -1;
-    double chi2_min = 0.0;
-    bool have_min = false;
-    bool early = false;  // decided here and finishing: chi2_p, chi2_min join the rescoring pass
-    float lb[kMaxTopK], ub[kMaxTopK];
-    bool full = false;
-    float tau = FLT_MAX, min_ub = FLT_MAX;
-    if (u >= 0) {
-        const float4 al = a.alpha[row];
-        int nvalid = 0;
-        for (int j = 0; j < topk; ++j) {
-            const int32_t gj = a.cidx[row * topk + j];
-            s_g[r][j] = gj;
-            lb[j] = a.cval[row * topk + j];
-            ub[j] = FLT_MAX;
-            if (gj < 0) continue;
-            ++nvalid;
-            const int64_t q = (int64_t)slot * a.G_pad + gj;
-            const float eps = bound_dot(al, a.gnorm[gj]) + (a.Qc[q] - a.Qb[q]);
-            ub[j] = lb[j] + 2.0f * eps + 4.7683716e-07f * (fabsf(lb[j]) + fabsf(a.Qc[q]) + 1.0f);
-            min_ub = fminf(min_ub, ub[j]);
-        }
-        // every grid point outside the list has LB >= the k-th kept value; an
-        // empty slot holds the seed tau0 = UB of the row's probe, so a list that is
-        // not full holds every point that can be the minimum
-        full = (nvalid == topk);
-        tau = lb[topk - 1] - 4.7683716e-07f * (fabsf(lb[topk - 1]) + 1.0f);
-        int nR = 0;
-        for (int j = 0; j < topk; ++j)
-            if (s_g[r][j] >= 0 && lb[j] <= min_ub) ++nR;
-        if (nvalid == 0) {
-            state = 3;  // nothing below the seed: only possible with non-finite data
-        } else if (nR == 1 && ub[0] < tau) {
-            state = 1;
-            g_best = s_g[r][0];
-            // a universe that finishes on this certificate needs chi2_p and chi2_min in residual
-            // form; they join the rescoring items below instead of a pass of their own
-            if (g_best == a.cur[u] || a.nscan[u] + 1 >= a.maxit[u]) {
-                early = true;
-                const int32_t pp = a.pt[u];
-                s_g[r][kItemP] = pp;
-                s_g[r][kItemMin] = g_best;
-                if (pp != g_best) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemP);
-                s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemMin);
+    double chi2_min = 0.0, chi2_p = 0.0;
+    bool have_min = false, have_p = false;
+    if (state == 1) {
+        g_best = D.g[0];
+        for (int k = 0; k < D.ncodes; ++k) {
+            if (D.code[k] == kItemMin) {
+                chi2_min = a.res[base + k];
+                have_min = true;
+            } else if (D.code[k] == kItemP) {
+                chi2_p = a.res[base + k];
+                have_p = true;
             }
-        } else {
-            state = 2;
-            for (int j = 0; j < topk; ++j)
-                if (s_g[r][j] >= 0 && lb[j] <= min_ub) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + j);
-            if (full && !(min_ub < tau)) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemCu);
         }
-    }
-    __syncthreads();
-    // ---- 2. binary64 residual-form rescoring of the open candidates
-    for (int it = threadIdx.x; it < s_nitem; it += blockDim.x) {
-        const int code = s_item[it];
-        const int rr = code / kItemCodes, j = code % kItemCodes;
-        const float* du = a.d + (size_t)s_u[rr] * n;
-        const float2* sv = (j == kItemCu) ? a.centre_df : a.Sdf + (int64_t)s_g[rr][j] * n;
-        s_res[rr][j] = resid_df(W, n, sv, du);
-    }
-    __syncthreads();
-    if (state == 2) {
-        double bchi = DBL_MAX;
+        atomicAdd(&s_cnt[0], 1);
+    } else if (state == 2) {
+        double bchi = DBL_MAX, cu = 0.0;
         int32_t bg = INT32_MAX;
-        for (int j = 0; j < topk; ++j) {
-            if (s_g[r][j] < 0 || lb[j] > min_ub) continue;
-            const double c = s_res[r][j];
-            if (c < bchi || (c == bchi && s_g[r][j] < bg)) {
-                bchi = c;
-                bg = s_g[r][j];
+        for (int k = 0; k < D.ncodes; ++k) {
+            const int c = D.code[k];
+            const double v = a.res[base + k];
+            if (c == kItemCu) {
+                cu = v;
+            } else if (v < bchi || (v == bchi && D.g[c] < bg)) {
+                bchi = v;
+                bg = D.g[c];
             }
         }
-        bool ok = !full || (min_ub < tau);
-        if (!ok) {
-            const double cu = s_res[r][kItemCu];
-            ok = (double)tau > (bchi - cu) + 1e-9 * (fabs(bchi) + fabs(cu));
-        }
+        bool ok = !D.full || (D.min_ub < D.tau);
+        if (!ok) ok = (double)D.tau > (bchi - cu) + 1e-9 * (fabs(bchi) + fabs(cu));
         if (ok) {
             state = 1;
             g_best = bg;
@@ -1167,38 +1307,29 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
             state = 3;
             atomicAdd(&s_cnt[2], 1);
             // every grid point that can still be the minimum has LB <= sigma* = chi2_min - c_u of the
-            // best candidate found: a second screen seeded with sigma* (rounded up) lists all of them
+            // best candidate found: a list screen seeded with sigma* (rounded up) lists all of them
             if (a.thr) {
-                const double cu = s_res[r][kItemCu];
                 const double sig = (bchi - cu) + 1e-9 * (fabs(bchi) + fabs(cu));
                 a.thr[u] = __double2float_ru(sig) + 4.7683716e-07f * (fabsf((float)sig) + 1.0f);
             }
         }
-    } else if (state == 1) {
-        atomicAdd(&s_cnt[0], 1);
     } else if (state == 3) {
         atomicAdd(&s_cnt[2], 1);
         if (a.thr) a.thr[u] = FLT_MAX;
     }
+    (void)topk;
     if (state == 1 && a.rmask)
-        a.rmask[u] |= a.round_bit ? a.round_bit : (have_min ? kDecidedRescored : kDecidedCert);
-    __syncthreads();
-    if (r == 0) s_nitem = 0;
-    __syncthreads();
-    // ---- 3. finish converged / exhausted universes, advance the others
-    bool finishing = false;
+        a.rmask[u] |= a.round_bit ? a.round_bit : (D.state == 2 ? kDecidedRescored : kDecidedCert);
+    // finish converged / exhausted universes, advance the others
+    bool finishing = false, tail = false;
     int32_t p = -1;
     if (state == 1) {
         a.best[u] = g_best;
         finishing = (g_best == a.cur[u]) || (a.nscan[u] + 1 >= a.maxit[u]);
         if (finishing) {
             p = a.pt[u];
-            if (!early) {
-                s_g[r][kItemP] = p;
-                s_g[r][kItemMin] = g_best;
-                if (p != g_best) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemP);
-                if (!have_min) s_item[atomicAdd(&s_nitem, 1)] = (uint16_t)(r * kItemCodes + kItemMin);
-            }
+            // a rescored row that finishes still needs chi2_p (the certified ones listed it already)
+            tail = (p != g_best) && !have_p;
         } else {
             a.cur[u] = g_best;
             a.nscan[u] = (int8_t)(a.nscan[u] + 1);
@@ -1207,26 +1338,38 @@ __global__ void __launch_bounds__(kBM) k_resolve(ResolveArgs a) {
     const bool to_next = (state == 1 && !finishing);
     const int my_next = to_next ? atomicAdd(&s_nnext, 1) : -1;
     const int my_fb = (state == 3) ? atomicAdd(&s_nfb, 1) : -1;
+    const int my_2 = tail ? atomicAdd(&s_n2, 1) : -1;
     __syncthreads();
     if (r == 0) {
         s_base_next = s_nnext ? atomicAdd(a.n_next, s_nnext) : 0;
         s_base_fb = s_nfb ? atomicAdd(a.n_fb, s_nfb) : 0;
+        s_base2 = s_n2 ? atomicAdd(&a.counts[1], s_n2) : 0;
+        a.tile_items2[t] = make_int2(s_base2, s_n2);
         if (s_cnt[0]) atomicAdd(&a.counters[0], (unsigned long long)s_cnt[0]);
         if (s_cnt[1]) atomicAdd(&a.counters[1], (unsigned long long)s_cnt[1]);
         if (s_cnt[2]) atomicAdd(&a.counters[2], (unsigned long long)s_cnt[2]);
     }
-    for (int it = threadIdx.x; it < s_nitem; it += blockDim.x) {
-        const int code = s_item[it];
-        const int rr = code / kItemCodes, j = code % kItemCodes;
-        const float* du = a.d + (size_t)s_u[rr] * n;
-        s_res[rr][j] = resid_df(W, n, a.Sdf + (int64_t)s_g[rr][j] * n, du);
-    }
     __syncthreads();
     if (to_next) a.next[s_base_next + my_next] = u;
     if (state == 3) a.fb[s_base_fb + my_fb] = u;
-    if (finishing) {
-        const double cmin = have_min ? chi2_min : s_res[r][kItemMin];
-        a.dchi2[u] = (p == g_best) ? 0.0 : s_res[r][kItemP] - cmin;
+    if (tail) {
+        a.items2[s_base2 + my_2] = make_int2((int32_t)row, p);
+        a.cmin2[s_base2 + my_2] = chi2_min;
+    } else if (finishing) {
+        a.dchi2[u] = (p == g_best) ? 0.0 : chi2_p - chi2_min;
+        if (a.chi2min) a.chi2min[u] = chi2_min;
+        a.nscan[u] = (int8_t)(a.nscan[u] + 1);
+        atomicSub(&a.job_left[a.job_of[u]], 1);
+    }
+}
+
+__global__ void k_resolve_tail(ResolveArgs a) {
+    const int64_t total = a.counts[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int u = a.tile_univ[a.items2[i].x];
+        const double cmin = a.cmin2[i];
+        a.dchi2[u] = a.res2[i] - cmin;
         if (a.chi2min) a.chi2min[u] = cmin;
         a.nscan[u] = (int8_t)(a.nscan[u] + 1);
         atomicSub(&a.job_left[a.job_of[u]], 1);
@@ -1678,11 +1821,32 @@ void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
     if (n_tiles <= 0) return;
-    const size_t smem = a.nfit <= kResolveMaxN ? (size_t)a.nfit * a.nfit * sizeof(double) : 0;
-    cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kResolveMaxN * kResolveMaxN * (int)sizeof(double));
-    count_launch();
-    k_resolve<<<(unsigned)n_tiles, kBM, smem, st>>>(a);
+    cudaMemsetAsync(a.counts, 0, 2 * sizeof(int32_t), st);
+    // the tail loops over its device-side count
+    const unsigned g3 = (unsigned)std::min<int64_t>(n_tiles, (int64_t)a.n_sm * 8);
+    const size_t smem = (a.nfit <= 64 ? (size_t)a.nfit * a.nfit : 0) * sizeof(float2);
+    auto resid = [&](const int2* items, const int2* tile_items, double* res) {
+        auto run = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * (int)sizeof(float2));
+            kern<<<(unsigned)n_tiles, kResidThreads, smem, st>>>(a, items, tile_items, res);
+        };
+        if (a.nfit <= 16)
+            run(k_resid_tiles<16>);
+        else if (a.nfit <= 32)
+            run(k_resid_tiles<32>);
+        else if (a.nfit <= 48)
+            run(k_resid_tiles<48>);
+        else if (a.nfit <= 64)
+            run(k_resid_tiles<64>);
+        else
+            run(k_resid_tiles<0>);
+    };
+    count_launch(5);
+    k_resolve_emit<<<(unsigned)n_tiles, kBM, 0, st>>>(a);
+    resid(a.items, a.tile_items, a.res);
+    k_resolve_conclude<<<(unsigned)n_tiles, kBM, 0, st>>>(a);
+    resid(a.items2, a.tile_items2, a.res2);
+    k_resolve_tail<<<g3, 256, 0, st>>>(a);
 }
 
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const int32_t* best, const UniverseState& us,

@@ -63,21 +63,37 @@ __device__ __forceinline__ float min32(const uint32_t (&r)[32]) {
     return fmin3(a, b, fminf(c, fminf(m[9], m[10])));
 }
 
-// (value, index) insertion into a sorted list, lexicographic order
+// (value, index) insertion into a list sorted in lexicographic order, the
+// last entry dropping out.  Every position compares with the new pair at once
+// (the outcomes are monotone in t because the list is sorted), then each entry
+// takes its left neighbour, the new pair or itself: a few dependent steps
+// instead of a chain through all TOPK positions, for an epilogue that waits on
+// latency, not on issue slots.
 template <int TOPK>
 __device__ __forceinline__ void topk_insert(float (&vals)[TOPK], int32_t (&idx)[TOPK], float x, int32_t g) {
-    float cx = x;
-    int32_t cg = g;
+    bool c[TOPK];
 #pragma unroll
-    for (int t = 0; t < TOPK; ++t) {
-        const bool sw = cx < vals[t] || (cx == vals[t] && cg < idx[t]);
-        const float tv = vals[t];
-        const int32_t ti = idx[t];
-        vals[t] = sw ? cx : tv;
-        idx[t] = sw ? cg : ti;
-        cx = sw ? tv : cx;
-        cg = sw ? ti : cg;
+    for (int t = 0; t < TOPK; ++t) c[t] = x < vals[t] || (x == vals[t] && g < idx[t]);
+#pragma unroll
+    for (int t = TOPK - 1; t >= 1; --t) {
+        vals[t] = c[t - 1] ? vals[t - 1] : (c[t] ? x : vals[t]);
+        idx[t] = c[t - 1] ? idx[t - 1] : (c[t] ? g : idx[t]);
     }
+    vals[0] = c[0] ? x : vals[0];
+    idx[0] = c[0] ? g : idx[0];
+}
+
+// Bit i set when value i of the chunk is at or below tau: four independent
+// 8-bit groups, combined at the end (a short dependency chain).
+__device__ __forceinline__ uint32_t below_mask(const uint32_t (&r)[32], float tau) {
+    uint32_t q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        q[k] = 0u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) q[k] |= (__uint_as_float(r[8 * k + i]) <= tau ? 1u : 0u) << i;
+    }
+    return (q[0] | (q[1] << 8)) | ((q[2] << 16) | (q[3] << 24));
 }
 
 // 32 lower bounds of one row (columns g0..g0+31): running top-k.  Fast path:
@@ -90,9 +106,7 @@ __device__ __forceinline__ void topk_chunk(float (&vals)[TOPK], int32_t (&idx)[T
                                            float m, int64_t g0, int64_t G, float* scratch, int lane) {
     if (m <= vals[TOPK - 1]) {
         const float tau = vals[TOPK - 1];
-        uint32_t mask = 0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) mask |= (__uint_as_float(r[i]) <= tau ? 1u : 0u) << i;
+        uint32_t mask = below_mask(r, tau);
         const int64_t lim = G - g0;
         if (lim < 32) mask &= (lim <= 0) ? 0u : ((1u << lim) - 1u);
         if (__popc(mask) == 1) {
@@ -131,9 +145,7 @@ constexpr int kModeList = 2;
 __device__ __forceinline__ void list_chunk(int32_t& n, int32_t cap, float* __restrict__ lval, int32_t* __restrict__ lidx,
                                            float seed, const uint32_t (&r)[32], float m, int64_t g0, int64_t G) {
     if (m <= seed) {
-        uint32_t mask = 0;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) mask |= (__uint_as_float(r[i]) <= seed ? 1u : 0u) << i;
+        uint32_t mask = below_mask(r, seed);
         const int64_t lim = G - g0;
         if (lim < 32) mask &= (lim <= 0) ? 0u : ((1u << lim) - 1u);
         while (mask) {
