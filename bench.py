@@ -37,10 +37,11 @@ UNIT = "chi2 evals/s"
 
 # DRAM bytes (read + write) per screened universe row of the tensor-core screen on the
 # 100x100 grid with N 90->45 (K = 48): an ncu capture of one top-8 launch over 10^6
-# universes read 368.0 MB and wrote 56.4 MB.  The traffic is the rows' A images, the
-# q-step rows of their covariance slots and the candidate lists, so a launch's traffic
-# is taken as proportional to the rows it screens.
-SCREEN_DRAM_BYTES_PER_ROW_CFG2 = 424.3
+# universes (the current kernel, parallel top-k insertion) read 367.0 MB and wrote
+# 56.3 MB.  The traffic is the rows' A images, the q-step rows of their covariance
+# slots and the candidate lists, so a launch's traffic is taken as proportional to the
+# rows it screens.
+SCREEN_DRAM_BYTES_PER_ROW_CFG2 = 423.3
 
 
 def _peaks():
@@ -135,6 +136,77 @@ def _oracle_sample(w, target_s: float, nthreads: int, seed: int = 0, max_points:
     return {"value": evals / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{P} true points x {U} universes of {w.name}, {evals:.3e} chi2 evals in {dt:.1f} s",
             "universes_per_s": P * U / dt}
+
+
+def resid_fp32_ops(n: int) -> int:
+    """binary32 operations of one double-float residual chi2 = |W (s - d)|^2 over n bins: 10 per element of
+    r = s - d, 12 per double-float multiply-add (n(n+1)/2 of them in W r, n in the squares), 45 to combine the
+    four partial sums of a row, 3 to round the total."""
+    return 6 * n * n + 73 * n + 3
+
+
+def _cfg3_step(fc, ctx, peak_bf16):
+    """One cold-cache step of the D=3 workload (2048 points x 500 universes), CUDA-event timed after one
+    untimed step: where the per-universe covariance refits decide the cost."""
+    import torch
+
+    import workloads
+
+    w = workloads.cfg3()
+    gid = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+    stream = torch.cuda.current_stream()
+    opts = dict(precision=fc.FC_PREC_MIXED, top_k=8, max_iter=w.max_iter)
+    n = len(w.points) * w.U
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ps = torch.from_numpy(w.points).to(dev)
+    outs = (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.int64, device=dev),
+            torch.empty(n, dtype=torch.int8, device=dev))
+    fc.fc_set_frac_cov(ctx, gid, w.F)
+    fc.fc_run_points(ctx, gid, ps, 1, w.U, opts, *outs)
+    fc.fc_set_frac_cov(ctx, gid, w.F)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fc.fc_run_points(ctx, gid, ps, 2, w.U, opts, *outs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = fc.fc_get_stats(ctx)
+    fc.fc_unload_grid(ctx, gid)
+    ms = st["ms_total"]
+    achieved = st["screen_flops"] / (st["ms_screen"] / 1e3) / 1e12 if st["ms_screen"] > 0 else 0.0
+    return {"workload": f"cfg3: D=3 64^3 grid (262144 points), N=120, {len(w.points)} true points x {w.U} universes, "
+                        "<= 5 scans, top-8, cold covariance cache",
+            "ms_per_step": ms, "wall_ms": wall * 1e3, "value": st["chi2_evals"] / (ms / 1e3), "unit": UNIT,
+            "universes_per_s": n / (ms / 1e3),
+            "stage_ms": {k: st[k] for k in ("ms_fake", "ms_cov", "ms_prep", "ms_screen", "ms_rescore")},
+            "scans": st["scans"], "distinct_cov": st["distinct_cov"],
+            "screen_fill": st["screen_rows"] / max(1, 128 * st["screen_tiles"]),
+            "screen_roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_bf16, "unit": "TFLOP/s",
+                                "frac": achieved / peak_bf16}}
+
+
+def _cfg4_below_saturation(fc, device, rate, window, drain):
+    """The serving stream (cfg4 pool, 80 GB budget) offered below its saturation rate: p50/p99 latency."""
+    import numpy as np
+
+    import workloads
+
+    pool = workloads.cfg4_pool()
+    ctx = fc.fc_create(device, 80 << 30, None)
+    try:
+        gids = []
+        for w in pool:
+            g = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+            fc.fc_set_frac_cov(ctx, g, w.F)
+            gids.append(g)
+        sizes = [w.G for w in pool]
+        for g, G in zip(gids, sizes):
+            fc.fc_run_points(ctx, g, np.array([G // 2], np.int64), 1, 128)
+        r = _serve_stream(fc, ctx, gids, sizes, rate, window, 7, drain)
+    finally:
+        fc.fc_destroy(ctx)
+    r["workload"] = ("cfg4 serving stream: 8 resident grids (D 2-4, G log-U[1e3,1e6], N U{40..200}), one true point "
+                     "per job, U log-U[100,1e4], Poisson arrivals, 80 GB budget")
+    return r
 
 
 def _dist_init():
@@ -294,7 +366,7 @@ def run_native(args):
     roofline = {"kernel": "k_screen (tcgen05 BF16 hi/lo screen + fused top-k)", "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"bf16_tflops_sustained ({peak_src})", "traffic": traffic,
-                "traffic_source": ("DRAM bytes per launch: an ncu capture of one top-8 launch (424.3 B per "
+                "traffic_source": ("DRAM bytes per launch: an ncu capture of one top-8 launch (423.3 B per "
                                    "screened row) scaled by the rows each launch screens") if traffic else None,
                 "flops_per_eval": 2 * w.n_fit, "launches": scr_launch,
                 "avg_launch_ms": scr_ms / max(scr_launch, 1)}
@@ -317,6 +389,18 @@ def run_native(args):
 
     line = None
     if rank == 0:
+        # measured fma rates of this GPU: denominators of the binary64 and double-float rooflines
+        fp64_peak, fp32_peak = fc.fc_measure_peaks(ctx)
+        # ---- rescoring: double-float residuals on the FP32 pipe (binary32 operations / s against the fma probe)
+        n_res = sum(s["residuals"] for s in stats)
+        res_ms = sum(s["ms_rescore"] for s in stats)
+        res_ops = n_res * resid_fp32_ops(w.n_fit) / (res_ms / 1e3) / 1e12 if res_ms > 0 else 0.0
+        roofline_rescoring = {"kernel": "k_resid_tiles / k_resolve_list (double-float residual chi2)",
+                              "bound": "alu", "achieved": res_ops, "peak": fp32_peak / 2.0, "unit": "Top/s",
+                              "frac": res_ops / (fp32_peak / 2.0) if fp32_peak else None,
+                              "peak_source": "fc_measure_peaks binary32 fma probe (this run), 1 op per fma",
+                              "residuals_per_step": n_res / len(stats),
+                              "ops_per_residual": resid_fp32_ops(w.n_fit)}
         # ---- plain binary64 GPU fit on a sample (same metric)
         plain = None
         if not args.no_plain:
@@ -336,8 +420,20 @@ def run_native(args):
             torch.cuda.synchronize()
             st = fc.fc_get_stats(ctx)
             pv = st["chi2_evals"] / (a.elapsed_time(b) / 1e3)
+            # the scan kernel's own rate: 2 N_fit binary64 flops per chi2 eval (one fma per bin)
+            scan_tf = 2.0 * w.n_fit * st["chi2_evals"] / (st["ms_scan64"] / 1e3) / 1e12 if st["ms_scan64"] else 0.0
             plain = {"value": pv, "unit": UNIT, "sample": f"{n_pp} true points x {U} universes, "
-                                                          "cold covariance cache", "mixed_speedup": value / ws / pv}
+                                                          "cold covariance cache", "mixed_speedup": value / ws / pv,
+                     "stage_ms": {k: st[k] for k in ("ms_fake", "ms_cov", "ms_scan64", "ms_finish")},
+                     "scan_roofline": {"kernel": "k_scan64 (register-tiled binary64 y.s contraction)",
+                                       "bound": "fp64", "achieved": scan_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                                       "frac": scan_tf / fp64_peak if fp64_peak else None,
+                                       "peak_source": "fc_measure_peaks (binary64 fma probe, this run)"}}
+        extras = {}
+        if not args.no_extras and args.config == "cfg2":
+            extras["cfg3"] = _cfg3_step(fc, ctx, peak)
+            extras["cfg4_below_saturation"] = _cfg4_below_saturation(fc, local_rank, args.serve_rate_low,
+                                                                       args.serve_seconds_low, args.serve_drain)
         cpu = None
         if not args.no_cpu_baseline:
             cpu = _oracle_sample(w, args.cpu_seconds, len(os.sched_getaffinity(0)))
@@ -357,8 +453,10 @@ def run_native(args):
                 "stage_ms_per_step": stage,
                 "scan_counts": {k: sum(s[k] for s in stats) for k in ("scans", "screened", "rescored", "fallback",
                                                                       "distinct_cov")},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
+                "roofline": roofline, "roofline_rescoring": roofline_rescoring,
+                "measured_fma_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), **extras}
         print(json.dumps(line), flush=True)
     fc.fc_destroy(ctx)
     if dist:
@@ -573,7 +671,11 @@ def main():
     ap.add_argument("--serve", action="store_true", help="cfg4 serving stream: p50/p99 job latency (own JSON line)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="offered jobs/s of the overload stream")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the overload stream")
-    ap.add_argument("--serve-seconds-low", type=float, default=20.0, help="arrival window below saturation")
+    ap.add_argument("--serve-seconds-low", type=float, default=15.0, help="arrival window below saturation")
+    ap.add_argument("--serve-rate-low", type=float, default=1.5,
+                    help="offered jobs/s of the default line's below-saturation cfg4 stream")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the cfg3 step and the cfg4 below-saturation stream of the default line")
     ap.add_argument("--serve-drain", type=float, default=240.0, help="seconds after a window before cancelling")
     ap.add_argument("--sweep", action="store_true", help="job time vs universes and vs grid size (own JSON line)")
     args = ap.parse_args()

@@ -127,6 +127,8 @@ typedef struct {
                                  (the budget held by running jobs)                   */
     int64_t device_bytes;     /* device memory the context holds now (all grids,
                                  caches, lanes and scratch)                          */
+    int64_t residuals;        /* mixed path: residual-form chi2 evaluated in
+                                 double-float (rescoring, chi2_p, chi2_min)          */
 } fc_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -339,6 +341,13 @@ FC_API fc_status fc_get_tuning(fc_ctx* ctx, int32_t grid_id, fc_tuning* t);
  * skips the timing, a miss appends the new result.  The covariance cache is
  * cleared afterwards.  Errors: as fc_run_points. */
 FC_API fc_status fc_autotune(fc_ctx* ctx, int32_t grid_id, const char* cache_path, fc_tuning* out);
+
+/* Measured fma rates of the context's device (TFLOP/s, 2 flops per fma):
+ * binary64 and binary32, each from a probe kernel of independent fma chains
+ * with no memory traffic, best of three timed launches.  The denominators of
+ * the plain path's roofline (binary64 pipe) and of the double-float
+ * rescoring's (binary32 pipe).  Errors: FC_ERR_ARG, FC_ERR_CUDA. */
+FC_API fc_status fc_measure_peaks(fc_ctx* ctx, double* fp64_tflops, double* fp32_tflops);
 
 /* Test hook for failure detection without a GPU fault.  Every wait of the
  * tensor-core screen on a pipeline barrier is bounded; when one runs out the

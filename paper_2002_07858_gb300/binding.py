@@ -33,7 +33,7 @@ EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
            "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
            "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats", "fc_data_dchi2", "fc_fc_region",
-           "fc_fc_region_adaptive", "fc_load_grid_osc", "fc_get_decided_by", "fc_set_wait_test"]
+           "fc_fc_region_adaptive", "fc_load_grid_osc", "fc_get_decided_by", "fc_set_wait_test", "fc_measure_peaks"]
 
 
 class FCError(RuntimeError):
@@ -62,7 +62,8 @@ class fc_stats(ctypes.Structure):
                                        "ms_scan64", "ms_finish", "ms_total")] + [
         ("evicted", ctypes.c_int64), ("cache_slots", ctypes.c_int64), ("max_distinct_cov", ctypes.c_int64),
         ("scan_waves", ctypes.c_int64), ("big_listed", ctypes.c_int64), ("screen_tiles", ctypes.c_int64),
-        ("screen_rows", ctypes.c_int64), ("deferred", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+        ("screen_rows", ctypes.c_int64), ("deferred", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("residuals", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -123,6 +124,7 @@ def load(build: bool = False):
         "fc_get_serve_stats": (st, [vp, ctypes.POINTER(fc_stats)]),
         "fc_get_decided_by": (st, [vp, vp, i64]),
         "fc_set_wait_test": (st, [vp, u64, i64]),
+        "fc_measure_peaks": (st, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "fc_data_dchi2": (st, [vp, i32, vp, vp, i32, ctypes.POINTER(fc_opts), vp, vp, vp]),
         "fc_fc_region": (st, [vp, vp, i32, i32, vp, ctypes.c_double, vp, vp]),
         "fc_fc_region_adaptive": (st, [vp, i32, vp, i32, vp, ctypes.c_double, i32, i32, ctypes.c_double, u64,
@@ -396,6 +398,13 @@ def fc_get_serve_stats(ctx) -> dict:
     s = fc_stats()
     _check(load().fc_get_serve_stats(ctx, ctypes.byref(s)), ctx)
     return s.as_dict()
+
+
+def fc_measure_peaks(ctx) -> tuple[float, float]:
+    """(fp64, fp32) fma TFLOP/s of the context's device, measured by probe kernels."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().fc_measure_peaks(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
 
 
 def fc_set_wait_test(ctx, wait_ns: int = 0, screen_stop_after: int = -1):

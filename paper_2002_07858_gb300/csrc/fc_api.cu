@@ -601,7 +601,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
     if (!q64_list.empty()) {
         FC_TRY(ensure_q64_storage(c, g));
         FC_CUDA(cudaMemcpyAsync(ds, q64_list.data(), q64_list.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        launch_qvec64(g->Sc, g->G, g->nfit, g->A64, ds, (int)q64_list.size(), g->G, g->Q64, c->stream);
+        launch_qvec64(g->Sc, g->G, g->nfit, g->W64, ds, (int)q64_list.size(), g->G, g->Q64, c->stream);
         FC_TRY(sync(c));
     }
     return FC_OK;
@@ -881,7 +881,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     us.maxit = L->maxit;
     us.job_of = L->job_of;
     us.job_left = L->job_left;
-    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 12 * sizeof(unsigned long long), c->stream));
+    FC_CUDA(cudaMemsetAsync(c->counters_dev, 0, 13 * sizeof(unsigned long long), c->stream));
     // exact binary64 scan for `list`, then advance / finish them
     auto exact_scan = [&](const int32_t* list, int64_t cnt) -> fc_status {
         std::vector<int32_t> fq;
@@ -903,6 +903,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             stage_begin(c);
             launch_scan_resid(list, cnt, fslot, d, g->Sdf, g->G, g->nfit, g->Wdf, pv, pg, nsp, L->best,
                               c->stream);
+            S->residuals += cnt * g->G;
             FC_TRY(stage_end(c, &S->ms_fallback));
         } else if (o.cov == FC_COV_IDENTITY) {
             FC_TRY(ensure_slots(c, g, fq, o.cov, false, true, nullptr));
@@ -943,6 +944,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             stage_begin(c);
             launch_finish(fin, n_fin, finslot, L->best, us, d, g->S_fit, g->nfit, g->W64, mixed ? g->Sdf : nullptr,
                           mixed ? g->Wdf : nullptr, L->dchi2, L->chi2min, c->stream);
+            if (mixed) S->residuals += 2 * (int64_t)n_fin;
             FC_TRY(stage_end(c, &S->ms_finish));
         }
         return FC_OK;
@@ -1055,6 +1057,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 ra.fb = fb_out;
                 ra.n_fb = n_fb_out;
                 ra.counters = c->counters_dev + 3 * round;
+                ra.n_resid = c->counters_dev + 12;
                 ra.thr = thr;
                 ra.lcount = (round == 2) ? lcount : nullptr;
                 ra.list_off = loff;
@@ -1262,7 +1265,8 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     FC_CUDA(cudaMemcpyAsync(&n_next, cnts + 2, 4, cudaMemcpyDeviceToHost, c->stream));
     // [0..2] round 1: screened, rescored, handed on; [3..5] round 2 likewise; [6] listed, [7] list
     // overflow; [9] resolved from exact-size lists, [10] their failures (counted with the fallback)
-    unsigned long long cn[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // [12] residual chi2 evaluated by the certified rounds
+    unsigned long long cn[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     FC_CUDA(cudaMemcpyAsync(cn, c->counters_dev, sizeof(cn), cudaMemcpyDeviceToHost, c->stream));
     FC_TRY(sync(c));
     std::swap(L->active, L->next);
@@ -1271,6 +1275,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     S->rescored += (int64_t)(cn[1] + cn[4] + cn[6] + cn[9]);
     S->rescreened += (int64_t)(cn[2] + cn[5]);
     S->big_listed += (int64_t)(cn[9] + cn[10]);
+    S->residuals += (int64_t)cn[12];
     return check_status(c);
 }
 
@@ -2410,6 +2415,15 @@ fc_status fc_get_serve_stats(fc_ctx* c, fc_stats* out) {
     *out = c->serve_stats;
     out->device_bytes = (int64_t)c->used;
     return FC_OK;
+}
+
+fc_status fc_measure_peaks(fc_ctx* c, double* fp64_tflops, double* fp32_tflops) {
+    if (!c || !fp64_tflops || !fp32_tflops) return fail(FC_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->api_mu);
+    cudaSetDevice(c->device);
+    if (!measure_fma_peaks(c->n_sm, fp64_tflops, fp32_tflops, c->stream))
+        return fail(FC_ERR_CUDA, "fma peak probe failed");
+    return sync(c);
 }
 
 fc_status fc_set_wait_test(fc_ctx* c, uint64_t wait_ns, int64_t screen_stop_after) {

@@ -90,8 +90,8 @@ void launch_chol_sys(const double* S_full, int nf, const double* F, const int64_
 void launch_build_cov(const double* S_full, int nf, int nfit, const int32_t* collapse, const double* F,
                       const int32_t* q_list, const int32_t* slot_list, int n, int cov_mode, double* A64,
                       double* W64, float* A32, float* rho, double* work, int* status, cudaStream_t st);
-// q_g = s~_g^T A s~_g for slots: binary64 (plain) or binary32 central + lower bound (mixed).
-void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
+// q_g = s~_g^T A s~_g for slots: binary64 |W s~_g|^2 (plain) or binary32 central + lower bound (mixed).
+void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* W64, const int32_t* slots, int n,
                    int64_t ldq, double* Q64, cudaStream_t st);
 void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
@@ -223,6 +223,7 @@ struct ResolveArgs {
     int32_t* counts;       // [0] items, [1] items2
     int2* tile_items;      // [n_tiles] (first item, item count) of each tile's items
     int2* tile_items2;     // [n_tiles] the same for items2
+    unsigned long long* n_resid;  // residual chi2 evaluated (all rounds)
     int n_sm;
 };
 // Bits of a universe's round record (the FC_DECIDED_* values of fc.h).
@@ -257,6 +258,9 @@ void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot_of_list,
 // advance: converged / exhausted universes -> finish list, others stay active
 void launch_advance(const int32_t* active, int64_t n_active, const int32_t* best, const UniverseState& us,
                     int32_t* next_active, int32_t* n_next, int32_t* finish_list, int32_t* n_finish, cudaStream_t st);
+
+// ---- peak probes: FP64 / FP32 fma rates of this device (TFLOP/s) ----
+bool measure_fma_peaks(int n_sm, double* fp64_tflops, double* fp32_tflops, cudaStream_t st);
 
 // ---- quantiles ----
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st);

@@ -595,17 +595,21 @@ __global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, cons
 }
 
 // q_g = s~_g^T A s~_g in binary64, one thread per g
-__global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, const double* __restrict__ A64,
+// q_g = s~_g^T A s~_g = |W s~_g|^2 (A = W^T W, W lower triangular): t_i = sum_{j<=i}
+// W_ij s~_j and q = sum_i t_i^2, each an fma chain in increasing index, so
+// N (N + 3) / 2 DFMA per point instead of the N^2 + N of s~^T (A s~).
+__global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, const double* __restrict__ W64,
                          const int32_t* __restrict__ slots, int64_t ldq, double* __restrict__ Q64) {
     const int slot = slots[blockIdx.y];
-    const double* A = A64 + (size_t)slot * nfit * nfit;
+    const double* W = W64 + (size_t)slot * nfit * nfit;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
         const double* s = Sc + g * nfit;
         double q = 0.0;
         for (int i = 0; i < nfit; ++i) {
+            const double* Wi = W + i * nfit;
             double t = 0.0;
-            for (int j = 0; j < nfit; ++j) t = fma(A[i * nfit + j], s[j], t);
-            q = fma(s[i], t, q);
+            for (int j = 0; j <= i; ++j) t = fma(Wi[j], s[j], t);
+            q = fma(t, t, q);
         }
         Q64[(size_t)slot * ldq + g] = q;
     }
@@ -775,45 +779,121 @@ __global__ void k_set_slots(const int32_t* __restrict__ q, const int32_t* __rest
 
 // ------------------------------------------------------ plain fp64 scan -----
 
-// One warp per universe: y = A (d - v), then chi2_g - c = q_g - 2 y.s~_g for
-// every g, first minimum in index order.
-__global__ void __launch_bounds__(256) k_scan64(const int32_t* __restrict__ list, int64_t n,
-                                                 const int32_t* __restrict__ uslot, const float* __restrict__ d,
-                                                 const double* __restrict__ centre, const double* __restrict__ Sc,
-                                                 int64_t G, int nfit, const double* __restrict__ A64,
-                                                 const double* __restrict__ Q64, int64_t ldq,
-                                                 int32_t* __restrict__ best) {
-    __shared__ double sy[8][kMaxBins];
-    __shared__ double sd[8][kMaxBins];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = blockIdx.x * 8LL + w;
-    if (i >= n) return;
-    const int u = list[i];
-    const int slot = uslot[i];
-    const double* A = A64 + (size_t)slot * nfit * nfit;
-    for (int j = lane; j < nfit; j += 32) sd[w][j] = (double)d[(size_t)u * nfit + j] - centre[j];
-    __syncwarp();
-    for (int r = lane; r < nfit; r += 32) {
-        double t = 0.0;
-        for (int j = 0; j < nfit; ++j) t = fma(A[r * nfit + j], sd[w][j], t);
-        sy[w][r] = t;
+// Plain binary64 scan: chi2_g - c = q_g - 2 y.s~_g with y = A (d - v) for every
+// g, the first minimum in index order.  The y.s~ products of 32 universes x 64
+// grid points are a small dense contraction on the FP64 pipe: y and a tile of
+// s~ (transposed to [j][g]) sit in shared memory and every thread keeps a 4 x 2
+// block of dot products in registers (the binary64 pipe is narrow, so operand
+// loads are never the limit; 16 universes per CTA keep enough CTAs for the
+// later scans, which hold fewer universes).  Every dot product is one fma chain
+// over j in increasing order, as in a per-pair loop, so the minimum found does
+// not depend on the blocking.
+constexpr int kS64U = 16;   // universes per CTA
+constexpr int kS64G = 64;   // grid points per staged tile
+constexpr int kS64LdS = kS64G + 2;  // row stride of the staged tile (fewer bank conflicts, 16-byte rows)
+constexpr int kS64Threads = 128;
+
+__global__ void __launch_bounds__(kS64Threads) k_scan64(const int32_t* __restrict__ list, int64_t n,
+                                                         const int32_t* __restrict__ uslot,
+                                                         const float* __restrict__ d, const double* __restrict__ centre,
+                                                         const double* __restrict__ Sc, int64_t G, int nfit,
+                                                         const double* __restrict__ A64,
+                                                         const double* __restrict__ Q64, int64_t ldq,
+                                                         int32_t* __restrict__ best) {
+    extern __shared__ double2 sm64v[];
+    double* sy = reinterpret_cast<double*>(sm64v);   // [nfit][kS64U]
+    double* ss = sy + (size_t)nfit * kS64U;          // [nfit][kS64LdS]
+    __shared__ double s_bv[kS64Threads / 4][kS64U];
+    __shared__ int32_t s_bg[kS64Threads / 4][kS64U];
+    __shared__ int s_slot[kS64U];
+    const int tid = threadIdx.x;
+    const int64_t u0 = (int64_t)blockIdx.x * kS64U;
+    const int nu = (int)((n - u0) < kS64U ? (n - u0) : kS64U);
+    if (tid < kS64U) s_slot[tid] = (tid < nu) ? uslot[u0 + tid] : 0;
+    // d - v of the CTA's universes, [j][u] (in the tile buffer, free until the first tile)
+    for (int e = tid; e < nfit * kS64U; e += kS64Threads) {
+        const int j = e / kS64U, uu = e - (e / kS64U) * kS64U;
+        ss[e] = (uu < nu) ? (double)d[(size_t)list[u0 + uu] * nfit + j] - centre[j] : 0.0;
     }
-    __syncwarp();
-    const double* Q = Q64 + (size_t)slot * ldq;
-    double bv = DBL_MAX;
-    int32_t bg = INT32_MAX;
-    for (int64_t g = lane; g < G; g += 32) {
-        const double* s = Sc + g * nfit;
-        double dot = 0.0;
-        for (int j = 0; j < nfit; ++j) dot = fma(sy[w][j], s[j], dot);
-        const double v = fma(-2.0, dot, Q[g]);
-        if (v < bv) {
-            bv = v;
-            bg = (int32_t)g;
+    __syncthreads();
+    // y_r = sum_j A_rj (d - v)_j, one fma chain in j order
+    for (int e = tid; e < nfit * kS64U; e += kS64Threads) {
+        const int r = e / kS64U, uu = e - (e / kS64U) * kS64U;
+        double t = 0.0;
+        if (uu < nu) {
+            const double* A = A64 + (size_t)s_slot[uu] * nfit * nfit + (size_t)r * nfit;
+            for (int j = 0; j < nfit; ++j) t = fma(A[j], ss[j * kS64U + uu], t);
+        }
+        sy[r * kS64U + uu] = t;
+    }
+    const int tu = tid & 3, tg = tid >> 2;  // universes 4 tu .. 4 tu + 3, tile points 2 tg, 2 tg + 1
+    double bv[4];
+    int32_t bg[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        bv[a] = DBL_MAX;
+        bg[a] = INT32_MAX;
+    }
+    for (int64_t g0 = 0; g0 < G; g0 += kS64G) {
+        __syncthreads();  // y complete / the previous tile's readers done
+        for (int e = tid; e < kS64G * nfit; e += kS64Threads) {
+            const int gg = e / nfit, j = e - (e / nfit) * nfit;
+            const int64_t g = g0 + gg;
+            ss[j * kS64LdS + gg] = (g < G) ? Sc[g * nfit + j] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) acc[a][b] = 0.0;
+        for (int j = 0; j < nfit; ++j) {
+            const double2 y01 = *reinterpret_cast<const double2*>(sy + j * kS64U + 4 * tu);
+            const double2 y23 = *reinterpret_cast<const double2*>(sy + j * kS64U + 4 * tu + 2);
+            const double2 s01 = *reinterpret_cast<const double2*>(ss + j * kS64LdS + 2 * tg);
+            const double y[4] = {y01.x, y01.y, y23.x, y23.y};
+            const double sv[2] = {s01.x, s01.y};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) acc[a][b] = fma(y[a], sv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int uu = 4 * tu + a;
+            if (uu >= nu) continue;
+            const double* Q = Q64 + (size_t)s_slot[uu] * ldq;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int64_t g = g0 + 2 * tg + b;
+                if (g >= G) continue;
+                const double v = fma(-2.0, acc[a][b], Q[g]);
+                if (v < bv[a] || (v == bv[a] && (int32_t)g < bg[a])) {
+                    bv[a] = v;
+                    bg[a] = (int32_t)g;
+                }
+            }
         }
     }
-    warp_argmin(bv, bg);
-    if (lane == 0) best[u] = bg;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        s_bv[tg][4 * tu + a] = bv[a];
+        s_bg[tg][4 * tu + a] = bg[a];
+    }
+    __syncthreads();
+    if (tid < nu) {
+        double v = DBL_MAX;
+        int32_t g = INT32_MAX;
+        for (int k = 0; k < kS64Threads / 4; ++k) {
+            const double x = s_bv[k][tid];
+            const int32_t xg = s_bg[k][tid];
+            if (x < v || (x == v && xg < g)) {
+                v = x;
+                g = xg;
+            }
+        }
+        best[list[u0 + tid]] = g;
+    }
 }
 
 // Exact residual-form scan (Algorithm 2 for every g) of the universes in
@@ -1204,6 +1284,7 @@ __global__ void __launch_bounds__(kBM) k_resolve_emit(ResolveArgs a) {
     if (threadIdx.x == 0) {
         s_base = total ? atomicAdd(&a.counts[0], total) : 0;
         a.tile_items[t] = make_int2(s_base, total);
+        if (total) atomicAdd(a.n_resid, (unsigned long long)total);
     }
     __syncthreads();
     const int base = s_base + off;
@@ -1345,6 +1426,7 @@ __global__ void __launch_bounds__(kBM) k_resolve_conclude(ResolveArgs a) {
         s_base_fb = s_nfb ? atomicAdd(a.n_fb, s_nfb) : 0;
         s_base2 = s_n2 ? atomicAdd(&a.counts[1], s_n2) : 0;
         a.tile_items2[t] = make_int2(s_base2, s_n2);
+        if (s_n2) atomicAdd(a.n_resid, (unsigned long long)s_n2);
         if (s_cnt[0]) atomicAdd(&a.counters[0], (unsigned long long)s_cnt[0]);
         if (s_cnt[1]) atomicAdd(&a.counters[1], (unsigned long long)s_cnt[1]);
         if (s_cnt[2]) atomicAdd(&a.counters[2], (unsigned long long)s_cnt[2]);
@@ -1435,6 +1517,7 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
         }
         warp_argmin(bv, bg);
         if (lane == 0 && a.rmask) a.rmask[u] |= a.round_bit;
+        if (lane == 0 && a.n_resid) atomicAdd(a.n_resid, (unsigned long long)(n0 + n1));
         const int32_t cur_u = a.cur[u];
         const bool finishing = (bg == cur_u) || (a.nscan[u] + 1 >= a.maxit[u]);
         if (finishing) {
@@ -1443,6 +1526,7 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
             if (p != bg) {
                 // chi2_p in residual form (row dot products over the lanes, the bits of resid_df)
                 cp = resid_df_warp(W, n, a.Sdf + (int64_t)p * n, du, s_r[warp], s_t[warp], lane);
+                if (lane == 0 && a.n_resid) atomicAdd(a.n_resid, 1ull);
             }
             if (lane == 0) {
                 a.best[u] = bg;
@@ -1594,6 +1678,63 @@ __global__ void k_quantiles(const double* __restrict__ x, int n, int npow2, cons
 
 }  // namespace
 
+// ---------------------------------------------------------- peak probes -----
+
+namespace {
+
+// Eight independent fma chains per thread, x <- x a + b with |a| < 1 (values
+// stay normal): 16 flops per iteration, no memory traffic.
+template <typename T>
+__global__ void k_fma_peak(T* out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += x[k];
+    if (sum == (T)-1) out[blockIdx.x] = sum;  // never true; keeps the chains live
+}
+
+}  // namespace
+
+// TFLOP/s of one fma probe: best of three timed launches after a warm-up.
+template <typename T>
+static double fma_peak_tflops(int n_sm, int iters, cudaStream_t st) {
+    T* out = nullptr;
+    if (cudaMalloc(&out, 4096 * sizeof(T)) != cudaSuccess) return 0.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const unsigned blocks = (unsigned)n_sm * 8;
+    const int threads = 256;
+    double best = 0.0;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, st);
+        k_fma_peak<T><<<blocks, threads, 0, st>>>(out, iters, (T)0.999999, (T)1e-3);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 16.0 * iters * (double)blocks * threads;
+        if (rep > 0 && ms > 0.0f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    return best;
+}
+
+bool measure_fma_peaks(int n_sm, double* fp64_tflops, double* fp32_tflops, cudaStream_t st) {
+    count_launch(8);
+    *fp64_tflops = fma_peak_tflops<double>(n_sm, 20000, st);
+    *fp32_tflops = fma_peak_tflops<float>(n_sm, 400000, st);
+    return cudaGetLastError() == cudaSuccess && *fp64_tflops > 0.0 && *fp32_tflops > 0.0;
+}
+
 // ------------------------------------------------------------- launchers ----
 
 void launch_collapse(const double* S, int64_t G, int nf, const int32_t* coll, int nfit, double* out,
@@ -1637,14 +1778,14 @@ void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, co
                                       status);
 }
 
-void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* A64, const int32_t* slots, int n,
+void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* W64, const int32_t* slots, int n,
                    int64_t ldq, double* Q64, cudaStream_t st) {
     // blockIdx.y is the slot within a launch: chunks of at most gridDim.y's limit
     for (int s0 = 0; s0 < n; s0 += 65535) {
         const int ns = n - s0 < 65535 ? n - s0 : 65535;
         dim3 grid(blocks_for(G, 128) < 64 ? blocks_for(G, 128) : 64, ns);
         count_launch();
-        k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, A64, slots + s0, ldq, Q64);
+        k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, W64, slots + s0, ldq, Q64);
     }
 }
 
@@ -1735,8 +1876,11 @@ void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const f
                    const double* Sc, int64_t G, int nfit, const double* A64, const double* Q64, int64_t ldq,
                    int32_t* best, cudaStream_t st) {
     if (n <= 0) return;
+    const size_t smem = (size_t)nfit * (kS64U + kS64LdS) * sizeof(double);
+    cudaFuncSetAttribute(k_scan64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    k_scan64<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(list, n, uslot, d, centre, Sc, G, nfit, A64, Q64, ldq, best);
+    k_scan64<<<(unsigned)((n + kS64U - 1) / kS64U), kS64Threads, smem, st>>>(list, n, uslot, d, centre, Sc, G, nfit,
+                                                                            A64, Q64, ldq, best);
 }
 
 void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const float2* Sdf,
