@@ -979,9 +979,9 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 float *cval = nullptr, *tau0 = nullptr;
                 float4* alpha = nullptr;
                 FC_TRY(scratch(c, "tcnt", (size_t)n_slots, &tcnt));
-                FC_TRY(scratch(c, "tbase", (size_t)n_slots, &tbase));
+                FC_TRY(scratch(c, "tbase", (size_t)n_slots + 1, &tbase));
                 FC_TRY(scratch(c, "tfill", (size_t)n_slots, &tfill));
-                FC_TRY(scratch(c, ("tslot" + sfx).c_str(), (size_t)max_tiles, &tslot));
+                FC_TRY(scratch(c, ("tslot" + sfx).c_str(), (size_t)max_tiles * kQuads, &tslot));
                 FC_TRY(scratch(c, ("tuniv" + sfx).c_str(), (size_t)max_tiles * kBM, &tuniv));
                 FC_TRY(scratch(c, ("Yt" + sfx).c_str(), (size_t)max_tiles * kBM * 2 * g->K, &Yt));
                 FC_TRY(scratch(c, ("alpha" + sfx).c_str(), (size_t)max_tiles * kBM, &alpha));
@@ -1025,7 +1025,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 FC_TRY(check_status(c));
                 S->screen_flops += 2.0 * g->nfit * (double)cnt * (double)g->G;
                 ResolveArgs ra{};
-                ra.tile_slot = tslot;
+                ra.quad_slot = tslot;
                 ra.tile_univ = tuniv;
                 ra.topk = rtopk;
                 ra.cval = cval;
@@ -1083,8 +1083,8 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     FC_TRY(scratch(c, "rs_res2", rows, &ra.res2));
                     FC_TRY(scratch(c, "rs_cmin2", rows, &ra.cmin2));
                     FC_TRY(scratch(c, "rs_counts", 2, &ra.counts));
-                    FC_TRY(scratch(c, "rs_tiles", (size_t)n_tiles, &ra.tile_items));
-                    FC_TRY(scratch(c, "rs_tiles2", (size_t)n_tiles, &ra.tile_items2));
+                    FC_TRY(scratch(c, "rs_tiles", (size_t)n_tiles * kQuads, &ra.tile_items));
+                    FC_TRY(scratch(c, "rs_tiles2", (size_t)n_tiles * kQuads, &ra.tile_items2));
                     ra.n_sm = c->n_sm;
                     launch_resolve(ra, n_tiles, c->stream);
                 }

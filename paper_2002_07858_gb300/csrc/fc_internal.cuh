@@ -16,8 +16,13 @@ extern std::atomic<long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Screen tile shape: BM universes (TMEM lanes) x BN grid points (TMEM columns).
+// A tile's rows come in four quadrants of 32 (the TMEM lane quadrants); each
+// quadrant holds universes of one covariance slot, so one tile can serve up to
+// four covariances (refit scans leave most covariances with few universes).
 constexpr int kBM = 128;
 constexpr int kBN = 256;
+constexpr int kQuadRows = 32;
+constexpr int kQuads = kBM / kQuadRows;
 constexpr int kMaxTopK = 16;
 constexpr int kMaxBins = 200;
 constexpr int kMaxScreenK = 208;  // screen_k(kMaxBins): K of the largest tensor-core screen
@@ -133,11 +138,12 @@ void launch_wdf(const double* W64, const int32_t* slots, int n, int nfit, float2
 void launch_to_df(const double* x, int64_t n, float2* y, cudaStream_t st);
 
 // ---- mixed path: grouping, y prep, screen, decision ----
-// counting sort of active universes by slot into BM-row tiles
+// counting sort of active universes by slot into 32-row quadrants, four per BM-row tile:
+// quad_slot [max_tiles * kQuads] (padding quadrants repeat the last slot), tile_univ [max_tiles * BM] (-1 = padding)
 void launch_group(const int32_t* active, int64_t n_active, const int32_t* uslot, int n_slots, int32_t* cnt,
-                  int32_t* tile_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* tile_slot, int32_t* tile_univ,
+                  int32_t* quad_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* quad_slot, int32_t* tile_univ,
                   int64_t max_tiles, cudaStream_t st);
-void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
+void launch_yprep(const int32_t* quad_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
                   const float* Sc32, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
                   uint16_t* Ytiles, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st);
@@ -167,13 +173,13 @@ struct WaitTest {
 bool screen_config_ok(int K, int stages, int ybuf);
 bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Ytiles, const uint16_t* Btiles,
                    const uint16_t* Qb3,
-                   const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
+                   const int32_t* quad_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
                    int nfit, const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st);
 // Resolution of one mixed-path scan per screen tile (see k_resolve).
 struct ResolveArgs {
-    const int32_t* tile_slot;
+    const int32_t* quad_slot;  // [n_tiles * kQuads] covariance slot of each 32-row quadrant
     const int32_t* tile_univ;
     int topk;
     const float* cval;
@@ -213,7 +219,7 @@ struct ResolveArgs {
     uint8_t round_bit;     // that bit; 0 = the top-k round (certificate alone or after rescoring)
     // top-k rounds: residual work lists of the flat resolution (launch_resolve), sized by the caller:
     // items/res [n_tiles * BM * (topk + 1)], item_base [n_tiles * BM], items2/res2/cmin2
-    // [n_tiles * BM], counts [2] (zeroed by launch_resolve)
+    // [n_tiles * BM], tile_items / tile_items2 [n_tiles * kQuads], counts [2] (zeroed by launch_resolve)
     int2* items;           // (tile row, grid index; -1 = the centre, for c_u)
     double* res;           // residual chi2 of each item
     int32_t* item_base;    // first item of each tile row
@@ -221,8 +227,8 @@ struct ResolveArgs {
     double* res2;
     double* cmin2;         // their chi2_min
     int32_t* counts;       // [0] items, [1] items2
-    int2* tile_items;      // [n_tiles] (first item, item count) of each tile's items
-    int2* tile_items2;     // [n_tiles] the same for items2
+    int2* tile_items;      // (first item, item count) of each quadrant's items (a quadrant shares one W)
+    int2* tile_items2;     // the same for items2
     unsigned long long* n_resid;  // residual chi2 evaluated (all rounds)
     int n_sm;
 };

@@ -974,7 +974,9 @@ __global__ void k_count_slots(const int32_t* __restrict__ uslot, int64_t n, int3
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[s], __popc(peers));
 }
 
-// exclusive scan of ceil(cnt/BM) over slots (single CTA), writes the tile count
+// exclusive scan of ceil(cnt / 32) over slots (single CTA): each slot's first
+// quadrant in base[s], the quadrant total in base[n_slots], the tile count
+// (quadrants rounded up to whole tiles) in *n_tiles
 __global__ void k_tile_scan(const int32_t* __restrict__ cnt, int n_slots, int32_t* __restrict__ base,
                             int32_t* __restrict__ n_tiles) {
     __shared__ int32_t warp_tot[32];
@@ -983,7 +985,7 @@ __global__ void k_tile_scan(const int32_t* __restrict__ cnt, int n_slots, int32_
     __syncthreads();
     for (int start = 0; start < n_slots; start += blockDim.x) {
         const int s = start + threadIdx.x;
-        const int32_t v = (s < n_slots) ? (cnt[s] + kBM - 1) / kBM : 0;
+        const int32_t v = (s < n_slots) ? (cnt[s] + kQuadRows - 1) / kQuadRows : 0;
         int32_t x = v;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -1009,15 +1011,24 @@ __global__ void k_tile_scan(const int32_t* __restrict__ cnt, int n_slots, int32_
         if (threadIdx.x == blockDim.x - 1) carry = excl + v;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *n_tiles = carry;
+    if (threadIdx.x == 0) {
+        base[n_slots] = carry;
+        *n_tiles = (carry + kQuads - 1) / kQuads;
+    }
 }
 
+// quadrant -> slot; the quadrants that pad the last tile take the slot of the
+// last used quadrant, so a tile whose used quadrants share a slot stays uniform
 __global__ void k_tile_slots(const int32_t* __restrict__ cnt, const int32_t* __restrict__ base, int n_slots,
-                             int32_t* __restrict__ tile_slot) {
+                             const int32_t* __restrict__ n_tiles, int32_t* __restrict__ quad_slot) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
-    const int nt = (cnt[s] + kBM - 1) / kBM;
-    for (int t = 0; t < nt; ++t) tile_slot[base[s] + t] = s;
+    const int nq = (cnt[s] + kQuadRows - 1) / kQuadRows;
+    for (int q = 0; q < nq; ++q) quad_slot[base[s] + q] = s;
+    // the slot that owns the last used quadrant also pads the last tile
+    const int used = base[n_slots];
+    if (nq > 0 && base[s] + nq == used)
+        for (int q = used; q < *n_tiles * kQuads; ++q) quad_slot[q] = s;
 }
 
 __global__ void k_scatter_tiles(const int32_t* __restrict__ active, int64_t n, const int32_t* __restrict__ uslot,
@@ -1034,7 +1045,8 @@ __global__ void k_scatter_tiles(const int32_t* __restrict__ active, int64_t n, c
     if (lane == leader) first = atomicAdd(&fill[s], __popc(peers));
     first = __shfl_sync(peers, first, leader);
     const int pos = first + __popc(peers & ((1u << lane) - 1u));
-    tile_univ[(int64_t)(base[s] + pos / kBM) * kBM + pos % kBM] = active[i];
+    // quadrant base[s] + pos / 32, row pos % 32 of it: rows are numbered quadrant * 32 + row
+    tile_univ[(int64_t)(base[s] + pos / kQuadRows) * kQuadRows + pos % kQuadRows] = active[i];
 }
 
 // ---------------------------------------------------------- mixed: y prep ---
@@ -1044,7 +1056,7 @@ __device__ __forceinline__ int64_t ytile_offset(int64_t t, int r, int c, int K) 
     return t * (int64_t)(2 * K * kBM) + (int64_t)(c >> 3) * (kBM * 8) + (r >> 3) * 64 + (r & 7) * 8 + (c & 7);
 }
 
-// One CTA per tile, one thread per row: y^ = A (d - v) in binary32, Y = -2 y^
+// One CTA per tile, one thread per row (its quadrant's covariance slot): y^ = A (d - v) in binary32, Y = -2 y^
 // split into bf16 hi + lo, and the error-bound coefficient alpha in the spare
 // column so that the screen directly yields a lower bound of chi2_g - c_u.
 // It also evaluates the row's screen value at its own covariance point q
@@ -1055,7 +1067,7 @@ __device__ __forceinline__ int64_t ytile_offset(int64_t t, int r, int c, int K) 
 // skipped); NR = 0: any N_fit, with d - v in a per-thread array.  Same
 // operations in the same order either way.
 template <int NR>
-__global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_slot,
+__global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ quad_slot,
                                                 const int32_t* __restrict__ tile_univ, const float* __restrict__ d,
                                                 const double* __restrict__ centre, int nfit, int K,
                                                 const float* __restrict__ A32, const float* __restrict__ rho,
@@ -1063,13 +1075,30 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
                                                 const float4* __restrict__ gnorm, const float* __restrict__ Qc,
                                                 const float* __restrict__ Qb, int64_t G_pad,
                                                 uint16_t* __restrict__ Yt, float4* __restrict__ alpha,
-                                                float* __restrict__ tau0, int32_t* __restrict__ tile_j0) {
+                                                float* __restrict__ tau0, int32_t* __restrict__ tile_j0,
+                                                bool stage_all) {
     extern __shared__ float sA[];
     const int64_t t = blockIdx.x;
-    const int slot = tile_slot[t];
-    for (int e = threadIdx.x; e < nfit * nfit; e += blockDim.x) sA[e] = A32[(size_t)slot * nfit * nfit + e];
-    __syncthreads();
     const int r = threadIdx.x;
+    const int slot = quad_slot[t * kQuads + r / kQuadRows];
+    // each distinct covariance of the tile's quadrants is staged once (up to four where they fit;
+    // otherwise the tile's first slot is staged and rows of other slots read theirs)
+    int qs[kQuads], first[kQuads];  // first[k]: the first quadrant holding qs[k]
+#pragma unroll
+    for (int k = 0; k < kQuads; ++k) {
+        qs[k] = quad_slot[t * kQuads + k];
+        first[k] = k;
+        for (int k2 = k - 1; k2 >= 0; --k2)
+            if (qs[k2] == qs[k]) first[k] = k2;
+    }
+    const int nn = nfit * nfit;
+    for (int k = 0; k < kQuads; ++k) {
+        if (first[k] != k || (!stage_all && k > 0)) continue;
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) sA[k * nn + e] = A32[(size_t)qs[k] * nn + e];
+    }
+    __syncthreads();
+    const int myq = r / kQuadRows;
+    const float* Arow = (stage_all || qs[myq] == qs[0]) ? sA + first[myq] * nn : A32 + (size_t)slot * nn;
     const int u = tile_univ[t * kBM + r];
     // the screen walks this tile's grid tiles starting at the one holding row 0's q
     if (r == 0) tile_j0[t] = (u >= 0) ? cur[u] / kBN : 0;
@@ -1109,7 +1138,7 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ tile_
             const int i = c8 * 8 + ii;
             if (i < nfit) {
                 float y = 0.0f;
-                const float* Ai = sA + i * nfit;
+                const float* Ai = Arow + i * nfit;
                 if (NR > 0) {
 #pragma unroll
                     for (int j = 0; j < (NR > 0 ? NR : 1); ++j)
@@ -1275,7 +1304,7 @@ __global__ void __launch_bounds__(kBM) k_resolve_emit(ResolveArgs a) {
     __shared__ int s_base;
     const int64_t t = blockIdx.x;
     const int64_t row = t * kBM + threadIdx.x;
-    const int slot = a.tile_slot[t];
+    const int slot = a.quad_slot[row / kQuadRows];
     const int u = a.tile_univ[row];
     RowDecision D;
     decide_row(a, row, slot, u, D);
@@ -1283,7 +1312,12 @@ __global__ void __launch_bounds__(kBM) k_resolve_emit(ResolveArgs a) {
     const int off = block_excl_scan(D.ncodes, s_warp, &total);
     if (threadIdx.x == 0) {
         s_base = total ? atomicAdd(&a.counts[0], total) : 0;
-        a.tile_items[t] = make_int2(s_base, total);
+        // a warp is a quadrant (one covariance): its rows' items are one contiguous range
+        int q0 = s_base;
+        for (int w = 0; w < kQuads; ++w) {
+            a.tile_items[t * kQuads + w] = make_int2(q0, s_warp[w]);
+            q0 += s_warp[w];
+        }
         if (total) atomicAdd(a.n_resid, (unsigned long long)total);
     }
     __syncthreads();
@@ -1296,11 +1330,13 @@ __global__ void __launch_bounds__(kBM) k_resolve_emit(ResolveArgs a) {
     }
 }
 
-// Residual chi2 of one tile's items (a contiguous range, tile_items[t]): the
-// tile's universes share one covariance, so its W is staged once in shared
-// memory and every lane reads the same element at once; the lanes then stride
-// over the items with no further barrier.  Small CTAs (two warps) keep the
-// last, partly filled round of a tile cheap.
+// Residual chi2 of one tile's items.  The items of each quadrant are a
+// contiguous range (tile_items[4t + w]) and the tile's quadrants follow each
+// other; a run of quadrants with one covariance slot shares one W, staged in
+// shared memory (every lane reads the same element at once), and the lanes
+// stride over the run's items with no barrier but the staging's.  A tile
+// whose quadrants share one slot stages once.  Small CTAs (two warps) keep the
+// last, partly filled round of a run cheap.
 constexpr int kResidThreads = 64;
 
 template <int NR>
@@ -1310,36 +1346,45 @@ __global__ void __launch_bounds__(kResidThreads, 6) k_resid_tiles(const ResolveA
     extern __shared__ float2 sWd[];
     const int n = a.nfit;
     const int64_t t = blockIdx.x;
-    const int2 range = tile_items[t];
-    if (range.y == 0) return;  // uniform over the CTA
-    const float2* Wg = a.Wdf + (size_t)a.tile_slot[t] * n * n;
-    const float2* W = Wg;
-    if constexpr (NR > 0) {  // staged where it fits (N_fit <= 64)
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) sWd[e] = Wg[e];
-        __syncthreads();
-        W = sWd;
-    }
-    for (int k = threadIdx.x; k < range.y; k += blockDim.x) {
-        const int64_t i = (int64_t)range.x + k;
-        const int2 it = items[i];
-        const int u = a.tile_univ[it.x];
-        const float2* sv = (it.y < 0) ? a.centre_df : a.Sdf + (int64_t)it.y * n;
-        res[i] = resid_mixed<NR>(W, n, sv, a.d + (size_t)u * n);
+    int w0 = 0;
+    while (w0 < kQuads) {  // every bound below is the same for all lanes
+        const int slot = a.quad_slot[t * kQuads + w0];
+        int w1 = w0 + 1;
+        while (w1 < kQuads && a.quad_slot[t * kQuads + w1] == slot) ++w1;
+        const int64_t i0 = tile_items[t * kQuads + w0].x;
+        const int2 last = tile_items[t * kQuads + w1 - 1];
+        const int64_t i1 = (int64_t)last.x + last.y;
+        w0 = w1;
+        if (i1 <= i0) continue;
+        const float2* Wg = a.Wdf + (size_t)slot * n * n;
+        const float2* W = Wg;
+        if constexpr (NR > 0) {  // staged where it fits (N_fit <= 64)
+            __syncthreads();      // the previous run's reads of sWd are done
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) sWd[e] = Wg[e];
+            __syncthreads();
+            W = sWd;
+        }
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int2 it = items[i];
+            const int u = a.tile_univ[it.x];
+            const float2* sv = (it.y < 0) ? a.centre_df : a.Sdf + (int64_t)it.y * n;
+            res[i] = resid_mixed<NR>(W, n, sv, a.d + (size_t)u * n);
+        }
     }
 }
 
 __global__ void __launch_bounds__(kBM) k_resolve_conclude(ResolveArgs a) {
-    __shared__ int s_nnext, s_nfb, s_n2, s_cnt[3];
+    __shared__ int s_nnext, s_nfb, s_n2[kQuads], s_cnt[3];
     __shared__ int s_base_next, s_base_fb, s_base2;
     const int64_t t = blockIdx.x;
     const int r = threadIdx.x;
     const int64_t row = t * kBM + r;
-    const int slot = a.tile_slot[t];
+    const int slot = a.quad_slot[row / kQuadRows];
     const int u = a.tile_univ[row];
     if (r == 0) {
         s_nnext = 0;
         s_nfb = 0;
-        s_n2 = 0;
+        for (int w = 0; w < kQuads; ++w) s_n2[w] = 0;
         s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
     }
     __syncthreads();
@@ -1419,14 +1464,21 @@ __global__ void __launch_bounds__(kBM) k_resolve_conclude(ResolveArgs a) {
     const bool to_next = (state == 1 && !finishing);
     const int my_next = to_next ? atomicAdd(&s_nnext, 1) : -1;
     const int my_fb = (state == 3) ? atomicAdd(&s_nfb, 1) : -1;
-    const int my_2 = tail ? atomicAdd(&s_n2, 1) : -1;
+    // chi2_p items stay grouped by quadrant (one W per residual CTA)
+    const int quad = r / kQuadRows;
+    const int my_2 = tail ? atomicAdd(&s_n2[quad], 1) : -1;
     __syncthreads();
     if (r == 0) {
         s_base_next = s_nnext ? atomicAdd(a.n_next, s_nnext) : 0;
         s_base_fb = s_nfb ? atomicAdd(a.n_fb, s_nfb) : 0;
-        s_base2 = s_n2 ? atomicAdd(&a.counts[1], s_n2) : 0;
-        a.tile_items2[t] = make_int2(s_base2, s_n2);
-        if (s_n2) atomicAdd(a.n_resid, (unsigned long long)s_n2);
+        const int n2 = s_n2[0] + s_n2[1] + s_n2[2] + s_n2[3];
+        s_base2 = n2 ? atomicAdd(&a.counts[1], n2) : 0;
+        int q0 = s_base2;
+        for (int w = 0; w < kQuads; ++w) {
+            a.tile_items2[t * kQuads + w] = make_int2(q0, s_n2[w]);
+            q0 += s_n2[w];
+        }
+        if (n2) atomicAdd(a.n_resid, (unsigned long long)n2);
         if (s_cnt[0]) atomicAdd(&a.counters[0], (unsigned long long)s_cnt[0]);
         if (s_cnt[1]) atomicAdd(&a.counters[1], (unsigned long long)s_cnt[1]);
         if (s_cnt[2]) atomicAdd(&a.counters[2], (unsigned long long)s_cnt[2]);
@@ -1435,8 +1487,10 @@ __global__ void __launch_bounds__(kBM) k_resolve_conclude(ResolveArgs a) {
     if (to_next) a.next[s_base_next + my_next] = u;
     if (state == 3) a.fb[s_base_fb + my_fb] = u;
     if (tail) {
-        a.items2[s_base2 + my_2] = make_int2((int32_t)row, p);
-        a.cmin2[s_base2 + my_2] = chi2_min;
+        int pos = s_base2 + my_2;
+        for (int w = 0; w < quad; ++w) pos += s_n2[w];
+        a.items2[pos] = make_int2((int32_t)row, p);
+        a.cmin2[pos] = chi2_min;
     } else if (finishing) {
         a.dchi2[u] = (p == g_best) ? 0.0 : chi2_p - chi2_min;
         if (a.chi2min) a.chi2min[u] = chi2_min;
@@ -1476,10 +1530,9 @@ __global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32
     if (w >= n_rows || w >= *n_rows_dev) return;
     {
         const int64_t row = rows[w];
-        const int64_t t = row / kBM;
         const int u = a.tile_univ[row];
         // W of the row's tile (double-float, read through L1: the warp's lanes read the same element)
-        const float2* W = a.Wdf + (size_t)a.tile_slot[t] * n * n;
+        const float2* W = a.Wdf + (size_t)a.quad_slot[row / kQuadRows] * n * n;
         const int n0 = cand_count[row * 2], n1 = cand_count[row * 2 + 1];
         // where the two half-row lists live and whether they are complete
         int64_t base0, base1;
@@ -1895,7 +1948,7 @@ void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, con
 }
 
 void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_slots, int32_t* cnt,
-                  int32_t* tile_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* tile_slot, int32_t* tile_univ,
+                  int32_t* tile_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* quad_slot, int32_t* tile_univ,
                   int64_t max_tiles, cudaStream_t st) {
     cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n_slots, st);
     cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)n_slots, st);
@@ -1907,24 +1960,26 @@ void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_
     count_launch();
     k_tile_scan<<<1, 1024, 0, st>>>(cnt, n_slots, tile_base, n_tiles_dev);
     count_launch();
-    k_tile_slots<<<blocks_for(n_slots), kThreads, 0, st>>>(cnt, tile_base, n_slots, tile_slot);
+    k_tile_slots<<<blocks_for(n_slots), kThreads, 0, st>>>(cnt, tile_base, n_slots, n_tiles_dev, quad_slot);
     if (n > 0) {
         count_launch();
         k_scatter_tiles<<<blocks_for(n), kThreads, 0, st>>>(active, n, uslot, tile_base, fill, tile_univ);
     }
 }
 
-void launch_yprep(const int32_t* tile_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
+void launch_yprep(const int32_t* quad_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
                   const float* Sc32, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
                   uint16_t* Yt, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st) {
     if (n_tiles <= 0) return;
-    const size_t smem = (size_t)nfit * nfit * sizeof(float);
+    // the A of every quadrant's slot up to N_fit = 64 (64 KB); beyond, the tile's first slot
+    const bool stage_all = nfit <= kResolveMaxN;
+    const size_t smem = (size_t)(stage_all ? kQuads : 1) * nfit * nfit * sizeof(float);
     auto kern = nfit <= 48 ? k_yprep<48> : k_yprep<0>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    kern<<<(unsigned)n_tiles, kBM, smem, st>>>(tile_slot, tile_univ, d, centre, nfit, K, A32, rho, cur, Sc32, gnorm, Qc,
-                                               Qb, G_pad, Yt, alpha, tau0, tile_j0);
+    kern<<<(unsigned)n_tiles, kBM, smem, st>>>(quad_slot, tile_univ, d, centre, nfit, K, A32, rho, cur, Sc32, gnorm, Qc,
+                                               Qb, G_pad, Yt, alpha, tau0, tile_j0, stage_all);
 }
 
 void launch_or_mask(const int32_t* list, int64_t n, uint8_t bit, uint8_t* rmask, cudaStream_t st) {

@@ -205,7 +205,7 @@ __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item
 
 // After a min-only pass: tau0 <- min(tau0, certified upper bound at the row's
 // minimum index bidx), one thread per row (bidx = INT32_MAX: no minimum).
-__global__ void k_min_seed(const uint16_t* __restrict__ Yt, const int32_t* __restrict__ tile_slot,
+__global__ void k_min_seed(const uint16_t* __restrict__ Yt, const int32_t* __restrict__ quad_slot,
                            const int32_t* __restrict__ bidx, float* __restrict__ tau0, int64_t n_rows, int64_t G,
                            int64_t G_pad, ProbeArgs pa, const int* __restrict__ status) {
     const int64_t orow = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -217,7 +217,7 @@ __global__ void k_min_seed(const uint16_t* __restrict__ Yt, const int32_t* __res
     if (bi < 0 || bi >= G || !(seed > -FLT_MAX)) return;
     const int64_t item = orow / kBM;
     const int row = (int)(orow % kBM);
-    tau0[orow] = fminf(seed, probe_upper_bound(Yt, item, row, tile_slot[item], bi, G_pad, pa));
+    tau0[orow] = fminf(seed, probe_upper_bound(Yt, item, row, quad_slot[orow / kQuadRows], bi, G_pad, pa));
 }
 
 constexpr int kTmemCols = 2 * kBN;  // two accumulator buffers
@@ -227,17 +227,20 @@ constexpr uint32_t kAChunk = kBM * 16u;  // one 8-column slab of the A image
 constexpr uint32_t kBChunk = kBN * 16u;  // one 8-column slab of the B image
 constexpr uint32_t kQBytes = kBN * 16u;  // one 8-column slab of q-step rows
 constexpr uint32_t kSmemMax = 232448u;   // dynamic shared memory per CTA
+constexpr uint32_t kSmemAlign = 128u;     // alignment of the plan's base (16 bytes would do for every operand)
 
 // Shared-memory plan of one screen launch.  A pipeline stage holds either a
 // whole B tile (2K columns x BN rows, for K <= 64) or, with kchunk, one
 // 16-column K slice of it (two hi slabs, two lo slabs) so that large K still
-// gets a deep pipeline; the stage's q-step slab follows its B part.
+// gets a deep pipeline; the stage's q-step slab follows its B part.  A tile
+// whose quadrants hold different covariances takes one more stage per grid
+// tile: the four slots' q-step slabs, in the B part.
 struct ScreenLayout {
     int K, stages, ybuf, kchunk;
     uint32_t y_bytes;       // one A-image tile: 2K columns x BM rows, bf16
     uint32_t bpart_bytes;   // B part of a stage
     uint32_t stage_bytes;   // B part + q slab
-    uint32_t off_b, off_ones, off_zero, off_scratch, off_bar, bytes;
+    uint32_t off_b, off_ones, off_zero, off_sel, off_scratch, off_bar, bytes;
 };
 
 constexpr int kNumBars(int stages) { return 2 + 2 + stages + stages + 2 + 2 + 1; }
@@ -254,24 +257,26 @@ inline ScreenLayout screen_layout(int K, int stages, int ybuf, int kchunk) {
     l.off_b = ybuf * l.y_bytes;
     l.off_ones = l.off_b + stages * l.stage_bytes;  // A slab of the q-step: [1,1,1,0..] per row
     l.off_zero = l.off_ones + kAChunk;               // second slab of the q-step, all zero
+    // selector slabs of a mixed tile's q-step, one per quadrant: [1,1,1,0..] in that quadrant's rows
+    l.off_sel = l.off_zero + kBChunk;
     // per epilogue warp 4 KB: slow-path scratch inside a tile, top-k hand-over at the end of a row tile
-    l.off_scratch = l.off_zero + kBChunk;
+    l.off_scratch = l.off_sel + kQuads * kAChunk;
     l.off_bar = l.off_scratch + kEpiWarps * 4096;
     // after the barriers: TMEM address, abort flag, pair flags [4][2]; then the alignment slack
-    l.bytes = l.off_bar + kNumBars(stages) * 8 + 48 + 1024;
+    l.bytes = l.off_bar + kNumBars(stages) * 8 + 48 + kSmemAlign;
     return l;
 }
 
 template <int TOPK, int MODE, bool KCHUNK>
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     k_screen(const uint16_t* __restrict__ Yt, const uint16_t* __restrict__ Bt, const uint16_t* __restrict__ Qb3,
-             const int32_t* __restrict__ tile_slot, float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
+             const int32_t* __restrict__ quad_slot, float* __restrict__ tau0, const int32_t* __restrict__ tile_j0,
              int64_t n_tiles, int64_t G, int64_t G_pad, float* __restrict__ cand_val, int32_t* __restrict__ cand_idx,
              int32_t* __restrict__ cand_count, int* __restrict__ status, ProbeArgs pa, ScreenLayout lay,
              ListArgs la, WaitTest wt) {
     static_assert(2 * TOPK * 32 * 4 <= 4096, "top-k hand-over exceeds the warp scratch");
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + (kSmemAlign - 1)) & ~(uintptr_t)(kSmemAlign - 1));
     const uint32_t sbase = smem_addr(smem);
     const int K = lay.K, STAGES = lay.stages, YBUF = lay.ybuf;
     uint64_t* bars = (uint64_t*)(smem + lay.off_bar);
@@ -298,6 +303,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         }
         uint32_t* zero = (uint32_t*)(smem + lay.off_zero);
         for (int i = threadIdx.x; i < (int)(kBChunk / 4); i += blockDim.x) zero[i] = 0u;
+        // selector slab k: the ones row of the q-step in the rows of quadrant k (16 bytes per row)
+        uint32_t* sel = (uint32_t*)(smem + lay.off_sel);
+        for (int i = threadIdx.x; i < (int)(kQuads * kAChunk / 4); i += blockDim.x) {
+            const int k = i / (int)(kAChunk / 4), row = (i % (int)(kAChunk / 4)) >> 2, w = i & 3;
+            const bool on = (row / kQuadRows) == k;
+            sel[i] = !on ? 0u : ((w == 0) ? 0x3F803F80u : (w == 1 ? 0x00003F80u : 0u));
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (threadIdx.x == 0) {
@@ -347,17 +359,32 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                      bar(Y_FULL + yb));
             y_par[yb] = (int)yph;
             if (++yb == YBUF) { yb = 0; yph ^= 1u; }
-            const uint16_t* qrow = Qb3 + (int64_t)tile_slot[item] * G_pad * 8;
+            const int32_t* qs = quad_slot + item * kQuads;
+            const bool mixed = qs[1] != qs[0] || qs[2] != qs[0] || qs[3] != qs[0];
+            const uint16_t* qrow = Qb3 + (int64_t)qs[0] * G_pad * 8;
             int j = ((tile_j0[item] % n_gt) + n_gt) % n_gt;
             for (int jj = 0; ok && !stopped && jj < n_gt; ++jj) {
                 const uint16_t* btile = Bt + (int64_t)j * tile_elems;
+                if (mixed) {
+                    // an extra stage: the q-step slabs of the four quadrants' slots, side by side
+                    if (wt.stop_after >= 0 && issued >= wt.stop_after) { stopped = true; break; }
+                    ++issued;
+                    if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag, wlim)) { ok = false; break; }
+                    const uint32_t st0 = sbase + lay.off_b + s * lay.stage_bytes;
+                    mbar_expect_tx(bar(B_FULL + s), kQuads * kQBytes);
+                    for (int k = 0; k < kQuads; ++k)
+                        bulk_g2s(st0 + k * kQBytes, Qb3 + ((int64_t)qs[k] * G_pad + (int64_t)j * kBN) * 8, kQBytes,
+                                 bar(B_FULL + s));
+                    b_par[s] = (int)ph;
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                }
                 for (int c = 0; c < NC; ++c) {
                     if (wt.stop_after >= 0 && issued >= wt.stop_after) { stopped = true; break; }
                     ++issued;
                     if (!mbar_wait(bar(B_EMPTY + s), ph ^ 1, abort_flag, wlim)) { ok = false; break; }
                     const uint32_t st0 = sbase + lay.off_b + s * lay.stage_bytes;
                     const uint32_t hi_bytes = KCHUNK ? 2u * kBChunk : lay.bpart_bytes / 2u;
-                    const uint32_t bytes = (kLo ? 2u * hi_bytes : hi_bytes) + (c == 0 ? kQBytes : 0u);
+                    const uint32_t bytes = (kLo ? 2u * hi_bytes : hi_bytes) + (c == 0 && !mixed ? kQBytes : 0u);
                     mbar_expect_tx(bar(B_FULL + s), bytes);
                     if (KCHUNK) {
                         // hi slabs 2c, 2c+1 and lo slabs K/8 + 2c, K/8 + 2c + 1 of the tile
@@ -368,7 +395,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                     } else {
                         bulk_g2s(st0, btile, kLo ? lay.bpart_bytes : hi_bytes, bar(B_FULL + s));
                     }
-                    if (c == 0)
+                    if (c == 0 && !mixed)
                         bulk_g2s(st0 + lay.bpart_bytes, qrow + (int64_t)j * kBN * 8, kQBytes, bar(B_FULL + s));
                     b_par[s] = (int)ph;
                     if (++s == STAGES) { s = 0; ph ^= 1u; }
@@ -392,23 +419,39 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         // --------------------------------------------------------------- MMA
         bool ok = true;
         const uint64_t a_q = smem_desc(sbase + lay.off_ones, lay.off_zero - lay.off_ones, 128);
+        // selector pairs of a mixed tile: quadrants 0 and 1 in K columns 0-7 and 8-15, then 2 and 3
+        const uint64_t a_s01 = smem_desc(sbase + lay.off_sel, kAChunk, 128);
+        const uint64_t a_s23 = smem_desc(sbase + lay.off_sel + 2 * kAChunk, kAChunk, 128);
         int yb = 0, s = 0, ab = 0;
         uint32_t yph = 0, ph = 0, aph = 0;
         for (int64_t item = blockIdx.x; ok && item < n_tiles; item += gridDim.x) {
             if (!mbar_wait(bar(Y_FULL + yb), yph, abort_flag, wlim)) { ok = false; break; }
             tc_fence_after();
             const uint32_t a0 = sbase + yb * lay.y_bytes;
+            const int32_t* qs = quad_slot + item * kQuads;
+            const bool mixed = qs[1] != qs[0] || qs[2] != qs[0] || qs[3] != qs[0];
             for (int jj = 0; ok && jj < n_gt; ++jj) {
                 if (!mbar_wait(bar(T_EMPTY + ab), aph ^ 1, abort_flag, wlim)) { ok = false; break; }
                 const uint32_t d = tmem_base + (uint32_t)(ab * kBN);
+                if (mixed) {
+                    // q-step stage: accumulator <- q_g of each row's own covariance (two selector MMAs;
+                    // a row takes its quadrant's slab and exact zeros from the other three)
+                    if (!mbar_wait(bar(B_FULL + s), ph, abort_flag, wlim)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t q0 = sbase + lay.off_b + s * lay.stage_bytes;
+                    mma_bf16(d, a_s01, smem_desc(q0, kQBytes, 128), kIdesc, 0u);
+                    mma_bf16(d, a_s23, smem_desc(q0 + 2 * kQBytes, kQBytes, 128), kIdesc, 1u);
+                    mma_commit(bar(B_EMPTY + s));
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                }
                 for (int c = 0; c < NC; ++c) {
                     if (!mbar_wait(bar(B_FULL + s), ph, abort_flag, wlim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t b0 = sbase + lay.off_b + s * lay.stage_bytes;
-                    if (c == 0) {
+                    if (c == 0 && !mixed) {
                         // q-step: accumulator <- qb_g
-                        const uint32_t qs = lay.off_b + s * lay.stage_bytes + lay.bpart_bytes;
-                        mma_bf16(d, a_q, smem_desc(sbase + qs, lay.off_zero - qs, 128), kIdesc, 0u);
+                        const uint32_t qoff = lay.off_b + s * lay.stage_bytes + lay.bpart_bytes;
+                        mma_bf16(d, a_q, smem_desc(sbase + qoff, lay.off_zero - qoff, 128), kIdesc, 0u);
                     }
                     // descriptors of the first K step; a step of 16 columns moves the start address by
                     // two slabs, i.e. adds (2 slab bytes) >> 4 to the descriptor's address field
@@ -598,7 +641,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 
 template <int TOPK, int MODE, bool KCHUNK>
 void run_screen(const ScreenLayout& lay, const uint16_t* Yt, const uint16_t* Bt, const uint16_t* Qb3,
-                const int32_t* tile_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
+                const int32_t* quad_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                 int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status, const ProbeArgs& pa,
                 const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st) {
     auto kern = k_screen<TOPK, MODE, KCHUNK>;
@@ -606,12 +649,12 @@ void run_screen(const ScreenLayout& lay, const uint16_t* Yt, const uint16_t* Bt,
     int64_t grid = n_tiles < n_sm ? n_tiles : n_sm;
     if (grid < 1) grid = 1;
     count_launch();
-    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, lay.bytes, st>>>(Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G,
+    kern<<<(unsigned)grid, 64 + 32 * kEpiWarps, lay.bytes, st>>>(Yt, Bt, Qb3, quad_slot, tau0, tile_j0, n_tiles, G,
                                                                    G_pad, cv, ci, cc, status, pa, lay, la, wt);
     if (MODE == kModeMin) {
         const int64_t rows = n_tiles * kBM;
         count_launch();
-        k_min_seed<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Yt, tile_slot, ci, tau0, rows, G, G_pad, pa,
+        k_min_seed<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(Yt, quad_slot, ci, tau0, rows, G, G_pad, pa,
                                                                    status);
     }
 }
@@ -641,11 +684,12 @@ bool screen_config_ok(int K, int stages, int ybuf) {
     if (stages != 0 && (stages < 2 || stages > 8)) return false;
     if (ybuf < 0 || ybuf > 2) return false;
     const ScreenLayout lay = choose_layout(K, stages, ybuf);
-    return lay.stages >= 2 && lay.bytes <= kSmemMax;
+    // a mixed tile's q-step stage puts the four quadrants' slabs in a stage's B part
+    return lay.stages >= 2 && lay.bytes <= kSmemMax && lay.bpart_bytes >= kQuads * kQBytes;
 }
 
 bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Yt, const uint16_t* Bt,
-                   const uint16_t* Qb3, const int32_t* tile_slot, float* tau0, const int32_t* tile_j0,
+                   const uint16_t* Qb3, const int32_t* quad_slot, float* tau0, const int32_t* tile_j0,
                    int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status,
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
                    int nfit, const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st) {
@@ -654,7 +698,7 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
     const ScreenLayout lay = choose_layout(K, stages, ybuf);
     const ProbeArgs pa{Qc, Qb, gnorm, alpha, Sc32, nfit};
 #define FC_SCREEN_RUN(TT, MM, CC) \
-    run_screen<TT, MM, CC>(lay, Yt, Bt, Qb3, tile_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, la, \
+    run_screen<TT, MM, CC>(lay, Yt, Bt, Qb3, quad_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, la, \
                            wt, n_sm, st)
 #define FC_SCREEN_MODES(TT, CC)                 \
     do {                                        \
