@@ -96,6 +96,9 @@ typedef struct {
     int32_t cache_slots;    /* covariance-cache slots at most, 0 = as memory allows;
                                one scan needs a slot per distinct covariance index */
     int32_t first_round;    /* FC_ROUND_*                                           */
+    int32_t slot_rows;      /* rows of a screen tile given to one covariance slot:
+                               32 (a TMEM lane quadrant; a tile serves up to four
+                               covariances) or 128 (a whole tile); 0 = built-in 32 */
 } fc_tuning;
 
 /* Counters and stage timings of the last synchronous call on a context.
@@ -328,15 +331,17 @@ FC_API fc_status fc_fake_data_noalloc(const double* S, int64_t G, int32_t N_full
 
 /* Set / read the kernel choices of a loaded grid.  A choice the grid cannot
  * use (FC_QVEC_TC above K = 128, a screen depth that does not fit in shared
- * memory) gives FC_ERR_ARG.  Lowering cache_slots below the slots in use
+ * memory, slot_rows other than 0, 32, 128) gives FC_ERR_ARG.  Lowering cache_slots below the slots in use
  * clears the grid's covariance cache.  fc_autotune keeps cache_slots and first_round.
  * Errors: FC_ERR_ARG, FC_ERR_NOT_FOUND. */
 FC_API fc_status fc_set_tuning(fc_ctx* ctx, int32_t grid_id, const fc_tuning* t);
 FC_API fc_status fc_get_tuning(fc_ctx* ctx, int32_t grid_id, fc_tuning* t);
 
-/* Time the candidate kernel choices of a grid on a short synthetic run (one
- * scan of fake universes at seeded grid points; the grid's F must be set),
- * keep the fastest, and return it in *out (nullable).  cache_path (nullable):
+/* Time the candidate kernel choices of a grid on short synthetic runs (one
+ * scan of fake universes at seeded grid points: 64 points x 256 universes for
+ * the q-vector kernel and the screen pipeline, 1024 points x 8 universes --
+ * sparse covariances, as after a refit -- for the tile shape slot_rows; the
+ * grid's F must be set), keep the fastest, and return it in *out (nullable).  cache_path (nullable):
  * a text file of earlier results keyed by device, G, N_full, N_fit; a hit
  * skips the timing, a miss appends the new result.  The covariance cache is
  * cleared afterwards.  Errors: as fc_run_points. */

@@ -71,7 +71,7 @@ class fc_stats(ctypes.Structure):
 
 class fc_tuning(ctypes.Structure):
     _fields_ = [("qvec", ctypes.c_int32), ("screen_stages", ctypes.c_int32), ("screen_ybuf", ctypes.c_int32),
-                ("cache_slots", ctypes.c_int32), ("first_round", ctypes.c_int32)]
+                ("cache_slots", ctypes.c_int32), ("first_round", ctypes.c_int32), ("slot_rows", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -376,8 +376,8 @@ def fc_cancel(ctx, ticket: int):
 
 
 def fc_set_tuning(ctx, grid_id: int, qvec: int = 0, screen_stages: int = 0, screen_ybuf: int = 0,
-                  cache_slots: int = 0, first_round: int = 0):
-    t = fc_tuning(qvec, screen_stages, screen_ybuf, cache_slots, first_round)
+                  cache_slots: int = 0, first_round: int = 0, slot_rows: int = 0):
+    t = fc_tuning(qvec, screen_stages, screen_ybuf, cache_slots, first_round, slot_rows)
     _check(load().fc_set_tuning(ctx, grid_id, ctypes.byref(t)), ctx)
 
 

@@ -995,7 +995,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 FC_TRY(scratch(c, "ccount", (size_t)max_tiles * kBM * 2, &ccount));
                 stage_begin(c);
                 launch_group(list, cnt, lslot, (int)n_slots, tcnt, tbase, tfill, cnts + 5, tslot, tuniv, max_tiles,
-                             c->stream);
+                             g->tune.slot_rows ? g->tune.slot_rows : kQuadRows, c->stream);
                 int32_t n_tiles = 0;
                 FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
                 FC_TRY(sync(c));
@@ -2282,6 +2282,8 @@ fc_status fc_set_tuning(fc_ctx* c, int32_t grid_id, const fc_tuning* t) {
         return fail(FC_ERR_ARG, "screen depth / buffering does not fit this K");
     if (t->cache_slots < 0 || t->cache_slots == 1) return fail(FC_ERR_ARG, "cache_slots must be 0 or >= 2");
     if (t->first_round < FC_ROUND_AUTO || t->first_round > FC_ROUND_LIST) return fail(FC_ERR_ARG, "bad first_round");
+    if (t->slot_rows != 0 && t->slot_rows != kQuadRows && t->slot_rows != kBM)
+        return fail(FC_ERR_ARG, "slot_rows must be 0, 32 or 128");
     // q-vectors from the other kernel have a different (still certified) bound: recompute them
     if (t->qvec != g->tune.qvec) std::fill(g->q32_ready.begin(), g->q32_ready.end(), 0);
     if (t->cache_slots > 0 && t->cache_slots < g->n_slots) reset_cache(c, g);
@@ -2306,12 +2308,13 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
     if (!g) return fail(FC_ERR_NOT_FOUND, "unknown grid id");
     if (!g->has_F) return fail(FC_ERR_STATE, "fractional covariance not set (fc_set_frac_cov)");
     char key[512];
-    snprintf(key, sizeof key, "fc-tune-v1 dev=%s sms=%d G=%lld nf=%d nfit=%d", c->dev_name.c_str(), c->n_sm,
+    snprintf(key, sizeof key, "fc-tune-v2 dev=%s sms=%d G=%lld nf=%d nfit=%d", c->dev_name.c_str(), c->n_sm,
              (long long)g->G, g->nf, g->nfit);
     auto valid = [&](const fc_tuning& t) {
         return t.qvec >= FC_QVEC_AUTO && t.qvec <= FC_QVEC_TC &&
                (t.qvec != FC_QVEC_TC || qvec_tc_supported(g->K)) &&
-               screen_config_ok(g->K, t.screen_stages, t.screen_ybuf);
+               screen_config_ok(g->K, t.screen_stages, t.screen_ybuf) &&
+               (t.slot_rows == kQuadRows || t.slot_rows == kBM);
     };
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
@@ -2324,7 +2327,8 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
                 fc_tuning r{};
                 r.cache_slots = g->tune.cache_slots;
                 r.first_round = g->tune.first_round;
-                if (sscanf(line + kl, " qvec=%d stages=%d ybuf=%d", &r.qvec, &r.screen_stages, &r.screen_ybuf) == 3 &&
+                if (sscanf(line + kl, " qvec=%d stages=%d ybuf=%d rows=%d", &r.qvec, &r.screen_stages, &r.screen_ybuf,
+                           &r.slot_rows) == 4 &&
                     valid(r)) {
                     t = r;
                     hit = true;
@@ -2358,6 +2362,7 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
     fc_tuning best{};
     best.cache_slots = saved.cache_slots;
     best.first_round = saved.first_round;
+    best.slot_rows = kQuadRows;
     fc_stats st{};
     fc_status rc = FC_OK;
     // q-vector kernel: covariance stage of a cold cache (P new covariances and q-vectors)
@@ -2393,6 +2398,28 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
                 }
             }
     }
+    // tile shape: rows per covariance slot, on sparse covariances (1024 points x 8 universes, one scan:
+    // 1024 slots of 8 universes, as refit scans leave them), total time of the scan, warm cache
+    if (rc == FC_OK) {
+        const int32_t P2 = (int32_t)std::min<int64_t>(1024, g->G), U2 = 8;
+        std::vector<int64_t> ps2(P2);
+        for (int32_t i = 0; i < P2; ++i) ps2[i] = (int64_t)i * g->G / P2;
+        std::vector<double> d2((size_t)P2 * U2);
+        best_ms = 1e300;
+        for (int rows : {kQuadRows, kBM}) {
+            fc_tuning t = best;
+            t.slot_rows = rows;
+            g->tune = t;
+            for (int rep = 0; rep < 2 && rc == FC_OK; ++rep)
+                rc = run_points_impl(c, grid_id, ps2.data(), P2, 0x5eed, U2, &o, d2.data(), nullptr, nullptr);
+            if (rc != FC_OK) break;
+            const double ms = c->stats.ms_prep + c->stats.ms_screen + c->stats.ms_rescore;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.slot_rows = rows;
+            }
+        }
+    }
     reset_cache(c, g);
     if (rc != FC_OK) {
         g->tune = saved;
@@ -2402,7 +2429,8 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
     if (out) *out = best;
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "%s qvec=%d stages=%d ybuf=%d\n", key, best.qvec, best.screen_stages, best.screen_ybuf);
+            fprintf(f, "%s qvec=%d stages=%d ybuf=%d rows=%d\n", key, best.qvec, best.screen_stages, best.screen_ybuf,
+                    best.slot_rows);
             fclose(f);
         }
     }

@@ -140,9 +140,10 @@ void launch_to_df(const double* x, int64_t n, float2* y, cudaStream_t st);
 // ---- mixed path: grouping, y prep, screen, decision ----
 // counting sort of active universes by slot into 32-row quadrants, four per BM-row tile:
 // quad_slot [max_tiles * kQuads] (padding quadrants repeat the last slot), tile_univ [max_tiles * BM] (-1 = padding)
+// slot_rows: rows per slot granule, 32 (quadrants) or 128 (whole tiles)
 void launch_group(const int32_t* active, int64_t n_active, const int32_t* uslot, int n_slots, int32_t* cnt,
                   int32_t* quad_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* quad_slot, int32_t* tile_univ,
-                  int64_t max_tiles, cudaStream_t st);
+                  int64_t max_tiles, int slot_rows, cudaStream_t st);
 void launch_yprep(const int32_t* quad_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
                   const float* Sc32, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,

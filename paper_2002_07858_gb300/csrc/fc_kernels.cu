@@ -977,7 +977,7 @@ __global__ void k_count_slots(const int32_t* __restrict__ uslot, int64_t n, int3
 // exclusive scan of ceil(cnt / 32) over slots (single CTA): each slot's first
 // quadrant in base[s], the quadrant total in base[n_slots], the tile count
 // (quadrants rounded up to whole tiles) in *n_tiles
-__global__ void k_tile_scan(const int32_t* __restrict__ cnt, int n_slots, int32_t* __restrict__ base,
+__global__ void k_tile_scan(const int32_t* __restrict__ cnt, int n_slots, int slot_rows, int32_t* __restrict__ base,
                             int32_t* __restrict__ n_tiles) {
     __shared__ int32_t warp_tot[32];
     __shared__ int32_t carry;
@@ -985,7 +985,8 @@ __global__ void k_tile_scan(const int32_t* __restrict__ cnt, int n_slots, int32_
     __syncthreads();
     for (int start = 0; start < n_slots; start += blockDim.x) {
         const int s = start + threadIdx.x;
-        const int32_t v = (s < n_slots) ? (cnt[s] + kQuadRows - 1) / kQuadRows : 0;
+        // quadrants of the slot: its rows in granules of slot_rows (32: a quadrant, 128: a tile)
+        const int32_t v = (s < n_slots) ? (cnt[s] + slot_rows - 1) / slot_rows * (slot_rows / kQuadRows) : 0;
         int32_t x = v;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -1023,7 +1024,7 @@ __global__ void k_tile_slots(const int32_t* __restrict__ cnt, const int32_t* __r
                              const int32_t* __restrict__ n_tiles, int32_t* __restrict__ quad_slot) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
-    const int nq = (cnt[s] + kQuadRows - 1) / kQuadRows;
+    const int nq = base[s + 1] - base[s];
     for (int q = 0; q < nq; ++q) quad_slot[base[s] + q] = s;
     // the slot that owns the last used quadrant also pads the last tile
     const int used = base[n_slots];
@@ -1949,7 +1950,7 @@ void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, con
 
 void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_slots, int32_t* cnt,
                   int32_t* tile_base, int32_t* fill, int32_t* n_tiles_dev, int32_t* quad_slot, int32_t* tile_univ,
-                  int64_t max_tiles, cudaStream_t st) {
+                  int64_t max_tiles, int slot_rows, cudaStream_t st) {
     cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n_slots, st);
     cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)n_slots, st);
     launch_fill_i32(tile_univ, max_tiles * kBM, -1, st);
@@ -1958,7 +1959,7 @@ void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_
         k_count_slots<<<blocks_for(n), kThreads, 0, st>>>(uslot, n, cnt);
     }
     count_launch();
-    k_tile_scan<<<1, 1024, 0, st>>>(cnt, n_slots, tile_base, n_tiles_dev);
+    k_tile_scan<<<1, 1024, 0, st>>>(cnt, n_slots, slot_rows, tile_base, n_tiles_dev);
     count_launch();
     k_tile_slots<<<blocks_for(n_slots), kThreads, 0, st>>>(cnt, tile_base, n_slots, n_tiles_dev, quad_slot);
     if (n > 0) {

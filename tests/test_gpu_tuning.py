@@ -120,6 +120,7 @@ def test_kernel_choices_do_not_change_results(fc, ctx, which, request):
     ref = _run_all(fc, ctx, gid, pts, 3, U)
     choices = [dict(qvec=fc.FC_QVEC_SIMT), dict(qvec=fc.FC_QVEC_TC), dict(qvec=fc.FC_QVEC_TC, screen_stages=2),
                dict(first_round=fc.FC_ROUND_LIST), dict(first_round=fc.FC_ROUND_TOPK, qvec=fc.FC_QVEC_TC)]
+    choices.append(dict(slot_rows=128))                           # one covariance per whole tile
     if which == "cfg1":
         choices.append(dict(screen_stages=2, screen_ybuf=2))       # whole-tile stages, double A image
     else:
@@ -136,7 +137,7 @@ def test_bad_tuning_rejected(fc, ctx):
     w = workloads.cfg1()
     gid = _load(fc, ctx, w)
     for bad in (dict(qvec=7), dict(screen_stages=1), dict(screen_stages=9), dict(screen_ybuf=3), dict(cache_slots=1),
-                dict(cache_slots=-4), dict(first_round=3)):
+                dict(cache_slots=-4), dict(first_round=3), dict(slot_rows=64)):
         with pytest.raises(fc.FCError) as e:
             fc.fc_set_tuning(ctx, gid, **bad)
         assert e.value.status == fc.FC_ERR_ARG
@@ -172,6 +173,7 @@ def test_autotune(fc, ctx, tmp_path):
     t = fc.fc_autotune(ctx, gid, path)
     assert t["qvec"] in (fc.FC_QVEC_SIMT, fc.FC_QVEC_TC)
     assert t["screen_stages"] >= 2
+    assert t["slot_rows"] in (32, 128)
     assert fc.fc_get_tuning(ctx, gid) == t
     assert os.path.exists(path)
     lines = open(path).read().splitlines()
