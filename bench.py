@@ -398,7 +398,7 @@ def run_native(args):
         n_res = sum(s["residuals"] for s in stats)
         res_ms = sum(s["ms_rescore"] for s in stats)
         res_ops = n_res * resid_fp32_ops(w.n_fit) / (res_ms / 1e3) / 1e12 if res_ms > 0 else 0.0
-        roofline_rescoring = {"kernel": "k_resid_tiles / k_resolve_list (double-float residual chi2)",
+        roofline_rescoring = {"kernel": "k_resid_tiles / k_list_chunks (double-float residual chi2)",
                               "bound": "alu", "achieved": res_ops, "peak": fp32_peak / 2.0, "unit": "Top/s",
                               "frac": res_ops / (fp32_peak / 2.0) if fp32_peak else None,
                               "peak_source": "fc_measure_peaks binary32 fma probe (this run), 1 op per fma",

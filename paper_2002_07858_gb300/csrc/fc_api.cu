@@ -1065,12 +1065,25 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 ra.rmask = L->rmask;
                 ra.round_bit = round == 0 ? 0 : (round == 1 ? kDecidedTop16 : (round == 2 ? kDecidedList
                                                                                           : kDecidedExactList));
+                ra.n_sm = c->n_sm;
                 stage_begin(c);
                 if (listing)
                 {
                     int32_t* lrows = nullptr;
                     FC_TRY(scratch(c, "lrows", (size_t)n_tiles * kBM, &lrows));
-                    launch_resolve_list(ra, ccount, n_tiles, cnt, lrows, cnts + 6, c->stream);
+                    // chunks: a complete list holds at most 2 kListCap points (round 2) or its exact
+                    // size (round 3, list_total over the rows), and a row adds at most one partial chunk
+                    ListPlan lp{};
+                    lp.max_chunks = loff ? list_total / kListChunk + cnt
+                                         : cnt * ((2 * kListCap + kListChunk - 1) / kListChunk);
+                    FC_TRY(scratch(c, "lp_chunk", (size_t)lp.max_chunks, &lp.chunk));
+                    FC_TRY(scratch(c, "lp_pv", (size_t)lp.max_chunks, &lp.pv));
+                    FC_TRY(scratch(c, "lp_pg", (size_t)lp.max_chunks, &lp.pg));
+                    FC_TRY(scratch(c, "lp_base", (size_t)cnt, &lp.row_base));
+                    FC_TRY(scratch(c, "lp_nc", (size_t)cnt, &lp.row_nc));
+                    FC_TRY(scratch(c, "lp_done", (size_t)cnt, &lp.row_done));
+                    FC_TRY(scratch(c, "lp_n", 1, &lp.n_chunk));
+                    launch_resolve_list(ra, ccount, n_tiles, cnt, lrows, cnts + 6, lp, c->stream);
                 }
                 else {
                     // work lists of the flat resolution: up to topk + 1 residuals per row, and
@@ -1085,7 +1098,6 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     FC_TRY(scratch(c, "rs_counts", 2, &ra.counts));
                     FC_TRY(scratch(c, "rs_tiles", (size_t)n_tiles * kQuads, &ra.tile_items));
                     FC_TRY(scratch(c, "rs_tiles2", (size_t)n_tiles * kQuads, &ra.tile_items2));
-                    ra.n_sm = c->n_sm;
                     launch_resolve(ra, n_tiles, c->stream);
                 }
                 FC_TRY(stage_end(c, &S->ms_rescore));

@@ -243,8 +243,20 @@ void launch_min_tau(const int32_t* tile_univ, int64_t n_tiles, const float* thr,
 // Third round: binary64 residual chi2 of every listed candidate of each row
 // (complete lists certify the minimum); overflowing rows go to `fb`.
 // list rounds: n_rows = universes in the round's tiles; rows [n_tiles * BM] and n_rows_dev are scratch
+// Work split of a list round: chunks of kListChunk listed points of one row.
+constexpr int kListChunk = 32;
+struct ListPlan {
+    int2* chunk;        // [max_chunks] (listed-row index w, chunk k of that row); w < 0: no work
+    int32_t* n_chunk;   // device count of chunks
+    int32_t* row_base;  // [n_rows] first chunk of row w
+    int32_t* row_nc;    // [n_rows] chunks of row w (0: the row has no list work)
+    int32_t* row_done;  // [n_rows] chunks of row w finished
+    double* pv;         // [max_chunks] chunk minimum
+    int32_t* pg;        // [max_chunks] its grid index
+    int64_t max_chunks;
+};
 void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, int64_t n_rows,
-                         int32_t* rows, int32_t* n_rows_dev, cudaStream_t st);
+                         int32_t* rows, int32_t* n_rows_dev, const ListPlan& lp, cudaStream_t st);
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st);
 
 // ---- final residual-form chi2 and dchi2 ----

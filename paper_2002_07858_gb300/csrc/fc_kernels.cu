@@ -1513,60 +1513,105 @@ __global__ void k_resolve_tail(ResolveArgs a) {
     }
 }
 
-// Third round: every grid point whose screen lower bound is at or below the
-// row's seed (an upper bound of the minimum) is listed, so the binary64
-// residual-form minimum over a complete list is the minimum of the scan.
-// One warp per listed row (rows[] holds the round's occupied tile rows, so no
-// warp idles on the padding of a sparsely filled tile); lanes split the list,
-// then the first minimum (lowest index among equal values) is taken across the
-// warp.  The row then finishes (dchi2) or advances exactly as in k_resolve;
-// rows whose list overflowed go to the exact scan.
-__global__ void __launch_bounds__(256) k_resolve_list(ResolveArgs a, const int32_t* __restrict__ cand_count,
-                                                      const int32_t* __restrict__ rows, int64_t n_rows,
-                                                      const int32_t* __restrict__ n_rows_dev) {
+// List rounds: every grid point whose screen lower bound is at or below the
+// row's seed (an upper bound of the minimum) is listed, so the residual-form
+// minimum over a complete list is the minimum of the scan.  A row's list is
+// cut into chunks of kListChunk points, one per lane of a warp, so a long list
+// spreads over many warps.  k_list_plan checks each listed row (rows[] holds
+// the round's occupied tile rows) and reserves its chunks; rows whose list
+// overflowed go to the exact scan (their counts size the next, exact-size list
+// round).
+__global__ void k_list_plan(ResolveArgs a, const int32_t* __restrict__ cand_count, const int32_t* __restrict__ rows,
+                            int64_t n_rows, const int32_t* __restrict__ n_rows_dev, ListPlan lp) {
+    const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (w >= n_rows || w >= *n_rows_dev) return;
+    const int64_t row = rows[w];
+    const int u = a.tile_univ[row];
+    const int n0 = cand_count[row * 2], n1 = cand_count[row * 2 + 1];
+    bool complete;
+    if (a.list_off) {
+        const int2 want = a.list_n[u];
+        complete = (n0 == want.x && n1 == want.y);
+    } else {
+        complete = (n0 >= 0 && n1 >= 0 && n0 <= kListCap && n1 <= kListCap);
+    }
+    lp.row_nc[w] = 0;
+    if (complete && n0 + n1 > 0) {
+        const int nc = (n0 + n1 + kListChunk - 1) / kListChunk;
+        const int base = atomicAdd(lp.n_chunk, nc);
+        if ((int64_t)base + nc <= lp.max_chunks) {
+            lp.row_base[w] = base;
+            lp.row_done[w] = 0;
+            lp.row_nc[w] = nc;
+            for (int k = 0; k < nc; ++k) lp.chunk[base + k] = make_int2((int32_t)w, k);
+            return;
+        }
+        // no room (the host's bound makes this unreachable): void the reservation, take the exact scan
+        for (int64_t k = base; k < lp.max_chunks && k < (int64_t)base + nc; ++k) lp.chunk[k] = make_int2(-1, 0);
+    }
+    if (a.lcount) a.lcount[u] = (n0 >= 0 && n1 >= 0) ? make_int2(n0, n1) : make_int2(-1, -1);
+    a.fb[atomicAdd(a.n_fb, 1)] = u;
+    atomicAdd(&a.counters[1], 1ull);
+}
+
+// One warp per chunk (grid-stride over the device count): lane l scores listed
+// point k * kListChunk + l with the canonical residual, the warp takes the
+// first minimum (lowest index among equal values) and publishes it.  The warp
+// that completes a row's last chunk takes the first minimum over the row's
+// chunks and finishes (dchi2) or advances the row.
+__global__ void __launch_bounds__(256) k_list_chunks(ResolveArgs a, const int32_t* __restrict__ cand_count,
+                                                     const int32_t* __restrict__ rows, ListPlan lp) {
     const int n = a.nfit;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ float2 s_r[8][kMaxBins], s_t[8][kMaxBins];
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (w >= n_rows || w >= *n_rows_dev) return;
-    {
+    const int64_t total = *lp.n_chunk < lp.max_chunks ? (int64_t)*lp.n_chunk : lp.max_chunks;
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; e < total; e += stride) {
+        const int2 ck = lp.chunk[e];
+        if (ck.x < 0) continue;
+        const int w = ck.x;
         const int64_t row = rows[w];
         const int u = a.tile_univ[row];
-        // W of the row's tile (double-float, read through L1: the warp's lanes read the same element)
+        // W of the row's quadrant (double-float, read through L1: the warp's lanes read the same element)
         const float2* W = a.Wdf + (size_t)a.quad_slot[row / kQuadRows] * n * n;
         const int n0 = cand_count[row * 2], n1 = cand_count[row * 2 + 1];
-        // where the two half-row lists live and whether they are complete
         int64_t base0, base1;
-        bool complete;
         if (a.list_off) {
-            const int2 want = a.list_n[u];
             base0 = a.list_off[u];
-            base1 = base0 + want.x;
-            complete = (n0 == want.x && n1 == want.y);
+            base1 = base0 + a.list_n[u].x;
         } else {
             base0 = row * 2 * (int64_t)kListCap;
             base1 = base0 + kListCap;
-            complete = (n0 >= 0 && n1 >= 0 && n0 <= kListCap && n1 <= kListCap);
-        }
-        if (!complete || n0 + n1 == 0) {
-            if (lane == 0) {
-                // counts of an overflowing list size the next, exact-size list round
-                if (a.lcount) a.lcount[u] = (n0 >= 0 && n1 >= 0) ? make_int2(n0, n1) : make_int2(-1, -1);
-                a.fb[atomicAdd(a.n_fb, 1)] = u;
-                atomicAdd(&a.counters[1], 1ull);
-            }
-            return;
         }
         const float* du = a.d + (size_t)u * n;
         double bv = DBL_MAX;
         int32_t bg = INT32_MAX;
-        for (int k = lane; k < n0 + n1; k += 32) {
-            const int64_t e = (k < n0) ? base0 + k : base1 + (k - n0);
-            const int32_t g = a.cidx[e];
-            const double c = resid_df(W, n, a.Sdf + (int64_t)g * n, du);
-            if (c < bv || (c == bv && g < bg)) {
-                bv = c;
-                bg = g;
+        const int k = ck.y * kListChunk + lane;
+        if (k < n0 + n1) {
+            const int32_t g = a.cidx[(k < n0) ? base0 + k : base1 + (k - n0)];
+            bv = resid_df(W, n, a.Sdf + (int64_t)g * n, du);
+            bg = g;
+        }
+        warp_argmin(bv, bg);
+        int last = 0;
+        if (lane == 0) {
+            const int pos = lp.row_base[w] + ck.y;
+            lp.pv[pos] = bv;
+            lp.pg[pos] = bg;
+            __threadfence();
+            last = (atomicAdd(&lp.row_done[w], 1) == lp.row_nc[w] - 1);
+        }
+        if (!__shfl_sync(0xffffffffu, last, 0)) continue;
+        __threadfence();
+        bv = DBL_MAX;
+        bg = INT32_MAX;
+        const int nc = lp.row_nc[w], rb = lp.row_base[w];
+        for (int j = lane; j < nc; j += 32) {
+            const double v = __ldcg(&lp.pv[rb + j]);
+            const int32_t gg = __ldcg(&lp.pg[rb + j]);
+            if (v < bv || (v == bv && gg < bg)) {
+                bv = v;
+                bg = gg;
             }
         }
         warp_argmin(bv, bg);
@@ -2010,13 +2055,18 @@ __global__ void k_list_rows(const int32_t* __restrict__ tile_univ, int64_t n, in
 }
 
 void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_t n_tiles, int64_t n_rows,
-                         int32_t* rows, int32_t* n_rows_dev, cudaStream_t st) {
+                         int32_t* rows, int32_t* n_rows_dev, const ListPlan& lp, cudaStream_t st) {
     if (n_tiles <= 0 || n_rows <= 0) return;
     cudaMemsetAsync(n_rows_dev, 0, 4, st);
+    cudaMemsetAsync(lp.n_chunk, 0, 4, st);
     count_launch();
     k_list_rows<<<blocks_for(n_tiles * kBM), kThreads, 0, st>>>(a.tile_univ, n_tiles * kBM, rows, n_rows_dev);
     count_launch();
-    k_resolve_list<<<(unsigned)((n_rows + 7) / 8), 256, 0, st>>>(a, cand_count, rows, n_rows, n_rows_dev);
+    k_list_plan<<<blocks_for(n_rows), kThreads, 0, st>>>(a, cand_count, rows, n_rows, n_rows_dev, lp);
+    // eight warps a CTA, grid-stride over the chunks the plan reserved
+    const int64_t want = (lp.max_chunks + 7) / 8, cap = (int64_t)a.n_sm * 8;
+    count_launch();
+    k_list_chunks<<<(unsigned)std::max<int64_t>(1, std::min(want, cap)), 256, 0, st>>>(a, cand_count, rows, lp);
 }
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
