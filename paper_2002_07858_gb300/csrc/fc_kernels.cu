@@ -90,16 +90,84 @@ __device__ __forceinline__ float2 df_row(const float2* __restrict__ Wi, const fl
     return df_add(a, b);
 }
 
-__device__ double resid_df(const float2* __restrict__ W, int n, const float2* __restrict__ s,
-                           const float* __restrict__ du) {
-    float2 r[kMaxBins];
+// Four consecutive entries W[k .. k+3] of a W row: two 16-byte loads when
+// rows start on 16 bytes at multiple-of-4 columns (even N_fit), else four.
+template <bool EVEN>
+__device__ __forceinline__ void w_load4(const float2* __restrict__ Wk, float2 (&w)[4]) {
+    if constexpr (EVEN) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(Wk));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(Wk) + 1);
+        w[0] = make_float2(a.x, a.y);
+        w[1] = make_float2(a.z, a.w);
+        w[2] = make_float2(b.x, b.y);
+        w[3] = make_float2(b.z, b.w);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[c] = __ldg(Wk + c);
+    }
+}
+
+// The residual chi2 computed four rows at a time: each group of four columns
+// of r is loaded once per block of rows i0 .. i0+3 (i0 a multiple of 4) and
+// meets the four rows' W entries.  Row i keeps df_row's four chains (column j
+// on chain j mod 4, each chain in increasing j) and the rows are squared and
+// summed in increasing i, so every operation and its order are df_row's and
+// the row loop's: the bits are the same, with a quarter of the loads of r.
+// In the last block, rows past N_fit read row N_fit - 1 and are dropped.
+template <bool EVEN>
+__device__ __forceinline__ double resid_df_blk(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+                                               const float* __restrict__ du) {
+    __align__(16) float2 r[kMaxBins + 4];
     for (int j = 0; j < n; ++j) r[j] = df_sub_f(s[j], du[j]);
     float2 acc = make_float2(0.0f, 0.0f);
-    for (int i = 0; i < n; ++i) {
-        const float2 t = df_row(W + i * n, r, i + 1);
-        acc = df_fma(acc, t, t);
+    for (int i0 = 0; i0 < n; i0 += 4) {
+        float2 p[4][4];
+        const float2* Wb[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            Wb[b] = W + (i0 + b < n ? i0 + b : n - 1) * n;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[b][c] = make_float2(0.0f, 0.0f);
+        }
+        // columns 0 .. i0-1: every row of the block takes all four of each group
+#pragma unroll 1
+        for (int j = 0; j < i0; j += 4) {
+            const float4 ra = *reinterpret_cast<const float4*>(&r[j]);
+            const float4 rb = *reinterpret_cast<const float4*>(&r[j + 2]);
+            const float2 rv[4] = {make_float2(ra.x, ra.y), make_float2(ra.z, ra.w), make_float2(rb.x, rb.y),
+                                  make_float2(rb.z, rb.w)};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float2 w[4];
+                w_load4<EVEN>(Wb[b] + j, w);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p[b][c] = df_fma(p[b][c], w[c], rv[c]);
+            }
+        }
+        // columns i0 .. i0+3: row i0+b takes columns up to its diagonal
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float2 rc = r[i0 + c];
+#pragma unroll
+            for (int b = c; b < 4; ++b) p[b][c] = df_fma(p[b][c], Wb[b][i0 + c], rc);
+        }
+        const int nb = (n - i0 < 4) ? n - i0 : 4;  // rows of this block that exist
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (b < nb) {
+                const float2 x = df_add(df_norm(p[b][0].x, p[b][0].y), df_norm(p[b][1].x, p[b][1].y));
+                const float2 y = df_add(df_norm(p[b][2].x, p[b][2].y), df_norm(p[b][3].x, p[b][3].y));
+                const float2 t = df_add(x, y);
+                acc = df_fma(acc, t, t);
+            }
+        }
     }
     return df_to(df_norm(acc.x, acc.y));
+}
+
+__device__ double resid_df(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+                           const float* __restrict__ du) {
+    return (n % 2 == 0) ? resid_df_blk<true>(W, n, s, du) : resid_df_blk<false>(W, n, s, du);
 }
 
 // resid_df with the residual vector in registers, for N_fit <= NR: every index
@@ -1374,6 +1442,23 @@ __global__ void __launch_bounds__(kResidThreads, 6) k_resid_tiles(const ResolveA
     }
 }
 
+// N_fit > 64: W is not staged, so the items are scored flat, one thread per
+// item, grid-stride over the device count.  A row's items follow each other and
+// the rows of a tile quadrant share a slot, so a warp's lanes mostly read the
+// same W element at once.
+__global__ void __launch_bounds__(256) k_resid_flat(const ResolveArgs a, const int2* __restrict__ items,
+                                                    const int32_t* __restrict__ count, double* __restrict__ res) {
+    const int n = a.nfit;
+    const int64_t total = *count;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 it = items[i];
+        const int u = a.tile_univ[it.x];
+        const float2* W = a.Wdf + (size_t)a.quad_slot[it.x / kQuadRows] * n * n;
+        const float2* sv = (it.y < 0) ? a.centre_df : a.Sdf + (int64_t)it.y * n;
+        res[i] = resid_df(W, n, sv, a.d + (size_t)u * n);
+    }
+}
+
 __global__ void __launch_bounds__(kBM) k_resolve_conclude(ResolveArgs a) {
     __shared__ int s_nnext, s_nfb, s_n2[kQuads], s_cnt[3];
     __shared__ int s_base_next, s_base_fb, s_base2;
@@ -2075,7 +2160,12 @@ void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
     // the tail loops over its device-side count
     const unsigned g3 = (unsigned)std::min<int64_t>(n_tiles, (int64_t)a.n_sm * 8);
     const size_t smem = (a.nfit <= 64 ? (size_t)a.nfit * a.nfit : 0) * sizeof(float2);
-    auto resid = [&](const int2* items, const int2* tile_items, double* res) {
+    auto resid = [&](const int2* items, const int2* tile_items, const int32_t* count, int64_t max_items, double* res) {
+        if (a.nfit > 64) {
+            const int64_t want = (max_items + 255) / 256, cap = (int64_t)a.n_sm * 4;
+            k_resid_flat<<<(unsigned)std::max<int64_t>(1, std::min(want, cap)), 256, 0, st>>>(a, items, count, res);
+            return;
+        }
         auto run = [&](auto kern) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * (int)sizeof(float2));
             kern<<<(unsigned)n_tiles, kResidThreads, smem, st>>>(a, items, tile_items, res);
@@ -2086,16 +2176,14 @@ void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
             run(k_resid_tiles<32>);
         else if (a.nfit <= 48)
             run(k_resid_tiles<48>);
-        else if (a.nfit <= 64)
-            run(k_resid_tiles<64>);
         else
-            run(k_resid_tiles<0>);
+            run(k_resid_tiles<64>);
     };
     count_launch(5);
     k_resolve_emit<<<(unsigned)n_tiles, kBM, 0, st>>>(a);
-    resid(a.items, a.tile_items, a.res);
+    resid(a.items, a.tile_items, a.counts, n_tiles * kBM * (a.topk + 1), a.res);
     k_resolve_conclude<<<(unsigned)n_tiles, kBM, 0, st>>>(a);
-    resid(a.items2, a.tile_items2, a.res2);
+    resid(a.items2, a.tile_items2, a.counts + 1, n_tiles * kBM, a.res2);
     k_resolve_tail<<<g3, 256, 0, st>>>(a);
 }
 
