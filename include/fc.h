@@ -185,6 +185,23 @@ typedef struct {
 FC_API fc_status fc_load_grid_osc(fc_ctx* ctx, const fc_osc_model* model, int32_t N_full, const int32_t* collapse,
                                   int32_t N_fit, int32_t* grid_id);
 
+/* fc_load_grid_osc with flags.  FC_GRID_RECOMPUTE: keep no spectra.  As in
+ * the paper's own kernels (§3, Table 2: S(q) recomputed from the physics model
+ * for every evaluation, no caching), every spectrum row a kernel needs (a
+ * covariance M(q), a true point's fake data, a rescored candidate, a probe, a
+ * plain-path scan tile) is evaluated from the model where it is read.  The
+ * sine of each term depends only on the value of its dm2 axis and the bin, so
+ * it is tabulated once ((sum of those axis lengths) x N_full values); an
+ * element then costs three multiplies and an add per term.  What stays
+ * resident is the model, the centre, and the screen's bf16 hi/lo image of
+ * s - centre with its per-point norms (4 K + 16 bytes per grid point instead
+ * of 8 N_full + 28 N_fit + 4 K + 16).  A grid gives bit-identical results
+ * stored or recomputed (both are filled by the same evaluation).  Other
+ * flags: FC_ERR_ARG. */
+enum { FC_GRID_RECOMPUTE = 1 };
+FC_API fc_status fc_load_grid_osc_ex(fc_ctx* ctx, const fc_osc_model* model, int32_t N_full,
+                                     const int32_t* collapse, int32_t N_fit, uint32_t flags, int32_t* grid_id);
+
 /* Set the fractional systematic covariance F (N_full x N_full float64,
  * symmetric) of a loaded grid.  The systematic covariance of spectrum s is
  * diag(s) F diag(s); the statistical part is diag(s).  Invalidates the grid's

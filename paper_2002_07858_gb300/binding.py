@@ -21,6 +21,7 @@ FC_PREC_FP64, FC_PREC_MIXED = 0, 1
 FC_FLUCT_POISSON_SYS, FC_FLUCT_GAUSS = 0, 1
 FC_COV_ITERATE, FC_COV_FIXED, FC_COV_IDENTITY = 0, 1, 2
 FC_QVEC_AUTO, FC_QVEC_SIMT, FC_QVEC_TC = 0, 1, 2
+FC_GRID_RECOMPUTE = 1
 FC_ROUND_AUTO, FC_ROUND_TOPK, FC_ROUND_LIST = 0, 1, 2
 FC_DECIDED_CERT, FC_DECIDED_RESCORED, FC_DECIDED_TOP16, FC_DECIDED_LIST = 1, 2, 4, 8
 FC_DECIDED_EXACT_LIST, FC_DECIDED_SCAN, FC_DECIDED_PLAIN = 16, 32, 64
@@ -33,7 +34,7 @@ EXPORTS = ["fc_default_opts", "fc_create", "fc_destroy", "fc_load_grid", "fc_set
            "fc_run_points", "fc_run_point", "fc_fake_data", "fc_covariance", "fc_scan", "fc_quantiles",
            "fc_submit", "fc_poll", "fc_cancel", "fc_get_stats", "fc_last_error", "fc_fake_data_noalloc",
            "fc_set_tuning", "fc_get_tuning", "fc_autotune", "fc_get_serve_stats", "fc_data_dchi2", "fc_fc_region",
-           "fc_fc_region_adaptive", "fc_load_grid_osc", "fc_get_decided_by", "fc_set_wait_test", "fc_measure_peaks"]
+           "fc_fc_region_adaptive", "fc_load_grid_osc", "fc_load_grid_osc_ex", "fc_get_decided_by", "fc_set_wait_test", "fc_measure_peaks"]
 
 
 class FCError(RuntimeError):
@@ -109,6 +110,8 @@ def load(build: bool = False):
         "fc_destroy": (st, [vp]),
         "fc_load_grid": (st, [vp, vp, i64, i32, vp, i32, ctypes.POINTER(i32)]),
         "fc_load_grid_osc": (st, [vp, ctypes.POINTER(fc_osc_model), i32, vp, i32, ctypes.POINTER(i32)]),
+        "fc_load_grid_osc_ex": (st, [vp, ctypes.POINTER(fc_osc_model), i32, vp, i32, ctypes.c_uint32,
+                                     ctypes.POINTER(i32)]),
         "fc_set_frac_cov": (st, [vp, i32, vp, i32]),
         "fc_unload_grid": (st, [vp, i32]),
         "fc_run_points": (st, [vp, i32, vp, i32, u64, i32, ctypes.POINTER(fc_opts), vp, vp, vp]),
@@ -211,9 +214,12 @@ def fc_load_grid(ctx, S, collapse=None, n_fit: int | None = None) -> int:
     return gid.value
 
 
-def fc_load_grid_osc(ctx, axes, terms, b, f, L, E, collapse=None, n_fit: int | None = None) -> int:
+def fc_load_grid_osc(ctx, axes, terms, b, f, L, E, collapse=None, n_fit: int | None = None,
+                     recompute: bool = False, flags: int | None = None) -> int:
     """Grid spectra generated on the device: axes = list of 1-D value arrays (axis 0 slowest),
-    terms = list of (amplitude axis, dm2 axis), b/L/E [N_full], f [n_terms][N_full]."""
+    terms = list of (amplitude axis, dm2 axis), b/L/E [N_full], f [n_terms][N_full].
+    recompute: keep no spectra, evaluate the model wherever a row is read (FC_GRID_RECOMPUTE);
+    flags, when given, are passed as they are."""
     axes = [_host(a, np.float64) for a in axes]
     lens = np.array([len(a) for a in axes], np.int32)
     vals = np.ascontiguousarray(np.concatenate(axes), np.float64)
@@ -227,9 +233,15 @@ def fc_load_grid_osc(ctx, axes, terms, b, f, L, E, collapse=None, n_fit: int | N
     m = fc_osc_model(len(axes), _ptr(lens), _ptr(vals), len(terms), _ptr(amp), _ptr(dm2), _ptr(b), _ptr(f), _ptr(L),
                      _ptr(E))
     gid = ctypes.c_int32()
-    _check(load().fc_load_grid_osc(ctx, ctypes.byref(m), nf, _ptr(coll) if coll is not None else None, nfit,
-                                   ctypes.byref(gid)), ctx)
+    _check(load().fc_load_grid_osc_ex(ctx, ctypes.byref(m), nf, _ptr(coll) if coll is not None else None, nfit,
+                                      (FC_GRID_RECOMPUTE if recompute else 0) if flags is None else flags,
+                                      ctypes.byref(gid)), ctx)
     return gid.value
+
+
+def fc_load_grid_osc_ex(ctx, axes, terms, b, f, L, E, collapse=None, n_fit: int | None = None, flags: int = 0) -> int:
+    """fc_load_grid_osc with the C entry point's flags (FC_GRID_RECOMPUTE)."""
+    return fc_load_grid_osc(ctx, axes, terms, b, f, L, E, collapse, n_fit, flags=flags)
 
 
 def fc_set_frac_cov(ctx, grid_id: int, F):

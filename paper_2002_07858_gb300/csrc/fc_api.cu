@@ -91,6 +91,31 @@ struct Grid {
     uint16_t* Bt = nullptr;     // screen B image [G_pad/BN][2K/8][BN/8][8][8]
     int32_t* collapse = nullptr;
     double* F = nullptr;
+    // shape-model grids: the model on the device (int and double arrays, sine
+    // table included); recompute = no spectra are stored, every row is evaluated
+    // where it is read (S_full, S_fit, Sc, Sdf, Sc32 stay null)
+    bool recompute = false;
+    int32_t* model_i = nullptr;
+    double* model_d = nullptr;
+    SpecModel model;
+    // where kernels read the grid's rows
+    GridSpec spec() const {
+        GridSpec s;
+        s.S_fit = S_fit;
+        s.Sc = Sc;
+        s.Sc32 = Sc32;
+        s.Sdf = Sdf;
+        s.centre = centre;
+        s.nfit = nfit;
+        s.m = model;
+        return s;
+    }
+    FullSrc full() const {
+        FullSrc f;
+        f.S = S_full;
+        f.m = model;
+        return f;
+    }
     // covariance cache: one slot per grid index used as a fit covariance (plus
     // one for A = I).  Grows by doubling up to max_cap; when full, the slots
     // least recently used by a scan are handed to new indices.
@@ -575,7 +600,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
         FC_TRY(scratch(c, "cov_work", new_q.size() * g->nfit * g->nfit, &work));
         FC_CUDA(cudaMemcpyAsync(dq, new_q.data(), new_q.size() * 4, cudaMemcpyHostToDevice, c->stream));
         FC_CUDA(cudaMemcpyAsync(ds, new_s.data(), new_s.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        launch_build_cov(g->S_full, g->nf, g->nfit, g->identity_collapse ? nullptr : g->collapse, g->F, dq, ds,
+        launch_build_cov(g->full(), g->nf, g->nfit, g->identity_collapse ? nullptr : g->collapse, g->F, dq, ds,
                          (int)new_q.size(), cov_mode == FC_COV_IDENTITY ? 2 : 0, g->A64, g->W64, g->A32, g->rho,
                          work, c->status_dev, c->stream);
         launch_wdf(g->W64, ds, (int)new_q.size(), g->nfit, g->Wdf, c->stream);
@@ -593,7 +618,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
             launch_qvec_tc(g->Bt, g->Wimg, g->wnorm, g->gnorm, ds, (int)q32_list.size(), g->G, g->G_pad, g->nfit,
                            g->K, g->Qc, g->Qb, g->Qb3, c->status_dev, c->n_sm, c->stream);
         } else {
-            launch_qvec32(g->Sc32, g->gnorm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(),
+            launch_qvec32(g->spec(), g->gnorm, g->G, g->G_pad, g->nfit, g->A32, g->rho, ds, (int)q32_list.size(),
                           g->Qc, g->Qb, g->Qb3, c->stream);
         }
         FC_TRY(check_status(c));
@@ -601,7 +626,7 @@ fc_status ensure_slots(fc_ctx* c, Grid* g, const std::vector<int32_t>& qs, int c
     if (!q64_list.empty()) {
         FC_TRY(ensure_q64_storage(c, g));
         FC_CUDA(cudaMemcpyAsync(ds, q64_list.data(), q64_list.size() * 4, cudaMemcpyHostToDevice, c->stream));
-        launch_qvec64(g->Sc, g->G, g->nfit, g->W64, ds, (int)q64_list.size(), g->G, g->Q64, c->stream);
+        launch_qvec64(g->spec(), g->G, g->nfit, g->W64, ds, (int)q64_list.size(), g->G, g->Q64, c->stream);
         FC_TRY(sync(c));
     }
     return FC_OK;
@@ -831,7 +856,7 @@ fc_status lane_admit(fc_ctx* c, Lane* L, const std::shared_ptr<LaneJob>& J, cons
         FC_TRY(scratch(c, "L64", (size_t)P * g->nf * g->nf, &L64));
         FC_TRY(scratch(c, "L32", (size_t)P * g->nf * g->nf, &L32));
         FC_TRY(scratch(c, "s32", (size_t)P * g->nf, &s32));
-        launch_chol_sys(g->S_full, g->nf, g->F, ps_dev, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
+        launch_chol_sys(g->full(), g->nf, g->F, ps_dev, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
                         c->status_dev, c->stream);
         FC_TRY(check_status(c));
         launch_fake_data(L32, s32, g->nf, g->identity_collapse ? nullptr : g->collapse, g->nfit, ps_dev, P, U, seed,
@@ -901,7 +926,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             FC_TRY(scratch(c, "fb_pv", (size_t)cnt * nsp, &pv));
             FC_TRY(scratch(c, "fb_pg", (size_t)cnt * nsp, &pg));
             stage_begin(c);
-            launch_scan_resid(list, cnt, fslot, d, g->Sdf, g->G, g->nfit, g->Wdf, pv, pg, nsp, L->best,
+            launch_scan_resid(list, cnt, fslot, d, g->spec(), g->G, g->nfit, g->Wdf, pv, pg, nsp, L->best,
                               c->stream);
             S->residuals += cnt * g->G;
             FC_TRY(stage_end(c, &S->ms_fallback));
@@ -923,7 +948,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
         }
         if (!mixed) {
             stage_begin(c);
-            launch_scan64(list, cnt, fslot, d, g->centre, g->Sc, g->G, g->nfit, g->A64, g->Q64, g->G, L->best,
+            launch_scan64(list, cnt, fslot, d, g->spec(), g->G, g->nfit, g->A64, g->Q64, g->G, L->best,
                           c->stream);
             FC_TRY(stage_end(c, &S->ms_scan64));
         }
@@ -942,8 +967,8 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
             else
                 launch_lookup_slots(fin, n_fin, cur, g->slot_of, finslot, c->stream);
             stage_begin(c);
-            launch_finish(fin, n_fin, finslot, L->best, us, d, g->S_fit, g->nfit, g->W64, mixed ? g->Sdf : nullptr,
-                          mixed ? g->Wdf : nullptr, L->dchi2, L->chi2min, c->stream);
+            launch_finish(fin, n_fin, finslot, L->best, us, d, g->spec(), g->nfit, g->W64, mixed ? g->Wdf : nullptr,
+                          L->dchi2, L->chi2min, c->stream);
             if (mixed) S->residuals += 2 * (int64_t)n_fin;
             FC_TRY(stage_end(c, &S->ms_finish));
         }
@@ -999,7 +1024,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 int32_t n_tiles = 0;
                 FC_CUDA(cudaMemcpyAsync(&n_tiles, cnts + 5, 4, cudaMemcpyDeviceToHost, c->stream));
                 FC_TRY(sync(c));
-                launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->Sc32,
+                launch_yprep(tslot, tuniv, n_tiles, d, g->centre, g->nfit, g->K, g->A32, g->rho, cur, g->spec(),
                              g->gnorm, g->Qc, g->Qb, g->G_pad, Yt, alpha, tau0, tj0, c->stream);
                 if (seeded) launch_min_tau(tuniv, n_tiles, thr, tau0, c->stream);
                 FC_TRY(stage_end(c, &S->ms_prep));
@@ -1012,7 +1037,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                     const int mode = pass == 0 ? kScreenMin : (listing ? kScreenList : kScreenTopK);
                     if (!launch_screen(g->K, rtopk, mode, g->tune.screen_stages, g->tune.screen_ybuf, Yt, g->Bt, g->Qb3,
                                        tslot, tau0, tj0, n_tiles, g->G, g->G_pad, cval, cidx, ccount, c->status_dev,
-                                       g->Qc, g->Qb, g->gnorm, alpha, g->Sc32, g->nfit, ListArgs{tuniv, loff, lnum},
+                                       g->Qc, g->Qb, g->gnorm, alpha, g->spec(), g->nfit, ListArgs{tuniv, loff, lnum},
                                        c->wait_test, c->n_sm, c->stream))
                         return fail(FC_ERR_ARG, "no tensor-core screen instance for K = " + std::to_string(g->K));
                     S->screen_launches += 1;
@@ -1037,11 +1062,10 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
                 ra.G_pad = g->G_pad;
                 ra.d = d;
                 ra.centre = g->centre;
-                ra.S_fit = g->S_fit;
                 ra.nfit = g->nfit;
                 ra.W64 = g->W64;
                 ra.Wdf = g->Wdf;
-                ra.Sdf = g->Sdf;
+                ra.gs = g->spec();
                 ra.centre_df = g->centre_df;
                 ra.cur = cur;
                 ra.pt = L->pt;
@@ -1493,7 +1517,7 @@ fc_status fake_data_impl(fc_ctx* c, int32_t grid_id, const int64_t* ps, int32_t 
     FC_TRY(scratch(c, "L64", (size_t)P * g->nf * g->nf, &L64));
     FC_TRY(scratch(c, "L32", (size_t)P * g->nf * g->nf, &L32));
     FC_TRY(scratch(c, "s32", (size_t)P * g->nf, &s32));
-    launch_chol_sys(g->S_full, g->nf, g->F, ps_dev, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
+    launch_chol_sys(g->full(), g->nf, g->F, ps_dev, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr,
                     c->status_dev, c->stream);
     FC_TRY(check_status(c));
     if (is_device_ptr(out)) {
@@ -1758,10 +1782,14 @@ fc_status check_grid_args(int64_t G, int32_t nf, const int32_t* collapse, int32_
 void free_grid_arrays(fc_ctx* c, Grid* g) {
     dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
     dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->Sdf); dfree(c, g->centre_df);
+    dfree(c, g->model_i); dfree(c, g->model_d);
 }
 
-// A new grid's sizes and its resident arrays (S_full still to be filled).
-fc_status alloc_grid(fc_ctx* c, Grid* g, int64_t G, int32_t nf, int32_t nfit, const std::vector<int32_t>& hcoll) {
+// A new grid's sizes and its resident arrays (S_full still to be filled).  A
+// recomputed grid keeps no spectra: only the centre, the screen's image and
+// norms, and the collapse map.
+fc_status alloc_grid(fc_ctx* c, Grid* g, int64_t G, int32_t nf, int32_t nfit, const std::vector<int32_t>& hcoll,
+                     bool recompute = false) {
     g->G = G;
     g->G_pad = ((G + kBN - 1) / kBN) * kBN;
     g->nf = nf;
@@ -1771,13 +1799,16 @@ fc_status alloc_grid(fc_ctx* c, Grid* g, int64_t G, int32_t nf, int32_t nfit, co
     if (!hcoll.empty())
         for (int i = 0; i < nf; ++i) ident = ident && (hcoll[i] == i) && (nf == nfit);
     g->identity_collapse = ident;
-    FC_TRY(dalloc_t(c, &g->S_full, (size_t)G * nf));
-    FC_TRY(dalloc_t(c, &g->S_fit, (size_t)G * nfit));
+    g->recompute = recompute;
+    if (!recompute) {
+        FC_TRY(dalloc_t(c, &g->S_full, (size_t)G * nf));
+        FC_TRY(dalloc_t(c, &g->S_fit, (size_t)G * nfit));
+        FC_TRY(dalloc_t(c, &g->Sc, (size_t)G * nfit));
+        FC_TRY(dalloc_t(c, &g->Sdf, (size_t)G * nfit));
+        FC_TRY(dalloc_t(c, &g->Sc32, (size_t)G * nfit));
+    }
     FC_TRY(dalloc_t(c, &g->centre, (size_t)nfit));
-    FC_TRY(dalloc_t(c, &g->Sc, (size_t)G * nfit));
-    FC_TRY(dalloc_t(c, &g->Sdf, (size_t)G * nfit));
     FC_TRY(dalloc_t(c, &g->centre_df, (size_t)nfit));
-    FC_TRY(dalloc_t(c, &g->Sc32, (size_t)G * nfit));
     FC_TRY(dalloc_t(c, &g->gnorm, (size_t)G));
     FC_TRY(dalloc_t(c, &g->Bt, (size_t)g->G_pad * 2 * g->K));
     FC_TRY(dalloc_t(c, &g->collapse, (size_t)nf));
@@ -1791,10 +1822,11 @@ fc_status alloc_grid(fc_ctx* c, Grid* g, int64_t G, int32_t nf, int32_t nfit, co
 fc_status finish_grid(fc_ctx* c, std::unique_ptr<Grid>& g, int32_t* grid_id) {
     const int64_t G = g->G;
     const int nf = g->nf, nfit = g->nfit;
-    launch_collapse(g->S_full, G, nf, g->identity_collapse ? nullptr : g->collapse, nfit, g->S_fit, c->stream);
-    launch_centre(g->S_fit, G, nfit, g->centre, nullptr, c->stream);
-    launch_centred(g->S_fit, g->centre, G, g->G_pad, nfit, g->K, g->Sc, g->Sc32, g->gnorm, g->Bt, c->stream);
-    launch_to_df(g->S_fit, G * nfit, g->Sdf, c->stream);
+    if (!g->recompute)
+        launch_collapse(g->S_full, G, nf, g->identity_collapse ? nullptr : g->collapse, nfit, g->S_fit, c->stream);
+    launch_centre(g->spec(), G, g->centre, c->stream);
+    launch_centred(g->spec(), G, g->G_pad, g->K, g->Sc, g->Sc32, g->gnorm, g->Bt, c->stream);
+    if (!g->recompute) launch_to_df(g->S_fit, G * nfit, g->Sdf, c->stream);
     launch_to_df(g->centre, nfit, g->centre_df, c->stream);
     FC_TRY(sync(c));
     std::lock_guard<std::mutex> lq(c->q_mu);
@@ -1838,9 +1870,16 @@ fc_status fc_load_grid(fc_ctx* c, const double* S, int64_t G, int32_t nf, const 
 
 fc_status fc_load_grid_osc(fc_ctx* c, const fc_osc_model* m, int32_t nf, const int32_t* collapse, int32_t nfit,
                            int32_t* grid_id) {
+    return fc_load_grid_osc_ex(c, m, nf, collapse, nfit, 0u, grid_id);
+}
+
+fc_status fc_load_grid_osc_ex(fc_ctx* c, const fc_osc_model* m, int32_t nf, const int32_t* collapse, int32_t nfit,
+                              uint32_t flags, int32_t* grid_id) {
     if (!c || !m || !grid_id || !m->axis_len || !m->axis_values || !m->amp_axis || !m->dm2_axis || !m->b || !m->f ||
         !m->L || !m->E)
         return fail(FC_ERR_ARG, "NULL argument");
+    if (flags & ~(uint32_t)FC_GRID_RECOMPUTE) return fail(FC_ERR_ARG, "unknown grid flag");
+    const bool recompute = (flags & FC_GRID_RECOMPUTE) != 0;
     if (m->D < 1 || m->D > kMaxOscAxes) return fail(FC_ERR_ARG, "D out of range [1, 8]");
     if (m->n_terms < 1 || m->n_terms > kMaxOscTerms) return fail(FC_ERR_ARG, "n_terms out of range [1, 4]");
     int64_t G = 1;
@@ -1861,43 +1900,87 @@ fc_status fc_load_grid_osc(fc_ctx* c, const fc_osc_model* m, int32_t nf, const i
             return fail(FC_ERR_ARG, "energies must be > 0 and baselines finite");
     std::vector<int32_t> hcoll;
     FC_TRY(check_grid_args(G, nf, collapse, nfit, &hcoll));
+    bool ident = true;
+    if (!hcoll.empty())
+        for (int i = 0; i < nf; ++i) ident = ident && (hcoll[i] == i) && (nf == nfit);
     std::lock_guard<std::mutex> lk(c->api_mu);
     cudaSetDevice(c->device);
-    // the model's small arrays, packed: lengths, offsets, term axes | axis values, b, f, L, E
+    // The model on the device, packed.  ints: axis lengths, axis offsets, term axes (amplitude, dm2),
+    // each term's first sine-table row, the generator's error count, then (a collapse other than the
+    // identity) each fit bin's first member and the members.  doubles: axis values, b, f, L, E, then
+    // the sine table (one row per dm2 value of each term).
+    const int D = m->D, T = m->n_terms;
     std::vector<int32_t> hi;
-    hi.insert(hi.end(), m->axis_len, m->axis_len + m->D);
+    hi.insert(hi.end(), m->axis_len, m->axis_len + D);
     hi.insert(hi.end(), off.begin(), off.end());
-    hi.insert(hi.end(), m->amp_axis, m->amp_axis + m->n_terms);
-    hi.insert(hi.end(), m->dm2_axis, m->dm2_axis + m->n_terms);
-    hi.push_back(0);  // the count of invalid entries
+    hi.insert(hi.end(), m->amp_axis, m->amp_axis + T);
+    hi.insert(hi.end(), m->dm2_axis, m->dm2_axis + T);
+    int32_t rows = 0;
+    for (int t = 0; t < T; ++t) {
+        hi.push_back(rows);
+        rows += m->axis_len[m->dm2_axis[t]];
+    }
+    const size_t o_bad = hi.size();
+    hi.push_back(0);
+    const size_t o_moff = hi.size();
+    if (!ident) {
+        std::vector<int32_t> moff(nfit + 1, 0), mem(nf), cur(nfit);
+        for (int i = 0; i < nf; ++i) ++moff[hcoll[i] + 1];
+        for (int j = 0; j < nfit; ++j) moff[j + 1] += moff[j];
+        for (int j = 0; j < nfit; ++j) cur[j] = moff[j];
+        for (int i = 0; i < nf; ++i) mem[cur[hcoll[i]]++] = i;  // increasing i within each fit bin
+        hi.insert(hi.end(), moff.begin(), moff.end());
+        hi.insert(hi.end(), mem.begin(), mem.end());
+    }
     std::vector<double> hd;
     hd.insert(hd.end(), m->axis_values, m->axis_values + n_vals);
     const size_t o_b = hd.size();
     hd.insert(hd.end(), m->b, m->b + nf);
     const size_t o_f = hd.size();
-    hd.insert(hd.end(), m->f, m->f + (size_t)m->n_terms * nf);
+    hd.insert(hd.end(), m->f, m->f + (size_t)T * nf);
     const size_t o_L = hd.size();
     hd.insert(hd.end(), m->L, m->L + nf);
     const size_t o_E = hd.size();
     hd.insert(hd.end(), m->E, m->E + nf);
-    int32_t* di = nullptr;
-    double* dd = nullptr;
-    FC_TRY(scratch(c, "osc_i", hi.size(), &di));
-    FC_TRY(scratch(c, "osc_d", hd.size(), &dd));
-    FC_CUDA(cudaMemcpyAsync(di, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, c->stream));
-    FC_CUDA(cudaMemcpyAsync(dd, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    const size_t o_sin = hd.size();
     auto g = std::make_unique<Grid>();
-    fc_status st = alloc_grid(c, g.get(), G, nf, nfit, hcoll);
+    fc_status st = dalloc_t(c, &g->model_i, hi.size());
+    if (st == FC_OK) st = dalloc_t(c, &g->model_d, o_sin + (size_t)rows * nf);
+    if (st == FC_OK && cudaMemcpyAsync(g->model_i, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, c->stream))
+        st = fail(FC_ERR_CUDA, "copying the model failed");
+    if (st == FC_OK && cudaMemcpyAsync(g->model_d, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice, c->stream))
+        st = fail(FC_ERR_CUDA, "copying the model failed");
+    if (st == FC_OK) st = alloc_grid(c, g.get(), G, nf, nfit, hcoll, recompute);
     int bad = 0;
     if (st == FC_OK) {
-        const int D = m->D, T = m->n_terms;
-        int* dbad = di + 2 * D + 2 * T;
-        launch_osc_spectra(G, nf, D, di, di + D, dd, T, di + 2 * D, di + 2 * D + T, dd + o_b, dd + o_f, dd + o_L,
-                           dd + o_E, g->S_full, dbad, c->stream);
+        SpecModel& sm = g->model;
+        const int32_t* di = g->model_i;
+        const double* dd = g->model_d;
+        sm.D = D;
+        sm.n_terms = T;
+        sm.nf = nf;
+        sm.nfit = nfit;
+        sm.axis_len = di;
+        sm.axis_off = di + D;
+        sm.amp_ax = di + 2 * D;
+        sm.dm2_ax = di + 2 * D + T;
+        sm.sin_off = di + 2 * D + 2 * T;
+        sm.axis_val = dd;
+        sm.b = dd + o_b;
+        sm.f = dd + o_f;
+        sm.sinT = dd + o_sin;
+        sm.mem_off = ident ? nullptr : di + o_moff;
+        sm.mem = ident ? nullptr : di + o_moff + nfit + 1;
+        int* dbad = g->model_i + o_bad;
+        launch_osc_sin(sm, rows, dd + o_L, dd + o_E, g->model_d + o_sin, c->stream);
+        // a stored grid is filled by the model's evaluation; a recomputed one is only checked
+        launch_osc_spectra(sm, G, g->S_full, dbad, c->stream);
         if (cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
             st = fail(FC_ERR_CUDA, "reading the generator's check back failed");
         if (st == FC_OK) st = sync(c);
         if (st == FC_OK && bad) st = fail(FC_ERR_ARG, "the model gives spectra that are not finite and >= 0");
+        // a stored grid reads its rows from memory from now on
+        if (!recompute) g->model = SpecModel{};
     }
     if (st == FC_OK) st = finish_grid(c, g, grid_id);
     if (st != FC_OK && g) free_grid_arrays(c, g.get());
@@ -1958,7 +2041,7 @@ fc_status fc_unload_grid(fc_ctx* c, int32_t grid_id) {
     free_cache(c, g);
     dfree(c, g->S_full); dfree(c, g->S_fit); dfree(c, g->centre); dfree(c, g->Sc); dfree(c, g->Sc32);
     dfree(c, g->gnorm); dfree(c, g->Bt); dfree(c, g->collapse); dfree(c, g->F); dfree(c, g->Sdf);
-    dfree(c, g->centre_df);
+    dfree(c, g->centre_df); dfree(c, g->model_i); dfree(c, g->model_d);
     return FC_OK;
 }
 
@@ -2006,7 +2089,7 @@ fc_status fc_covariance(fc_ctx* c, int32_t grid_id, int64_t q, double* A, double
         FC_TRY(scratch(c, "cov_L32", (size_t)g->nf * g->nf, &L32));
         FC_TRY(scratch(c, "cov_s32", (size_t)g->nf, &s32));
         FC_CUDA(cudaMemcpyAsync(pd, &q, 8, cudaMemcpyHostToDevice, c->stream));
-        launch_chol_sys(g->S_full, g->nf, g->F, pd, 1, 0, L64, L32, s32, nullptr, c->status_dev, c->stream);
+        launch_chol_sys(g->full(), g->nf, g->F, pd, 1, 0, L64, L32, s32, nullptr, c->status_dev, c->stream);
         FC_TRY(check_status(c));
         FC_TRY(copy_out(c, L_sys, L64, (size_t)g->nf * g->nf * 8));
     }

@@ -35,6 +35,45 @@ enum : int {
     kDevBadIndex = 4,
 };
 
+// ---- where a grid's spectra come from (device functions in fc_spec.cuh) ----
+constexpr int kMaxOscAxes = 8;
+constexpr int kMaxOscTerms = 4;
+
+// The oscillation shape model of a grid on the device; axis_len == nullptr: none.
+struct SpecModel {
+    int D = 0, n_terms = 0, nf = 0, nfit = 0;
+    const int32_t* axis_len = nullptr;  // [D]
+    const int32_t* axis_off = nullptr;  // [D] first value of each axis in axis_val
+    const int32_t* amp_ax = nullptr;    // [n_terms]
+    const int32_t* dm2_ax = nullptr;    // [n_terms]
+    const int32_t* sin_off = nullptr;   // [n_terms] first row of each term's sine table
+    const double* axis_val = nullptr;
+    const double* b = nullptr;          // [nf]
+    const double* f = nullptr;          // [n_terms][nf]
+    const double* sinT = nullptr;       // [rows][nf] sin(1.27 dm2 L_i / E_i), one row per dm2 value of a term
+    const int32_t* mem_off = nullptr;   // [nfit + 1] CSR of the collapse; nullptr: identity
+    const int32_t* mem = nullptr;       // [nf] full bins of each fit bin in increasing order
+};
+
+// Full-bin spectra rows: stored [G][nf] (S), or the model when S is null.
+struct FullSrc {
+    const double* S = nullptr;
+    SpecModel m;
+};
+
+// Fit-space rows of a grid and the copies derived from them.  A null array is
+// derived where it is read: from S_fit, or from the model when S_fit is null
+// too, with the operation that fills the stored copy.
+struct GridSpec {
+    const double* S_fit = nullptr;   // [G][nfit]
+    const double* Sc = nullptr;      // [G][nfit] S_fit - centre
+    const float* Sc32 = nullptr;     // [G][nfit] (float)(S_fit - centre)
+    const float2* Sdf = nullptr;     // [G][nfit] double-float S_fit
+    const double* centre = nullptr;  // [nfit]
+    int nfit = 0;
+    SpecModel m;
+};
+
 // Padded fit dimension of the tensor-core screen: three spare columns (they
 // carry the error-bound terms), rounded up to the MMA K-step of 16.
 __host__ __device__ inline int screen_k(int nfit) { return ((nfit + 3 + 15) / 16) * 16; }
@@ -83,22 +122,24 @@ __device__ __forceinline__ void store_qb3(uint16_t* o, float qb) {
 // ---- ingest (a1) ----
 void launch_collapse(const double* S_full, int64_t G, int nf, const int32_t* collapse, int nfit, double* S_fit,
                      cudaStream_t st);
-void launch_centre(const double* S_fit, int64_t G, int nfit, double* centre, double* work, cudaStream_t st);
-void launch_centred(const double* S_fit, const double* centre, int64_t G, int64_t G_pad, int nfit, int K,
-                    double* Sc, float* Sc32, float4* gnorm, uint16_t* Btiles, cudaStream_t st);
+// centre <- per-bin approximate median of the fit-space rows of gs
+void launch_centre(const GridSpec& gs, int64_t G, double* centre, cudaStream_t st);
+// the screen's image and norms from gs (gs.centre set); Sc / Sc32 stored when given
+void launch_centred(const GridSpec& gs, int64_t G, int64_t G_pad, int K, double* Sc, float* Sc32, float4* gnorm,
+                    uint16_t* Btiles, cudaStream_t st);
 
 // ---- covariances (a2) ----
 // L_p (binary64 and binary32 copies) for every true point; gauss adds diag(s).
-void launch_chol_sys(const double* S_full, int nf, const double* F, const int64_t* ps, int P, int gauss,
+void launch_chol_sys(const FullSrc& src, int nf, const double* F, const int64_t* ps, int P, int gauss,
                      double* L64, float* L32, float* s32, double* work, int* status, cudaStream_t st);
 // A(q) = M(q)^-1 for a list of (slot, q): A64, W64 (A = W^T W), A32, rho (max abs row sum of A).
-void launch_build_cov(const double* S_full, int nf, int nfit, const int32_t* collapse, const double* F,
+void launch_build_cov(const FullSrc& src, int nf, int nfit, const int32_t* collapse, const double* F,
                       const int32_t* q_list, const int32_t* slot_list, int n, int cov_mode, double* A64,
                       double* W64, float* A32, float* rho, double* work, int* status, cudaStream_t st);
 // q_g = s~_g^T A s~_g for slots: binary64 |W s~_g|^2 (plain) or binary32 central + lower bound (mixed).
-void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* W64, const int32_t* slots, int n,
+void launch_qvec64(const GridSpec& gs, int64_t G, int nfit, const double* W64, const int32_t* slots, int n,
                    int64_t ldq, double* Q64, cudaStream_t st);
-void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
+void launch_qvec32(const GridSpec& gs, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
                    cudaStream_t st);
 
@@ -126,11 +167,11 @@ void launch_set_slots(const int32_t* q_list, const int32_t* slot_list, int n, in
 
 // ---- plain binary64 scan ----
 void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot_of_list, const float* d,
-                   const double* centre, const double* Sc, int64_t G, int nfit, const double* A64,
+                   const GridSpec& gs, int64_t G, int nfit, const double* A64,
                    const double* Q64, int64_t ldq, int32_t* best, cudaStream_t st);
 
 // exact residual-form scan of the mixed path (double-float, split over nsp CTAs per universe)
-void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const float2* Sdf,
+void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const GridSpec& gs,
                        int64_t G, int nfit, const float2* Wdf, double* part_v, int32_t* part_g, int nsp,
                        int32_t* best, cudaStream_t st);
 // double-float copies: W of a list of slots; any binary64 array
@@ -146,7 +187,7 @@ void launch_group(const int32_t* active, int64_t n_active, const int32_t* uslot,
                   int64_t max_tiles, int slot_rows, cudaStream_t st);
 void launch_yprep(const int32_t* quad_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
-                  const float* Sc32, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
+                  const GridSpec& gs, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
                   uint16_t* Ytiles, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st);
 // Tensor-core screen of BM-row tiles (see fc_screen.cu).  mode: kScreenTopK,
 // kScreenMin (first pass; tightens tau0 in place) or kScreenList (every point
@@ -176,7 +217,7 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
                    const uint16_t* Qb3,
                    const int32_t* quad_slot, float* tau0, const int32_t* tile_j0, int64_t n_tiles, int64_t G,
                    int64_t G_pad, float* cand_val, int32_t* cand_idx, int32_t* cand_count, int* status,
-                   const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
+                   const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const GridSpec& gs,
                    int nfit, const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st);
 // Resolution of one mixed-path scan per screen tile (see k_resolve).
 struct ResolveArgs {
@@ -192,11 +233,10 @@ struct ResolveArgs {
     int64_t G_pad;
     const float* d;
     const double* centre;
-    const double* S_fit;
+    GridSpec gs;           // the grid's fit-space rows (stored or recomputed)
     int nfit;
     const double* W64;
     const float2* Wdf;     // [slots][nfit][nfit] double-float W
-    const float2* Sdf;     // [G][nfit] double-float S_fit
     const float2* centre_df;  // [nfit] double-float centre
     int32_t* cur;          // [n] covariance grid index, advanced for continuing universes
     const int32_t* pt;     // [n] true point of the universe
@@ -270,10 +310,10 @@ struct UniverseState {
     const int32_t* job_of;
     int32_t* job_left;
 };
-// Sdf / Wdf given: the mixed path's double-float residuals; null: binary64 (plain path)
+// Wdf given: the mixed path's double-float residuals; null: binary64 (plain path)
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot_of_list, const int32_t* best,
-                   const UniverseState& us, const float* d, const double* S_fit, int nfit, const double* W64,
-                   const float2* Sdf, const float2* Wdf, double* dchi2, double* chi2min, cudaStream_t st);
+                   const UniverseState& us, const float* d, const GridSpec& gs, int nfit, const double* W64,
+                   const float2* Wdf, double* dchi2, double* chi2min, cudaStream_t st);
 // advance: converged / exhausted universes -> finish list, others stay active
 void launch_advance(const int32_t* active, int64_t n_active, const int32_t* best, const UniverseState& us,
                     int32_t* next_active, int32_t* n_next, int32_t* finish_list, int32_t* n_finish, cudaStream_t st);
@@ -283,13 +323,11 @@ bool measure_fma_peaks(int n_sm, double* fp64_tflops, double* fp32_tflops, cudaS
 
 // ---- quantiles ----
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st);
-// grid spectra of an oscillation shape model (see fc_load_grid_osc); *bad += entries not finite and >= 0
-constexpr int kMaxOscAxes = 8;
-constexpr int kMaxOscTerms = 4;
-void launch_osc_spectra(int64_t G, int nf, int D, const int32_t* axis_len, const int32_t* axis_off,
-                        const double* axis_val, int n_terms, const int32_t* amp_ax, const int32_t* dm2_ax,
-                        const double* b, const double* f, const double* L, const double* E, double* S, int* bad,
-                        cudaStream_t st);
+// The shape model's sine table (m.sinT, rows rows of m.nf), from the bins' L and E.
+void launch_osc_sin(const SpecModel& m, int rows, const double* L, const double* E, double* sinT, cudaStream_t st);
+// Full-bin spectra of the model into S [G][nf] (S null: only checked); bad counts
+// entries that are not finite and >= 0.
+void launch_osc_spectra(const SpecModel& m, int64_t G, double* S, int* bad, cudaStream_t st);
 // counts[r] += #{u : x[r][u] < thr[r]} for rows r < rows of x [rows][n]
 void launch_count_below(const double* x, int rows, int n, const double* thr, int64_t* counts, cudaStream_t st);
 

@@ -16,6 +16,7 @@
 #include "fc_df.cuh"
 #include "fc_internal.cuh"
 #include "fc_sampler.cuh"
+#include "fc_spec.cuh"
 
 namespace fcdev {
 
@@ -114,8 +115,8 @@ __device__ __forceinline__ void w_load4(const float2* __restrict__ Wk, float2 (&
 // summed in increasing i, so every operation and its order are df_row's and
 // the row loop's: the bits are the same, with a quarter of the loads of r.
 // In the last block, rows past N_fit read row N_fit - 1 and are dropped.
-template <bool EVEN>
-__device__ __forceinline__ double resid_df_blk(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+template <bool EVEN, class SRow>
+__device__ __forceinline__ double resid_df_blk(const float2* __restrict__ W, int n, const SRow& s,
                                                const float* __restrict__ du) {
     __align__(16) float2 r[kMaxBins + 4];
     for (int j = 0; j < n; ++j) r[j] = df_sub_f(s[j], du[j]);
@@ -165,8 +166,9 @@ __device__ __forceinline__ double resid_df_blk(const float2* __restrict__ W, int
     return df_to(df_norm(acc.x, acc.y));
 }
 
-__device__ double resid_df(const float2* __restrict__ W, int n, const float2* __restrict__ s,
-                           const float* __restrict__ du) {
+// s: the row s_g as double-float (a stored row, or a DfRow that may evaluate the shape model)
+template <class SRow>
+__device__ double resid_df(const float2* __restrict__ W, int n, const SRow& s, const float* __restrict__ du) {
     return (n % 2 == 0) ? resid_df_blk<true>(W, n, s, du) : resid_df_blk<false>(W, n, s, du);
 }
 
@@ -176,8 +178,8 @@ __device__ double resid_df(const float2* __restrict__ W, int n, const float2* __
 // across the warp because all its lanes walk the same rows).  The operations
 // and their order are resid_df's, term for term, so the bits are the same;
 // what changes is that no per-thread array lives in local memory.
-template <int NR>
-__device__ __forceinline__ double resid_df_reg(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+template <int NR, class SRow>
+__device__ __forceinline__ double resid_df_reg(const float2* __restrict__ W, int n, const SRow& s,
                                                const float* __restrict__ du) {
     static_assert(NR % 4 == 0, "NR is a multiple of 4");
     float2 r[NR];
@@ -211,8 +213,8 @@ __device__ __forceinline__ double resid_df_reg(const float2* __restrict__ W, int
 }
 
 // The mixed path's residual chi2 for a compile-time bound NR on N_fit (0 = any N_fit).
-template <int NR>
-__device__ __forceinline__ double resid_mixed(const float2* __restrict__ W, int n, const float2* __restrict__ s,
+template <int NR, class SRow>
+__device__ __forceinline__ double resid_mixed(const float2* __restrict__ W, int n, const SRow& s,
                                               const float* __restrict__ du) {
     if constexpr (NR > 0)
         return resid_df_reg<NR>(W, n, s, du);
@@ -223,8 +225,9 @@ __device__ __forceinline__ double resid_mixed(const float2* __restrict__ W, int 
 // resid_df spread over a warp with the same bits: r_j = s_j - d_j is formed in
 // this warp's shared vector r, lanes form the rows t_i into t, lane 0 sums
 // t_i^2 in row order.  The result is lane 0's.
-__device__ double resid_df_warp(const float2* __restrict__ W, int n, const float2* __restrict__ s,
-                                const float* __restrict__ du, float2* r, float2* t, int lane) {
+template <class SRow>
+__device__ double resid_df_warp(const float2* __restrict__ W, int n, const SRow& s, const float* __restrict__ du,
+                                float2* r, float2* t, int lane) {
     for (int j = lane; j < n; j += 32) r[j] = df_sub_f(s[j], du[j]);
     __syncwarp();
     for (int i = lane; i < n; i += 32) t[i] = df_row(W + i * n, r, i + 1);
@@ -234,6 +237,19 @@ __device__ double resid_df_warp(const float2* __restrict__ W, int n, const float
         for (int i = 0; i < n; ++i) acc = df_fma(acc, t[i], t[i]);
     __syncwarp();
     return df_to(df_norm(acc.x, acc.y));
+}
+
+// Row g of s for the residual routines (g = -1: the centre).  The kernels that
+// score residuals are instantiated twice: MODEL = false reads the stored
+// double-float rows through a plain pointer, MODEL = true (a recomputed grid)
+// evaluates the shape model through a DfRow.  Both feed the same routines, so
+// the bits agree and the stored path carries none of the model's registers.
+template <bool MODEL>
+__device__ __forceinline__ auto srow(const GridSpec& gs, const float2* centre_df, int64_t g) {
+    if constexpr (MODEL)
+        return df_row_of(gs, centre_df, g);
+    else
+        return (g < 0) ? centre_df : gs.Sdf + g * gs.nfit;
 }
 
 // double-float copies of W for a list of slots
@@ -263,42 +279,40 @@ __global__ void k_collapse(const double* __restrict__ S, int64_t G, int nf, cons
     for (int j = 0; j < nfit; ++j) out[g * nfit + j] = acc[j];
 }
 
+// Sine table of an oscillation shape model: for each term t and each value k
+// of its dm2 axis, sin(1.27 dm2_k L_i / E_i) for every full bin i, with the
+// products and the quotient in that order.
+__global__ void k_osc_sin(SpecModel m, int rows, const double* __restrict__ L, const double* __restrict__ E,
+                          double* __restrict__ sinT) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rows * m.nf) return;
+    const int row = (int)(e / m.nf), i = (int)(e % m.nf);
+    int t = 0;
+    while (t + 1 < m.n_terms && row >= m.sin_off[t + 1]) ++t;
+    const int a = m.dm2_ax[t];
+    const double dm2 = m.axis_val[m.axis_off[a] + (row - m.sin_off[t])];
+    sinT[e] = sin(__ddiv_rn(__dmul_rn(__dmul_rn(1.27, dm2), L[i]), E[i]));
+}
+
 // Grid spectra from an oscillation shape model, one thread per (grid point,
 // full bin): s_i(p) = b_i + sum_t amp_t(p) sin^2(1.27 dm2_t(p) L_i / E_i) f_ti,
-// the terms added in order t = 0, 1, ... to b_i.  Grid point p is the
-// row-major index over the axes (axis 0 slowest); term t reads its amplitude
-// from axis amp_ax[t] and its dm2 from axis dm2_ax[t].  bad counts entries
-// that are not finite and >= 0.
-__global__ void k_osc_spectra(int64_t G, int nf, int D, const int32_t* __restrict__ axis_len,
-                              const int32_t* __restrict__ axis_off, const double* __restrict__ axis_val, int n_terms,
-                              const int32_t* __restrict__ amp_ax, const int32_t* __restrict__ dm2_ax,
-                              const double* __restrict__ b, const double* __restrict__ f,
-                              const double* __restrict__ L, const double* __restrict__ E, double* __restrict__ S,
-                              int* __restrict__ bad) {
+// the terms added in order t = 0, 1, ... to b_i (model_full).  Grid point p is
+// the row-major index over the axes (axis 0 slowest); term t reads its
+// amplitude from axis amp_ax[t] and its dm2 from axis dm2_ax[t].  S null: the
+// spectra are only checked.  bad counts entries that are not finite and >= 0.
+__global__ void k_osc_spectra(SpecModel m, int64_t G, double* __restrict__ S, int* __restrict__ bad) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= G * nf) return;
-    const int64_t g = e / nf;
-    const int i = (int)(e % nf);
-    int idx[kMaxOscAxes];
-    int64_t rem = g;
-    for (int a = D - 1; a >= 0; --a) {
-        idx[a] = (int)(rem % axis_len[a]);
-        rem /= axis_len[a];
-    }
-    double v = b[i];
-    for (int t = 0; t < n_terms; ++t) {
-        const double amp = axis_val[axis_off[amp_ax[t]] + idx[amp_ax[t]]];
-        const double dm2 = axis_val[axis_off[dm2_ax[t]] + idx[dm2_ax[t]]];
-        const double sn = sin(1.27 * dm2 * L[i] / E[i]);
-        v += amp * (sn * sn) * f[t * nf + i];
-    }
-    S[e] = v;
+    if (e >= G * m.nf) return;
+    const int64_t g = e / m.nf;
+    const int i = (int)(e % m.nf);
+    const double v = model_full(m, model_row(m, g), i);
+    if (S) S[e] = v;
     if (!(v >= 0.0) || !isfinite(v)) atomicAdd(bad, 1);
 }
 
 // Approximate per-bin median of the grid spectra by two rounds of a 4096-bucket
 // histogram; it only chooses the centring vector of the screen, any value works.
-__global__ void k_centre(const double* __restrict__ S, int64_t G, int nfit, double* __restrict__ centre) {
+__global__ void k_centre(GridSpec gs, int64_t G, double* __restrict__ centre) {
     constexpr int NB = 4096;
     __shared__ unsigned hist[NB];
     __shared__ double red_lo[kThreads / 32], red_hi[kThreads / 32];
@@ -308,7 +322,7 @@ __global__ void k_centre(const double* __restrict__ S, int64_t G, int nfit, doub
     const int j = blockIdx.x;
     double lo = DBL_MAX, hi = -DBL_MAX;
     for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
-        const double x = S[g * nfit + j];
+        const double x = row_fit(gs, fit_row(gs, g), j);
         lo = fmin(lo, x);
         hi = fmax(hi, x);
     }
@@ -339,7 +353,7 @@ __global__ void k_centre(const double* __restrict__ S, int64_t G, int nfit, doub
         __syncthreads();
         const double w = (bhi - blo) / NB;
         for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
-            const double x = S[g * nfit + j];
+            const double x = row_fit(gs, fit_row(gs, g), j);
             if (x < blo || x > bhi) continue;
             int b = (w > 0.0) ? (int)((x - blo) / w) : 0;
             b = b < 0 ? 0 : (b >= NB ? NB - 1 : b);
@@ -374,16 +388,20 @@ __device__ __forceinline__ int64_t btile_offset(int64_t g, int c, int K) {
     return t * (int64_t)(2 * K * kBN) + (int64_t)(c >> 3) * (kBN * 8) + (r >> 3) * 64 + (r & 7) * 8 + (c & 7);
 }
 
-__global__ void k_centred(const double* __restrict__ Sfit, const double* __restrict__ centre, int64_t G, int nfit,
-                          int K, double* __restrict__ Sc, float* __restrict__ Sc32, float4* __restrict__ gnorm,
-                          uint16_t* __restrict__ Bt) {
+// The screen's bf16 hi/lo image of s~ = s - centre and the norms of its split,
+// one thread per grid point; the binary64 and binary32 centred rows are stored
+// when Sc / Sc32 are given.
+__global__ void k_centred(GridSpec gs, int64_t G, int K, double* __restrict__ Sc, float* __restrict__ Sc32,
+                          float4* __restrict__ gnorm, uint16_t* __restrict__ Bt) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= G) return;
+    const int nfit = gs.nfit;
+    const FitRow fr = fit_row(gs, g);
     double ss = 0.0, sl = 0.0, sr = 0.0;
     for (int j = 0; j < nfit; ++j) {
-        const double x = Sfit[g * nfit + j] - centre[j];
-        Sc[g * nfit + j] = x;
-        Sc32[g * nfit + j] = (float)x;
+        const double x = __dsub_rn(row_fit(gs, fr, j), gs.centre[j]);
+        if (Sc) Sc[g * nfit + j] = x;
+        if (Sc32) Sc32[g * nfit + j] = (float)x;
         ss = fma(x, x, ss);
         const __nv_bfloat16 h = __double2bfloat16(x);
         const double rem = x - (double)__bfloat162float(h);
@@ -477,12 +495,14 @@ __device__ bool chol_inplace(double* L, int n) {
     return s_bad == 0;
 }
 
-__global__ void k_chol_sys(const double* __restrict__ S, int nf, const double* __restrict__ F,
-                           const int64_t* __restrict__ ps, int gauss, double* __restrict__ L64,
-                           float* __restrict__ L32, float* __restrict__ s32, int* __restrict__ status) {
+__global__ void k_chol_sys(FullSrc src, int nf, const double* __restrict__ F, const int64_t* __restrict__ ps,
+                           int gauss, double* __restrict__ L64, float* __restrict__ L32, float* __restrict__ s32,
+                           int* __restrict__ status) {
     extern __shared__ double sL[];
+    __shared__ double s_row[kMaxBins];
     const int ip = blockIdx.x;
-    const double* s = S + ps[ip] * nf;
+    stage_full_row(src, nf, ps[ip], s_row);
+    const double* s = s_row;
     double* Lg = L64 + (size_t)ip * nf * nf;
     float* Lf = L32 + (size_t)ip * nf * nf;
     // element (i, j), j <= i, of diag(s) F diag(s) (+ diag(s) in the Gaussian mode)
@@ -527,7 +547,7 @@ __global__ void k_chol_sys(const double* __restrict__ S, int nf, const double* _
 // busy lanes would hold the pipe for whole warps) and a column's divisions
 // become one reciprocal and multiplies.  These factors feed the fit, not the
 // fake data, so they need not repeat the oracle's rounding bit for bit.
-__global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, const int32_t* __restrict__ coll,
+__global__ void k_build_cov(FullSrc src, int nf, int nfit, const int32_t* __restrict__ coll,
                             const double* __restrict__ F, const int32_t* __restrict__ q_list,
                             const int32_t* __restrict__ slot_list, int cov_mode, double* __restrict__ A64,
                             double* __restrict__ W64, float* __restrict__ A32, float* __restrict__ rho,
@@ -545,7 +565,9 @@ __global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, cons
     double* Wg = W64 + (size_t)slot * n * n;
     double* W = staged ? sLW + n * n : Wg;
     double* A = A64 + (size_t)slot * n * n;
-    const double* s = S + (int64_t)q * nf;
+    __shared__ double s_row[kMaxBins];
+    stage_full_row(src, nf, q, s_row);
+    const double* s = s_row;
     if (cov_mode == 2) {  // identity test mode
         for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
             const double v = (e / n == e % n) ? 1.0 : 0.0;
@@ -666,12 +688,17 @@ __global__ void k_build_cov(const double* __restrict__ S, int nf, int nfit, cons
 // q_g = s~_g^T A s~_g = |W s~_g|^2 (A = W^T W, W lower triangular): t_i = sum_{j<=i}
 // W_ij s~_j and q = sum_i t_i^2, each an fma chain in increasing index, so
 // N (N + 3) / 2 DFMA per point instead of the N^2 + N of s~^T (A s~).
-__global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, const double* __restrict__ W64,
+__global__ void k_qvec64(GridSpec gs, int64_t G, int nfit, const double* __restrict__ W64,
                          const int32_t* __restrict__ slots, int64_t ldq, double* __restrict__ Q64) {
     const int slot = slots[blockIdx.y];
     const double* W = W64 + (size_t)slot * nfit * nfit;
+    double sl[kMaxBins];  // the row, when it is recomputed rather than stored
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-        const double* s = Sc + g * nfit;
+        const double* s = gs.Sc ? gs.Sc + g * nfit : sl;
+        if (!gs.Sc) {
+            const FitRow fr = fit_row(gs, g);
+            for (int j = 0; j < nfit; ++j) sl[j] = row_sc(gs, fr, j);
+        }
         double q = 0.0;
         for (int i = 0; i < nfit; ++i) {
             const double* Wi = W + i * nfit;
@@ -686,7 +713,7 @@ __global__ void k_qvec64(const double* __restrict__ Sc, int64_t G, int nfit, con
 // binary32 q_g with its rounding bound; s~_g held in registers (NMAX >= nfit,
 // NMAX a multiple of 4), A staged in shared memory with rows padded to NMAX.
 template <int NMAX>
-__global__ void k_qvec32(const float* __restrict__ Sc32, const float4* __restrict__ gnorm, int64_t G, int64_t G_pad,
+__global__ void k_qvec32(GridSpec gs, const float4* __restrict__ gnorm, int64_t G, int64_t G_pad,
                          int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
                          const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb,
                          uint16_t* __restrict__ Qb3) {
@@ -703,8 +730,14 @@ __global__ void k_qvec32(const float* __restrict__ Sc32, const float4* __restric
         float qc = 0.0f, qb = 3.0e38f;
         if (g < G) {
             float s[NMAX];
+            if (gs.Sc32) {
 #pragma unroll
-            for (int j = 0; j < NMAX; ++j) s[j] = (j < nfit) ? Sc32[g * nfit + j] : 0.0f;
+                for (int j = 0; j < NMAX; ++j) s[j] = (j < nfit) ? gs.Sc32[g * nfit + j] : 0.0f;
+            } else {
+                const FitRow fr = fit_row(gs, g);
+#pragma unroll
+                for (int j = 0; j < NMAX; ++j) s[j] = (j < nfit) ? row_sc32(gs, fr, j) : 0.0f;
+            }
             float q = 0.0f;
 #pragma unroll
             for (int i = 0; i < NMAX; ++i) {
@@ -732,17 +765,22 @@ __global__ void k_qvec32(const float* __restrict__ Sc32, const float4* __restric
     }
 }
 
-__global__ void k_qvec32_generic(const float* __restrict__ Sc32, const float4* __restrict__ gnorm, int64_t G,
+__global__ void k_qvec32_generic(GridSpec gs, const float4* __restrict__ gnorm, int64_t G,
                                  int64_t G_pad, int nfit, const float* __restrict__ A32, const float* __restrict__ rho,
                                  const int32_t* __restrict__ slots, float* __restrict__ Qc, float* __restrict__ Qb,
                                  uint16_t* __restrict__ Qb3) {
     const int slot = slots[blockIdx.y];
     const float* A = A32 + (size_t)slot * nfit * nfit;
     const float r = rho[slot];
+    float sl[kMaxBins];  // the row, when it is recomputed rather than stored
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G_pad; g += (int64_t)gridDim.x * blockDim.x) {
         float qc = 0.0f, qb = 3.0e38f;
         if (g < G) {
-            const float* s = Sc32 + g * nfit;
+            const float* s = gs.Sc32 ? gs.Sc32 + g * nfit : sl;
+            if (!gs.Sc32) {
+                const FitRow fr = fit_row(gs, g);
+                for (int j = 0; j < nfit; ++j) sl[j] = row_sc32(gs, fr, j);
+            }
             float q = 0.0f;
             for (int i = 0; i < nfit; ++i) {
                 float t = 0.0f;
@@ -863,9 +901,8 @@ constexpr int kS64Threads = 128;
 
 __global__ void __launch_bounds__(kS64Threads) k_scan64(const int32_t* __restrict__ list, int64_t n,
                                                          const int32_t* __restrict__ uslot,
-                                                         const float* __restrict__ d, const double* __restrict__ centre,
-                                                         const double* __restrict__ Sc, int64_t G, int nfit,
-                                                         const double* __restrict__ A64,
+                                                         const float* __restrict__ d, GridSpec gs, int64_t G,
+                                                         int nfit, const double* __restrict__ A64,
                                                          const double* __restrict__ Q64, int64_t ldq,
                                                          int32_t* __restrict__ best) {
     extern __shared__ double2 sm64v[];
@@ -881,7 +918,7 @@ __global__ void __launch_bounds__(kS64Threads) k_scan64(const int32_t* __restric
     // d - v of the CTA's universes, [j][u] (in the tile buffer, free until the first tile)
     for (int e = tid; e < nfit * kS64U; e += kS64Threads) {
         const int j = e / kS64U, uu = e - (e / kS64U) * kS64U;
-        ss[e] = (uu < nu) ? (double)d[(size_t)list[u0 + uu] * nfit + j] - centre[j] : 0.0;
+        ss[e] = (uu < nu) ? (double)d[(size_t)list[u0 + uu] * nfit + j] - gs.centre[j] : 0.0;
     }
     __syncthreads();
     // y_r = sum_j A_rj (d - v)_j, one fma chain in j order
@@ -904,10 +941,23 @@ __global__ void __launch_bounds__(kS64Threads) k_scan64(const int32_t* __restric
     }
     for (int64_t g0 = 0; g0 < G; g0 += kS64G) {
         __syncthreads();  // y complete / the previous tile's readers done
-        for (int e = tid; e < kS64G * nfit; e += kS64Threads) {
-            const int gg = e / nfit, j = e - (e / nfit) * nfit;
-            const int64_t g = g0 + gg;
-            ss[j * kS64LdS + gg] = (g < G) ? Sc[g * nfit + j] : 0.0;
+        if (gs.Sc) {
+            for (int e = tid; e < kS64G * nfit; e += kS64Threads) {
+                const int gg = e / nfit, j = e - (e / nfit) * nfit;
+                const int64_t g = g0 + gg;
+                ss[j * kS64LdS + gg] = (g < G) ? gs.Sc[g * nfit + j] : 0.0;
+            }
+        } else {
+            // recomputed rows: one point per thread, decoded once
+            for (int gg = tid; gg < kS64G; gg += kS64Threads) {
+                const int64_t g = g0 + gg;
+                if (g < G) {
+                    const FitRow fr = fit_row(gs, g);
+                    for (int j = 0; j < nfit; ++j) ss[j * kS64LdS + gg] = row_sc(gs, fr, j);
+                } else {
+                    for (int j = 0; j < nfit; ++j) ss[j * kS64LdS + gg] = 0.0;
+                }
+            }
         }
         __syncthreads();
         double acc[4][2];
@@ -969,8 +1019,9 @@ __global__ void __launch_bounds__(kS64Threads) k_scan64(const int32_t* __restric
 // binary64 q-vectors.  Grid (universe, split): each CTA stages W of the
 // universe's covariance in shared memory and scans every split-th grid point;
 // k_scan_resid_reduce takes the first minimum over the splits.
+template <bool MODEL>
 __global__ void __launch_bounds__(256) k_scan_resid(const int32_t* __restrict__ list, const int32_t* __restrict__ uslot,
-                                                     const float* __restrict__ d, const float2* __restrict__ Sdf,
+                                                     const float* __restrict__ d, GridSpec gs,
                                                      int64_t G, int nfit, const float2* __restrict__ Wdf,
                                                      double* __restrict__ part_v, int32_t* __restrict__ part_g) {
     extern __shared__ float2 sWd[];
@@ -988,7 +1039,7 @@ __global__ void __launch_bounds__(256) k_scan_resid(const int32_t* __restrict__ 
     double bv = DBL_MAX;
     int32_t bg = INT32_MAX;
     for (int64_t g = (int64_t)sp * blockDim.x + threadIdx.x; g < G; g += (int64_t)nsp * blockDim.x) {
-        const double c = resid_df(W, nfit, Sdf + g * nfit, du);
+        const double c = resid_df(W, nfit, srow<MODEL>(gs, nullptr, g), du);
         if (c < bv) {
             bv = c;
             bg = (int32_t)g;
@@ -1140,7 +1191,7 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ quad_
                                                 const int32_t* __restrict__ tile_univ, const float* __restrict__ d,
                                                 const double* __restrict__ centre, int nfit, int K,
                                                 const float* __restrict__ A32, const float* __restrict__ rho,
-                                                const int32_t* __restrict__ cur, const float* __restrict__ Sc32,
+                                                const int32_t* __restrict__ cur, GridSpec gs,
                                                 const float4* __restrict__ gnorm, const float* __restrict__ Qc,
                                                 const float* __restrict__ Qb, int64_t G_pad,
                                                 uint16_t* __restrict__ Yt, float4* __restrict__ alpha,
@@ -1179,7 +1230,12 @@ __global__ void __launch_bounds__(kBM) k_yprep(const int32_t* __restrict__ quad_
         return;
     }
     const int q = cur[u];
-    const float* sq = Sc32 + (int64_t)q * nfit;
+    float sql[kMaxBins];  // the probe row, when it is recomputed rather than stored
+    const float* sq = gs.Sc32 ? gs.Sc32 + (int64_t)q * nfit : sql;
+    if (!gs.Sc32) {
+        const FitRow fr = fit_row(gs, q);
+        for (int j = 0; j < nfit; ++j) sql[j] = row_sc32(gs, fr, j);
+    }
 
     float dt[NR > 0 ? NR : kMaxBins];
     float dn2 = 0.0f;
@@ -1436,8 +1492,7 @@ __global__ void __launch_bounds__(kResidThreads, 6) k_resid_tiles(const ResolveA
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
             const int2 it = items[i];
             const int u = a.tile_univ[it.x];
-            const float2* sv = (it.y < 0) ? a.centre_df : a.Sdf + (int64_t)it.y * n;
-            res[i] = resid_mixed<NR>(W, n, sv, a.d + (size_t)u * n);
+            res[i] = resid_mixed<NR>(W, n, srow<false>(a.gs, a.centre_df, it.y), a.d + (size_t)u * n);
         }
     }
 }
@@ -1446,6 +1501,7 @@ __global__ void __launch_bounds__(kResidThreads, 6) k_resid_tiles(const ResolveA
 // item, grid-stride over the device count.  A row's items follow each other and
 // the rows of a tile quadrant share a slot, so a warp's lanes mostly read the
 // same W element at once.
+template <bool MODEL>
 __global__ void __launch_bounds__(256) k_resid_flat(const ResolveArgs a, const int2* __restrict__ items,
                                                     const int32_t* __restrict__ count, double* __restrict__ res) {
     const int n = a.nfit;
@@ -1454,8 +1510,7 @@ __global__ void __launch_bounds__(256) k_resid_flat(const ResolveArgs a, const i
         const int2 it = items[i];
         const int u = a.tile_univ[it.x];
         const float2* W = a.Wdf + (size_t)a.quad_slot[it.x / kQuadRows] * n * n;
-        const float2* sv = (it.y < 0) ? a.centre_df : a.Sdf + (int64_t)it.y * n;
-        res[i] = resid_df(W, n, sv, a.d + (size_t)u * n);
+        res[i] = resid_df(W, n, srow<MODEL>(a.gs, a.centre_df, it.y), a.d + (size_t)u * n);
     }
 }
 
@@ -1644,6 +1699,7 @@ __global__ void k_list_plan(ResolveArgs a, const int32_t* __restrict__ cand_coun
 // first minimum (lowest index among equal values) and publishes it.  The warp
 // that completes a row's last chunk takes the first minimum over the row's
 // chunks and finishes (dchi2) or advances the row.
+template <bool MODEL>
 __global__ void __launch_bounds__(256) k_list_chunks(ResolveArgs a, const int32_t* __restrict__ cand_count,
                                                      const int32_t* __restrict__ rows, ListPlan lp) {
     const int n = a.nfit;
@@ -1674,7 +1730,7 @@ __global__ void __launch_bounds__(256) k_list_chunks(ResolveArgs a, const int32_
         const int k = ck.y * kListChunk + lane;
         if (k < n0 + n1) {
             const int32_t g = a.cidx[(k < n0) ? base0 + k : base1 + (k - n0)];
-            bv = resid_df(W, n, a.Sdf + (int64_t)g * n, du);
+            bv = resid_df(W, n, srow<MODEL>(a.gs, nullptr, g), du);
             bg = g;
         }
         warp_argmin(bv, bg);
@@ -1709,7 +1765,7 @@ __global__ void __launch_bounds__(256) k_list_chunks(ResolveArgs a, const int32_
             double cp = 0.0;
             if (p != bg) {
                 // chi2_p in residual form (row dot products over the lanes, the bits of resid_df)
-                cp = resid_df_warp(W, n, a.Sdf + (int64_t)p * n, du, s_r[warp], s_t[warp], lane);
+                cp = resid_df_warp(W, n, srow<MODEL>(a.gs, nullptr, p), du, s_r[warp], s_t[warp], lane);
                 if (lane == 0 && a.n_resid) atomicAdd(a.n_resid, 1ull);
             }
             if (lane == 0) {
@@ -1747,11 +1803,11 @@ __global__ void k_min_tau(const int32_t* __restrict__ tile_univ, int64_t n_rows,
 
 // One warp per finishing universe: chi2_p and chi2_min in residual form under
 // the last scan's covariance (A = W^T W), dchi2 = chi2_p - chi2_min.
+template <bool MODEL>
 __global__ void __launch_bounds__(128) k_finish(const int32_t* __restrict__ list, int64_t n,
                                                  const int32_t* __restrict__ uslot, const int32_t* __restrict__ best,
-                                                 UniverseState us, const float* __restrict__ d,
-                                                 const double* __restrict__ Sfit, int nfit,
-                                                 const double* __restrict__ W64, const float2* __restrict__ Sdf,
+                                                 UniverseState us, const float* __restrict__ d, GridSpec gs,
+                                                 int nfit, const double* __restrict__ W64,
                                                  const float2* __restrict__ Wdf, double* __restrict__ dchi2,
                                                  double* __restrict__ chi2min) {
     __shared__ double rp[4][kMaxBins], rm[4][kMaxBins], tt[4][kMaxBins];
@@ -1768,13 +1824,14 @@ __global__ void __launch_bounds__(128) k_finish(const int32_t* __restrict__ list
     if (Wdf) {
         // mixed path: the double-float residual of every other mixed-path kernel
         const float2* W = Wdf + (size_t)slot * nfit * nfit;
-        cp = (p == g) ? 0.0 : resid_df_warp(W, nfit, Sdf + (int64_t)p * nfit, du, fr[w], ft[w], lane);
-        cm = resid_df_warp(W, nfit, Sdf + (int64_t)g * nfit, du, fr[w], ft[w], lane);
+        cp = (p == g) ? 0.0 : resid_df_warp(W, nfit, srow<MODEL>(gs, nullptr, p), du, fr[w], ft[w], lane);
+        cm = resid_df_warp(W, nfit, srow<MODEL>(gs, nullptr, g), du, fr[w], ft[w], lane);
     } else {
         // plain path: binary64, in the summation order of resid_chi2_warp
+        const FitRow rowp = fit_row(gs, p), rowg = fit_row(gs, g);
         for (int j = lane; j < nfit; j += 32) {
-            rp[w][j] = Sfit[(int64_t)p * nfit + j] - (double)du[j];
-            rm[w][j] = Sfit[(int64_t)g * nfit + j] - (double)du[j];
+            rp[w][j] = __dsub_rn(row_fit(gs, rowp, j), (double)du[j]);
+            rm[w][j] = __dsub_rn(row_fit(gs, rowg, j), (double)du[j]);
         }
         __syncwarp();
         const double* W = W64 + (size_t)slot * nfit * nfit;
@@ -1927,19 +1984,19 @@ void launch_collapse(const double* S, int64_t G, int nf, const int32_t* coll, in
     k_collapse<<<blocks_for(G, 128), 128, 0, st>>>(S, G, nf, coll, nfit, out);
 }
 
-void launch_centre(const double* S_fit, int64_t G, int nfit, double* centre, double*, cudaStream_t st) {
+void launch_centre(const GridSpec& gs, int64_t G, double* centre, cudaStream_t st) {
     count_launch();
-    k_centre<<<nfit, kThreads, 0, st>>>(S_fit, G, nfit, centre);
+    k_centre<<<gs.nfit, kThreads, 0, st>>>(gs, G, centre);
 }
 
-void launch_centred(const double* S_fit, const double* centre, int64_t G, int64_t G_pad, int nfit, int K,
-                    double* Sc, float* Sc32, float4* gnorm, uint16_t* Bt, cudaStream_t st) {
+void launch_centred(const GridSpec& gs, int64_t G, int64_t G_pad, int K, double* Sc, float* Sc32, float4* gnorm,
+                    uint16_t* Bt, cudaStream_t st) {
     cudaMemsetAsync(Bt, 0, (size_t)G_pad * 2 * K * sizeof(uint16_t), st);
     count_launch();
-    k_centred<<<blocks_for(G, 128), 128, 0, st>>>(S_fit, centre, G, nfit, K, Sc, Sc32, gnorm, Bt);
+    k_centred<<<blocks_for(G, 128), 128, 0, st>>>(gs, G, K, Sc, Sc32, gnorm, Bt);
 }
 
-void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps, int P, int gauss, double* L64,
+void launch_chol_sys(const FullSrc& src, int nf, const double* F, const int64_t* ps, int P, int gauss, double* L64,
                      float* L32, float* s32, double*, int* status, cudaStream_t st) {
     if (P <= 0) return;
     count_launch();
@@ -1947,10 +2004,10 @@ void launch_chol_sys(const double* S, int nf, const double* F, const int64_t* ps
     // the attribute belongs to the current device, so it is set at every launch (a cheap host call)
     cudaFuncSetAttribute(k_chol_sys, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kCholPackN * (kCholPackN + 1) / 2 * (int)sizeof(double));
-    k_chol_sys<<<P, 256, smem, st>>>(S, nf, F, ps, gauss, L64, L32, s32, status);
+    k_chol_sys<<<P, 256, smem, st>>>(src, nf, F, ps, gauss, L64, L32, s32, status);
 }
 
-void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, const double* F, const int32_t* q_list,
+void launch_build_cov(const FullSrc& src, int nf, int nfit, const int32_t* coll, const double* F, const int32_t* q_list,
                       const int32_t* slot_list, int n, int cov_mode, double* A64, double* W64, float* A32,
                       float* rho, double* work, int* status, cudaStream_t st) {
     if (n <= 0) return;
@@ -1958,29 +2015,29 @@ void launch_build_cov(const double* S, int nf, int nfit, const int32_t* coll, co
     const size_t smem = nfit <= kResolveMaxN ? 2 * (size_t)nfit * nfit * sizeof(double) : 0;
     cudaFuncSetAttribute(k_build_cov, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          2 * kResolveMaxN * kResolveMaxN * (int)sizeof(double));
-    k_build_cov<<<n, 256, smem, st>>>(S, nf, nfit, coll, F, q_list, slot_list, cov_mode, A64, W64, A32, rho, work,
-                                      status);
+    k_build_cov<<<n, 256, smem, st>>>(src, nf, nfit, coll, F, q_list, slot_list, cov_mode, A64, W64, A32, rho,
+                                      work, status);
 }
 
-void launch_qvec64(const double* Sc, int64_t G, int nfit, const double* W64, const int32_t* slots, int n,
+void launch_qvec64(const GridSpec& gs, int64_t G, int nfit, const double* W64, const int32_t* slots, int n,
                    int64_t ldq, double* Q64, cudaStream_t st) {
     // blockIdx.y is the slot within a launch: chunks of at most gridDim.y's limit
     for (int s0 = 0; s0 < n; s0 += 65535) {
         const int ns = n - s0 < 65535 ? n - s0 : 65535;
         dim3 grid(blocks_for(G, 128) < 64 ? blocks_for(G, 128) : 64, ns);
         count_launch();
-        k_qvec64<<<grid, 128, 0, st>>>(Sc, G, nfit, W64, slots + s0, ldq, Q64);
+        k_qvec64<<<grid, 128, 0, st>>>(gs, G, nfit, W64, slots + s0, ldq, Q64);
     }
 }
 
-void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
+void launch_qvec32(const GridSpec& gs, const float4* gnorm, int64_t G, int64_t G_pad, int nfit, const float* A32,
                    const float* rho, const int32_t* slots, int n, float* Qc, float* Qb, uint16_t* Qb3,
                    cudaStream_t st) {
     if (n <= 0) return;
     if (n > 65535) {
         // blockIdx.y is the slot within a launch: chunks of at most gridDim.y's limit
         for (int s0 = 0; s0 < n; s0 += 65535)
-            launch_qvec32(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots + s0, n - s0 < 65535 ? n - s0 : 65535, Qc, Qb,
+            launch_qvec32(gs, gnorm, G, G_pad, nfit, A32, rho, slots + s0, n - s0 < 65535 ? n - s0 : 65535, Qc, Qb,
                           Qb3, st);
         return;
     }
@@ -1990,15 +2047,15 @@ void launch_qvec32(const float* Sc32, const float4* gnorm, int64_t G, int64_t G_
     dim3 grid(gx, n);
     count_launch();
     if (nfit <= 16)
-        k_qvec32<16><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<16><<<grid, 128, 0, st>>>(gs, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 32)
-        k_qvec32<32><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<32><<<grid, 128, 0, st>>>(gs, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 48)
-        k_qvec32<48><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<48><<<grid, 128, 0, st>>>(gs, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else if (nfit <= 64)
-        k_qvec32<64><<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32<64><<<grid, 128, 0, st>>>(gs, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
     else
-        k_qvec32_generic<<<grid, 128, 0, st>>>(Sc32, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
+        k_qvec32_generic<<<grid, 128, 0, st>>>(gs, gnorm, G, G_pad, nfit, A32, rho, slots, Qc, Qb, Qb3);
 }
 
 void launch_fake_data(const float* L32, const float* s32, int nf, const int32_t* coll, int nfit, const int64_t* ps,
@@ -2056,25 +2113,28 @@ void launch_set_slots(const int32_t* q, const int32_t* s, int n, int32_t* slot_o
     k_set_slots<<<blocks_for(n), kThreads, 0, st>>>(q, s, n, slot_of);
 }
 
-void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const double* centre,
-                   const double* Sc, int64_t G, int nfit, const double* A64, const double* Q64, int64_t ldq,
-                   int32_t* best, cudaStream_t st) {
+void launch_scan64(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const GridSpec& gs,
+                   int64_t G, int nfit, const double* A64, const double* Q64, int64_t ldq, int32_t* best,
+                   cudaStream_t st) {
     if (n <= 0) return;
     const size_t smem = (size_t)nfit * (kS64U + kS64LdS) * sizeof(double);
     cudaFuncSetAttribute(k_scan64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    k_scan64<<<(unsigned)((n + kS64U - 1) / kS64U), kS64Threads, smem, st>>>(list, n, uslot, d, centre, Sc, G, nfit,
-                                                                            A64, Q64, ldq, best);
+    k_scan64<<<(unsigned)((n + kS64U - 1) / kS64U), kS64Threads, smem, st>>>(list, n, uslot, d, gs, G, nfit, A64,
+                                                                            Q64, ldq, best);
 }
 
-void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const float2* Sdf,
+void launch_scan_resid(const int32_t* list, int64_t n, const int32_t* uslot, const float* d, const GridSpec& gs,
                        int64_t G, int nfit, const float2* Wdf, double* part_v, int32_t* part_g, int nsp,
                        int32_t* best, cudaStream_t st) {
     if (n <= 0) return;
     const size_t smem = nfit <= kResolveMaxN ? (size_t)nfit * nfit * sizeof(float2) : 0;
     count_launch(2);
-    k_scan_resid<<<dim3((unsigned)n, (unsigned)nsp), 256, smem, st>>>(list, uslot, d, Sdf, G, nfit, Wdf, part_v,
-                                                                      part_g);
+    const dim3 grid((unsigned)n, (unsigned)nsp);
+    if (gs.Sdf)
+        k_scan_resid<false><<<grid, 256, smem, st>>>(list, uslot, d, gs, G, nfit, Wdf, part_v, part_g);
+    else
+        k_scan_resid<true><<<grid, 256, smem, st>>>(list, uslot, d, gs, G, nfit, Wdf, part_v, part_g);
     k_scan_resid_reduce<<<blocks_for(n), kThreads, 0, st>>>(list, n, nsp, part_v, part_g, best);
 }
 
@@ -2100,7 +2160,7 @@ void launch_group(const int32_t* active, int64_t n, const int32_t* uslot, int n_
 
 void launch_yprep(const int32_t* quad_slot, const int32_t* tile_univ, int64_t n_tiles, const float* d,
                   const double* centre, int nfit, int K, const float* A32, const float* rho, const int32_t* cur,
-                  const float* Sc32, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
+                  const GridSpec& gs, const float4* gnorm, const float* Qc, const float* Qb, int64_t G_pad,
                   uint16_t* Yt, float4* alpha, float* tau0, int32_t* tile_j0, cudaStream_t st) {
     if (n_tiles <= 0) return;
     // the A of every quadrant's slot up to N_fit = 64 (64 KB); beyond, the tile's first slot
@@ -2109,7 +2169,7 @@ void launch_yprep(const int32_t* quad_slot, const int32_t* tile_univ, int64_t n_
     auto kern = nfit <= 48 ? k_yprep<48> : k_yprep<0>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    kern<<<(unsigned)n_tiles, kBM, smem, st>>>(quad_slot, tile_univ, d, centre, nfit, K, A32, rho, cur, Sc32, gnorm, Qc,
+    kern<<<(unsigned)n_tiles, kBM, smem, st>>>(quad_slot, tile_univ, d, centre, nfit, K, A32, rho, cur, gs, gnorm, Qc,
                                                Qb, G_pad, Yt, alpha, tau0, tile_j0, stage_all);
 }
 
@@ -2151,7 +2211,11 @@ void launch_resolve_list(const ResolveArgs& a, const int32_t* cand_count, int64_
     // eight warps a CTA, grid-stride over the chunks the plan reserved
     const int64_t want = (lp.max_chunks + 7) / 8, cap = (int64_t)a.n_sm * 8;
     count_launch();
-    k_list_chunks<<<(unsigned)std::max<int64_t>(1, std::min(want, cap)), 256, 0, st>>>(a, cand_count, rows, lp);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, cap));
+    if (a.gs.Sdf)
+        k_list_chunks<false><<<grid, 256, 0, st>>>(a, cand_count, rows, lp);
+    else
+        k_list_chunks<true><<<grid, 256, 0, st>>>(a, cand_count, rows, lp);
 }
 
 void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
@@ -2161,9 +2225,13 @@ void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
     const unsigned g3 = (unsigned)std::min<int64_t>(n_tiles, (int64_t)a.n_sm * 8);
     const size_t smem = (a.nfit <= 64 ? (size_t)a.nfit * a.nfit : 0) * sizeof(float2);
     auto resid = [&](const int2* items, const int2* tile_items, const int32_t* count, int64_t max_items, double* res) {
-        if (a.nfit > 64) {
+        if (a.nfit > 64 || !a.gs.Sdf) {  // recomputed rows: the flat form for every N_fit
             const int64_t want = (max_items + 255) / 256, cap = (int64_t)a.n_sm * 4;
-            k_resid_flat<<<(unsigned)std::max<int64_t>(1, std::min(want, cap)), 256, 0, st>>>(a, items, count, res);
+            const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, cap));
+            if (a.gs.Sdf)
+                k_resid_flat<false><<<grid, 256, 0, st>>>(a, items, count, res);
+            else
+                k_resid_flat<true><<<grid, 256, 0, st>>>(a, items, count, res);
             return;
         }
         auto run = [&](auto kern) {
@@ -2188,12 +2256,15 @@ void launch_resolve(const ResolveArgs& a, int64_t n_tiles, cudaStream_t st) {
 }
 
 void launch_finish(const int32_t* list, int64_t n, const int32_t* uslot, const int32_t* best, const UniverseState& us,
-                   const float* d, const double* Sfit, int nfit, const double* W64, const float2* Sdf,
-                   const float2* Wdf, double* dchi2, double* chi2min, cudaStream_t st) {
+                   const float* d, const GridSpec& gs, int nfit, const double* W64, const float2* Wdf, double* dchi2,
+                   double* chi2min, cudaStream_t st) {
     if (n <= 0) return;
     count_launch();
-    k_finish<<<(unsigned)((n + 3) / 4), 128, 0, st>>>(list, n, uslot, best, us, d, Sfit, nfit, W64, Sdf, Wdf, dchi2,
-                                                       chi2min);
+    const unsigned grid = (unsigned)((n + 3) / 4);
+    if (gs.Sdf || !Wdf)
+        k_finish<false><<<grid, 128, 0, st>>>(list, n, uslot, best, us, d, gs, nfit, W64, Wdf, dchi2, chi2min);
+    else
+        k_finish<true><<<grid, 128, 0, st>>>(list, n, uslot, best, us, d, gs, nfit, W64, Wdf, dchi2, chi2min);
 }
 
 void launch_wdf(const double* W64, const int32_t* slots, int n, int nfit, float2* Wdf, cudaStream_t st) {
@@ -2221,15 +2292,18 @@ void launch_count_below(const double* x, int rows, int n, const double* thr, int
     k_count_below<<<rows, 256, 0, st>>>(x, n, thr, counts);
 }
 
-void launch_osc_spectra(int64_t G, int nf, int D, const int32_t* axis_len, const int32_t* axis_off,
-                        const double* axis_val, int n_terms, const int32_t* amp_ax, const int32_t* dm2_ax,
-                        const double* b, const double* f, const double* L, const double* E, double* S, int* bad,
-                        cudaStream_t st) {
-    const int64_t n = G * nf;
+void launch_osc_sin(const SpecModel& m, int rows, const double* L, const double* E, double* sinT, cudaStream_t st) {
+    const int64_t n = (int64_t)rows * m.nf;
     if (n <= 0) return;
     count_launch();
-    k_osc_spectra<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, nf, D, axis_len, axis_off, axis_val, n_terms, amp_ax,
-                                                                dm2_ax, b, f, L, E, S, bad);
+    k_osc_sin<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, rows, L, E, sinT);
+}
+
+void launch_osc_spectra(const SpecModel& m, int64_t G, double* S, int* bad, cudaStream_t st) {
+    const int64_t n = G * m.nf;
+    if (n <= 0) return;
+    count_launch();
+    k_osc_spectra<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, G, S, bad);
 }
 
 void launch_quantiles(double* x, int rows, int n, const double* probs, int nq, double* out, cudaStream_t st) {

@@ -130,7 +130,7 @@ fc_status fc_fake_data_noalloc(const double* S, int64_t G, int32_t N_full, const
     if (h & fcdev::kDevBadIndex) return noalloc_fail(FC_ERR_ARG, "true point index out of range");
     if (h & kDevBadCollapse)
         return noalloc_fail(FC_ERR_ARG, "collapse map entry out of [0, N_fit) or a fit bin left empty");
-    fcdev::launch_chol_sys(S, N_full, F, ps, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr, status, st);
+    fcdev::launch_chol_sys(fcdev::FullSrc{S, {}}, N_full, F, ps, P, fluct == FC_FLUCT_GAUSS, L64, L32, s32, nullptr, status, st);
     if (!launched()) return FC_ERR_CUDA;
     fcdev::launch_fake_data(L32, s32, N_full, collapse, N_fit, ps, P, U, seed, fluct == FC_FLUCT_GAUSS, d, st);
     if (!launched()) return FC_ERR_CUDA;

@@ -33,6 +33,7 @@
 #include <cstdint>
 
 #include "fc_internal.cuh"
+#include "fc_spec.cuh"
 #include "fc_tc.cuh"
 
 namespace fcdev {
@@ -133,7 +134,7 @@ struct ProbeArgs {
     const float* Qb;
     const float4* gnorm;
     const float4* alpha;
-    const float* Sc32;
+    GridSpec gs;  // the probe rows s~_g (binary32)
     int nfit;
 };
 
@@ -186,14 +187,15 @@ __device__ float probe_upper_bound(const uint16_t* __restrict__ Yt, int64_t item
                                    int64_t G_pad, const ProbeArgs& pa) {
     const int n = pa.nfit;
     const int K = screen_k(n);
-    const float* sg = pa.Sc32 + (int64_t)g * n;
+    const FitRow fr = fit_row(pa.gs, g);
     float dot = 0.0f, adot = 0.0f;
     for (int i = 0; i < n; ++i) {
         const float h = __uint_as_float((uint32_t)Yt[ytile_elem(item, row, i, K)] << 16);
         const float l = __uint_as_float((uint32_t)Yt[ytile_elem(item, row, K + i, K)] << 16);
         const float y = h + l;
-        dot = fmaf(y, sg[i], dot);
-        adot = fmaf(fabsf(y), fabsf(sg[i]), adot);
+        const float sgi = row_sc32(pa.gs, fr, i);
+        dot = fmaf(y, sgi, dot);
+        adot = fmaf(fabsf(y), fabsf(sgi), adot);
     }
     const int64_t qi = (int64_t)slot * G_pad + g;
     const float qc = pa.Qc[qi];
@@ -691,12 +693,12 @@ bool screen_config_ok(int K, int stages, int ybuf) {
 bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16_t* Yt, const uint16_t* Bt,
                    const uint16_t* Qb3, const int32_t* quad_slot, float* tau0, const int32_t* tile_j0,
                    int64_t n_tiles, int64_t G, int64_t G_pad, float* cv, int32_t* ci, int32_t* cc, int* status,
-                   const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const float* Sc32,
+                   const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const GridSpec& gs,
                    int nfit, const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
     if (!screen_config_ok(K, stages, ybuf) || (topk != 8 && topk != 16)) return false;
     const ScreenLayout lay = choose_layout(K, stages, ybuf);
-    const ProbeArgs pa{Qc, Qb, gnorm, alpha, Sc32, nfit};
+    const ProbeArgs pa{Qc, Qb, gnorm, alpha, gs, nfit};
 #define FC_SCREEN_RUN(TT, MM, CC) \
     run_screen<TT, MM, CC>(lay, Yt, Bt, Qb3, quad_slot, tau0, tile_j0, n_tiles, G, G_pad, cv, ci, cc, status, pa, la, \
                            wt, n_sm, st)

@@ -341,6 +341,74 @@ def test_device_generated_grid(fc, ctx, w2):
         assert e.value.status == fc.FC_ERR_ARG
 
 
+def _osc_case(case):
+    """(model arrays, collapse, N_fit, host spectra [G][N_full], true points) of a recompute case."""
+    if case == "d2_pairs":
+        # the 100 x 100 grid behind cfg2: one term, N 90 -> 45 pairwise (fit bins sum two model bins)
+        m2 = workloads.osc_2d_model(100, 100, 90, seed=0)
+        m = dict(axes=[m2["dm2"], m2["s2t"]], terms=[(1, 0)], b=m2["b"], f=m2["f"][None, :], L=m2["L"], E=m2["E"],
+                 F=m2["F"])
+        S = workloads.osc_2d(100, 100, 90, seed=0)[0]
+        return m, workloads.pair_collapse(90), 45, S, np.array([0, 1234, 5050, 7777, 9999], np.int64)
+    # D = 4, two terms, N = 70 (K = 80: the residuals of the flat path, q-vectors in K slices)
+    m = workloads.osc_terms_model(6, 2, 70, seed=21)
+    S = m["rows"](np.arange(m["G"]))
+    return m, None, 70, S, np.array([7, 300, 777, 1295], np.int64)
+
+
+def _load_osc(fc, ctx, m, coll, n_fit, recompute):
+    g = fc.fc_load_grid_osc(ctx, m["axes"], m["terms"], m["b"], m["f"], m["L"], m["E"], coll, n_fit,
+                            recompute=recompute)
+    fc.fc_set_frac_cov(ctx, g, m["F"])
+    return g
+
+
+@pytest.mark.parametrize("case", ["d2_pairs", "d4_n70"])
+def test_recomputed_grid(fc, ctx, case):
+    """A grid kept as its shape model (FC_GRID_RECOMPUTE: no spectra stored, every row evaluated
+    from the model where a kernel reads it, the paper's no-caching choice) gives the stored
+    grid's outputs bit for bit on the mixed, plain, list-first, fixed-covariance and fake-data
+    paths; both agree with the oracle run on the host's spectra; and it holds a fraction of the
+    stored grid's device memory."""
+    m, coll, n_fit, S, pts = _osc_case(case)
+    b0 = fc.fc_get_stats(ctx)["device_bytes"]
+    gs = _load_osc(fc, ctx, m, coll, n_fit, False)
+    b1 = fc.fc_get_stats(ctx)["device_bytes"]
+    gr = _load_osc(fc, ctx, m, coll, n_fit, True)
+    b2 = fc.fc_get_stats(ctx)["device_bytes"]
+    stored, kept = b1 - b0, b2 - b1
+    nf = S.shape[1]
+    K = ((n_fit + 3 + 15) // 16) * 16
+    # stored: S_full, S_fit, Sc (f64), Sdf (2 x f32), Sc32 per point; both: the bf16 image and norms
+    assert stored >= S.shape[0] * (8 * nf + 28 * n_fit), (stored, kept)
+    assert kept <= S.shape[0] * (4 * K + 16) + (1 << 20), (stored, kept)
+    U, seed = 96, 5
+    runs = [("mixed", None, {}), ("plain", dict(precision=fc.FC_PREC_FP64), {}),
+            ("list first", None, dict(first_round=fc.FC_ROUND_LIST)), ("fixed covariance", dict(cov=fc.FC_COV_FIXED), {})]
+    for label, opts, tuning in runs:
+        for g in (gs, gr):
+            fc.fc_set_tuning(ctx, g, **tuning)
+        a = fc.fc_run_points(ctx, gs, pts, seed, U, opts)
+        r = fc.fc_run_points(ctx, gr, pts, seed, U, opts)
+        for x, y in zip(a, r):
+            np.testing.assert_array_equal(x, y, err_msg=f"{case}: {label}")
+    for g in (gs, gr):
+        fc.fc_set_tuning(ctx, g)
+    np.testing.assert_array_equal(fc.fc_fake_data(ctx, gs, pts, 3, 32, n_fit),
+                                  fc.fc_fake_data(ctx, gr, pts, 3, 32, n_fit))
+    # the recomputed grid against the oracle on the host's spectra (numpy's sine may differ from the
+    # device's in the last bits, hence the contract's tolerances rather than bit equality)
+    d, b, n = fc.fc_run_points(ctx, gr, pts, seed, U)
+    od, ob, on = oracle.run_points(S, m["F"], pts, seed, U, collapse=coll, n_fit=n_fit)
+    w = workloads.Workload(f"osc_{case}", S, m["F"], coll, n_fit, pts, U, 5, seed)
+    _parity.check_grid(fc, ctx, gr, w, pts, seed, d, b, n, od, ob, on, label=f"recomputed {case}")
+    fc.fc_unload_grid(ctx, gs)
+    fc.fc_unload_grid(ctx, gr)
+    with pytest.raises(fc.FCError) as e:
+        fc.fc_load_grid_osc(ctx, m["axes"], m["terms"], m["b"], m["f"], m["L"], m["E"], coll, n_fit, flags=2)
+    assert e.value.status == fc.FC_ERR_ARG
+
+
 def _adaptive_reference(w, pts, data_dchi2, cl, U0, U_max, z, seed):
     """The adaptive acceptance rule restated on the oracle's universes: round r draws
     U0, then as many universes as a still-open point has (key seed + r), counts those

@@ -265,6 +265,39 @@ def cfg5(n_axis: int = 16, n_points: int = 256, U: int = 16) -> Workload:
     return Workload("cfg5_d6_16pow6_n64", S, F, None, n, pts, U, 5, 0, (amp, dm2))
 
 
+def osc_terms_model(n_axis: int, n_terms: int, n_full: int, seed: int, amp_hi: float = 0.1) -> dict:
+    """A 2 n_terms-axis shape model: axes (A_1, dm2_1, ..., A_T, dm2_T), each with
+    n_axis points (A_t linear over [0, amp_hi], dm2_t log-spaced over [1e-2, 1e2]),
+    s_i = b_i + sum_t A_t sin^2(1.27 dm2_t L_i / E_i) f_ti, the terms added in
+    order t = 0, 1, ....  Draw order from default_rng(seed): b, f [T][N], then
+    the fractional covariance, then L.  Returns the model arrays (the form
+    fc_load_grid_osc takes) and a function that evaluates the rows of a list of
+    grid points on the host."""
+    rng = np.random.default_rng(seed)
+    n = n_full
+    b = rng.uniform(50.0, 500.0, n)
+    f = rng.uniform(5.0, 50.0, (n_terms, n))
+    F, _ = _frac_cov(rng, n)
+    L = rng.choice(np.array([110.0, 470.0, 600.0]), n)
+    E = np.linspace(0.2, 3.0, n)
+    amp = np.linspace(0.0, amp_hi, n_axis)
+    dm2 = np.logspace(-2, 2, n_axis)
+    axes = [amp, dm2] * n_terms
+    terms = [(2 * t, 2 * t + 1) for t in range(n_terms)]
+    osc = np.sin(1.27 * dm2[:, None] * L[None, :] / E[None, :]) ** 2      # [n_axis, n]
+
+    def rows(g):
+        g = np.asarray(g, np.int64)
+        idx = np.stack(np.unravel_index(g, (n_axis,) * (2 * n_terms)), -1)
+        s = np.repeat(b[None, :], len(g), 0)
+        for t in range(n_terms):
+            s = s + (amp[idx[:, 2 * t]][:, None] * osc[idx[:, 2 * t + 1]]) * f[t]
+        return s
+
+    return {"axes": axes, "terms": terms, "b": b, "f": f, "L": L, "E": E, "F": F, "G": n_axis ** (2 * n_terms),
+            "rows": rows}
+
+
 def linear_gauss(n_axis: int = 121, n: int = 12, half_width: float = 6.0, seed: int = 3, U: int = 10000):
     """Linear signal model s(theta) = s0 + J theta (D=2) on a grid of +-half_width sigma.
 
