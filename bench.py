@@ -278,6 +278,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _cfg5(workloads, args):
+    """cfg5's workload: host spectra (stored grid), or its shape model when the grid is recomputed."""
+    if args.recompute:
+        return workloads.cfg5_model(U=args.universes or 16)
+    return workloads.cfg5(U=args.universes or 16)
+
+
+def _load_grid(fc, ctx, w):
+    """A workload's grid: from its host spectra, or recomputed from its shape model (S is None)."""
+    if w.S is None:
+        m = w.meta["model"]
+        return fc.fc_load_grid_osc(ctx, m["axes"], m["terms"], m["b"], m["f"], m["L"], m["E"], w.collapse, w.n_fit,
+                                   recompute=True)
+    return fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -295,10 +311,11 @@ def run_native(args):
                 f"universes, <= {w.max_iter} scans, top-{args.top_k}")
         l2 = "working set per step > L2 (screen B image 134 MB, q-vectors 6.3 MB per covariance)"
     elif args.config == "cfg5":
-        w = workloads.cfg5(U=args.universes or 16)
+        w = _cfg5(workloads, args)
         pts = w.points if args.points is None else w.points[np.linspace(0, len(w.points) - 1, args.points).astype(int)]
         desc = (f"cfg5: D=6 16^6 grid (16777216 points), N=64, {len(pts)} seeded true points x {w.U} universes "
-                f"(one batch of {len(pts) * w.U}), <= {w.max_iter} scans, top-{args.top_k}")
+                f"(one batch of {len(pts) * w.U}), <= {w.max_iter} scans, top-{args.top_k}"
+                + (", spectra recomputed from the shape model (none stored)" if args.recompute else ""))
         l2 = "working set per step > L2 (screen B image 4.3 GB, q-vectors 0.4 GB per covariance)"
     else:
         w = workloads.cfg2(U=args.universes or 1000)
@@ -312,7 +329,9 @@ def run_native(args):
     n = P * U
     stream = torch.cuda.Stream()
     ctx = fc.fc_create(local_rank, 0, stream.cuda_stream)
-    gid = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+    bytes0 = fc.fc_get_stats(ctx)["device_bytes"]
+    gid = _load_grid(fc, ctx, w)
+    grid_bytes = fc.fc_get_stats(ctx)["device_bytes"] - bytes0
     fc.fc_set_frac_cov(ctx, gid, w.F)
     # kernel choices and tile shape (rows per covariance slot) picked by the library's autotuner
     tuning = fc.fc_autotune(ctx, gid)
@@ -438,7 +457,7 @@ def run_native(args):
             extras["cfg4_below_saturation"] = _cfg4_below_saturation(fc, local_rank, args.serve_rate_low,
                                                                        args.serve_seconds_low, args.serve_drain)
         cpu = None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and w.S is not None:  # the oracle scans host spectra
             cpu = _oracle_sample(w, args.cpu_seconds, len(os.sched_getaffinity(0)))
         clocks = clk.summary()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -450,7 +469,7 @@ def run_native(args):
                            "global_batch": n * ws, "true_points": P, "universes_per_point": U,
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "covariance_cache": "cold every step", "autotuned": tuning,
-                           "l2": l2},
+                           "grid_device_bytes": grid_bytes, "l2": l2},
                 "universes_per_s": univ / (ms / 1e3),
                 "plain_fp64_gpu": plain,
                 "stage_ms_per_step": stage,
@@ -640,13 +659,13 @@ def run_once(args):
 
     fc.load()
     if args.config in ("cfg3", "cfg5"):
-        w = workloads.cfg3(U=args.universes or 500) if args.config == "cfg3" else workloads.cfg5(U=args.universes or 16)
+        w = workloads.cfg3(U=args.universes or 500) if args.config == "cfg3" else _cfg5(workloads, args)
         pts = w.points if args.points is None else w.points[np.linspace(0, len(w.points) - 1, args.points).astype(int)]
     else:
         w = workloads.cfg2(U=args.universes or 1000)
         pts = np.linspace(0, w.G - 1, args.points).round().astype(np.int64) if args.points else w.points
     ctx = fc.fc_create(0)
-    gid = fc.fc_load_grid(ctx, w.S, w.collapse, w.n_fit)
+    gid = _load_grid(fc, ctx, w)
     fc.fc_set_frac_cov(ctx, gid, w.F)
     fc.fc_run_points(ctx, gid, pts, 1, w.U, dict(precision=args.precision, top_k=args.top_k))
     print(json.dumps({"once": {"points": int(len(pts)), "universes": w.U, **fc.fc_get_stats(ctx)}}), flush=True)
@@ -677,6 +696,8 @@ def main():
     ap.add_argument("--serve-seconds-low", type=float, default=15.0, help="arrival window below saturation")
     ap.add_argument("--serve-rate-low", type=float, default=1.5,
                     help="offered jobs/s of the default line's below-saturation cfg4 stream")
+    ap.add_argument("--recompute", action="store_true",
+                    help="cfg5: keep the grid as its shape model (no spectra stored; FC_GRID_RECOMPUTE)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the cfg3 step and the cfg4 below-saturation stream of the default line")
     ap.add_argument("--serve-drain", type=float, default=240.0, help="seconds after a window before cancelling")

@@ -52,7 +52,7 @@ class Workload:
 
     @property
     def G(self) -> int:
-        return int(self.S.shape[0])
+        return int(self.S.shape[0]) if self.S is not None else int(self.meta["model"]["G"])
 
     @property
     def n_full(self) -> int:
@@ -296,6 +296,21 @@ def osc_terms_model(n_axis: int, n_terms: int, n_full: int, seed: int, amp_hi: f
 
     return {"axes": axes, "terms": terms, "b": b, "f": f, "L": L, "E": E, "F": F, "G": n_axis ** (2 * n_terms),
             "rows": rows}
+
+
+def cfg5_model(n_axis: int = 16, n_points: int = 256, U: int = 16) -> Workload:
+    """cfg5 as its shape model (no host spectra): the same draws as cfg5 (b, f, F, L
+    from default_rng(0), then the true points), so its grid is cfg5's up to the
+    summation order of the three terms.  S is None; meta["model"] holds the
+    arrays fc_load_grid_osc takes."""
+    m = osc_terms_model(n_axis, 3, 64, seed=0)
+    rng = np.random.default_rng(0)
+    rng.uniform(50.0, 500.0, 64)
+    rng.uniform(5.0, 50.0, (3, 64))
+    _frac_cov(rng, 64)
+    rng.choice(np.array([110.0, 470.0, 600.0]), 64)
+    pts = np.sort(rng.choice(m["G"], n_points, replace=False)).astype(np.int64)
+    return Workload("cfg5_d6_16pow6_n64_model", None, m["F"], None, 64, pts, U, 5, 0, (), meta={"model": m})
 
 
 def linear_gauss(n_axis: int = 121, n: int = 12, half_width: float = 6.0, seed: int = 3, U: int = 10000):
