@@ -56,7 +56,7 @@ class Workload:
 
     @property
     def n_full(self) -> int:
-        return int(self.S.shape[1])
+        return int(self.S.shape[1]) if self.S is not None else int(len(self.meta["model"]["b"]))
 
 
 def digest(*arrays) -> str:
