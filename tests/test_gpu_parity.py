@@ -350,6 +350,10 @@ def _osc_case(case):
                  F=m2["F"])
         S = workloads.osc_2d(100, 100, 90, seed=0)[0]
         return m, workloads.pair_collapse(90), 45, S, np.array([0, 1234, 5050, 7777, 9999], np.int64)
+    if case == "d6_3terms":
+        # the shape of cfg5 at 8 points per axis: D = 6, three terms, N = 64 (K = 80), 262 144 points
+        m = workloads.osc_terms_model(8, 3, 64, seed=5)
+        return m, None, 64, None, np.array([11, 99_999, 262_143], np.int64)
     # D = 4, two terms, N = 70 (K = 80: the residuals of the flat path, q-vectors in K slices)
     m = workloads.osc_terms_model(6, 2, 70, seed=21)
     S = m["rows"](np.arange(m["G"]))
@@ -363,7 +367,7 @@ def _load_osc(fc, ctx, m, coll, n_fit, recompute):
     return g
 
 
-@pytest.mark.parametrize("case", ["d2_pairs", "d4_n70"])
+@pytest.mark.parametrize("case", ["d2_pairs", "d4_n70", "d6_3terms"])
 def test_recomputed_grid(fc, ctx, case):
     """A grid kept as its shape model (FC_GRID_RECOMPUTE: no spectra stored, every row evaluated
     from the model where a kernel reads it, the paper's no-caching choice) gives the stored
@@ -377,12 +381,12 @@ def test_recomputed_grid(fc, ctx, case):
     gr = _load_osc(fc, ctx, m, coll, n_fit, True)
     b2 = fc.fc_get_stats(ctx)["device_bytes"]
     stored, kept = b1 - b0, b2 - b1
-    nf = S.shape[1]
+    nf, G = len(m["b"]), int(m["G"]) if "G" in m else S.shape[0]
     K = ((n_fit + 3 + 15) // 16) * 16
     # stored: S_full, S_fit, Sc (f64), Sdf (2 x f32), Sc32 per point; both: the bf16 image and norms
-    assert stored >= S.shape[0] * (8 * nf + 28 * n_fit), (stored, kept)
-    assert kept <= S.shape[0] * (4 * K + 16) + (1 << 20), (stored, kept)
-    U, seed = 96, 5
+    assert stored >= G * (8 * nf + 28 * n_fit), (stored, kept)
+    assert kept <= G * (4 * K + 16) + (1 << 20), (stored, kept)
+    U, seed = (96, 5) if S is not None else (16, 5)
     runs = [("mixed", None, {}), ("plain", dict(precision=fc.FC_PREC_FP64), {}),
             ("list first", None, dict(first_round=fc.FC_ROUND_LIST)), ("fixed covariance", dict(cov=fc.FC_COV_FIXED), {})]
     for label, opts, tuning in runs:
@@ -397,11 +401,13 @@ def test_recomputed_grid(fc, ctx, case):
     np.testing.assert_array_equal(fc.fc_fake_data(ctx, gs, pts, 3, 32, n_fit),
                                   fc.fc_fake_data(ctx, gr, pts, 3, 32, n_fit))
     # the recomputed grid against the oracle on the host's spectra (numpy's sine may differ from the
-    # device's in the last bits, hence the contract's tolerances rather than bit equality)
-    d, b, n = fc.fc_run_points(ctx, gr, pts, seed, U)
-    od, ob, on = oracle.run_points(S, m["F"], pts, seed, U, collapse=coll, n_fit=n_fit)
-    w = workloads.Workload(f"osc_{case}", S, m["F"], coll, n_fit, pts, U, 5, seed)
-    _parity.check_grid(fc, ctx, gr, w, pts, seed, d, b, n, od, ob, on, label=f"recomputed {case}")
+    # device's in the last bits, hence the contract's tolerances rather than bit equality); the
+    # 262 144-point case is held to the stored grid only (the oracle's full scans take minutes there)
+    if S is not None:
+        d, b, n = fc.fc_run_points(ctx, gr, pts, seed, U)
+        od, ob, on = oracle.run_points(S, m["F"], pts, seed, U, collapse=coll, n_fit=n_fit)
+        w = workloads.Workload(f"osc_{case}", S, m["F"], coll, n_fit, pts, U, 5, seed)
+        _parity.check_grid(fc, ctx, gr, w, pts, seed, d, b, n, od, ob, on, label=f"recomputed {case}")
     fc.fc_unload_grid(ctx, gs)
     fc.fc_unload_grid(ctx, gr)
     with pytest.raises(fc.FCError) as e:
