@@ -66,26 +66,25 @@ __device__ double resid_chi2_warp(const double* __restrict__ W, int n, const dou
 }
 
 // The mixed path's residual chi2 = |W (s - d)|^2 in double-float (fc_df.cuh):
-// r_j = s_j - d_j, t_i = sum_{j<=i} W_ij r_j (df_row), chi2 = sum_i t_i^2 in
+// r_j = s_j - d_j, t_i = sum_j W_ij r_j (df_row), chi2 = sum_i t_i^2 in
 // increasing i.  Every mixed-path kernel evaluates
 // it in this order, so a universe's result has the same bits whichever
 // certified round decided it.  W and s are double-float copies of the
 // binary64 arrays; the value is returned as binary64.
 // Row i of W r: four interleaved partial sums (j = 0, 1, 2, 3 mod 4, each in
 // increasing j) so that four double-float chains run side by side, combined
-// as (p0 + p1) + (p2 + p3) and renormalised.
-__device__ __forceinline__ float2 df_row(const float2* __restrict__ Wi, const float2* __restrict__ r, int len) {
+// as (p0 + p1) + (p2 + p3) and renormalised.  A row runs over whole blocks of
+// four columns, j < min(4 ceil((i + 1) / 4), N_fit): W is lower triangular
+// with exact zeros above the diagonal (k_build_cov), so the columns past the
+// diagonal add exact zeros and every kernel takes the same blocks.
+__device__ __forceinline__ float2 df_row(const float2* __restrict__ Wi, const float2* __restrict__ r, int len, int n) {
     float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0, p3 = p0;
-    int j = 0;
-    for (; j + 3 < len; j += 4) {
+    for (int j = 0; j < len; j += 4) {
         p0 = df_fma(p0, Wi[j], r[j]);
-        p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
-        p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
-        p3 = df_fma(p3, Wi[j + 3], r[j + 3]);
+        if (j + 1 < n) p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
+        if (j + 2 < n) p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
+        if (j + 3 < n) p3 = df_fma(p3, Wi[j + 3], r[j + 3]);
     }
-    if (j < len) p0 = df_fma(p0, Wi[j], r[j]);
-    if (j + 1 < len) p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
-    if (j + 2 < len) p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
     const float2 a = df_add(df_norm(p0.x, p0.y), df_norm(p1.x, p1.y));
     const float2 b = df_add(df_norm(p2.x, p2.y), df_norm(p3.x, p3.y));
     return df_add(a, b);
@@ -145,12 +144,15 @@ __device__ __forceinline__ double resid_df_blk(const float2* __restrict__ W, int
                 for (int c = 0; c < 4; ++c) p[b][c] = df_fma(p[b][c], w[c], rv[c]);
             }
         }
-        // columns i0 .. i0+3: row i0+b takes columns up to its diagonal
+        // columns i0 .. i0+3 (those below N_fit): the whole block for every row of the block
+        // (W is zero above the diagonal)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const float2 rc = r[i0 + c];
+            if (i0 + c < n) {
+                const float2 rc = r[i0 + c];
 #pragma unroll
-            for (int b = c; b < 4; ++b) p[b][c] = df_fma(p[b][c], Wb[b][i0 + c], rc);
+                for (int b = 0; b < 4; ++b) p[b][c] = df_fma(p[b][c], Wb[b][i0 + c], rc);
+            }
         }
         const int nb = (n - i0 < 4) ? n - i0 : 4;  // rows of this block that exist
 #pragma unroll
@@ -193,15 +195,11 @@ __device__ __forceinline__ double resid_df_reg(const float2* __restrict__ W, int
         float2 p0 = make_float2(0.0f, 0.0f), p1 = p0, p2 = p0, p3 = p0;
 #pragma unroll
         for (int j = 0; j < NR; j += 4) {
-            if (j + 3 < len) {
+            if (j < len) {  // whole blocks (df_row)
                 p0 = df_fma(p0, Wi[j], r[j]);
-                p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
-                p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
-                p3 = df_fma(p3, Wi[j + 3], r[j + 3]);
-            } else if (j < len) {
-                p0 = df_fma(p0, Wi[j], r[j]);
-                if (j + 1 < len) p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
-                if (j + 2 < len) p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
+                if (j + 1 < n) p1 = df_fma(p1, Wi[j + 1], r[j + 1]);
+                if (j + 2 < n) p2 = df_fma(p2, Wi[j + 2], r[j + 2]);
+                if (j + 3 < n) p3 = df_fma(p3, Wi[j + 3], r[j + 3]);
             }
         }
         const float2 a = df_add(df_norm(p0.x, p0.y), df_norm(p1.x, p1.y));
@@ -230,7 +228,7 @@ __device__ double resid_df_warp(const float2* __restrict__ W, int n, const SRow&
                                 float2* r, float2* t, int lane) {
     for (int j = lane; j < n; j += 32) r[j] = df_sub_f(s[j], du[j]);
     __syncwarp();
-    for (int i = lane; i < n; i += 32) t[i] = df_row(W + i * n, r, i + 1);
+    for (int i = lane; i < n; i += 32) t[i] = df_row(W + i * n, r, i + 1, n);
     __syncwarp();
     float2 acc = make_float2(0.0f, 0.0f);
     if (lane == 0)
