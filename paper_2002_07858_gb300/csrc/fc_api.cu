@@ -2493,15 +2493,14 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
                 }
             }
     }
-    // tile shape: rows per covariance slot, on sparse covariances (1024 points x 8 universes, one scan:
-    // 1024 slots of 8 universes, as refit scans leave them), total time of the scan, warm cache
+    // tile shape: rows per covariance slot, on a short full fit (the 64 points x 256 universes, up to
+    // five scans, warm cache), so the refit scans leave covariances as sparse as this grid makes them;
+    // prep + screen + rescoring, the best of three runs after a warm-up, and whole tiles must beat the
+    // 32-row default by 5 % (a timing job of 1024 one-scan covariances with 8 universes each, dominated
+    // by per-tile overheads on small grids, picked whole tiles where a real job runs slower with them)
     if (rc == FC_OK) {
-        const int32_t P2 = (int32_t)std::min<int64_t>(1024, g->G), U2 = 8;
-        std::vector<int64_t> ps2(P2);
-        for (int32_t i = 0; i < P2; ++i) ps2[i] = (int64_t)i * g->G / P2;
-        std::vector<double> d2((size_t)P2 * U2);
-        // a few ms per run: the best of three runs after a warm-up, and whole tiles must beat the
-        // 32-row default by 5 % (single runs flipped the choice between boxes)
+        fc_opts o5 = o;
+        o5.max_iter = 5;
         double ms_rows[2] = {1e300, 1e300};
         const int rows_of[2] = {kQuadRows, kBM};
         for (int k = 0; k < 2 && rc == FC_OK; ++k) {
@@ -2509,7 +2508,7 @@ fc_status fc_autotune(fc_ctx* c, int32_t grid_id, const char* cache_path, fc_tun
             t.slot_rows = rows_of[k];
             g->tune = t;
             for (int rep = 0; rep < 4 && rc == FC_OK; ++rep) {
-                rc = run_points_impl(c, grid_id, ps2.data(), P2, 0x5eed, U2, &o, d2.data(), nullptr, nullptr);
+                rc = run_points_impl(c, grid_id, ps.data(), P, 0x5eed, U, &o5, dchi2.data(), nullptr, nullptr);
                 const double ms = c->stats.ms_prep + c->stats.ms_screen + c->stats.ms_rescore;
                 if (rep > 0 && ms < ms_rows[k]) ms_rows[k] = ms;
             }
