@@ -565,6 +565,11 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                 if (lane == 0) mbar_arrive(bar(T_EMPTY + ab));
                 // the four chunk minima first (independent trees), then the rare slow paths
                 const float m0 = min32(r0), m1 = min32(r1), m2 = min32(r2), m3 = min32(r3);
+                // top-k: a chunk acts only at or below the row's k-th value, so a warp none of whose
+                // 128 values reaches it skips the four chunk steps (the common case once lists fill)
+                if (MODE == kModeTopK &&
+                    !__any_sync(0xffffffffu, fminf(fminf(m0, m1), fminf(m2, m3)) <= vals[TOPK - 1]))
+                    continue;
                 chunk(r0, m0, g0 + 0);
                 __syncwarp();
                 chunk(r1, m1, g0 + 32);
