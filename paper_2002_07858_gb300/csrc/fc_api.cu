@@ -886,7 +886,7 @@ fc_status scan_once(fc_ctx* c, Lane* L) {
     const int64_t n_active = L->n_active;
     if (n_active == 0) return FC_OK;
     const bool mixed = (o.precision == FC_PREC_MIXED);
-    const int topk = o.top_k <= 8 ? 8 : 16;
+    const int topk = o.top_k <= 4 ? 4 : (o.top_k <= 8 ? 8 : 16);
     // The probe at the true point is a loose first seed; when most universes
     // are on their first scan a min-only pass tightens the seeds first.
     const bool first_heavy = 2 * L->n_first >= n_active;

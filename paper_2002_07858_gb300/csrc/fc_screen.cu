@@ -701,7 +701,7 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
                    const float* Qc, const float* Qb, const float4* gnorm, const float4* alpha, const GridSpec& gs,
                    int nfit, const ListArgs& la, const WaitTest& wt, int n_sm, cudaStream_t st) {
     if (n_tiles <= 0) return true;
-    if (!screen_config_ok(K, stages, ybuf) || (topk != 8 && topk != 16)) return false;
+    if (!screen_config_ok(K, stages, ybuf) || (topk != 4 && topk != 8 && topk != 16)) return false;
     const ScreenLayout lay = choose_layout(K, stages, ybuf);
     const ProbeArgs pa{Qc, Qb, gnorm, alpha, gs, nfit};
 #define FC_SCREEN_RUN(TT, MM, CC) \
@@ -716,7 +716,13 @@ bool launch_screen(int K, int topk, int mode, int stages, int ybuf, const uint16
         else                                    \
             FC_SCREEN_RUN(TT, kModeTopK, CC);   \
     } while (0)
-    if (topk == 8) {
+    if (topk == 4 && mode == kModeTopK) {
+        // top-4 lists; the min and list passes of a top-4 scan use the top-8 instance (they keep no list)
+        if (lay.kchunk)
+            FC_SCREEN_RUN(4, kModeTopK, true);
+        else
+            FC_SCREEN_RUN(4, kModeTopK, false);
+    } else if (topk <= 8) {
         if (lay.kchunk)
             FC_SCREEN_MODES(8, true);
         else

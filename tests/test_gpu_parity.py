@@ -144,7 +144,7 @@ def test_mixed_cfg1(fc, ctx, w1):
     assert np.all(rounds != 0) and not np.any(rounds & fc.FC_DECIDED_PLAIN)
 
 
-@pytest.mark.parametrize("topk", [8, 16])
+@pytest.mark.parametrize("topk", [4, 8, 16])
 def test_mixed_cfg2_subset(fc, ctx, w2, topk):
     gid = grid(fc, ctx, w2)
     pts = _cfg2_points(w2, 8)
