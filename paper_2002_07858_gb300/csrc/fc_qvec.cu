@@ -331,9 +331,6 @@ __global__ void __launch_bounds__(64 + 32 * kQEpiWarps, 1)
         int ab = 0;
         uint32_t aph = 0;
         qvec_items(n_groups, n_tq, [&](int64_t grp, int64_t t) {
-            // the row's norms do not depend on the accumulator: load them before waiting for it
-            const int64_t g = t * kQM + row;
-            const float4 gn = g < G ? gnorm[g] : make_float4(0.f, 0.f, 0.f, 0.f);
             const bool w_ok = mbar_wait(bar(T_FULL + ab), aph, abort_flag);
             if (!__all_sync(0xffffffffu, w_ok)) {
                 if (lane == 0) {
@@ -345,23 +342,17 @@ __global__ void __launch_bounds__(64 + 32 * kQEpiWarps, 1)
             tc_fence_after();
             const uint32_t tb = tmem_base + lane_base + (uint32_t)(ab * 256);
             const int mg = group_size(grp);
+            const int64_t g = t * kQM + row;
+            const float4 gn = g < G ? gnorm[g] : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int i = half; i < mg; i += 2) {
-                // sum of squares of the slot's K columns in column order, up to 64 columns per TMEM wait
+                // sum of squares of the slot's K columns in column order
                 float q = 0.0f;
-                for (int c0 = i * K; c0 < (i + 1) * K; c0 += 64) {
-                    const int nb = ((i + 1) * K - c0) / 16 < 4 ? ((i + 1) * K - c0) / 16 : 4;  // warp-uniform
-                    uint32_t r[4][16];
+                for (int c0 = i * K; c0 < (i + 1) * K; c0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tb + c0, r);
+                    tmem_wait(r);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < nb) tmem_ld16(tb + c0 + 16 * k, r[k]);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < nb) tmem_wait(r[k]);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (k < nb)
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) q = fmaf(__uint_as_float(r[k][e]), __uint_as_float(r[k][e]), q);
+                    for (int k = 0; k < 16; ++k) q = fmaf(__uint_as_float(r[k]), __uint_as_float(r[k]), q);
                 }
                 const int slot = slots[grp * M + i];
                 float qc = 0.0f, qb = 3.0e38f;
